@@ -1,0 +1,94 @@
+"""Oracle: Alg. TSVD and Alg. RSVD of Kohn et al. (Sec. II), plain FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Library primitives used as steps: ``numpy.linalg.svd`` (LAPACK gesdd) for
+every "compute the SVD" step and ``numpy.linalg.qr`` (LAPACK Householder
+geqrf/orgqr) for every "orthonormalise" step.  No blocking, fusion or
+reordering beyond what the algorithms state.
+
+Readings where the paper is silent (the CUDA path applies the same ones):
+
+* QR sign: R_ii >= 0 (Q unique for full-rank input).
+* Singular-vector sign: u_i is flipped (with v_i) so that its entry of
+  largest magnitude is positive, the lowest row index winning ties.
+* Power iteration: the paper's step 2 forms Y = (A A^T)^q A Omega "as a power
+  iteration with subsequent QR factorizations" (Halko-Martinsson-Tropp 2011,
+  Algorithm 4.4), i.e. 2q+1 orthonormalisations:
+  Q0 = qr(A Omega); for j = 1..q: Z = qr(A^T Q), Q = qr(A Z).
+* l = min(k + p, m, n): the sample can never have more columns than A has
+  independent rows or columns.
+"""
+import numpy as np
+
+from .philox import gaussian_test_matrix
+
+
+def qr_pos(Y):
+    """Thin QR with non-negative diagonal of R; returns Q (Alg. RSVD step 3)."""
+    Q, R = np.linalg.qr(Y, mode="reduced")
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d[None, :]
+
+
+def canonical_signs(U, s, Vt):
+    """Flip (u_i, v_i) pairs so the largest-|.| entry of each u_i is positive."""
+    U = U.copy()
+    Vt = Vt.copy()
+    for i in range(U.shape[1]):
+        j = int(np.argmax(np.abs(U[:, i])))  # argmax returns the lowest index on ties
+        if U[j, i] < 0:
+            U[:, i] = -U[:, i]
+            Vt[i, :] = -Vt[i, :]
+    return U, s, Vt
+
+
+def tsvd(A, k):
+    """Alg. TSVD (Sec. II.A): full SVD of A, keep the k largest singular triplets.
+
+    Returns (U_k, s_k, Vt_k): U_k is m-by-k, s_k descending, Vt_k is k-by-n.
+    """
+    U, s, Vt = np.linalg.svd(np.asarray(A, dtype=np.float64), full_matrices=False)
+    return canonical_signs(U[:, :k], s[:k], Vt[:k, :])
+
+
+def sample_width(m, n, k, p):
+    """l = min(k + p, m, n)."""
+    return min(k + p, m, n)
+
+
+def rsvd_basis(A, l, q, seed, stream=0, omega=None):
+    """Alg. RSVD steps 1-3: orthonormal basis Q (m-by-l) of the sampled range."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    if omega is None:
+        omega = gaussian_test_matrix(n, l, seed, stream)      # step 1
+    Q = qr_pos(A @ omega)                                       # step 2, j = 0
+    for _ in range(q):                                          # step 2, j = 1..q
+        Z = qr_pos(A.T @ Q)
+        Q = qr_pos(A @ Z)
+    return Q                                                    # step 3
+
+
+def rsvd(A, k, p, q, seed, stream=0, omega=None):
+    """Alg. RSVD (Sec. II.B): approximate rank-k truncated SVD of A.
+
+    Step 4 takes the rank-k TSVD of B = Q^T A (l-by-n); the left factor is
+    lifted back as U = Q U~, the right factor is V~ itself.  Both are exact
+    isometries (Sec. II.B).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    l = sample_width(m, n, k, p)
+    Q = rsvd_basis(A, l, q, seed, stream, omega)
+    B = Q.T @ A                                                 # step 4
+    Ub, s, Vt = np.linalg.svd(B, full_matrices=False)
+    U = Q @ Ub[:, :k]
+    return canonical_signs(U, s[:k], Vt[:k, :])
+
+
+def truncation_error_frobenius(s_full, k):
+    """Eckart-Young-Mirsky (Sec. II.A): minimal Frobenius error of a rank-k factorization."""
+    s_full = np.asarray(s_full, dtype=np.float64)
+    return float(np.sqrt(np.sum(s_full[k:] ** 2)))

@@ -1,0 +1,188 @@
+"""Oracle: imaginary-time TEBD of the open transverse-field Ising chain.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Model (Sec. III.B, Eq. for H_chain at S = 1/2): the paper writes
+H = -sum X_j X_{j+1} + h sum Z_j with Pauli X, Z; this build uses the unitarily
+equivalent form H = -sum Z_j Z_{j+1} - h sum X_j (exchange the x and z axes,
+then rotate by pi about x to flip the field's sign), which has the same
+spectrum.  Open boundaries; critical point h = 1.
+
+TEBD (Sec. III.A "block update (B)", Sec. III.C protocol), readings where the
+paper is silent:
+
+* MPS in right-canonical "B" form (Hastings' variant of Vidal's form): tensors
+  B[i] of shape (D[i], d, D[i+1]), Schmidt values lam[j] on virtual bond j
+  (lam[0] = lam[L] = [1]).  No division by Schmidt values is ever needed.
+* Bond dimensions are fixed at the caps D[j] = min(d^j, d^(L-j), chi) from the
+  first step on (zero-padded), so every bond update keeps rank k = D[i+1].
+* Field split: an interior site gives h/2 to each of its two bonds; an edge
+  site gives its full field to its only bond.
+* Second-order Trotter step: exp(-dt/2 H_A) exp(-dt H_B) exp(-dt/2 H_A), where
+  layer A holds the bonds (0,1), (2,3), ... and layer B the bonds (1,2), (3,4), ...
+* Bond update on sites (i, i+1) with gate G (d^2 x d^2):
+    theta_B[a,s1,s2,c] = sum G[(s1 s2),(t1 t2)] B[i][a,t1,b] B[i+1][b,t2,c]
+    theta = lam[i][a] * theta_B, reshaped (D[i] d) x (d D[i+2])
+    (U, S, V^T) = rank-D[i+1] truncated factorization of theta
+    B[i+1] <- V^T,  B[i] <- theta_B V / ||S||,  lam[i+1] <- S / ||S||
+* Philox stream of a bond update: (3 * step + layer) * L + i, layer in {0,1,2}.
+* Energy: exact contraction <psi|H|psi> / <psi|psi> (no canonical-form
+  assumption).
+"""
+import numpy as np
+
+from .rsvd import rsvd, tsvd
+
+PAULI_X = np.array([[0.0, 1.0], [1.0, 0.0]])
+PAULI_Z = np.array([[1.0, 0.0], [0.0, -1.0]])
+EYE2 = np.eye(2)
+
+
+def bond_dims(L, d, chi):
+    """D[j] = min(d^j, d^(L-j), chi), j = 0..L."""
+    return [int(min(d ** min(j, L - j), chi)) for j in range(L + 1)]
+
+
+def bond_hamiltonian(i, L, h):
+    """Two-site term of bond (i, i+1) as a 4x4 matrix on (s_i, s_{i+1})."""
+    fl = 1.0 if i == 0 else 0.5
+    fr = 1.0 if i + 1 == L - 1 else 0.5
+    return -np.kron(PAULI_Z, PAULI_Z) - h * (fl * np.kron(PAULI_X, EYE2) + fr * np.kron(EYE2, PAULI_X))
+
+
+def gate(hb, tau):
+    """exp(-tau h_b) of a symmetric bond Hamiltonian, through its eigenbasis."""
+    w, V = np.linalg.eigh(hb)
+    return (V * np.exp(-tau * w)[None, :]) @ V.T
+
+
+def product_state(vectors, D):
+    """Zero-padded MPS of a product state: B[i][0, :, 0] = vectors[i]."""
+    L, d = vectors.shape
+    B = []
+    for i in range(L):
+        t = np.zeros((D[i], d, D[i + 1]))
+        t[0, :, 0] = vectors[i] / np.linalg.norm(vectors[i])
+        B.append(t)
+    lam = []
+    for j in range(L + 1):
+        v = np.zeros(D[j])
+        v[0] = 1.0
+        lam.append(v)
+    return B, lam
+
+
+def bond_update(B, lam, i, G, compress, stream):
+    """One TEBD block update on sites (i, i+1); returns the discarded weight."""
+    Dl, d, _ = B[i].shape
+    Dr = B[i + 1].shape[2]
+    k = B[i].shape[2]
+    two = np.einsum("atb,buc->atuc", B[i], B[i + 1])
+    G4 = G.reshape(d, d, d, d)
+    thetaB = np.einsum("stxy,axyc->astc", G4, two)
+    theta = lam[i][:, None, None, None] * thetaB
+    M = theta.reshape(Dl * d, d * Dr)
+    MB = thetaB.reshape(Dl * d, d * Dr)
+    U, S, Vt = compress(M, k, stream)
+    nrm = float(np.linalg.norm(S))
+    B[i + 1] = Vt.reshape(k, d, Dr).copy()
+    B[i] = (MB @ Vt.T / nrm).reshape(Dl, d, k)
+    lam[i + 1] = S / nrm
+    tot = float(np.sum(M * M))
+    return max(0.0, 1.0 - nrm * nrm / tot) if tot > 0 else 0.0
+
+
+def make_compressor(kind, p=10, q=2, seed=0):
+    """compress(M, k, stream) -> (U, S, Vt) via Alg. RSVD or Alg. TSVD."""
+    if kind == "rsvd":
+        return lambda M, k, stream: rsvd(M, k, p, q, seed, stream)
+    if kind == "tsvd":
+        return lambda M, k, stream: tsvd(M, k)
+    raise ValueError(kind)
+
+
+def layers(L):
+    """Bonds of layer A (i even) and layer B (i odd)."""
+    return list(range(0, L - 1, 2)), list(range(1, L - 1, 2))
+
+
+def trotter_step(B, lam, L, h, dt, compress, step):
+    """One second-order Trotter step; returns the summed discarded weight."""
+    la, lb = layers(L)
+    err = 0.0
+    for layer, (bonds, tau) in enumerate(((la, dt / 2), (lb, dt), (la, dt / 2))):
+        for i in bonds:
+            G = gate(bond_hamiltonian(i, L, h), tau)
+            err += bond_update(B, lam, i, G, compress, (3 * step + layer) * L + i)
+    return err
+
+
+def mps_energy(B, L, h):
+    """<psi|H|psi> / <psi|psi> by exact contraction of psi = B[0] B[1] ... B[L-1]."""
+    left = [np.ones((1, 1))]
+    for i in range(L):
+        left.append(np.einsum("ab,asc,bsd->cd", left[i], B[i], B[i]))
+    right = [None] * (L + 1)
+    right[L] = np.ones((1, 1))
+    for i in range(L - 1, -1, -1):
+        right[i] = np.einsum("asc,bsd,cd->ab", B[i], B[i], right[i + 1])
+    norm = float(left[L][0, 0])
+    e = 0.0
+    d = B[0].shape[1]
+    for i in range(L - 1):
+        two = np.einsum("atb,buc->atuc", B[i], B[i + 1])
+        hb = bond_hamiltonian(i, L, h).reshape(d, d, d, d)
+        htwo = np.einsum("stxy,axyc->astc", hb, two)
+        e += float(np.einsum("ab,astc,bstd,cd->", left[i], htwo, two, right[i + 2]))
+    return e / norm
+
+
+def mps_to_dense(B):
+    """Dense state vector of a (small) MPS, site 0 as the most significant index."""
+    psi = B[0].reshape(B[0].shape[1], B[0].shape[2])
+    for t in B[1:]:
+        psi = np.einsum("xa,asb->xsb", psi, t).reshape(-1, t.shape[2])
+    return psi.reshape(-1)
+
+
+def dense_hamiltonian(L, h):
+    """H = -sum Z_j Z_{j+1} - h sum X_j as a dense 2^L x 2^L matrix (brute force)."""
+    def site_op(op, j):
+        out = np.ones((1, 1))
+        for s in range(L):
+            out = np.kron(out, op if s == j else EYE2)
+        return out
+    H = np.zeros((2 ** L, 2 ** L))
+    for j in range(L - 1):
+        H -= site_op(PAULI_Z, j) @ site_op(PAULI_Z, j + 1)
+    for j in range(L):
+        H -= h * site_op(PAULI_X, j)
+    return H
+
+
+def exact_ground_energy_ed(L, h):
+    """Lowest eigenvalue of the dense Hamiltonian (exact diagonalisation)."""
+    return float(np.linalg.eigvalsh(dense_hamiltonian(L, h))[0])
+
+
+def free_fermion_ground_energy(L, h, J=1.0):
+    """Ground energy of the open chain from its free-fermion solution.
+
+    After the Jordan-Wigner transformation the single-particle energies are the
+    singular values of the L x L upper-bidiagonal matrix with h on the diagonal
+    and J on the superdiagonal; the ground energy is minus their sum.
+    """
+    M = np.diag(np.full(L, float(h))) + np.diag(np.full(L - 1, float(J)), 1)
+    return -float(np.sum(np.linalg.svd(M, compute_uv=False)))
+
+
+def critical_ground_energy(L):
+    """Closed form at h = J = 1: E0 = 1 - 1 / sin(pi / (2 (2L + 1)))."""
+    return 1.0 - 1.0 / np.sin(np.pi / (2.0 * (2 * L + 1)))
+
+
+def entanglement_entropy(lam_j):
+    """Von Neumann entropy S_N = -sum lam^2 log lam^2 of one bond (Sec. III.C)."""
+    p = np.asarray(lam_j, dtype=np.float64) ** 2
+    p = p[p > 0]
+    return float(-np.sum(p * np.log(p)))

@@ -1,0 +1,172 @@
+"""Pins of the oracle's Alg. TSVD and Alg. RSVD (Sec. II) against mathematics.
+
+* prescribed spectra of A = U diag(s) V^T are recovered;
+* Eckart-Young-Mirsky: the Frobenius error of the rank-k truncation is
+  sqrt(sum_{j>k} s_j^2) and the spectral error is s_{k+1} (Sec. II.A);
+* 2 x 2 brute force: singular values from the eigenvalues of A^T A in closed form;
+* exactness: l >= rank(A) reproduces the TSVD;
+* interlacing: every RSVD singular value is <= the exact one (B = Q^T A with
+  orthonormal Q);
+* isometry of Q U~ and V~ (Sec. II.B);
+* literal Alg. RSVD step 2, Y = (A A^T)^q A Omega formed without intermediate
+  orthonormalisation, spans the same space as the re-orthonormalised power
+  iteration (checked where Y is well conditioned);
+* the Halko-Martinsson-Tropp expectation bound for the power scheme (HMT 2011,
+  Cor. 10.10) holds on average over seeds, and q = 2 beats q = 0.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import philox
+from oracle.rsvd import canonical_signs, qr_pos, rsvd, rsvd_basis, tsvd
+from paper_1710_01463_gb300 import inputs
+
+
+def test_tsvd_recovers_prescribed_spectrum():
+    A = inputs.dense_case()
+    s_true = inputs.exp_spectrum(256)
+    U, s, Vt = tsvd(A, 32)
+    np.testing.assert_allclose(s, s_true[:32], rtol=1e-13)
+    np.testing.assert_allclose(U.T @ U, np.eye(32), atol=1e-13)
+    np.testing.assert_allclose(Vt @ Vt.T, np.eye(32), atol=1e-13)
+
+
+def test_eckart_young_frobenius_and_spectral():
+    A = inputs.dense_case()
+    s_true = inputs.exp_spectrum(256)
+    k = 32
+    U, s, Vt = tsvd(A, k)
+    R = A - (U * s) @ Vt
+    assert np.linalg.norm(R, "fro") == pytest.approx(math.sqrt(np.sum(s_true[k:] ** 2)), rel=1e-11)
+    assert np.linalg.norm(R, 2) == pytest.approx(s_true[k], rel=1e-11)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_two_by_two_closed_form(seed):
+    A = np.random.default_rng(seed).standard_normal((2, 2))
+    # eigenvalues of A^T A from trace and determinant
+    tr = float(np.sum(A * A))
+    det = float(np.linalg.det(A)) ** 2
+    disc = math.sqrt(max(tr * tr / 4 - det, 0.0))
+    s1 = math.sqrt(tr / 2 + disc)
+    s2 = math.sqrt(max(tr / 2 - disc, 0.0))
+    _, s, _ = tsvd(A, 2)
+    np.testing.assert_allclose(s, [s1, s2], rtol=1e-12, atol=1e-15)
+
+
+def test_three_by_three_brute_force():
+    A = np.random.default_rng(9).standard_normal((3, 3))
+    # singular values = square roots of the roots of det(A^T A - x I) (cubic)
+    M = A.T @ A
+    c2 = -np.trace(M)
+    c1 = 0.5 * (np.trace(M) ** 2 - np.trace(M @ M))
+    c0 = -np.linalg.det(M)
+    roots = np.sort(np.roots([1.0, c2, c1, c0]).real)[::-1]
+    _, s, _ = tsvd(A, 3)
+    np.testing.assert_allclose(s, np.sqrt(roots), rtol=1e-10)
+
+
+def test_canonical_sign_rule():
+    A = inputs.random_dense(20, 12, 3)
+    U, s, Vt = tsvd(A, 5)
+    for i in range(5):
+        j = int(np.argmax(np.abs(U[:, i])))
+        assert U[j, i] > 0
+    np.testing.assert_allclose((U * s) @ Vt, (lambda u, s_, v: (u * s_) @ v)(*tsvd(A, 5)), atol=1e-14)
+
+
+def test_qr_pos_unique_factor():
+    Y = inputs.random_dense(30, 7, 4)
+    Q = qr_pos(Y)
+    R = Q.T @ Y
+    np.testing.assert_allclose(Q.T @ Q, np.eye(7), atol=1e-14)
+    np.testing.assert_allclose(np.tril(R, -1), 0, atol=1e-13)
+    assert np.all(np.diag(R) > 0)
+
+
+@pytest.mark.parametrize("shape,r", [((60, 40), 10), ((40, 60), 10), ((50, 50), 18)])
+def test_rsvd_exact_when_rank_fits(shape, r):
+    m, n = shape
+    A = inputs.spectral_matrix(m, n, np.linspace(3.0, 0.5, r), 77)
+    U, s, Vt = rsvd(A, k=8, p=12, q=1, seed=11)   # l = 20 >= r
+    Ut, st, Vtt = tsvd(A, 8)
+    np.testing.assert_allclose(s, st, rtol=1e-12)
+    np.testing.assert_allclose(U, Ut, atol=1e-10)
+    np.testing.assert_allclose(Vt, Vtt, atol=1e-10)
+
+
+def test_rsvd_interlacing_and_isometry():
+    A = inputs.dense_case()
+    U, s, Vt = rsvd(A, 32, 8, 2, seed=201)
+    s_true = inputs.exp_spectrum(256)[:32]
+    assert np.all(s <= s_true * (1 + 1e-13))
+    np.testing.assert_allclose(U.T @ U, np.eye(32), atol=1e-13)
+    np.testing.assert_allclose(Vt @ Vt.T, np.eye(32), atol=1e-13)
+    # cfg (sigma_40 / sigma_32)^(4q) = e^-4: leading values accurate, trailing ones measurably below
+    assert abs(s[0] - s_true[0]) / s_true[0] < 1e-9
+    assert (s_true[31] - s[31]) / s_true[31] > 1e-4
+
+
+def test_literal_power_form_spans_same_space():
+    # Y = (A A^T)^q A Omega without intermediate QRs is fine when Y is well conditioned
+    s_true = np.linspace(1.0, 0.3, 40)
+    A = inputs.spectral_matrix(80, 60, s_true, 31)
+    l, q = 12, 2
+    omega = philox.gaussian_test_matrix(60, l, seed=3)
+    Y = A @ omega
+    for _ in range(q):
+        Y = A @ (A.T @ Y)
+    Qlit, _ = np.linalg.qr(Y)
+    Q = rsvd_basis(A, l, q, seed=3)
+    # same range: projectors agree
+    np.testing.assert_allclose(Q @ Q.T, Qlit @ Qlit.T, atol=1e-11)
+
+
+def test_wrong_power_operand_would_be_detected():
+    # A @ Q in place of A^T @ Q gives a different (worse) subspace for non-normal A
+    s_true = inputs.power_spectrum(60, 0.7)
+    A = inputs.spectral_matrix(60, 60, s_true, 32)
+    l, q = 10, 2
+    omega = philox.gaussian_test_matrix(60, l, seed=4)
+    Q = rsvd_basis(A, l, q, seed=4)
+    Qw = qr_pos(A @ omega)
+    for _ in range(q):
+        Qw = qr_pos(A @ Qw)
+        Qw = qr_pos(A @ Qw)
+    e_right = np.linalg.norm(A - Q @ (Q.T @ A), 2)
+    e_wrong = np.linalg.norm(A - Qw @ (Qw.T @ A), 2)
+    assert e_right < 0.9 * e_wrong
+
+
+def hmt_power_bound(s, k, p, q):
+    """HMT 2011, Cor. 10.10: bound on E || (I - P_Y) A || for Y = (A A^T)^q A Omega."""
+    t = 2 * q + 1
+    tail = s[k:]
+    val = (1 + math.sqrt(k / (p - 1))) * tail[0] ** t + (math.e * math.sqrt(k + p) / p) * math.sqrt(np.sum(tail ** (2 * t)))
+    return val ** (1.0 / t)
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_hmt_expectation_bound(q):
+    s_true = inputs.power_spectrum(100, 0.5)       # slow decay
+    A = inputs.spectral_matrix(100, 100, s_true, 55)
+    k, p = 10, 5
+    errs = []
+    for seed in range(100):
+        Q = rsvd_basis(A, k + p, q, seed=seed)
+        errs.append(np.linalg.norm(A - Q @ (Q.T @ A), 2))
+    assert np.mean(errs) <= hmt_power_bound(s_true, k, p, q)
+    assert np.mean(errs) >= s_true[k + p] * (1 - 1e-12)   # can never beat sigma_{l+1}
+
+
+def test_power_iterations_improve_accuracy():
+    s_true = inputs.power_spectrum(200, 0.5)
+    A = inputs.spectral_matrix(200, 200, s_true, 56)
+    err = {}
+    for q in (0, 2):
+        U, s, Vt = rsvd(A, 20, 8, q, seed=7)
+        err[q] = np.linalg.norm(A - (U * s) @ Vt, 2)
+    assert err[2] < 0.8 * err[0]
+    assert err[2] >= s_true[20] * (1 - 1e-12)
