@@ -1,0 +1,412 @@
+"""Benchmark: RSVD bond truncations/s of imaginary-time TEBD on one GB300.
+
+Workload (one "step" = one second-order Trotter step = every bond update of the
+chain once per layer, 95 truncations): open transverse-field Ising chain,
+L = 64, h = 1, d = 2, chi = 128, dt = 0.01, FP64; each bond update is an RSVD
+of the (chi d) x (chi d) = 256 x 256 two-site matrix truncated to chi
+(p = 10, q = 2).  The state is first evolved from a seeded product state (20
+untimed steps at dt = 0.1) so that the timed bond matrices carry the decaying
+spectra of a converging TEBD run.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank evolves its own chain
+(replicas; the chain is not sharded) and the value is the total over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RSVD truncations/s & TFLOP/s vs full-SVD-truncate, 1 GB300, at stated error"
+UNIT = "truncations/s"
+L_SITES, CHI, D_LOC, H_FIELD, DT, P_OVER, Q_POW, SEED = 64, 128, 2, 1.0, 0.01, 10, 2, 5
+PREP_STEPS, PREP_DT = 20, 0.1
+WORKLOAD = "tebd_tfim_L64_chi128_d2_dt0.01_p10_q2_fp64"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+def base_config():
+    return {"workload": WORKLOAD, "L": L_SITES, "chi": CHI, "d": D_LOC, "h": H_FIELD, "dt": DT,
+            "p": P_OVER, "q": Q_POW, "bond_matrix": f"{CHI * D_LOC}x{CHI * D_LOC}",
+            "truncations_per_step": truncations_per_step(), "l2": "flushed (512 MB write) before every timed step"}
+
+
+def truncations_per_step():
+    a = len(range(0, L_SITES - 1, 2))
+    b = len(range(1, L_SITES - 1, 2))
+    return 2 * a + b
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 7:
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+            except ValueError:
+                continue
+            for nme, v in zip(names, r[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nme)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ flop model
+def bond_shapes():
+    D = [int(min(D_LOC ** min(j, L_SITES - j), CHI)) for j in range(L_SITES + 1)]
+    out = []
+    for layer in (0, 1, 0):
+        for i in range(layer, L_SITES - 1, 2):
+            m, n, k = D[i] * D_LOC, D_LOC * D[i + 2], D[i + 1]
+            out.append((m, n, k, D[i + 1], min(k + P_OVER, m, n)))
+    return out
+
+
+def step_flops(info):
+    """Algorithmic FP64 flops of one Trotter step, split by kernel class.
+
+    GEMMs: sketch / power / projection (2q+2) 2mnl, two-site contraction 2mnD,
+    B update 2mnk.  Orthonormalisation (2q+1 per bond, two CholeskyQR passes):
+    Gram rows l^2 (symmetric), Cholesky l^3/3, triangular inverse l^3/3,
+    Y R^-1 rows l^2 (triangular).  Jacobi (from the device counts): every sweep
+    forms all l(l-1)/2 inner products (2n each) and the row norms (2nl); each
+    applied rotation costs 6n + 6l.
+    """
+    import numpy as np
+    flops = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "jacobi": 0.0}
+    inf = info.reshape(-1, info.shape[-1])
+    shapes = bond_shapes()
+    for idx, (m, n, k, Dm, l) in enumerate(shapes):
+        exact = m <= l
+        flops["gemm"] += 2.0 * m * n * Dm + 2.0 * m * n * k
+        if not exact:
+            flops["gemm"] += (2 * Q_POW + 2) * 2.0 * m * n * l
+            for it in range(2 * Q_POW + 1):
+                rows = m if it % 2 == 0 else n
+                flops["gram"] += 2 * rows * l * l
+                flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
+                flops["gemm"] += 2 * rows * l * l
+        rec = inf[idx]
+        sweeps, rots = int(rec[3]), int(rec[5])
+        flops["jacobi"] += sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * (6.0 * n + 6.0 * l) + (sweeps + 1) * 2.0 * n * l
+    return flops
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1710_01463_gb300 import _lib, inputs
+    from paper_1710_01463_gb300.tebd import TebdChain
+
+    lib = _lib.load()
+    ch = TebdChain(L_SITES, CHI, h=H_FIELD, p=P_OVER, q=Q_POW, seed=SEED + 1000 * rank)
+    ch.set_product_state(inputs.product_state_vectors(L_SITES, D_LOC, 102 + rank))
+    ch.set_dt(PREP_DT)
+    for s in range(PREP_STEPS):
+        ch.step(s)
+    ch.set_dt(DT)
+    for s in range(args.warmup):
+        ch.step(PREP_STEPS + s)
+    torch.cuda.synchronize()
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    clocks = ClockSampler(local)
+    lib.rsvd_profile_enable(200000)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.time()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        ch.step(PREP_STEPS + args.warmup + s)
+        ev[s][1].record(stream)
+        infos.append(ch.info.clone())
+    torch.cuda.synchronize()
+    wall = time.time() - t0
+    clk = clocks.stop()
+    nclass = 16
+    ms_c = (ctypes.c_double * nclass)()
+    cnt_c = (ctypes.c_int * nclass)()
+    ncls = lib.rsvd_profile_collect(ms_c, cnt_c, nclass)
+    lib.rsvd_profile_enable(0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = ws * truncations_per_step() / (ms_per_step / 1e3)
+
+    # algorithmic flops from the device-reported sweep / rotation counts
+    fl = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "jacobi": 0.0}
+    for inf in infos:
+        f = step_flops(inf.cpu().numpy())
+        for key in fl:
+            fl[key] += f[key]
+    tflops = sum(fl.values()) / (tot_ms / 1e3) / 1e12 * ws / ws
+    classes = {lib.rsvd_profile_class_name(c).decode(): (ms_c[c], cnt_c[c]) for c in range(ncls)}
+    total_kernel_ms = sum(v[0] for v in classes.values())
+    kernels = {}
+    for name, (ms, cnt) in classes.items():
+        if cnt == 0:
+            continue
+        entry = {"launch_groups": cnt, "ms_total": round(ms, 3), "share": round(ms / total_kernel_ms, 4)}
+        if name in fl and ms > 0:
+            entry["tflops"] = round(fl[name] / (ms / 1e3) / 1e12, 4)
+            entry["frac_fp64_peak"] = round(fl[name] / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4)
+        kernels[name] = entry
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    dom_ach = fl.get(dom, 0.0) / (classes[dom][0] / 1e3) / 1e12 if classes[dom][0] > 0 else 0.0
+    launches = 0
+    per_group = {"gram": 2, "select": 2}
+    for name, (ms, cnt) in classes.items():
+        launches += cnt * per_group.get(name, 1)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(dom_ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(dom_ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s; "
+                               "DFMA microbenchmark on this GB300: 1.20 TFLOP/s)"}
+
+    result = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+              "config": dict(base_config(), parallelism=f"replicas{ws}"),
+              "tflops": round(tflops, 4), "roofline": roofline, "kernels": kernels,
+              "gpu_launches": launches, "clocks": clk, "wall_s_timed_loop": round(wall, 3)}
+    trunc = torch.stack([i for i in infos]).cpu().numpy()
+    result["device_status"] = {"max_jacobi_sweeps": int(trunc[..., 3].max()),
+                               "mean_jacobi_sweeps": round(float(trunc[..., 3].mean()), 3),
+                               "householder_fallbacks_per_step": round(float(trunc[..., 2].sum()) / args.steps, 2),
+                               "nonzero_status": int((trunc[..., 0] != 0).sum())}
+    if rank == 0 and not args.no_extras:
+        result["e2e"] = e2e_leg(ch, args)
+        result["error"] = error_leg(ch)
+        result["comparator"] = comparator_leg()
+        result["cpu_baseline"] = cpu_leg(ch)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def e2e_leg(ch, args):
+    """Same metric through the public API with the MPS in pinned host memory:
+    every step copies the state host->device, runs the Trotter step, and copies
+    the new state device->host."""
+    import torch
+    hB = torch.empty(ch.B.shape, dtype=torch.float64, pin_memory=True)
+    hl = torch.empty(ch.lam.shape, dtype=torch.float64, pin_memory=True)
+    hB.copy_(ch.B)
+    hl.copy_(ch.lam)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(steps):
+        ch.B.copy_(hB, non_blocking=True)
+        ch.lam.copy_(hl, non_blocking=True)
+        ch.step(10_000 + s)
+        hB.copy_(ch.B, non_blocking=True)
+        hl.copy_(ch.lam, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    nbytes = hB.numel() * 8 + hl.numel() * 8
+    return {"value": round(truncations_per_step() / (ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": round(ms, 4), "steps": steps}
+
+
+def center_theta(ch):
+    """Host copy of the center bond's two-site matrix theta = lam . (B_i B_{i+1}) (no gate)."""
+    import numpy as np
+    B = ch.tensors()
+    lam = ch.schmidt_values()
+    i = L_SITES // 2 - 1
+    two = np.einsum("atb,buc->atuc", B[i], B[i + 1])
+    th = lam[i][:, None, None, None] * two
+    return th.reshape(B[i].shape[0] * D_LOC, D_LOC * B[i + 1].shape[2])
+
+
+def error_leg(ch):
+    """RSVD error on a live bond matrix: GPU RSVD vs the exact truncated SVD."""
+    import numpy as np
+    import torch
+    from paper_1710_01463_gb300 import api
+    A = center_theta(ch)
+    U, S, Vt, info = api.rsvd_truncate(torch.from_numpy(A).cuda(), CHI, P_OVER, Q_POW, SEED, 0)
+    torch.cuda.synchronize()
+    s_full = np.linalg.svd(A, compute_uv=False)
+    u, s, vt = U.cpu().numpy(), S.cpu().numpy(), Vt.cpu().numpy()
+    err = np.linalg.norm(A - (u * s) @ vt)
+    dtr = np.sqrt(np.sum(s_full[CHI:] ** 2))
+    big = s_full[:CHI] > 1e-8 * s_full[0]
+    return {"bond": "center", "fro_err_over_delta_trunc": float(err / dtr) if dtr > 0 else None,
+            "delta_trunc_fro": float(dtr), "sigma_chi_over_sigma_1": float(s_full[CHI - 1] / s_full[0]),
+            "max_rel_sigma_err_above_1e-8": float(np.max(np.abs(s[big] - s_full[:CHI][big]) / s_full[:CHI][big]))}
+
+
+def comparator_leg():
+    """Full SVD + truncate with torch.linalg.svd (cuSOLVER) FP64 on 32 bond-sized matrices."""
+    import torch
+    from paper_1710_01463_gb300 import inputs
+    A = torch.stack([torch.from_numpy(inputs.dense_case(CHI * D_LOC, CHI * D_LOC, seed=300 + j)) for j in range(32)]).cuda()
+    torch.linalg.svd(A[:2], full_matrices=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    U, S, Vh = torch.linalg.svd(A, full_matrices=False)
+    Uk, Sk, Vk = U[..., :CHI].contiguous(), S[..., :CHI].contiguous(), Vh[..., :CHI, :].contiguous()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"kind": "torch.linalg.svd (cuSOLVER) FP64 + slice to chi, batch of 32 256x256 matrices",
+            "truncations_per_s": round(32 / (ms / 1e3), 3), "ms_per_truncation": round(ms / 32, 4)}
+
+
+def cpu_leg(ch):
+    """The oracle (numpy FP64, as it stands) on the host: a bounded sample of the
+    same workload - the bond updates of one layer-A sweep over the 8 central
+    bonds, from the current GPU state."""
+    import numpy as np
+    from oracle import tebd as otebd
+    B = ch.tensors()
+    lam = ch.schmidt_values()
+    comp = otebd.make_compressor("rsvd", p=P_OVER, q=Q_POW, seed=SEED)
+    bonds = [i for i in range(0, L_SITES - 1, 2)][12:20]
+    t0 = time.time()
+    n = 0
+    while True:
+        for i in bonds:
+            G = otebd.gate(otebd.bond_hamiltonian(i, L_SITES, H_FIELD), DT / 2)
+            otebd.bond_update(B, lam, i, G, comp, 7 * L_SITES + i)
+            n += 1
+        if time.time() - t0 > 10.0:
+            break
+    el = time.time() - t0
+    return {"value": round(n / el, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} central 256x256 bond updates (RSVD k=128, p=10, q=2) of the L=64 chain, numpy FP64, "
+                      f"BLAS threads = all host cores, Philox in pure Python"}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import tebd as otebd
+    from paper_1710_01463_gb300 import inputs
+    D = otebd.bond_dims(L_SITES, D_LOC, CHI)
+    B, lam = otebd.product_state(inputs.product_state_vectors(L_SITES, D_LOC, 102), D)
+    comp = otebd.make_compressor("rsvd", p=P_OVER, q=Q_POW, seed=SEED)
+    # a step of the reference arm: 4 central bond updates (a bounded sample of one Trotter step)
+    bonds = [i for i in range(0, L_SITES - 1, 2)][14:18]
+
+    def one(step):
+        for i in bonds:
+            G = otebd.gate(otebd.bond_hamiltonian(i, L_SITES, H_FIELD), DT / 2)
+            otebd.bond_update(B, lam, i, G, comp, (3 * step) * L_SITES + i)
+
+    for s in range(args.warmup):
+        one(s)
+    t0 = time.time()
+    for s in range(args.steps):
+        one(args.warmup + s)
+    el = time.time() - t0
+    value = len(bonds) * args.steps / el
+    sample = (f"{len(bonds)} central 256x256 bond updates per step (RSVD k=128, p=10, q=2), numpy FP64 oracle, "
+              f"bond matrices from a product state")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(base_config(), parallelism=f"replicas{ws}"),
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e / error / comparator / CPU legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

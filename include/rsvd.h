@@ -1,0 +1,210 @@
+/*
+ * librsvd - randomized truncated SVD (RSVD) for tensor-network bond
+ * compression on one GB300 (sm_103a).
+ *
+ * Method: Kohn, Tschirsich, Keck, Plenio, Tamascelli, Montangero,
+ * "Probabilistic low-rank factorization accelerates tensor network simulations
+ * of critical quantum many-body ground states", arXiv:1710.01463.
+ *   - Alg. TSVD (Sec. II.A): the rank-chi truncated SVD that every call returns.
+ *   - Alg. RSVD (Sec. II.B): Gaussian test matrix Omega, power iteration with
+ *     re-orthonormalisation after every product, Q = orth(Y), B = Q^T A, small
+ *     SVD of B, U = Q U~.
+ *   - Sec. III.A: block-diagonal (symmetry-sector) matrices compressed block by
+ *     block with a global post-selection of the chi largest singular values;
+ *     TEBD "block update" of two neighbouring MPS tensors.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are ROW-MAJOR with a leading dimension (elements between the
+ *     starts of consecutive rows) >= the number of columns.
+ *   - Every pointer to matrix / vector data is a DEVICE pointer unless stated
+ *     otherwise; arrays of per-matrix sizes and of device pointers passed to
+ *     the batched calls are HOST arrays.
+ *   - The caller owns every buffer, including the workspace (size from the
+ *     *_workspace_size queries).  The library allocates no device memory and
+ *     keeps no state between calls.  Inputs are never written.
+ *   - Every call is asynchronous on the given CUDA stream (a cudaStream_t,
+ *     passed as void*; NULL = legacy default stream).  The return value covers
+ *     only the host-side argument checks; conditions found on the device are
+ *     written to the caller's rsvd_info records (device memory), readable after
+ *     the caller synchronises the stream.
+ *   - Singular values are returned in descending order, FP64.  Singular vector
+ *     pairs (u_i, v_i) are sign-normalised: the entry of u_i with the largest
+ *     magnitude is positive (lowest row index on ties).
+ *   - l = min(k + p, m, n) columns are sampled (the paper's l; k is its chi).
+ *   - The Gaussian test matrix of matrix b of a call uses the Philox4x64-10 key
+ *     (seed, stream + b); see rsvd_gaussian.
+ */
+#ifndef RSVD_H
+#define RSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RSVD_OK                 0
+#define RSVD_ERR_INVALID_SIZE  -1   /* m, n, k, l, batch or a leading dimension out of range */
+#define RSVD_ERR_NULL_POINTER  -2   /* a required pointer is NULL */
+#define RSVD_ERR_PRECISION     -3   /* precision not supported by this entry point */
+#define RSVD_ERR_WORKSPACE     -4   /* workspace smaller than the size query returned */
+#define RSVD_ERR_LAUNCH        -5   /* a CUDA launch failed (message via rsvd_status_string) */
+#define RSVD_ERR_NONFINITE     -6   /* device: NaN or Inf met in the input (info.status) */
+#define RSVD_WARN_NOCONV        1   /* device: the Jacobi SVD hit its sweep cap (info.status) */
+
+/* Paths recorded in rsvd_info.path (bit set). */
+#define RSVD_PATH_EXACT         1   /* m <= l: Q = I, B = A (the sample covers the range) */
+#define RSVD_PATH_HOUSEHOLDER   2   /* CholeskyQR2 broke down at least once; Householder QR used */
+
+/* Arithmetic of the products with A (the sketch, the power iteration and the
+ * projection).  The Gram matrix, the Cholesky factor and the SVD of B are
+ * always computed in FP64. */
+typedef enum {
+  RSVD_F64 = 0,   /* A, U, V^T are double; every product in FP64 */
+  RSVD_F32 = 1    /* A, U, V^T are float; products in FP32 (FFMA) */
+} rsvd_prec;
+
+typedef struct {
+  int k;            /* target rank chi (>= 1, <= min(m, n)); batched calls may override per matrix */
+  int p;            /* oversampling (>= 0); l = min(k + p, m, n) */
+  int q;            /* power iterations (>= 0); 2q + 1 orthonormalisations */
+  int prec;         /* rsvd_prec */
+  uint64_t seed;    /* Philox key word 0 */
+  uint64_t stream;  /* Philox key word 1 of the first matrix; matrix b uses stream + b */
+  int max_sweeps;   /* Jacobi sweep cap (0 = default 40) */
+  int flags;        /* reserved, must be 0 */
+} rsvd_params;
+
+/* Device-written record, one per matrix. */
+typedef struct {
+  int status;          /* RSVD_OK, RSVD_WARN_NOCONV or RSVD_ERR_NONFINITE */
+  int path;            /* RSVD_PATH_* bits */
+  int chol_fallbacks;  /* orthonormalisations that fell back to Householder QR */
+  int jacobi_sweeps;   /* sweeps of the one-sided Jacobi SVD of B */
+  int l;               /* sample width used */
+  int rotations;       /* plane rotations applied by the Jacobi SVD (all sweeps) */
+} rsvd_info;
+
+/*
+ * rsvd_gaussian - Alg. RSVD step 1 (Sec. II.B): the n-by-l standard normal
+ * test matrix Omega, FP64, row-major with leading dimension ld >= l.
+ * Element (r, c) has linear index e = c*n + r (columns nest as l grows); it is
+ * slot e % 4 of the Philox4x64-10 block with counter (e / 4, 0, 0, 0) and key
+ * (seed, stream), mapped to a normal by the Box-Muller transform
+ * (u = ((w >> 11) + 1/2) 2^-53; slots 0/1 = cos/sin of words 0,1; 2/3 of words 2,3).
+ * Errors: RSVD_ERR_INVALID_SIZE (n < 1, l < 1, ld < l), RSVD_ERR_NULL_POINTER.
+ */
+int rsvd_gaussian(int n, int l, uint64_t seed, uint64_t stream, double* omega, int ld, void* cuda_stream);
+
+/*
+ * rsvd_workspace_size - bytes of device workspace rsvd_truncate needs for an
+ * m-by-n matrix with parameters p (256-byte aligned base required).
+ */
+int rsvd_workspace_size(int m, int n, const rsvd_params* p, size_t* bytes);
+
+/*
+ * rsvd_truncate - Alg. RSVD (Sec. II.B) returning the rank-k truncated SVD
+ * A ~ U diag(S) V^T of one m-by-n matrix.
+ *   A    [in]  device, m x n, lda >= n; double (RSVD_F64) or float (RSVD_F32)
+ *   S    [out] device, k doubles, descending
+ *   U    [out] device, m x k, ldu >= k, same type as A; orthonormal columns
+ *   Vt   [out] device, k x n, ldvt >= n, same type as A; orthonormal rows,
+ *        except that rows of numerically negligible singular values
+ *        (sigma_i <= 2^-52 sigma_1, below the rounding level of any FP64
+ *        method) are orthogonal to the other rows but not to each other;
+ *        a row whose singular value is exactly 0 is returned as 0
+ *   work [tmp] device workspace of rsvd_workspace_size bytes, 256-byte aligned
+ *   info [out] device, one rsvd_info
+ * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_PRECISION,
+ * RSVD_ERR_WORKSPACE (host checks, nothing launched); RSVD_ERR_LAUNCH.
+ */
+int rsvd_truncate(int m, int n, const void* A, int lda, const rsvd_params* p,
+                  double* S, void* U, int ldu, void* Vt, int ldvt,
+                  void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
+ * rsvd_batched_workspace_size - workspace bytes of rsvd_truncate_batched for
+ * `batch` matrices of sizes m[b] x n[b] at trial ranks k[b] (host arrays).
+ */
+int rsvd_batched_workspace_size(int batch, const int* m, const int* n, const int* k,
+                                const rsvd_params* p, size_t* bytes);
+
+/*
+ * rsvd_truncate_batched - Alg. RSVD on `batch` independent matrices of
+ * possibly different sizes, in one sequence of launches (Sec. III.A: the
+ * blocks of a block-diagonal bond matrix, or the bonds of one TEBD layer).
+ * All size / leading-dimension / pointer arrays are HOST arrays of length
+ * batch; the pointers they hold are device pointers.  Matrix b is compressed
+ * at trial rank k[b] with Philox stream p->stream + b; S[b] holds k[b]
+ * doubles, U[b] is m[b] x k[b], Vt[b] is k[b] x n[b].
+ * chi_global > 0: after the factorizations, the chi_global largest singular
+ * values over all matrices are selected (ties: lower matrix index, then lower
+ * position) and k_out[b] (DEVICE int array) receives how many of matrix b's
+ * values are kept; the leading k_out[b] triplets of each matrix are the kept
+ * ones.  chi_global == 0: k_out may be NULL; nothing is selected.
+ * info: DEVICE array of `batch` records.
+ * Errors as rsvd_truncate.
+ */
+int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* const* A, const int* lda,
+                          const int* k, const rsvd_params* p,
+                          double* const* S, void* const* U, const int* ldu, void* const* Vt, const int* ldvt,
+                          int chi_global, int* k_out,
+                          void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
+ * tebd_workspace_size - workspace bytes of tebd_bond_update for up to nb
+ * bonds of an MPS with bond dimensions D (host array, L + 1 entries).
+ */
+int tebd_workspace_size(int L, int d, const int* D, int nb, const rsvd_params* p, size_t* bytes);
+
+/*
+ * tebd_bond_update - TEBD "block update" (Sec. III.A) of nb independent bonds
+ * of one Trotter layer, FP64, in place on a device-resident MPS.
+ * MPS layout (right-canonical B tensors, Schmidt values on the virtual bonds):
+ *   B    device, L tensors; tensor i is D[i] x d x D[i+1] (row-major, index
+ *        order (a, s, b)) starting at B + i * tensor_stride doubles.
+ *   lam  device, L + 1 vectors; vector j (D[j] entries) starts at
+ *        lam + j * lam_stride doubles; lam[0] = lam[L] = {1}.
+ *   D    HOST array of the L + 1 bond dimensions (D[0] = D[L] = 1).
+ *   bond HOST array of the nb left sites i (0 <= i < L-1, pairwise |i-j| >= 2).
+ *   gate device, nb gates, gate b is d^2 x d^2 row-major ((s1 s2), (t1 t2)) at
+ *        gate + b * d^4.
+ * Per bond i, with k = D[i+1]:
+ *   theta_B = gate . (B[i] B[i+1]);  theta = lam[i] (row scaling) theta_B,
+ *   reshaped (D[i] d) x (d D[i+2]);  (U, S, V^T) = RSVD(theta, k, p, q);
+ *   B[i+1] <- V^T;  B[i] <- theta_B V / ||S||;  lam[i+1] <- S / ||S||;
+ *   trunc_err[b] (device) <- 1 - ||S||^2 / ||theta||_F^2 (discarded weight).
+ * Bond b uses Philox stream p->stream + bond[b].  p->prec must be RSVD_F64.
+ * info: DEVICE array of nb records.
+ * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_PRECISION,
+ * RSVD_ERR_WORKSPACE, RSVD_ERR_LAUNCH.
+ */
+int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond,
+                     double* B, size_t tensor_stride, double* lam, size_t lam_stride,
+                     const double* gate, const rsvd_params* p, double* trunc_err,
+                     void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
+ * Optional kernel timing (measurement aid, not part of the method).
+ * rsvd_profile_enable(n): from now on, CUDA events are recorded on the
+ * launching stream around each of up to n kernel launches of this library
+ * (n <= 0 disables and releases the events).  Not thread-safe.
+ * rsvd_profile_collect(ms, launches, nclass): waits for the recorded events,
+ * adds each launch's duration (ms) and count to ms[c] / launches[c] for its
+ * kernel class c < nclass (host arrays), clears the records and returns the
+ * number of classes; classes are named by rsvd_profile_class_name.
+ */
+int rsvd_profile_enable(int max_launches);
+int rsvd_profile_collect(double* ms, int* launches, int nclass);
+const char* rsvd_profile_class_name(int cls);
+
+/* rsvd_status_string - static description of a status code (never NULL). */
+const char* rsvd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSVD_H */

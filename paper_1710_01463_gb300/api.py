@@ -1,0 +1,137 @@
+"""Python entry points of librsvd with the same names as the C ABI.
+
+PyTorch provides device memory and the current CUDA stream; every step of the
+computation runs in librsvd's kernels.  Inputs must be CUDA tensors; there is
+no CPU path.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+
+_DTYPE_PREC = {torch.float64: _lib.RSVD_F64, torch.float32: _lib.RSVD_F32}
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _params(k, p, q, prec, seed, stream, max_sweeps=0):
+    return _lib.RsvdParams(int(k), int(p), int(q), int(prec), int(seed) & ((1 << 64) - 1),
+                           int(stream) & ((1 << 64) - 1), int(max_sweeps), 0)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise ValueError("librsvd works on CUDA tensors only")
+
+
+def info_dicts(info):
+    """Decode a (batch, 6) int32 info tensor into a list of dicts."""
+    rows = info.view(-1, _lib.INFO_INTS).cpu().tolist()
+    keys = ("status", "path", "chol_fallbacks", "jacobi_sweeps", "l", "rotations")
+    return [dict(zip(keys, r)) for r in rows]
+
+
+def rsvd_gaussian(n, l, seed, stream=0, device="cuda", out=None):
+    """Omega (n x l, FP64) of Alg. RSVD step 1; see include/rsvd.h."""
+    lib = _lib.load()
+    if out is None:
+        out = torch.empty((n, l), dtype=torch.float64, device=device)
+    _require_cuda(out)
+    _lib.check(lib.rsvd_gaussian(int(n), int(l), int(seed), int(stream), ctypes.c_void_p(out.data_ptr()),
+                                 int(out.stride(0)), _stream_handle()), "rsvd_gaussian")
+    return out
+
+
+def rsvd_workspace_size(m, n, k, p=8, q=2, dtype=torch.float64):
+    lib = _lib.load()
+    par = _params(k, p, q, _DTYPE_PREC[dtype], 0, 0)
+    sz = ctypes.c_size_t(0)
+    _lib.check(lib.rsvd_workspace_size(int(m), int(n), ctypes.byref(par), ctypes.byref(sz)), "rsvd_workspace_size")
+    return sz.value
+
+
+def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None):
+    """Rank-k RSVD of one matrix: returns (U, S, Vt, info) as CUDA tensors."""
+    lib = _lib.load()
+    _require_cuda(A)
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a row-major 2-D tensor")
+    prec = _DTYPE_PREC[A.dtype]
+    m, n = A.shape
+    par = _params(k, p, q, prec, seed, stream, max_sweeps)
+    sz = ctypes.c_size_t(0)
+    _lib.check(lib.rsvd_workspace_size(m, n, ctypes.byref(par), ctypes.byref(sz)), "rsvd_workspace_size")
+    if work is None or work.numel() < sz.value:
+        work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=A.device)
+    U = torch.empty((m, k), dtype=A.dtype, device=A.device)
+    S = torch.empty((k,), dtype=torch.float64, device=A.device)
+    Vt = torch.empty((k, n), dtype=A.dtype, device=A.device)
+    info = torch.zeros((1, _lib.INFO_INTS), dtype=torch.int32, device=A.device)
+    rc = lib.rsvd_truncate(m, n, ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.byref(par),
+                           ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(U.data_ptr()), U.stride(0),
+                           ctypes.c_void_p(Vt.data_ptr()), Vt.stride(0), ctypes.c_void_p(work.data_ptr()),
+                           work.numel(), ctypes.c_void_p(info.data_ptr()), _stream_handle())
+    _lib.check(rc, "rsvd_truncate")
+    return U, S, Vt, info
+
+
+class BatchedPlan:
+    """Preallocated outputs and workspace of rsvd_truncate_batched for fixed shapes."""
+
+    def __init__(self, shapes, ks, p=8, q=2, seed=0, stream=0, dtype=torch.float64, device="cuda",
+                 max_sweeps=0, chi_global=0):
+        lib = _lib.load()
+        self.shapes = [(int(m), int(n)) for m, n in shapes]
+        self.ks = [int(k) for k in ks]
+        self.dtype = dtype
+        self.chi_global = int(chi_global)
+        self.par = _params(self.ks[0], p, q, _DTYPE_PREC[dtype], seed, stream, max_sweeps)
+        B = len(self.shapes)
+        self.m_arr = _lib.int_array([s[0] for s in self.shapes])
+        self.n_arr = _lib.int_array([s[1] for s in self.shapes])
+        self.k_arr = _lib.int_array(self.ks)
+        sz = ctypes.c_size_t(0)
+        _lib.check(lib.rsvd_batched_workspace_size(B, self.m_arr, self.n_arr, self.k_arr, ctypes.byref(self.par),
+                                                   ctypes.byref(sz)), "rsvd_batched_workspace_size")
+        self.work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=device)
+        self.U = [torch.empty((m, k), dtype=dtype, device=device) for (m, _), k in zip(self.shapes, self.ks)]
+        self.S = [torch.empty((k,), dtype=torch.float64, device=device) for k in self.ks]
+        self.Vt = [torch.empty((k, n), dtype=dtype, device=device) for (_, n), k in zip(self.shapes, self.ks)]
+        self.info = torch.zeros((B, _lib.INFO_INTS), dtype=torch.int32, device=device)
+        self.k_out = torch.zeros((B,), dtype=torch.int32, device=device)
+        self.S_ptr = _lib.ptr_array([t.data_ptr() for t in self.S])
+        self.U_ptr = _lib.ptr_array([t.data_ptr() for t in self.U])
+        self.V_ptr = _lib.ptr_array([t.data_ptr() for t in self.Vt])
+        self.ldu = _lib.int_array([t.stride(0) for t in self.U])
+        self.ldv = _lib.int_array([t.stride(0) for t in self.Vt])
+
+    def run(self, As, stream=None):
+        lib = _lib.load()
+        if len(As) != len(self.shapes):
+            raise ValueError("batch size mismatch")
+        for A, (m, n) in zip(As, self.shapes):
+            _require_cuda(A)
+            if tuple(A.shape) != (m, n) or A.dtype != self.dtype or A.stride(1) != 1:
+                raise ValueError("matrix shape / dtype / layout mismatch")
+        A_ptr = _lib.ptr_array([A.data_ptr() for A in As])
+        lda = _lib.int_array([A.stride(0) for A in As])
+        rc = lib.rsvd_truncate_batched(len(As), self.m_arr, self.n_arr, A_ptr, lda, self.k_arr, ctypes.byref(self.par),
+                                       self.S_ptr, self.U_ptr, self.ldu, self.V_ptr, self.ldv, self.chi_global,
+                                       ctypes.c_void_p(self.k_out.data_ptr()), ctypes.c_void_p(self.work.data_ptr()),
+                                       self.work.numel(), ctypes.c_void_p(self.info.data_ptr()),
+                                       _stream_handle(stream))
+        _lib.check(rc, "rsvd_truncate_batched")
+        return self.U, self.S, self.Vt
+
+
+def rsvd_truncate_batched(As, ks, p=8, q=2, seed=0, stream=0, chi_global=0, max_sweeps=0):
+    """Alg. RSVD on a list of matrices; returns (U list, S list, Vt list, k_out, info)."""
+    plan = BatchedPlan([tuple(A.shape) for A in As], ks, p, q, seed, stream, As[0].dtype, As[0].device,
+                       max_sweeps, chi_global)
+    U, S, Vt = plan.run(As)
+    return U, S, Vt, plan.k_out, plan.info

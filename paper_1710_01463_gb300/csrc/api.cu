@@ -1,0 +1,499 @@
+// C ABI of librsvd (declarations and contracts in include/rsvd.h).
+//
+// Host side: argument checks, workspace layout, and the launch sequence of
+// Alg. RSVD (Sec. II.B) for a batch of matrices.  Every step runs in the
+// kernels of this library; the host only enqueues launches on the caller's
+// stream and never synchronises, so a whole call can be captured in a CUDA
+// graph.  Matrices of a batch are processed together, kMaxJobs per launch.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rsvd {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxSample = 1024;  // largest sample width l supported
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Prob {
+  int m, n, k, l;
+  int exact;
+  int want_u;
+  const void* A;
+  int lda;
+  double* S;
+  void* U;
+  int ldu;
+  void* Vt;
+  int ldvt;
+  unsigned long long seed, stream;
+  rsvd_info* info;
+  int max_sweeps;
+  // workspace
+  void *Y0, *Y1, *Z0, *Z1, *Rinv, *Ps;
+  double *G, *part, *hw, *hq, *Bm, *Bg, *Pg, *sig;
+  int* flag;
+  int csize, use_global;
+};
+
+// Workspace of one matrix (bytes), with the buffer offsets when `p` is given.
+size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base) {
+  const int mx = std::max(m, n);
+  const int nchunk = ceil_div(mx, kGramChunk);
+  const int cs = jacobi_cluster_size(l, n);
+  const int glob = jacobi_fits_smem(l, n, cs) ? 0 : 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return base ? (void*)(base + o) : nullptr;
+  };
+  void* Y0 = take((size_t)m * l * tsize);
+  void* Y1 = take((size_t)m * l * tsize);
+  void* Z0 = take((size_t)n * l * tsize);
+  void* Z1 = take((size_t)n * l * tsize);
+  void* Rinv = take((size_t)l * l * tsize);
+  void* Ps = take((size_t)std::max(k, 1) * l * tsize);
+  void* G = take((size_t)l * l * 8);
+  void* part = take((size_t)nchunk * l * l * 8);
+  void* hw = take((size_t)(mx + 16) * l * 8);
+  void* hq = take((size_t)(mx + 16) * l * 8);
+  void* Bm = take((size_t)l * n * 8);
+  void* Bg = take(glob ? (size_t)l * (n + 16) * 8 : 0);
+  void* Pg = take(glob ? (size_t)l * (l + 16) * 8 : 0);
+  void* sig = take((size_t)l * 8);
+  void* flag = take(sizeof(int) * 4);
+  if (p) {
+    p->Y0 = Y0; p->Y1 = Y1; p->Z0 = Z0; p->Z1 = Z1; p->Rinv = Rinv; p->Ps = Ps;
+    p->G = (double*)G; p->part = (double*)part; p->hw = (double*)hw; p->hq = (double*)hq;
+    p->Bm = (double*)Bm; p->Bg = (double*)Bg; p->Pg = (double*)Pg; p->sig = (double*)sig;
+    p->flag = (int*)flag;
+    p->csize = cs;
+    p->use_global = glob;
+  }
+  return off;
+}
+
+inline int sample_width(int m, int n, int k, int p) { return std::min(k + p, std::min(m, n)); }
+
+#define RSVD_TRY(x)                              \
+  do {                                           \
+    cudaError_t err__ = (x);                     \
+    if (err__ != cudaSuccess) {                  \
+      last_cuda_error() = err__;                 \
+      return RSVD_ERR_LAUNCH;                    \
+    }                                            \
+  } while (0)
+
+cudaError_t& last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
+template <typename T>
+OrthBatch<T> orth_batch(const std::vector<Prob*>& ps, bool onY) {
+  OrthBatch<T> b;
+  b.count = (int)ps.size();
+  b.max_chunks = 0;
+  b.max_tilepairs = 0;
+  for (size_t i = 0; i < ps.size(); ++i) {
+    Prob& p = *ps[i];
+    OrthJob<T>& J = b.job[i];
+    J.rows = onY ? p.m : p.n;
+    J.l = p.l;
+    J.Y = (T*)(onY ? p.Y0 : p.Z0);
+    J.Y1 = (T*)(onY ? p.Y1 : p.Z1);
+    J.part = p.part;
+    J.G = p.G;
+    J.Rinv = (T*)p.Rinv;
+    J.hw = p.hw;
+    J.hq = p.hq;
+    J.flag = p.flag;
+    J.info = p.info;
+    // nearly square samples: Householder QR directly (CholeskyQR2 has no flop
+    // advantage there and such samples are often numerically rank deficient)
+    J.hh_first = 3 * J.l > J.rows ? 1 : 0;
+  }
+  return b;
+}
+
+// Alg. RSVD for up to kMaxJobs matrices of one precision.
+template <typename T>
+int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
+  const int cnt = (int)probs.size();
+  std::vector<Prob*> rs;  // matrices on the randomized path
+  for (auto& p : probs)
+    if (!p.exact) rs.push_back(&p);
+
+  {
+    PrepBatch<T> b;
+    b.count = cnt;
+    for (int i = 0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      b.job[i] = PrepJob<T>{p.m, p.n, p.l, p.exact, (const T*)p.A, p.lda, (T*)p.Y0, p.Bm, p.flag, p.info};
+    }
+    RSVD_TRY(launch_prep<T>(b, s));
+  }
+  if (!rs.empty()) {
+    const int rc = (int)rs.size();
+    {  // step 1: Omega (n x l) into Z0
+      OmegaBatch<T> b;
+      b.count = rc;
+      for (int i = 0; i < rc; ++i) {
+        Prob& p = *rs[i];
+        b.job[i] = OmegaJob<T>{p.n, p.l, p.l, (T*)p.Z0, p.seed, p.stream};
+      }
+      RSVD_TRY(launch_omega<T>(b, s));
+    }
+    auto gemm_AZ = [&]() {  // Y0 = A Z0
+      GemmBatch<T, T> g;
+      g.count = rc;
+      for (int i = 0; i < rc; ++i) {
+        Prob& p = *rs[i];
+        g.job[i] = GemmJob<T, T>{p.m, p.l, p.n, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Z0, (T*)p.Y0, nullptr, nullptr, 0};
+      }
+      return launch_gemm<T, T, false, false>(g, s);
+    };
+    auto gemm_AtY = [&]() {  // Z0 = A^T Y0
+      GemmBatch<T, T> g;
+      g.count = rc;
+      for (int i = 0; i < rc; ++i) {
+        Prob& p = *rs[i];
+        g.job[i] = GemmJob<T, T>{p.n, p.l, p.m, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Y0, (T*)p.Z0, nullptr, nullptr, 0};
+      }
+      return launch_gemm<T, T, true, false>(g, s);
+    };
+    // step 2: Y = A Omega, Q = orth(Y); then q times Z = orth(A^T Q), Q = orth(A Z)
+    RSVD_TRY(gemm_AZ());
+    RSVD_TRY(launch_orth<T>(orth_batch<T>(rs, true), s));
+    for (int it = 0; it < q; ++it) {
+      RSVD_TRY(gemm_AtY());
+      RSVD_TRY(launch_orth<T>(orth_batch<T>(rs, false), s));
+      RSVD_TRY(gemm_AZ());
+      RSVD_TRY(launch_orth<T>(orth_batch<T>(rs, true), s));
+    }
+    {  // step 4: B = Q^T A (l x n) in FP64
+      GemmBatch<T, double> g;
+      g.count = rc;
+      for (int i = 0; i < rc; ++i) {
+        Prob& p = *rs[i];
+        g.job[i] = GemmJob<T, double>{p.l, p.n, p.m, p.l, p.lda, p.n, (const T*)p.Y0, (const T*)p.A, p.Bm, nullptr, nullptr, 0};
+      }
+      RSVD_TRY((launch_gemm<T, double, true, false>(g, s)));
+    }
+  }
+  // SVD of B by one-sided Jacobi; matrices grouped by cluster size / storage
+  {
+    std::vector<int> done(cnt, 0);
+    for (int i0 = 0; i0 < cnt; ++i0) {
+      if (done[i0]) continue;
+      JacobiBatch<T> b;
+      b.count = 0;
+      b.csize = probs[i0].csize;
+      b.use_global = probs[i0].use_global;
+      for (int i = i0; i < cnt; ++i) {
+        Prob& p = probs[i];
+        if (done[i] || p.csize != b.csize || p.use_global != b.use_global) continue;
+        done[i] = 1;
+        JacobiJob<T>& J = b.job[b.count++];
+        J.l = p.l; J.n = p.n; J.k = p.k;
+        J.Bm = p.Bm; J.Bg = p.Bg; J.Pg = p.Pg;
+        J.S = p.S; J.sig = p.sig;
+        J.Vt = (T*)p.Vt; J.ldvt = p.ldvt;
+        J.Ps = (T*)p.Ps;
+        J.info = p.info;
+        J.max_sweeps = p.max_sweeps;
+        J.want_vt = 1;
+      }
+      RSVD_TRY(launch_jacobi<T>(b, s));
+    }
+  }
+  // lift U = Q U~ and fix the signs
+  {
+    GemmBatch<T, T> g;
+    g.count = 0;
+    SignBatch<T> sb;
+    sb.count = 0;
+    for (int i = 0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      if (!p.want_u) continue;
+      g.job[g.count++] = GemmJob<T, T>{p.m, p.k, p.l, p.l, p.l, p.ldu, (const T*)p.Y0, (const T*)p.Ps, (T*)p.U, nullptr, nullptr, 0};
+      sb.job[sb.count++] = SignJob<T>{p.m, p.n, p.k, (T*)p.U, p.ldu, (T*)p.Vt, p.ldvt};
+    }
+    RSVD_TRY((launch_gemm<T, T, false, true>(g, s)));
+    RSVD_TRY(launch_sign<T>(sb, s));
+  }
+  return RSVD_OK;
+}
+
+int check_params(const rsvd_params* p) {
+  if (!p) return RSVD_ERR_NULL_POINTER;
+  if (p->p < 0 || p->q < 0 || p->q > 64 || p->max_sweeps < 0 || p->flags != 0) return RSVD_ERR_INVALID_SIZE;
+  if (p->prec != RSVD_F64 && p->prec != RSVD_F32) return RSVD_ERR_PRECISION;
+  return RSVD_OK;
+}
+
+size_t tsize_of(int prec) { return prec == RSVD_F64 ? 8 : 4; }
+
+int run_batched(std::vector<Prob>& probs, const rsvd_params* p, char* work, size_t work_bytes, cudaStream_t s) {
+  const size_t ts = tsize_of(p->prec);
+  size_t need = 0;
+  for (auto& pr : probs) need += layout(nullptr, pr.m, pr.n, pr.k, pr.l, ts, nullptr);
+  if (need > work_bytes) return RSVD_ERR_WORKSPACE;
+  size_t off = 0;
+  for (auto& pr : probs) {
+    off += layout(&pr, pr.m, pr.n, pr.k, pr.l, ts, work + off);
+  }
+  for (size_t c0 = 0; c0 < probs.size(); c0 += kMaxJobs) {
+    std::vector<Prob> chunk(probs.begin() + c0, probs.begin() + std::min(probs.size(), c0 + kMaxJobs));
+    int rc = p->prec == RSVD_F64 ? run_chunk<double>(chunk, p->q, s) : run_chunk<float>(chunk, p->q, s);
+    if (rc != RSVD_OK) return rc;
+  }
+  return RSVD_OK;
+}
+
+}  // namespace
+}  // namespace rsvd
+
+using namespace rsvd;
+
+extern "C" {
+
+const char* rsvd_status_string(int status) {
+  switch (status) {
+    case RSVD_OK: return "ok";
+    case RSVD_ERR_INVALID_SIZE: return "invalid size, rank or leading dimension";
+    case RSVD_ERR_NULL_POINTER: return "required pointer is NULL";
+    case RSVD_ERR_PRECISION: return "precision not supported";
+    case RSVD_ERR_WORKSPACE: return "workspace too small";
+    case RSVD_ERR_LAUNCH: return cudaGetErrorString(last_cuda_error());
+    case RSVD_ERR_NONFINITE: return "non-finite value in the input";
+    case RSVD_WARN_NOCONV: return "Jacobi SVD reached its sweep cap";
+    default: return "unknown status";
+  }
+}
+
+int rsvd_gaussian(int n, int l, uint64_t seed, uint64_t stream, double* omega, int ld, void* cuda_stream) {
+  if (n < 1 || l < 1 || ld < l) return RSVD_ERR_INVALID_SIZE;
+  if (!omega) return RSVD_ERR_NULL_POINTER;
+  RSVD_TRY(launch_omega_f64_single(n, l, ld, omega, seed, stream, (cudaStream_t)cuda_stream));
+  return RSVD_OK;
+}
+
+int rsvd_batched_workspace_size(int batch, const int* m, const int* n, const int* k, const rsvd_params* p,
+                                size_t* bytes) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!m || !n || !k || !bytes) return RSVD_ERR_NULL_POINTER;
+  if (batch < 1) return RSVD_ERR_INVALID_SIZE;
+  size_t tot = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (m[b] < 1 || n[b] < 1 || k[b] < 1 || k[b] > std::min(m[b], n[b])) return RSVD_ERR_INVALID_SIZE;
+    const int l = sample_width(m[b], n[b], k[b], p->p);
+    if (l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+    tot += layout(nullptr, m[b], n[b], k[b], l, tsize_of(p->prec), nullptr);
+  }
+  *bytes = tot;
+  return RSVD_OK;
+}
+
+int rsvd_workspace_size(int m, int n, const rsvd_params* p, size_t* bytes) {
+  if (!p) return RSVD_ERR_NULL_POINTER;
+  return rsvd_batched_workspace_size(1, &m, &n, &p->k, p, bytes);
+}
+
+int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* const* A, const int* lda, const int* k,
+                          const rsvd_params* p, double* const* S, void* const* U, const int* ldu, void* const* Vt,
+                          const int* ldvt, int chi_global, int* k_out, void* work, size_t work_bytes, rsvd_info* info,
+                          void* cuda_stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (batch < 1 || chi_global < 0) return RSVD_ERR_INVALID_SIZE;
+  if (!m || !n || !A || !lda || !k || !S || !U || !ldu || !Vt || !ldvt || !work || !info) return RSVD_ERR_NULL_POINTER;
+  if (chi_global > 0 && !k_out) return RSVD_ERR_NULL_POINTER;
+  if (chi_global > 0 && batch > kMaxJobs) return RSVD_ERR_INVALID_SIZE;
+  if (((uintptr_t)work) % kAlign) return RSVD_ERR_WORKSPACE;
+  std::vector<Prob> probs(batch);
+  int total_k = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (m[b] < 1 || n[b] < 1 || k[b] < 1 || k[b] > std::min(m[b], n[b])) return RSVD_ERR_INVALID_SIZE;
+    if (lda[b] < n[b] || ldu[b] < k[b] || ldvt[b] < n[b]) return RSVD_ERR_INVALID_SIZE;
+    if (!A[b] || !S[b] || !U[b] || !Vt[b]) return RSVD_ERR_NULL_POINTER;
+    Prob& pr = probs[b];
+    std::memset(&pr, 0, sizeof(Prob));
+    pr.m = m[b]; pr.n = n[b]; pr.k = k[b];
+    pr.l = sample_width(m[b], n[b], k[b], p->p);
+    if (pr.l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+    pr.exact = pr.m <= pr.l ? 1 : 0;
+    pr.want_u = 1;
+    pr.A = A[b]; pr.lda = lda[b];
+    pr.S = S[b]; pr.U = U[b]; pr.ldu = ldu[b]; pr.Vt = Vt[b]; pr.ldvt = ldvt[b];
+    pr.seed = p->seed; pr.stream = p->stream + (uint64_t)b;
+    pr.info = info + b;
+    pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    total_k += k[b];
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  rc = run_batched(probs, p, (char*)work, work_bytes, s);
+  if (rc) return rc;
+  if (chi_global > 0) {
+    SelectBatch sb;
+    sb.count = batch;
+    sb.chi = chi_global;
+    sb.total = total_k;
+    sb.k_out = k_out;
+    for (int b = 0; b < batch; ++b) sb.job[b] = SelectJob{S[b], k[b]};
+    RSVD_TRY(launch_select(sb, s));
+  }
+  return RSVD_OK;
+}
+
+int rsvd_truncate(int m, int n, const void* A, int lda, const rsvd_params* p, double* S, void* U, int ldu, void* Vt,
+                  int ldvt, void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream) {
+  if (!p) return RSVD_ERR_NULL_POINTER;
+  const void* Aa[1] = {A};
+  double* Sa[1] = {S};
+  void* Ua[1] = {U};
+  void* Va[1] = {Vt};
+  return rsvd_truncate_batched(1, &m, &n, Aa, &lda, &p->k, p, Sa, Ua, &ldu, Va, &ldvt, 0, nullptr, work, work_bytes,
+                               info, cuda_stream);
+}
+
+// ---------------------------------------------------------------- TEBD
+namespace {
+struct TebdLayout {
+  size_t t2, thetaB, theta, S, nrm, fro2, rsvd;
+};
+size_t tebd_bond_bytes(int m, int n, int k, int l, TebdLayout* o) {
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t x = off;
+    off += align_up(b);
+    return x;
+  };
+  TebdLayout L;
+  L.t2 = take((size_t)m * n * 8);
+  L.thetaB = take((size_t)m * n * 8);
+  L.theta = take((size_t)m * n * 8);
+  L.S = take((size_t)k * 8);
+  L.nrm = take(8);
+  L.fro2 = take(64 * 8);
+  L.rsvd = off;
+  off += layout(nullptr, m, n, k, l, 8, nullptr);
+  if (o) *o = L;
+  return off;
+}
+}  // namespace
+
+int tebd_workspace_size(int L, int d, const int* D, int nb, const rsvd_params* p, size_t* bytes) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!D || !bytes) return RSVD_ERR_NULL_POINTER;
+  if (L < 2 || d < 1 || nb < 1) return RSVD_ERR_INVALID_SIZE;
+  size_t mx = 0;
+  for (int i = 0; i + 1 < L; ++i) {
+    const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
+    if (k < 1 || k > std::min(m, n)) return RSVD_ERR_INVALID_SIZE;
+    if (sample_width(m, n, k, p->p) > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+    mx = std::max(mx, tebd_bond_bytes(m, n, k, sample_width(m, n, k, p->p), nullptr));
+  }
+  *bytes = mx * (size_t)nb;
+  return RSVD_OK;
+}
+
+int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double* B, size_t tensor_stride, double* lam,
+                     size_t lam_stride, const double* gate, const rsvd_params* p, double* trunc_err, void* work,
+                     size_t work_bytes, rsvd_info* info, void* cuda_stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->prec != RSVD_F64) return RSVD_ERR_PRECISION;
+  if (!D || !bond || !B || !lam || !gate || !trunc_err || !work || !info) return RSVD_ERR_NULL_POINTER;
+  if (L < 2 || d < 1 || nb < 1 || nb > kMaxJobs) return RSVD_ERR_INVALID_SIZE;
+  if (D[0] != 1 || D[L] != 1) return RSVD_ERR_INVALID_SIZE;
+  if (((uintptr_t)work) % kAlign) return RSVD_ERR_WORKSPACE;
+  for (int b = 0; b < nb; ++b) {
+    const int i = bond[b];
+    if (i < 0 || i + 1 >= L) return RSVD_ERR_INVALID_SIZE;
+    for (int c = 0; c < b; ++c)
+      if (std::abs(bond[c] - i) < 2) return RSVD_ERR_INVALID_SIZE;
+    const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
+    if (k < 1 || k > std::min(m, n)) return RSVD_ERR_INVALID_SIZE;
+    if (sample_width(m, n, k, p->p) > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+    if ((size_t)D[i] * d * D[i + 1] > tensor_stride || (size_t)D[i + 1] * d * D[i + 2] > tensor_stride) return RSVD_ERR_INVALID_SIZE;
+    if ((size_t)D[i + 1] > lam_stride) return RSVD_ERR_INVALID_SIZE;
+  }
+  size_t per = 0;
+  for (int i = 0; i + 1 < L; ++i) {
+    const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
+    per = std::max(per, tebd_bond_bytes(m, n, k, sample_width(m, n, k, p->p), nullptr));
+  }
+  if (per * (size_t)nb > work_bytes) return RSVD_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  char* base = (char*)work;
+  std::vector<TebdLayout> lay(nb);
+  std::vector<Prob> probs(nb);
+  GemmBatch<double, double> g2;
+  g2.count = nb;
+  TebdBatch tb;
+  tb.count = nb;
+  for (int b = 0; b < nb; ++b) {
+    const int i = bond[b];
+    const int Dl = D[i], Dm = D[i + 1], Dr = D[i + 2];
+    const int m = Dl * d, n = d * Dr, k = Dm;
+    const int l = sample_width(m, n, k, p->p);
+    char* wb = base + per * b;
+    tebd_bond_bytes(m, n, k, l, &lay[b]);
+    double* T2 = (double*)(wb + lay[b].t2);
+    double* thB = (double*)(wb + lay[b].thetaB);
+    double* th = (double*)(wb + lay[b].theta);
+    double* Bi = B + tensor_stride * i;
+    double* Bj = B + tensor_stride * (i + 1);
+    // T2[(a,t1),(t2,c)] = sum_b B_i[(a,t1), b] B_{i+1}[b, (t2,c)]
+    g2.job[b] = GemmJob<double, double>{m, n, Dm, Dm, n, n, Bi, Bj, T2, nullptr, nullptr, 0};
+    tb.job[b] = TebdJob{Dl, Dr, d, T2, gate + (size_t)b * d * d * d * d, lam + lam_stride * i, thB, th,
+                        (double*)(wb + lay[b].fro2)};
+    Prob& pr = probs[b];
+    std::memset(&pr, 0, sizeof(Prob));
+    pr.m = m; pr.n = n; pr.k = k; pr.l = l;
+    pr.exact = m <= l ? 1 : 0;
+    pr.want_u = 0;
+    pr.A = th; pr.lda = n;
+    pr.S = (double*)(wb + lay[b].S);
+    pr.U = nullptr; pr.ldu = k;
+    pr.Vt = Bj; pr.ldvt = n;     // V^T is the new B_{i+1} (k x d D_r)
+    pr.seed = p->seed; pr.stream = p->stream + (uint64_t)i;
+    pr.info = info + b;
+    pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    layout(&pr, m, n, k, l, 8, wb + lay[b].rsvd);
+  }
+  RSVD_TRY((launch_gemm<double, double, false, false>(g2, s)));
+  RSVD_TRY(launch_tebd_theta(tb, s));
+  rc = run_chunk<double>(probs, p->q, s);
+  if (rc) return rc;
+  TebdFinBatch fb;
+  fb.count = nb;
+  GemmBatch<double, double> g3;
+  g3.count = nb;
+  for (int b = 0; b < nb; ++b) {
+    const int i = bond[b];
+    char* wb = base + per * b;
+    const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
+    double* nrm = (double*)(wb + lay[b].nrm);
+    fb.job[b] = TebdFinJob{k, (double*)(wb + lay[b].S), lam + lam_stride * (i + 1), nrm,
+                           (double*)(wb + lay[b].fro2), trunc_err + b};
+    // B_i <- theta_B V / ||S||   (V^T now stored in B_{i+1})
+    g3.job[b] = GemmJob<double, double>{m, k, n, n, n, k, (double*)(wb + lay[b].thetaB), B + tensor_stride * (i + 1),
+                                        B + tensor_stride * i, nrm, nullptr, 0};
+  }
+  RSVD_TRY(launch_tebd_finish(fb, s));
+  RSVD_TRY((launch_gemm<double, double, false, true>(g3, s)));
+  return RSVD_OK;
+}
+
+}  // extern "C"

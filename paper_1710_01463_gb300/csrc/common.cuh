@@ -1,0 +1,207 @@
+// Internal declarations shared by the translation units of librsvd.
+// Kernel job descriptors are passed BY VALUE as kernel parameters (up to
+// kMaxJobs per launch), so no descriptor array has to be copied to the device
+// and every launch sequence can be captured in a CUDA graph.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/rsvd.h"
+
+namespace rsvd {
+
+constexpr int kMaxJobs = 64;       // jobs per launch (larger batches are chunked)
+constexpr int kGramChunk = 256;    // rows of Y per Gram partial
+constexpr int kGramTile = 32;      // Gram tile edge
+
+// ---- batched GEMM: C = op(A) * op(X) [/ *div] ----------------------------
+// op(A) is M x K, op(X) is K x N, C is M x N; all row-major.
+// TA: op(A) = A^T with A stored K x M.  TX: op(X) = X^T with X stored N x K.
+template <typename Tin, typename Tout>
+struct GemmJob {
+  int M, N, K;
+  int lda, ldx, ldc;
+  const Tin* A;
+  const Tin* X;
+  Tout* C;
+  const double* div;   // optional: divide C by *div
+  const int* gate;     // optional: run only if *gate == gate_val
+  int gate_val;
+};
+
+template <typename Tin, typename Tout>
+struct GemmBatch {
+  int count;
+  int tiles_m, tiles_n;
+  GemmJob<Tin, Tout> job[kMaxJobs];
+};
+
+// ---- Omega --------------------------------------------------------------
+template <typename T>
+struct OmegaJob {
+  int n, l, ld;
+  T* out;
+  unsigned long long seed, stream;
+};
+template <typename T>
+struct OmegaBatch {
+  int count;
+  OmegaJob<T> job[kMaxJobs];
+};
+
+// ---- orthonormalisation (CholeskyQR2 + Householder fallback) ------------
+template <typename T>
+struct OrthJob {
+  int rows, l;
+  T* Y;              // rows x l (ld = l), in: sample, out: Q
+  T* Y1;             // rows x l scratch
+  double* part;      // Gram partials, nchunk x l x l
+  double* G;         // l x l
+  T* Rinv;           // l x l
+  double* hw;        // (rows + 16) x l FP64 scratch (Householder slices)
+  double* hq;        // (rows + 16) x l FP64 scratch (Householder slices)
+  int* flag;         // breakdown flag
+  rsvd_info* info;
+  int hh_first;      // 1: skip CholeskyQR2, use Householder QR directly
+};
+template <typename T>
+struct OrthBatch {
+  int count;
+  int max_chunks;
+  int max_tilepairs;
+  OrthJob<T> job[kMaxJobs];
+};
+
+// ---- one-sided Jacobi SVD of B (l x n, FP64) -----------------------------
+template <typename T>
+struct JacobiJob {
+  int l, n, k;
+  const double* Bm;  // l x n input (ld = n)
+  double* Bg;        // global slice storage when shared memory is too small (l x n)
+  double* Pg;        // global slice storage for P (l x l)
+  double* S;         // k outputs
+  double* sig;       // l outputs (sorted)
+  T* Vt;             // k x n (ldvt)
+  int ldvt;
+  T* Ps;             // k x l, rows of P in sorted order
+  rsvd_info* info;
+  int max_sweeps;
+  int want_vt;
+};
+template <typename T>
+struct JacobiBatch {
+  int count;
+  int csize;         // CTAs per matrix (cluster size)
+  int use_global;    // 1: slices live in global memory
+  JacobiJob<T> job[kMaxJobs];
+};
+
+// ---- misc -----------------------------------------------------------------
+template <typename T>
+struct PrepJob {
+  int m, n, l;
+  int exact;         // 1: Q = I (written to Y), Bm = A
+  const T* A;
+  int lda;
+  T* Y;
+  double* Bm;
+  int* flag;
+  rsvd_info* info;
+};
+template <typename T>
+struct PrepBatch {
+  int count;
+  PrepJob<T> job[kMaxJobs];
+};
+
+template <typename T>
+struct SignJob {
+  int m, n, k;
+  T* U;
+  int ldu;
+  T* Vt;
+  int ldvt;
+};
+template <typename T>
+struct SignBatch {
+  int count;
+  SignJob<T> job[kMaxJobs];
+};
+
+struct SelectJob {
+  const double* S;
+  int k;
+};
+struct SelectBatch {
+  int count;
+  int chi;
+  int total;
+  int* k_out;
+  SelectJob job[kMaxJobs];
+};
+
+// TEBD: theta = lam (row scale) * gate . (B_i B_{i+1}); T2 = B_i B_{i+1} from a GEMM.
+struct TebdJob {
+  int Dl, Dr, d;
+  const double* T2;     // (Dl d) x (d Dr): T2[(a,t1),(t2,c)]
+  const double* gate;   // d^2 x d^2
+  const double* lam;    // Dl
+  double* thetaB;       // (Dl d) x (d Dr)
+  double* theta;        // (Dl d) x (d Dr)
+  double* fro2;         // ||theta||_F^2 partial sums (one double, atomically accumulated)
+};
+struct TebdBatch {
+  int count;
+  TebdJob job[kMaxJobs];
+};
+struct TebdFinJob {
+  int k;
+  const double* S;
+  double* lam;          // k outputs
+  double* nrm;          // ||S||
+  const double* fro2;
+  double* trunc_err;
+};
+struct TebdFinBatch {
+  int count;
+  TebdFinJob job[kMaxJobs];
+};
+
+// ---- optional per-kernel timing (CUDA events around launches) -------------
+enum KernelClass {
+  KC_PREP = 0, KC_OMEGA, KC_GEMM, KC_GRAM, KC_CHOL, KC_HOUSEHOLDER, KC_JACOBI, KC_SIGN, KC_SELECT, KC_TEBD,
+  KC_COUNT
+};
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaStream_t s);
+
+// ---- launchers (defined in the .cu files) ---------------------------------
+template <typename Tin, typename Tout, bool TA, bool TX>
+cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_omega(const OmegaBatch<T>& b, cudaStream_t s);
+cudaError_t launch_omega_f64_single(int n, int l, int ld, double* out, unsigned long long seed,
+                                    unsigned long long stream, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prep(const PrepBatch<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_jacobi(const JacobiBatch<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sign(const SignBatch<T>& b, cudaStream_t s);
+cudaError_t launch_select(const SelectBatch& b, cudaStream_t s);
+cudaError_t launch_tebd_theta(const TebdBatch& b, cudaStream_t s);
+cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s);
+
+// shared-memory budget of the Jacobi kernel for given sizes (bytes), and the
+// cluster size chosen for them
+int jacobi_cluster_size(int l, int n);
+size_t jacobi_smem_bytes(int l, int n, int csize);
+bool jacobi_fits_smem(int l, int n, int csize);
+
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace rsvd

@@ -1,0 +1,191 @@
+// Batched tall-skinny GEMM C = op(A) op(X) for the products of Alg. RSVD
+// (Sec. II.B): the sketch Y = A Omega, the power-iteration products A^T Q and
+// A Z, the projection B = Q^T A, the change of basis Y R^-1 of CholeskyQR and
+// the lift U = Q U~.
+//
+// SIMT kernel (FFMA for float, DFMA for double): on GB300 FP64 has no tensor
+// core path, so the FP64 products are bound by the DFMA pipe.  64 x 64 output
+// tile per CTA, K staged through shared memory in slices of 16, a 4 x 4
+// register tile per thread with a stride-16 layout (conflict-free shared
+// reads, 16-wide coalesced stores).  Register double-buffering of the next K
+// slice overlaps the global loads with the FMAs.
+#include "common.cuh"
+
+namespace rsvd {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <typename Tin, bool TA>
+__device__ __forceinline__ void load_a(const Tin* __restrict__ A, int lda, int M, int K,
+                                       int m0, int k0, Tin (&ra)[4]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int idx = t + q * NT;  // 0..1023 over a 64 x 16 tile
+    int i, kk;
+    if (!TA) {  // A is M x K: k fastest
+      kk = idx % BK;
+      i = idx / BK;
+    } else {    // A is K x M: m fastest
+      i = idx % BM;
+      kk = idx / BM;
+    }
+    const int gi = m0 + i, gk = k0 + kk;
+    Tin v = (Tin)0;
+    if (gi < M && gk < K) v = TA ? A[(long long)gk * lda + gi] : A[(long long)gi * lda + gk];
+    ra[q] = v;
+  }
+}
+
+template <typename Tin, bool TA>
+__device__ __forceinline__ void store_a(Tin (*As)[BM + 1], const Tin (&ra)[4]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int idx = t + q * NT;
+    int i, kk;
+    if (!TA) {
+      kk = idx % BK;
+      i = idx / BK;
+    } else {
+      i = idx % BM;
+      kk = idx / BM;
+    }
+    As[kk][i] = ra[q];
+  }
+}
+
+template <typename Tin, bool TX>
+__device__ __forceinline__ void load_x(const Tin* __restrict__ X, int ldx, int N, int K, int n0, int k0, Tin (&rx)[4]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int idx = t + q * NT;
+    int j, kk;
+    if (!TX) {  // X is K x N: n fastest
+      j = idx % BN;
+      kk = idx / BN;
+    } else {    // X is N x K: k fastest
+      kk = idx % BK;
+      j = idx / BK;
+    }
+    const int gj = n0 + j, gk = k0 + kk;
+    Tin v = (Tin)0;
+    if (gj < N && gk < K) v = TX ? X[(long long)gj * ldx + gk] : X[(long long)gk * ldx + gj];
+    rx[q] = v;
+  }
+}
+
+template <typename Tin, bool TX>
+__device__ __forceinline__ void store_x(Tin (*Xs)[BN + 1], const Tin (&rx)[4]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int idx = t + q * NT;
+    int j, kk;
+    if (!TX) {
+      j = idx % BN;
+      kk = idx / BN;
+    } else {
+      kk = idx % BK;
+      j = idx / BK;
+    }
+    Xs[kk][j] = rx[q];
+  }
+}
+
+template <typename Tin, typename Tout, bool TA, bool TX>
+__global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBatch<Tin, Tout> b) {
+  const GemmJob<Tin, Tout>& J = b.job[blockIdx.z];
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (m0 >= J.M || n0 >= J.N) return;
+  if (J.gate && *J.gate != J.gate_val) return;
+
+  __shared__ Tin As[2][BK][BM + 1];
+  __shared__ Tin Xs[2][BK][BN + 1];
+
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  Tin acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (Tin)0;
+
+  Tin ra[4], rx[4];
+  load_a<Tin, TA>(J.A, J.lda, J.M, J.K, m0, 0, ra);
+  load_x<Tin, TX>(J.X, J.ldx, J.N, J.K, n0, 0, rx);
+  store_a<Tin, TA>(As[0], ra);
+  store_x<Tin, TX>(Xs[0], rx);
+  __syncthreads();
+
+  const int nk = (J.K + BK - 1) / BK;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) {
+      load_a<Tin, TA>(J.A, J.lda, J.M, J.K, m0, (kt + 1) * BK, ra);
+      load_x<Tin, TX>(J.X, J.ldx, J.N, J.K, n0, (kt + 1) * BK, rx);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      Tin av[4], xv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[cur][kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) xv[j] = Xs[cur][kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], xv[j], acc[i][j]);
+    }
+    if (kt + 1 < nk) {
+      store_a<Tin, TA>(As[cur ^ 1], ra);
+      store_x<Tin, TX>(Xs[cur ^ 1], rx);
+    }
+    __syncthreads();
+  }
+
+  double scale = 1.0;
+  if (J.div) scale = 1.0 / *J.div;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = m0 + ty + 16 * i;
+    if (gi >= J.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = n0 + tx + 16 * j;
+      if (gj < J.N) {
+        Tout v = J.div ? (Tout)((double)acc[i][j] * scale) : (Tout)acc[i][j];
+        J.C[(long long)gi * J.ldc + gj] = v;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+template <typename Tin, typename Tout, bool TA, bool TX>
+cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  int tm = 1, tn = 1;
+  for (int i = 0; i < b.count; ++i) {
+    tm = max(tm, ceil_div(b.job[i].M, BM));
+    tn = max(tn, ceil_div(b.job[i].N, BN));
+  }
+  prof_begin(KC_GEMM, s);
+  gemm_kernel<Tin, Tout, TA, TX><<<dim3(tn, tm, b.count), NT, 0, s>>>(b);
+  prof_end(KC_GEMM, s);
+  return cudaGetLastError();
+}
+
+#define INST(Tin, Tout)                                                                           \
+  template cudaError_t launch_gemm<Tin, Tout, false, false>(const GemmBatch<Tin, Tout>&, cudaStream_t); \
+  template cudaError_t launch_gemm<Tin, Tout, true, false>(const GemmBatch<Tin, Tout>&, cudaStream_t);  \
+  template cudaError_t launch_gemm<Tin, Tout, false, true>(const GemmBatch<Tin, Tout>&, cudaStream_t);
+INST(double, double)
+INST(float, float)
+INST(float, double)
+#undef INST
+
+}  // namespace rsvd

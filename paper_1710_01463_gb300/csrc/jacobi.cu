@@ -1,0 +1,336 @@
+// Small SVD of B = Q^T A (l x n, FP64): Alg. RSVD step 4 (Sec. II.B), the
+// rank-k TSVD of B.  One-sided Jacobi (Hestenes; Demmel-Veselic) on the ROWS
+// of B: plane rotations P B = W until the rows of W are mutually orthogonal;
+// then sigma_i = ||w_i||, V~ rows = w_i / sigma_i and U~ = P^T.
+//
+// GB300 layout: one thread-block CLUSTER per matrix.  The n columns of B (and
+// the l columns of the rotation accumulator P) are split across the CTAs of
+// the cluster and stay in each CTA's shared memory for the whole
+// factorization.  Rows are paired by the round-robin (circle) ordering, l/2
+// disjoint pairs per round, one team of 8 lanes per pair.  Per round every CTA
+// forms the partial inner products <b_i, b_j> of its column slice, the cluster
+// exchanges them through distributed shared memory (one cluster barrier per
+// round, double-buffered; lane r of a team reads rank r's partial), and every
+// CTA reduces them with the same shuffle tree - so all CTAs take bit-identical
+// rotation decisions - and rotates its own slice.
+//
+// Row norms are recomputed exactly at the start of every sweep and updated by
+// the rotation identities (alpha - t gamma, beta + t gamma) inside it.  A pair
+// is rotated when |gamma| > tol sqrt(alpha beta), tol = n 2^-53.
+// Deflation: at the start of every sweep, rows whose norm is at most 2^-52 of
+// the largest row norm are set to zero - they are rounding noise of the
+// computed B (a backward perturbation below eps ||B||) - and the round-robin
+// ordering then runs over the remaining live rows only.  Zero rows give
+// singular value 0 with a zero row of V^T.  The loop ends after a sweep
+// without rotations or at the sweep cap (status RSVD_WARN_NOCONV).
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rsvd {
+
+namespace {
+
+constexpr int kJacobiThreads = 512;
+constexpr int kTeam = 8;   // lanes per row pair; lane t of a team reads the partials of ranks t, t + 8
+constexpr size_t kSmemBudget = 220 * 1024;
+
+__device__ __forceinline__ void round_pair(int r, int s, int lp, int& i, int& j) {
+  const int m = lp - 1;
+  int a, bb;
+  if (s == 0) {
+    a = m;
+    bb = r;
+  } else {
+    a = (r + s) % m;
+    bb = (r - s + m) % m;
+  }
+  i = min(a, bb);
+  j = max(a, bb);
+}
+
+struct JLayout {
+  int nc, np, npairs, lp;
+};
+
+__host__ __device__ inline JLayout jlayout(int l, int n, int csize) {
+  JLayout L;
+  L.nc = (n + csize - 1) / csize;
+  L.np = (l + csize - 1) / csize;
+  L.lp = l + (l & 1);
+  L.npairs = L.lp / 2;
+  return L;
+}
+
+__host__ __device__ inline size_t jsmem_small(int l, const JLayout& L) {
+  // norms, nrm_part, gpart[2][npairs], order (int, padded to doubles)
+  return sizeof(double) * ((size_t)2 * l + 2 * (size_t)L.npairs + (size_t)(l + 1) / 2 + 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const __grid_constant__ JacobiBatch<T> b) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = b.csize;
+  const int rank = (int)cluster.block_rank();
+  const JacobiJob<T>& J = b.job[blockIdx.y];
+  const int l = J.l, n = J.n;
+  const JLayout L = jlayout(l, n, C);
+  const int c0 = rank * L.nc, ncl = max(0, min(n, c0 + L.nc) - c0);
+  const int p0 = rank * L.np, npl = max(0, min(l, p0 + L.np) - p0);
+
+  extern __shared__ double sm[];
+  double* norms = sm;
+  double* nrm_part = norms + l;
+  double* gpart = nrm_part + l;                 // [2][npairs]
+  int* order = (int*)(gpart + 2 * L.npairs);
+  double* Bs;
+  double* Ps;
+  if (b.use_global) {
+    Bs = J.Bg + (size_t)rank * l * L.nc;
+    Ps = J.Pg + (size_t)rank * l * L.np;
+  } else {
+    Bs = sm + jsmem_small(l, L) / sizeof(double);
+    Ps = Bs + (size_t)l * L.nc;
+  }
+  __shared__ int rot_count;
+  __shared__ int nonfinite;
+  __shared__ int nlive;
+  __shared__ double rowmax;
+  int* live = order;  // live-row list during the sweeps; the sort order afterwards
+
+  const int tid = threadIdx.x;
+  const int team = tid / kTeam, tl = tid % kTeam, nteam = kJacobiThreads / kTeam;
+  const unsigned tmask = 0xffu << ((tid % 32) / kTeam * kTeam);  // this team's lanes
+  for (int e = tid; e < l * L.nc; e += kJacobiThreads) {
+    const int i = e / L.nc, c = e % L.nc;
+    Bs[e] = (c < ncl) ? J.Bm[(size_t)i * n + c0 + c] : 0.0;
+  }
+  for (int e = tid; e < l * L.np; e += kJacobiThreads) {
+    const int i = e / L.np, c = e % L.np;
+    Ps[e] = (c < npl && i == p0 + c) ? 1.0 : 0.0;
+  }
+  if (tid == 0) nonfinite = 0;
+  __syncthreads();
+
+  const double tol = (double)max(n, 1) * 0x1.0p-53;
+  const int max_sweeps = J.max_sweeps;
+  int sweeps = 0;
+  long long total_rot = 0;
+  bool converged = false;
+  for (;;) {
+    // exact row norms of this sweep
+    for (int i = tid; i < l; i += kJacobiThreads) {
+      double s = 0.0;
+      for (int c = 0; c < ncl; ++c) s = fma(Bs[i * L.nc + c], Bs[i * L.nc + c], s);
+      nrm_part[i] = s;
+    }
+    cluster.sync();
+    for (int i = tid; i < l; i += kJacobiThreads) {
+      double s = 0.0;
+      for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(nrm_part, r)[i];
+      norms[i] = s;
+    }
+    if (tid == 0) rot_count = 0;
+    __syncthreads();
+    for (int i = tid; i < l; i += kJacobiThreads)
+      if (!isfinite(norms[i])) nonfinite = 1;
+    __syncthreads();
+    if (nonfinite) break;  // identical in every CTA of the cluster
+    if (tid < 32) {
+      double mx = 0.0;
+      for (int i = tid; i < l; i += 32) mx = fmax(mx, norms[i]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (tid == 0) rowmax = mx;
+    }
+    __syncthreads();
+    {
+      const double floor_ = rowmax * 0x1.0p-104;  // (2^-52)^2 of the largest squared row norm
+      for (int e = tid; e < l * L.nc; e += kJacobiThreads)
+        if (!(norms[e / L.nc] > floor_)) Bs[e] = 0.0;
+      __syncthreads();
+      for (int i = tid; i < l; i += kJacobiThreads)
+        if (!(norms[i] > floor_)) norms[i] = 0.0;
+      if (tid == 0) {
+        int nl = 0;
+        for (int i = 0; i < l; ++i)
+          if (norms[i] > 0.0) live[nl++] = i;
+        nlive = nl;
+      }
+      __syncthreads();
+    }
+    if (converged || sweeps >= max_sweeps) break;
+
+    const int lpl = nlive + (nlive & 1);
+    const int npl2 = lpl / 2;
+    for (int r = 0; r < lpl - 1; ++r) {
+      double* gp = gpart + (r & 1) * L.npairs;
+      for (int s = team; s < npl2; s += nteam) {
+        int a, bq;
+        round_pair(r, s, lpl, a, bq);
+        double g = 0.0;
+        if (bq < nlive) {
+          const int i = live[a], j = live[bq];
+          for (int c = tl; c < ncl; c += kTeam) g = fma(Bs[i * L.nc + c], Bs[j * L.nc + c], g);
+        }
+#pragma unroll
+        for (int o = kTeam / 2; o > 0; o >>= 1) g += __shfl_xor_sync(tmask, g, o, kTeam);
+        if (tl == 0) gp[s] = g;
+      }
+      cluster.sync();
+      for (int s = team; s < npl2; s += nteam) {
+        int a, bq;
+        round_pair(r, s, lpl, a, bq);
+        if (bq >= nlive) continue;
+        const int i = live[a], j = live[bq];
+        const double al = norms[i], be = norms[j];
+        double g = 0.0;
+        for (int rr = tl; rr < C; rr += kTeam) g += cluster.map_shared_rank(gp, rr)[s];
+#pragma unroll
+        for (int o = kTeam / 2; o > 0; o >>= 1) g += __shfl_xor_sync(tmask, g, o, kTeam);
+        // rotation scalars on the team's lane 0 only (FP64 sqrt / divide are costly on this part)
+        double t = 0.0, cs = 1.0, sn = 0.0;
+        int rot = 0;
+        if (tl == 0 && al > 0.0 && be > 0.0 && fabs(g) > tol * sqrt(al * be)) {
+          rot = 1;
+          const double zeta = (be - al) / (2.0 * g);
+          // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); 1 / (2 zeta) once zeta^2 would overflow
+          t = fabs(zeta) < 1e150 ? (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)) : 0.5 / zeta;
+          cs = 1.0 / sqrt(1.0 + t * t);
+          sn = cs * t;
+        }
+        const int tb = (tid % 32) / kTeam * kTeam;
+        rot = __shfl_sync(tmask, rot, tb);
+        if (!rot) continue;
+        t = __shfl_sync(tmask, t, tb);
+        cs = __shfl_sync(tmask, cs, tb);
+        sn = __shfl_sync(tmask, sn, tb);
+        for (int c = tl; c < ncl; c += kTeam) {
+          const double x = Bs[i * L.nc + c], y = Bs[j * L.nc + c];
+          Bs[i * L.nc + c] = cs * x - sn * y;
+          Bs[j * L.nc + c] = sn * x + cs * y;
+        }
+        for (int c = tl; c < npl; c += kTeam) {
+          const double x = Ps[i * L.np + c], y = Ps[j * L.np + c];
+          Ps[i * L.np + c] = cs * x - sn * y;
+          Ps[j * L.np + c] = sn * x + cs * y;
+        }
+        if (tl == 0) {
+          norms[i] = al - t * g;
+          norms[j] = be + t * g;
+          atomicAdd(&rot_count, 1);
+        }
+      }
+      __syncthreads();
+    }
+    ++sweeps;
+    total_rot += rot_count;
+    converged = (rot_count == 0);
+  }
+  // norms now hold the exact final row norms (computed at the loop head)
+  double* sig = nrm_part;  // reuse: all remote reads of nrm_part finished before the last __syncthreads
+  cluster.sync();          // make sure no CTA still reads this CTA's nrm_part
+  for (int i = tid; i < l; i += kJacobiThreads) {
+    const double v = sqrt(norms[i]);
+    sig[i] = v;
+    if (!isfinite(v)) nonfinite = 1;
+  }
+  __syncthreads();
+  for (int i = tid; i < l; i += kJacobiThreads) {
+    const double ki = isfinite(sig[i]) ? sig[i] : -1.0;
+    int rk = 0;
+    for (int j = 0; j < l; ++j) {
+      const double kj = isfinite(sig[j]) ? sig[j] : -1.0;
+      rk += (kj > ki) || (kj == ki && j < i);
+    }
+    order[rk] = i;
+  }
+  __syncthreads();
+  const int k = J.k;
+  if (rank == 0) {
+    for (int r = tid; r < l; r += kJacobiThreads) {
+      const double v = sig[order[r]];
+      J.sig[r] = v;
+      if (r < k) J.S[r] = v;
+    }
+    if (tid == 0) {
+      J.info->jacobi_sweeps = sweeps;
+      J.info->rotations = (int)min(total_rot, (long long)0x7fffffff);
+      if (nonfinite)
+        J.info->status = RSVD_ERR_NONFINITE;
+      else if (!converged && J.info->status == RSVD_OK)
+        J.info->status = RSVD_WARN_NOCONV;
+    }
+  }
+  if (J.want_vt) {
+    for (int e = tid; e < k * ncl; e += kJacobiThreads) {
+      const int r = e / ncl, c = e % ncl;
+      const int src = order[r];
+      const double v = sig[src];
+      J.Vt[(size_t)r * J.ldvt + c0 + c] = (T)(v > 0.0 ? Bs[src * L.nc + c] / v : 0.0);
+    }
+  }
+  for (int e = tid; e < k * npl; e += kJacobiThreads) {
+    const int r = e / npl, c = e % npl;
+    J.Ps[(size_t)r * l + p0 + c] = (T)Ps[order[r] * L.np + c];
+  }
+  cluster.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+}  // namespace
+
+int jacobi_cluster_size(int l, int n) {
+  int c = n / 32;
+  if (c < 1) c = 1;
+  if (c > 8) c = 8;
+  // grow to 16 when a slice of 8 would not fit in shared memory
+  if (c == 8 && !jacobi_fits_smem(l, n, 8) && jacobi_fits_smem(l, n, 16)) c = 16;
+  return c;
+}
+
+size_t jacobi_smem_bytes(int l, int n, int csize) {
+  const JLayout L = jlayout(l, n, csize);
+  return jsmem_small(l, L) + sizeof(double) * ((size_t)l * L.nc + (size_t)l * L.np);
+}
+
+bool jacobi_fits_smem(int l, int n, int csize) { return jacobi_smem_bytes(l, n, csize) <= kSmemBudget; }
+
+template <typename T>
+cudaError_t launch_jacobi(const JacobiBatch<T>& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  size_t smem = 0;
+  for (int i = 0; i < b.count; ++i) {
+    const int l = b.job[i].l, n = b.job[i].n;
+    const size_t need = b.use_global ? jsmem_small(l, jlayout(l, n, b.csize)) : jacobi_smem_bytes(l, n, b.csize);
+    smem = max(smem, need);
+  }
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (b.csize > 8) {
+    e = cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b.csize, b.count, 1);
+  cfg.blockDim = dim3(kJacobiThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = b.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  prof_begin(KC_JACOBI, s);
+  e = cudaLaunchKernelEx(&cfg, jacobi_kernel<T>, b);
+  prof_end(KC_JACOBI, s);
+  return e;
+}
+
+template cudaError_t launch_jacobi<double>(const JacobiBatch<double>&, cudaStream_t);
+template cudaError_t launch_jacobi<float>(const JacobiBatch<float>&, cudaStream_t);
+
+}  // namespace rsvd

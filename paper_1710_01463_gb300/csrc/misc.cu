@@ -1,0 +1,196 @@
+// Small kernels around the factorization:
+//  - sign canonicalisation of the singular vector pairs (u_i, v_i);
+//  - the global post-selection of the chi largest singular values over the
+//    blocks of a block-diagonal matrix (Sec. III.A);
+//  - the two-site contraction and Schmidt-value update of a TEBD block update
+//    (Sec. III.A, "block update (B)").
+#include "common.cuh"
+
+namespace rsvd {
+
+namespace {
+
+// ---------------------------------------------------------------- signs
+// Flip (u_i, v_i) so that the largest-|.| entry of u_i is positive (lowest row
+// index on ties).  One warp per column.
+template <typename T>
+__global__ void __launch_bounds__(256) sign_kernel(const __grid_constant__ SignBatch<T> b) {
+  const SignJob<T>& J = b.job[blockIdx.y];
+  const int lane = threadIdx.x % 32;
+  const int col = blockIdx.x * 8 + threadIdx.x / 32;
+  if (col >= J.k) return;
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int r = lane; r < J.m; r += 32) {
+    const double v = fabs((double)J.U[(size_t)r * J.ldu + col]);
+    if (v > best) {
+      best = v;
+      bi = r;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (bi >= J.m) return;
+  const double lead = (double)J.U[(size_t)bi * J.ldu + col];
+  __syncwarp();
+  if (!(lead < 0.0)) return;
+  for (int r = lane; r < J.m; r += 32) J.U[(size_t)r * J.ldu + col] = -J.U[(size_t)r * J.ldu + col];
+  for (int c = lane; c < J.n; c += 32) J.Vt[(size_t)col * J.ldvt + c] = -J.Vt[(size_t)col * J.ldvt + c];
+}
+
+// ---------------------------------------------------------------- global top-chi
+__device__ __forceinline__ double skey(double v) { return isfinite(v) ? v : -1.0; }
+
+// number of entries of the descending array s[0..k) with key > v (gt) and >= v (ge)
+__device__ __forceinline__ void count_desc(const double* s, int k, double v, int& gt, int& ge) {
+  int lo = 0, hi = k;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (skey(s[mid]) > v) lo = mid + 1; else hi = mid;
+  }
+  gt = lo;
+  hi = k;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (skey(s[mid]) >= v) lo = mid + 1; else hi = mid;
+  }
+  ge = lo;
+}
+
+__global__ void select_zero_kernel(int* k_out, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) k_out[i] = 0;
+}
+
+// candidate (b, i) is kept when fewer than chi candidates precede it in the
+// order (value descending, then matrix index, then position)
+__global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ SelectBatch b) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.total) return;
+  int bb = 0, off = 0;
+  while (bb < b.count && g >= off + b.job[bb].k) {
+    off += b.job[bb].k;
+    ++bb;
+  }
+  const int i = g - off;
+  const double v = skey(b.job[bb].S[i]);
+  int before = 0;
+  for (int c = 0; c < b.count; ++c) {
+    int gt, ge;
+    count_desc(b.job[c].S, b.job[c].k, v, gt, ge);
+    before += gt;
+    if (c < bb) before += ge - gt;
+    else if (c == bb) before += i - gt;  // equal values at lower positions of the same matrix
+  }
+  if (before < b.chi) atomicMax(&b.k_out[bb], i + 1);
+}
+
+// ---------------------------------------------------------------- TEBD
+// theta_B[(a,s1),(s2,c)] = sum_{t1,t2} G[(s1 s2),(t1 t2)] T2[(a,t1),(t2,c)],
+// theta = lam[a] theta_B, and per-block partial sums of ||theta||_F^2.
+constexpr int kTebdBlocks = 64;
+
+__global__ void __launch_bounds__(256) tebd_theta_kernel(const __grid_constant__ TebdBatch b) {
+  const TebdJob& J = b.job[blockIdx.y];
+  const int d = J.d, Dl = J.Dl, Dr = J.Dr;
+  const int rows = Dl * d, cols = d * Dr;
+  const long long tot = (long long)rows * cols;
+  double acc = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(e / cols), col = (int)(e % cols);
+    const int a = row / d, s1 = row % d;
+    const int s2 = col / Dr, c = col % Dr;
+    double v = 0.0;
+    for (int t1 = 0; t1 < d; ++t1)
+      for (int t2 = 0; t2 < d; ++t2)
+        v = fma(J.gate[(s1 * d + s2) * d * d + t1 * d + t2], J.T2[(long long)(a * d + t1) * cols + t2 * Dr + c], v);
+    J.thetaB[e] = v;
+    const double w = J.lam[a] * v;
+    J.theta[e] = w;
+    acc = fma(w, w, acc);
+  }
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    J.fro2[blockIdx.x] = s;
+  }
+}
+
+// lam <- S / ||S||, nrm <- ||S||, trunc_err <- 1 - ||S||^2 / ||theta||_F^2
+__global__ void __launch_bounds__(256) tebd_finish_kernel(const __grid_constant__ TebdFinBatch b) {
+  const TebdFinJob& J = b.job[blockIdx.x];
+  __shared__ double red[8];
+  __shared__ double nrm;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < J.k; r += blockDim.x) acc = fma(J.S[r], J.S[r], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    double f = 0.0;
+    for (int q = 0; q < kTebdBlocks; ++q) f += J.fro2[q];
+    nrm = sqrt(s);
+    *J.nrm = nrm;
+    double te = f > 0.0 ? 1.0 - s / f : 0.0;
+    *J.trunc_err = te > 0.0 ? te : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < J.k; r += blockDim.x) J.lam[r] = nrm > 0.0 ? J.S[r] / nrm : 0.0;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_sign(const SignBatch<T>& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  int mk = 1;
+  for (int i = 0; i < b.count; ++i) mk = max(mk, b.job[i].k);
+  prof_begin(KC_SIGN, s);
+  sign_kernel<T><<<dim3(ceil_div(mk, 8), b.count), 256, 0, s>>>(b);
+  prof_end(KC_SIGN, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select(const SelectBatch& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  prof_begin(KC_SELECT, s);
+  select_zero_kernel<<<1, 256, 0, s>>>(b.k_out, b.count);
+  if (b.total > 0) select_kernel<<<ceil_div(b.total, 256), 256, 0, s>>>(b);
+  prof_end(KC_SELECT, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tebd_theta(const TebdBatch& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  prof_begin(KC_TEBD, s);
+  tebd_theta_kernel<<<dim3(kTebdBlocks, b.count), 256, 0, s>>>(b);
+  prof_end(KC_TEBD, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  prof_begin(KC_TEBD, s);
+  tebd_finish_kernel<<<b.count, 256, 0, s>>>(b);
+  prof_end(KC_TEBD, s);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_sign<double>(const SignBatch<double>&, cudaStream_t);
+template cudaError_t launch_sign<float>(const SignBatch<float>&, cudaStream_t);
+
+}  // namespace rsvd

@@ -1,0 +1,509 @@
+// Orthonormalisation of a sample Y (rows x l): Alg. RSVD steps 2-3 (Sec. II.B)
+// re-orthonormalise after every product with A or A^T.
+//
+// Primary path: CholeskyQR2 (Yamamoto, Nakatsukasa, Yanagisawa, Fukaya 2015).
+//   G = Y^T Y (FP64 accumulation, deterministic two-stage reduction),
+//   G = R^T R (FP64 Cholesky, upper R with positive diagonal),
+//   Q1 = Y R^-1, then once more on Q1.  Q R equals the unique thin QR with
+//   R_ii > 0 in exact arithmetic.
+// A pivot below 1e-14 of its diagonal entry (Y numerically rank deficient, or
+// conditioned beyond what two CholeskyQR passes can repair) sets a per-matrix
+// flag; the remaining CholeskyQR launches skip that matrix and a Householder QR
+// (FP64, one CTA per matrix) orthonormalises the ORIGINAL sample instead,
+// again with R_ii >= 0.  The fallback is counted in rsvd_info.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rsvd {
+
+namespace {
+
+constexpr double kPivotTol = 1e-14;
+
+// ---------------------------------------------------------------- prep
+template <typename T>
+__global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepBatch<T> b) {
+  const PrepJob<T>& J = b.job[blockIdx.y];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    J.info->status = RSVD_OK;
+    J.info->path = J.exact ? RSVD_PATH_EXACT : 0;
+    J.info->chol_fallbacks = 0;
+    J.info->jacobi_sweeps = 0;
+    J.info->l = J.l;
+    J.info->rotations = 0;
+    *J.flag = 0;
+  }
+  if (!J.exact) return;
+  // Q = I (m x l, l = m) and B = A (l x n, FP64)
+  const long long tq = (long long)J.m * J.l;
+  const long long tb = (long long)J.l * J.n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tq + tb;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < tq) {
+      const long long r = e / J.l, c = e - r * J.l;
+      J.Y[e] = (T)(r == c ? 1 : 0);
+    } else {
+      const long long f = e - tq;
+      const long long r = f / J.n, c = f - r * J.n;
+      J.Bm[f] = (double)J.A[r * J.lda + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Gram
+__device__ __forceinline__ void tilepair(int idx, int T, int& ti, int& tj) {
+  ti = 0;
+  while (idx >= T - ti) {
+    idx -= T - ti;
+    ++ti;
+  }
+  tj = ti + idx;
+}
+
+// partial G over one chunk of rows for one 32 x 32 tile (ti <= tj)
+template <typename T>
+__global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ OrthBatch<T> b, int gated, int src1) {
+  const OrthJob<T>& J = b.job[blockIdx.z];
+  if (J.hh_first || (gated && *J.flag != 0)) return;
+  const int l = J.l;
+  const int nt = (l + kGramTile - 1) / kGramTile;
+  if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
+  const int nchunk = (J.rows + kGramChunk - 1) / kGramChunk;
+  const int c = blockIdx.y;
+  if (c >= nchunk) return;
+  int ti, tj;
+  tilepair(blockIdx.x, nt, ti, tj);
+  const T* Y = src1 ? J.Y1 : J.Y;
+
+  __shared__ double Si[32][33], Sj[32][33];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  const int r_begin = c * kGramChunk;
+  const int r_end = min(J.rows, r_begin + kGramChunk);
+  for (int r0 = r_begin; r0 < r_end; r0 += 32) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int rr = e / 32, cc = e % 32;
+      const int r = r0 + rr;
+      const int ci = ti * 32 + cc, cj = tj * 32 + cc;
+      Si[rr][cc] = (r < r_end && ci < l) ? (double)Y[(long long)r * l + ci] : 0.0;
+      Sj[rr][cc] = (r < r_end && cj < l) ? (double)Y[(long long)r * l + cj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+      const double a0 = Si[rr][ty], a1 = Si[rr][ty + 16];
+      const double b0 = Sj[rr][tx], b1 = Sj[rr][tx + 16];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+      const int i = ti * 32 + ty + 16 * a, j = tj * 32 + tx + 16 * bb;
+      if (i < l && j < l) J.part[((long long)c * l + i) * l + j] = acc[a][bb];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant__ OrthBatch<T> b, int gated) {
+  const OrthJob<T>& J = b.job[blockIdx.y];
+  if (J.hh_first || (gated && *J.flag != 0)) return;
+  const int l = J.l;
+  const int nchunk = (J.rows + kGramChunk - 1) / kGramChunk;
+  const long long tot = (long long)l * l;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / l), j = (int)(e % l);
+    if (i > j) continue;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += J.part[((long long)c * l + i) * l + j];
+    J.G[(long long)i * l + j] = s;
+    J.G[(long long)j * l + i] = s;
+  }
+}
+
+// ---------------------------------------------------------------- Cholesky + R^-1
+// One CTA per matrix.  R (upper, R^T R = G) is built in shared memory when l is
+// small enough, else in place in G.  Breakdown (a pivot that is not above
+// kPivotTol times its original diagonal entry) sets the flag; the matrix then
+// takes the Householder path.
+template <typename T>
+__global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ OrthBatch<T> b, int pass, int use_smem) {
+  const OrthJob<T>& J = b.job[blockIdx.x];
+  if (pass == 0 && J.hh_first) {
+    if (threadIdx.x == 0) *J.flag = 1;
+    return;
+  }
+  if (pass == 1 && *J.flag != 0) return;
+  extern __shared__ double sm[];
+  const int l = J.l;
+  double* diag0 = sm;
+  double* R = use_smem ? sm + l : J.G;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const double g = J.G[e];
+    if (use_smem) R[e] = g;
+    if (e / l == e % l) diag0[e / l] = g;
+  }
+  __syncthreads();
+  for (int j = 0; j < l; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = R[j * l + j];
+      if (!(d > kPivotTol * diag0[j]) || !(diag0[j] > 0.0)) {
+        bad = 1;
+      } else {
+        R[j * l + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double rjj = R[j * l + j];
+    for (int c = j + 1 + threadIdx.x; c < l; c += blockDim.x) R[j * l + c] /= rjj;
+    __syncthreads();
+    const int w = l - j - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int r = j + 1 + e / w, c = j + 1 + e % w;
+      if (c >= r) R[r * l + c] = fma(-R[j * l + r], R[j * l + c], R[r * l + c]);
+    }
+    __syncthreads();
+  }
+  if (pass == 0 && threadIdx.x == 0) *J.flag = bad;  // every orthonormalisation starts afresh
+  if (bad) {
+    if (threadIdx.x == 0) *J.flag = 1;
+    return;
+  }
+  // X = R^-1 (upper): column j by back substitution, one thread per column
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    for (int i = l - 1; i > j; --i) J.Rinv[(long long)i * l + j] = (T)0;
+    const double xj = 1.0 / R[j * l + j];
+    J.Rinv[(long long)j * l + j] = (T)xj;
+    for (int i = j - 1; i >= 0; --i) {
+      double s = R[i * l + j] * xj;
+      for (int t = i + 1; t < j; ++t) s = fma(R[i * l + t], (double)J.Rinv[(long long)t * l + j], s);
+      J.Rinv[(long long)i * l + j] = (T)(-s / R[i * l + i]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Householder QR
+// Householder QR of Y (rows x l) by one thread-block CLUSTER per matrix: the
+// rows are split across the CTAs (FP64 slices in shared memory, or in global
+// scratch when they do not fit).  For column j every CTA forms the partial
+// ||x||^2 and x_0 of its rows, the cluster sums them through distributed
+// shared memory (same rank order everywhere -> identical reflectors), each CTA
+// scales its part of v_j, forms the partial products v_j^T Y[:, c] of its
+// rows, and after a second exchange applies the reflector to its rows.  Q is
+// then accumulated backwards, Q = H_0 ... H_{l-1} [I; 0], one exchange per
+// reflector, and written back into Y with column signs making R_ii >= 0.
+// Runs for matrices whose flag is set (CholeskyQR2 breakdown, or the
+// Householder-first policy of nearly square samples).
+constexpr int kHhThreads = 512;
+constexpr int kHhTeam = 8;  // lanes per column in the partial products and their exchange
+
+struct HLayout {
+  int rs;  // rows per CTA
+};
+
+__host__ __device__ inline size_t hh_small_doubles(int l) { return (size_t)l + 2 * (size_t)l + 2 * 2 + 2 + (size_t)l; }
+
+template <typename T>
+__global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_constant__ OrthBatch<T> b, int csize,
+                                                                  int use_global) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const OrthJob<T>& J = b.job[blockIdx.y];
+  if (*J.flag == 0) return;  // cluster-uniform: one matrix per cluster
+  const int C = csize;
+  const int rank = (int)cluster.block_rank();
+  const int rows = J.rows, l = J.l;
+  const int rs = (rows + C - 1) / C;
+  const int r0 = rank * rs;
+  const int nr = max(0, min(rows, r0 + rs) - r0);
+  extern __shared__ double sm[];
+  double* alpha = sm;            // l
+  double* pd = alpha + l;        // [2][l] partial dot products
+  double* pn = pd + 2 * l;       // [2][2] partial (||x||^2, x_0)
+  double* sc = pn + 4;           // [2] reduced (||x||^2, x_0)
+  double* dsum = sc + 2;         // l reduced dot products
+  double* Ys;
+  double* Qs;
+  if (use_global) {
+    Ys = J.hw + (size_t)rank * rs * l;
+    Qs = J.hq + (size_t)rank * rs * l;
+  } else {
+    Ys = sm + hh_small_doubles(l);
+    Qs = Ys + (size_t)rs * l;
+  }
+  const int tid = threadIdx.x;
+  const int team = tid / kHhTeam, tl = tid % kHhTeam, nteam = kHhThreads / kHhTeam;
+  const unsigned tmask = 0xffu << ((tid % 32) / kHhTeam * kHhTeam);
+  for (int e = tid; e < nr * l; e += kHhThreads) Ys[e] = (double)J.Y[(size_t)r0 * l + e];
+  __shared__ double red[kHhThreads / 32][2];
+  __syncthreads();
+
+  for (int j = 0; j < l; ++j) {
+    // phase 1: partial ||x||^2 and x_0 over own rows r >= j
+    double a = 0.0, x0 = 0.0;
+    for (int rr = tid; rr < nr; rr += kHhThreads) {
+      const int r = r0 + rr;
+      if (r >= j) {
+        const double v = Ys[rr * l + j];
+        a = fma(v, v, a);
+        if (r == j) x0 = v;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      x0 += __shfl_xor_sync(0xffffffffu, x0, o);
+    }
+    if (tid % 32 == 0) {
+      red[tid / 32][0] = a;
+      red[tid / 32][1] = x0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int w = 0; w < kHhThreads / 32; ++w) {
+        s0 += red[w][0];
+        s1 += red[w][1];
+      }
+      pn[(j & 1) * 2 + 0] = s0;
+      pn[(j & 1) * 2 + 1] = s1;
+    }
+    cluster.sync();
+    if (tid < 32) {
+      double s0 = 0.0, s1 = 0.0;
+      if (tid < C) {
+        const double* rp = cluster.map_shared_rank(pn, tid);
+        s0 = rp[(j & 1) * 2 + 0];
+        s1 = rp[(j & 1) * 2 + 1];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      if (tid == 0) {  // the reflector's scalars, once (FP64 sqrt / divide are costly on this part)
+        const double nrm2 = s0, xj0 = s1;
+        double al0 = 0.0, inv0 = 0.0;
+        if (nrm2 > 0.0) {
+          al0 = xj0 >= 0.0 ? -sqrt(nrm2) : sqrt(nrm2);
+          const double v0 = xj0 - al0;
+          const double vn2 = nrm2 - xj0 * xj0 + v0 * v0;
+          inv0 = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
+        }
+        alpha[j] = al0;
+        sc[0] = inv0;
+        sc[1] = xj0;
+      }
+    }
+    __syncthreads();
+    const double xj = sc[1], al = alpha[j], inv = sc[0];
+    for (int rr = tid; rr < nr; rr += kHhThreads) {
+      const int r = r0 + rr;
+      if (r >= j) Ys[rr * l + j] = (r == j ? (xj - al) : Ys[rr * l + j]) * inv;
+    }
+    __syncthreads();
+    // phase 2: partial v^T Y[:, c] for c > j
+    double* pdj = pd + (j & 1) * l;
+    for (int c = j + 1 + team; c < l; c += nteam) {
+      double d = 0.0;
+      for (int rr = max(0, j - r0) + tl; rr < nr; rr += kHhTeam) d = fma(Ys[rr * l + j], Ys[rr * l + c], d);
+#pragma unroll
+      for (int o = kHhTeam / 2; o > 0; o >>= 1) d += __shfl_xor_sync(tmask, d, o, kHhTeam);
+      if (tl == 0) pdj[c] = d;
+    }
+    cluster.sync();
+    for (int c = j + 1 + team; c < l; c += nteam) {
+      double d = 0.0;
+      for (int r = tl; r < C; r += kHhTeam) d += cluster.map_shared_rank(pdj, r)[c];
+#pragma unroll
+      for (int o = kHhTeam / 2; o > 0; o >>= 1) d += __shfl_xor_sync(tmask, d, o, kHhTeam);
+      if (tl == 0) dsum[c] = d;
+    }
+    __syncthreads();
+    const int w = l - j - 1;
+    for (int e = tid; e < nr * w; e += kHhThreads) {
+      const int rr = e / w, c = j + 1 + e % w;
+      if (r0 + rr >= j) Ys[rr * l + c] = fma(-2.0 * Ys[rr * l + j], dsum[c], Ys[rr * l + c]);
+    }
+    __syncthreads();
+  }
+  cluster.sync();  // every remote read of pd / pn is done before they are reused below
+  for (int e = tid; e < nr * l; e += kHhThreads) {
+    const int rr = e / l, c = e % l;
+    Qs[e] = (r0 + rr == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = l - 1; j >= 0; --j) {
+    double* pdj = pd + (j & 1) * l;
+    for (int c = j + team; c < l; c += nteam) {
+      double d = 0.0;
+      for (int rr = max(0, j - r0) + tl; rr < nr; rr += kHhTeam) d = fma(Ys[rr * l + j], Qs[rr * l + c], d);
+#pragma unroll
+      for (int o = kHhTeam / 2; o > 0; o >>= 1) d += __shfl_xor_sync(tmask, d, o, kHhTeam);
+      if (tl == 0) pdj[c] = d;
+    }
+    cluster.sync();
+    for (int c = j + team; c < l; c += nteam) {
+      double d = 0.0;
+      for (int r = tl; r < C; r += kHhTeam) d += cluster.map_shared_rank(pdj, r)[c];
+#pragma unroll
+      for (int o = kHhTeam / 2; o > 0; o >>= 1) d += __shfl_xor_sync(tmask, d, o, kHhTeam);
+      if (tl == 0) dsum[c] = d;
+    }
+    __syncthreads();
+    const int w = l - j;
+    for (int e = tid; e < nr * w; e += kHhThreads) {
+      const int rr = e / w, c = j + e % w;
+      if (r0 + rr >= j) Qs[rr * l + c] = fma(-2.0 * Ys[rr * l + j], dsum[c], Qs[rr * l + c]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nr * l; e += kHhThreads) {
+    const int c = e % l;
+    const double sg = alpha[c] < 0.0 ? -1.0 : 1.0;
+    J.Y[(size_t)r0 * l + e] = (T)(sg * Qs[e]);
+  }
+  if (rank == 0 && tid == 0) {
+    if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
+    atomicOr(&J.info->path, RSVD_PATH_HOUSEHOLDER);
+  }
+  cluster.sync();  // no CTA leaves while others may read its shared memory
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_prep(const PrepBatch<T>& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  long long mx = 1;
+  for (int i = 0; i < b.count; ++i)
+    if (b.job[i].exact) mx = max(mx, (long long)b.job[i].m * b.job[i].l + (long long)b.job[i].l * b.job[i].n);
+  int gx = (int)min(1024LL, (mx + 255) / 256);
+  prof_begin(KC_PREP, s);
+  prep_kernel<T><<<dim3(gx, b.count), 256, 0, s>>>(b);
+  prof_end(KC_PREP, s);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  int maxl = 1, maxchunk = 1, maxtp = 1;
+  long long maxll = 1;
+  for (int i = 0; i < b.count; ++i) {
+    const int l = b.job[i].l;
+    maxl = max(maxl, l);
+    maxll = max(maxll, (long long)l * l);
+    maxchunk = max(maxchunk, ceil_div(b.job[i].rows, kGramChunk));
+    const int nt = ceil_div(l, kGramTile);
+    maxtp = max(maxtp, nt * (nt + 1) / 2);
+  }
+  // shared-memory Cholesky when R fits (l <= 160)
+  const size_t smem_full = (size_t)(maxl + (size_t)maxl * maxl) * sizeof(double);
+  const int use_smem = smem_full <= 210 * 1024 ? 1 : 0;
+  const size_t smem = use_smem ? smem_full : (size_t)maxl * sizeof(double);
+  cudaError_t e;
+  e = cudaFuncSetAttribute(cholinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int rgx = (int)min(1024LL, (maxll + 255) / 256);
+
+  // pass 1: Y -> Y1 = Y R1^-1
+  prof_begin(KC_GRAM, s);
+  gram_kernel<T><<<dim3(maxtp, maxchunk, b.count), 256, 0, s>>>(b, 0, 0);
+  gram_reduce_kernel<T><<<dim3(rgx, b.count), 256, 0, s>>>(b, 0);
+  prof_end(KC_GRAM, s);
+  prof_begin(KC_CHOL, s);
+  cholinv_kernel<T><<<b.count, 512, smem, s>>>(b, 0, use_smem);
+  prof_end(KC_CHOL, s);
+  {
+    GemmBatch<T, T> g;
+    g.count = b.count;
+    for (int i = 0; i < b.count; ++i) {
+      const OrthJob<T>& J = b.job[i];
+      g.job[i] = GemmJob<T, T>{J.rows, J.l, J.l, J.l, J.l, J.l, J.Y, J.Rinv, J.Y1, nullptr, J.flag, 0};
+    }
+    e = launch_gemm<T, T, false, false>(g, s);
+    if (e != cudaSuccess) return e;
+  }
+  // pass 2: Y1 -> Y = Y1 R2^-1
+  prof_begin(KC_GRAM, s);
+  gram_kernel<T><<<dim3(maxtp, maxchunk, b.count), 256, 0, s>>>(b, 1, 1);
+  gram_reduce_kernel<T><<<dim3(rgx, b.count), 256, 0, s>>>(b, 1);
+  prof_end(KC_GRAM, s);
+  prof_begin(KC_CHOL, s);
+  cholinv_kernel<T><<<b.count, 512, smem, s>>>(b, 1, use_smem);
+  prof_end(KC_CHOL, s);
+  {
+    GemmBatch<T, T> g;
+    g.count = b.count;
+    for (int i = 0; i < b.count; ++i) {
+      const OrthJob<T>& J = b.job[i];
+      g.job[i] = GemmJob<T, T>{J.rows, J.l, J.l, J.l, J.l, J.l, J.Y1, J.Rinv, J.Y, nullptr, J.flag, 0};
+    }
+    e = launch_gemm<T, T, false, false>(g, s);
+    if (e != cudaSuccess) return e;
+  }
+  // fallback for flagged matrices: Householder QR of the original sample
+  // Householder for flagged matrices, grouped by cluster size / storage
+  {
+    int maxrows = 1;
+    for (int i = 0; i < b.count; ++i) maxrows = max(maxrows, b.job[i].rows);
+    int csize = min(8, max(1, ceil_div(maxrows, 32)));
+    auto bytes = [&](int cs) {
+      size_t mx = 0;
+      for (int i = 0; i < b.count; ++i) {
+        const int rs = ceil_div(b.job[i].rows, cs), l = b.job[i].l;
+        mx = max(mx, (hh_small_doubles(l) + 2 * (size_t)rs * l) * sizeof(double));
+      }
+      return mx;
+    };
+    if (bytes(csize) > 200 * 1024 && csize == 8 && bytes(16) <= 200 * 1024) csize = 16;
+    const int use_global = bytes(csize) > 200 * 1024 ? 1 : 0;
+    size_t hsmem = 0;
+    if (use_global) {
+      for (int i = 0; i < b.count; ++i) hsmem = max(hsmem, hh_small_doubles(b.job[i].l) * sizeof(double));
+    } else {
+      hsmem = bytes(csize);
+    }
+    e = cudaFuncSetAttribute(householder_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+    if (e != cudaSuccess) return e;
+    if (csize > 8) {
+      e = cudaFuncSetAttribute(householder_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize, b.count, 1);
+    cfg.blockDim = dim3(kHhThreads, 1, 1);
+    cfg.dynamicSmemBytes = hsmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    prof_begin(KC_HOUSEHOLDER, s);
+    e = cudaLaunchKernelEx(&cfg, householder_kernel<T>, b, csize, use_global);
+    prof_end(KC_HOUSEHOLDER, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_prep<double>(const PrepBatch<double>&, cudaStream_t);
+template cudaError_t launch_prep<float>(const PrepBatch<float>&, cudaStream_t);
+template cudaError_t launch_orth<double>(const OrthBatch<double>&, cudaStream_t);
+template cudaError_t launch_orth<float>(const OrthBatch<float>&, cudaStream_t);
+
+}  // namespace rsvd

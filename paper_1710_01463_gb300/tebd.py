@@ -1,0 +1,127 @@
+"""Imaginary-time TEBD driver on a device-resident MPS (Sec. III.A, III.C).
+
+The open spin-1/2 transverse-field Ising chain H = -sum Z_j Z_{j+1} - h sum X_j
+(unitarily equivalent to the paper's spin-1/2 H_chain, Sec. III.B) evolved by
+second-order Trotter steps exp(-dt/2 H_A) exp(-dt H_B) exp(-dt/2 H_A), layer A
+holding the bonds (0,1), (2,3), ... and layer B the bonds (1,2), (3,4), ...
+Each layer is ONE call of tebd_bond_update over all of its bonds, which are
+independent.  Bond dimensions are fixed at min(d^j, d^(L-j), chi); an interior
+site gives half of its field to each of its two bonds, an edge site all of it.
+
+The gates (4 x 4 matrix exponentials of the bond Hamiltonians) are inputs of
+the bond update and are formed once on the host.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from .api import _params, _stream_handle
+
+_X = np.array([[0.0, 1.0], [1.0, 0.0]])
+_Z = np.array([[1.0, 0.0], [0.0, -1.0]])
+_I = np.eye(2)
+
+
+def bond_hamiltonian(i, L, h):
+    """Two-site term of bond (i, i+1), 4 x 4 on (s_i, s_{i+1})."""
+    fl = 1.0 if i == 0 else 0.5
+    fr = 1.0 if i + 1 == L - 1 else 0.5
+    return -np.kron(_Z, _Z) - h * (fl * np.kron(_X, _I) + fr * np.kron(_I, _X))
+
+
+def bond_gate(hb, tau):
+    """exp(-tau h_b) through the eigenbasis of the symmetric h_b."""
+    w, V = np.linalg.eigh(hb)
+    return (V * np.exp(-tau * w)[None, :]) @ V.T
+
+
+class TebdChain:
+    """MPS of an L-site chain with right-canonical tensors B[i] and Schmidt values lam[j]."""
+
+    def __init__(self, L, chi, h=1.0, p=10, q=2, seed=0, device="cuda", max_sweeps=0):
+        if L < 2:
+            raise ValueError("L >= 2 required")
+        self.L, self.d, self.chi, self.h = L, 2, chi, h
+        self.p, self.q, self.seed, self.max_sweeps = p, q, seed, max_sweeps
+        self.device = torch.device(device)
+        d = self.d
+        self.D = [int(min(d ** min(j, L - j), chi)) for j in range(L + 1)]
+        self.tensor_stride = max(self.D[i] * d * self.D[i + 1] for i in range(L))
+        self.lam_stride = max(self.D)
+        self.B = torch.zeros((L, self.tensor_stride), dtype=torch.float64, device=self.device)
+        self.lam = torch.zeros((L + 1, self.lam_stride), dtype=torch.float64, device=self.device)
+        self.layers = [list(range(0, L - 1, 2)), list(range(1, L - 1, 2))]
+        self.D_arr = _lib.int_array(self.D)
+        nb = max(len(x) for x in self.layers)
+        lib = _lib.load()
+        par = _params(1, p, q, _lib.RSVD_F64, seed, 0)
+        sz = ctypes.c_size_t(0)
+        _lib.check(lib.tebd_workspace_size(L, d, self.D_arr, nb, ctypes.byref(par), ctypes.byref(sz)),
+                   "tebd_workspace_size")
+        self.work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=self.device)
+        self.trunc_err = torch.zeros((3, nb), dtype=torch.float64, device=self.device)
+        self.info = torch.zeros((3, nb, _lib.INFO_INTS), dtype=torch.int32, device=self.device)
+        self.bond_arr = [_lib.int_array(b) for b in self.layers]
+        self.dt = None
+
+    def set_dt(self, dt):
+        """Form the gates of the three layers of one Trotter step."""
+        self.dt = float(dt)
+        gates = []
+        for layer, tau in ((0, dt / 2), (1, dt), (0, dt / 2)):
+            g = [bond_gate(bond_hamiltonian(i, self.L, self.h), tau).ravel() for i in self.layers[layer]]
+            gates.append(torch.tensor(np.stack(g), dtype=torch.float64, device=self.device))
+        self.gates = gates
+
+    def set_product_state(self, vectors):
+        """B[i][0, :, 0] = vectors[i] / |vectors[i]|, lam[j] = (1, 0, ...)."""
+        v = np.asarray(vectors, dtype=np.float64)
+        self.B.zero_()
+        self.lam.zero_()
+        host = np.zeros((self.L, self.tensor_stride))
+        for i in range(self.L):
+            t = np.zeros((self.D[i], self.d, self.D[i + 1]))
+            t[0, :, 0] = v[i] / np.linalg.norm(v[i])
+            host[i, : t.size] = t.ravel()
+        self.B.copy_(torch.from_numpy(host))
+        lam = np.zeros((self.L + 1, self.lam_stride))
+        lam[:, 0] = 1.0
+        self.lam.copy_(torch.from_numpy(lam))
+
+    def step(self, step_index, stream=None):
+        """One second-order Trotter step (three layers), asynchronous."""
+        lib = _lib.load()
+        sh = _stream_handle(stream)
+        for j, layer in enumerate((0, 1, 0)):
+            bonds = self.layers[layer]
+            if not bonds:
+                continue
+            par = _params(1, self.p, self.q, _lib.RSVD_F64, self.seed, (3 * step_index + j) * self.L,
+                          self.max_sweeps)
+            rc = lib.tebd_bond_update(self.L, self.d, self.D_arr, len(bonds), self.bond_arr[layer],
+                                      ctypes.c_void_p(self.B.data_ptr()), self.tensor_stride,
+                                      ctypes.c_void_p(self.lam.data_ptr()), self.lam_stride,
+                                      ctypes.c_void_p(self.gates[j].data_ptr()), ctypes.byref(par),
+                                      ctypes.c_void_p(self.trunc_err[j].data_ptr()),
+                                      ctypes.c_void_p(self.work.data_ptr()), self.work.numel(),
+                                      ctypes.c_void_p(self.info[j].data_ptr()), sh)
+            _lib.check(rc, "tebd_bond_update")
+
+    def tensors(self):
+        """Host copies of the B tensors, shaped (D[i], d, D[i+1])."""
+        host = self.B.cpu().numpy()
+        return [host[i, : self.D[i] * self.d * self.D[i + 1]].reshape(self.D[i], self.d, self.D[i + 1]).copy()
+                for i in range(self.L)]
+
+    def schmidt_values(self):
+        host = self.lam.cpu().numpy()
+        return [host[j, : self.D[j]].copy() for j in range(self.L + 1)]
+
+    def state_to_host(self):
+        return self.B.cpu().numpy().copy(), self.lam.cpu().numpy().copy()
+
+    def state_from_host(self, B, lam):
+        self.B.copy_(torch.from_numpy(np.asarray(B)))
+        self.lam.copy_(torch.from_numpy(np.asarray(lam)))
