@@ -103,42 +103,48 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ flop model
 def bond_shapes():
+    """(m, n, k, l) of every bond update of one Trotter step, per layer (A, B, A)."""
     D = [int(min(D_LOC ** min(j, L_SITES - j), CHI)) for j in range(L_SITES + 1)]
     out = []
     for layer in (0, 1, 0):
+        lay = []
         for i in range(layer, L_SITES - 1, 2):
             m, n, k = D[i] * D_LOC, D_LOC * D[i + 2], D[i + 1]
-            out.append((m, n, k, D[i + 1], min(k + P_OVER, m, n)))
+            lay.append((m, n, k, min(k + P_OVER, m, n)))
+        out.append(lay)
     return out
 
 
 def step_flops(info):
     """Algorithmic FP64 flops of one Trotter step, split by kernel class.
 
-    GEMMs: sketch / power / projection (2q+2) 2mnl, two-site contraction 2mnD,
-    B update 2mnk.  Orthonormalisation (2q+1 per bond, two CholeskyQR passes):
-    Gram rows l^2 (symmetric), Cholesky l^3/3, triangular inverse l^3/3,
-    Y R^-1 rows l^2 (triangular).  Jacobi (from the device counts): every sweep
-    forms all l(l-1)/2 inner products (2n each) and the row norms (2nl); each
-    applied rotation costs 6n + 6l.
+    GEMMs: sketch / power / projection (2q+2) 2mnl, two-site contraction 2mnk,
+    B update 2mnk.  Each of the 2q+1 orthonormalisations of a rows x l sample:
+    CholeskyQR2 (two passes of Gram rows l^2, Cholesky + triangular inverse
+    2 l^3 / 3, Y R^-1 rows l^2) or, for nearly square samples (3l > rows),
+    Householder QR (factor 2 rows l^2 - 2 l^3 / 3, forming Q the same).  Jacobi
+    (from the device counts): every sweep forms the row norms (2nl) and the
+    inner products of all l(l-1)/2 pairs (2n each); each applied rotation
+    costs 6n + 6l.
     """
-    import numpy as np
-    flops = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "jacobi": 0.0}
-    inf = info.reshape(-1, info.shape[-1])
-    shapes = bond_shapes()
-    for idx, (m, n, k, Dm, l) in enumerate(shapes):
-        exact = m <= l
-        flops["gemm"] += 2.0 * m * n * Dm + 2.0 * m * n * k
-        if not exact:
-            flops["gemm"] += (2 * Q_POW + 2) * 2.0 * m * n * l
-            for it in range(2 * Q_POW + 1):
-                rows = m if it % 2 == 0 else n
-                flops["gram"] += 2 * rows * l * l
-                flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
-                flops["gemm"] += 2 * rows * l * l
-        rec = inf[idx]
-        sweeps, rots = int(rec[3]), int(rec[5])
-        flops["jacobi"] += sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * (6.0 * n + 6.0 * l) + (sweeps + 1) * 2.0 * n * l
+    flops = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0}
+    for j, lay in enumerate(bond_shapes()):
+        for b, (m, n, k, l) in enumerate(lay):
+            flops["gemm"] += 2.0 * m * n * k + 2.0 * m * n * k
+            if m > l:
+                flops["gemm"] += (2 * Q_POW + 2) * 2.0 * m * n * l
+                for it in range(2 * Q_POW + 1):
+                    rows = m if it % 2 == 0 else n
+                    if 3 * l > rows:
+                        flops["householder"] += 2 * (2.0 * rows * l * l - 2.0 * l ** 3 / 3.0)
+                    else:
+                        flops["gram"] += 2 * rows * l * l
+                        flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
+                        flops["gemm"] += 2 * rows * l * l
+            rec = info[j][b]
+            sweeps, rots = int(rec[3]), int(rec[5])
+            flops["jacobi"] += (sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * (6.0 * n + 6.0 * l)
+                                + (sweeps + 1) * 2.0 * n * l)
     return flops
 
 
@@ -203,12 +209,12 @@ def run_ours(args):
     value = ws * truncations_per_step() / (ms_per_step / 1e3)
 
     # algorithmic flops from the device-reported sweep / rotation counts
-    fl = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "jacobi": 0.0}
+    fl = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0}
     for inf in infos:
         f = step_flops(inf.cpu().numpy())
         for key in fl:
             fl[key] += f[key]
-    tflops = sum(fl.values()) / (tot_ms / 1e3) / 1e12 * ws / ws
+    tflops = ws * sum(fl.values()) / (tot_ms / 1e3) / 1e12
     classes = {lib.rsvd_profile_class_name(c).decode(): (ms_c[c], cnt_c[c]) for c in range(ncls)}
     total_kernel_ms = sum(v[0] for v in classes.values())
     kernels = {}
@@ -399,7 +405,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / error / comparator / CPU legs")
+    ap.add_argument("--chain-length", type=int, default=64,
+                    help="L (default 64); a shorter chain keeps the 256 x 256 central bonds (profiling case)")
     args = ap.parse_args()
+    global L_SITES, WORKLOAD
+    if args.chain_length != L_SITES:
+        L_SITES = args.chain_length
+        WORKLOAD = WORKLOAD.replace("L64", f"L{L_SITES}")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
