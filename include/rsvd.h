@@ -52,6 +52,7 @@ extern "C" {
 #define RSVD_ERR_WORKSPACE     -4   /* workspace smaller than the size query returned */
 #define RSVD_ERR_LAUNCH        -5   /* a CUDA launch failed (message via rsvd_status_string) */
 #define RSVD_ERR_NONFINITE     -6   /* device: NaN or Inf met in the input (info.status) */
+#define RSVD_ERR_SCRATCH_LIMIT -7   /* rsvd_truncate_noalloc: the matrix needs more scratch than its fixed array */
 #define RSVD_WARN_NOCONV        1   /* device: the Jacobi SVD hit its sweep cap (info.status) */
 
 /* Paths recorded in rsvd_info.path (bit set). */
@@ -185,6 +186,37 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond,
                      double* B, size_t tensor_stride, double* lam, size_t lam_stride,
                      const double* gate, const rsvd_params* p, double* trunc_err,
                      void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
+ * rsvd_truncate_noalloc - rsvd_truncate for callers that cannot allocate or
+ * own a device workspace: code that runs where device allocation is forbidden
+ * or unavailable after start-up (a host framework that owns and pre-reserves
+ * all device memory, a real-time loop with a fixed memory budget, a plain C
+ * caller without an allocator).  The paper has no counterpart; this is a
+ * deployment variant of rsvd_truncate with identical arguments and results,
+ * minus the workspace.
+ *   Scratch: a fixed 16 MiB array inside the library's device image
+ *   (rsvd_noalloc_scratch_bytes), present on every GPU that loads the library
+ *   until the process exits.  A matrix whose rsvd_workspace_size exceeds it is
+ *   rejected with RSVD_ERR_SCRATCH_LIMIT before anything is launched (FP64:
+ *   e.g. 256 x 256 at l = 138 needs about 2.3 MiB, 1024 x 1024 at l = 144 about
+ *   10 MiB).
+ *   No cudaMalloc, cudaFree or other allocating call is made.  The first call
+ *   on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   with that device current) and caches it; make that first call before any
+ *   stream capture.
+ *   All calls share the one array and it keeps the previous call's contents
+ *   (every word a call reads it has written itself first): calls whose work
+ *   overlaps on the GPU - different streams, or host threads issuing at once -
+ *   race on it and must be serialised by the caller.
+ * Errors: as rsvd_truncate, plus RSVD_ERR_SCRATCH_LIMIT.
+ */
+int rsvd_truncate_noalloc(int m, int n, const void* A, int lda, const rsvd_params* p,
+                          double* S, void* U, int ldu, void* Vt, int ldvt,
+                          rsvd_info* info, void* cuda_stream);
+
+/* rsvd_noalloc_scratch_bytes - size of rsvd_truncate_noalloc's fixed scratch array. */
+size_t rsvd_noalloc_scratch_bytes(void);
 
 /*
  * Optional kernel timing (measurement aid, not part of the method).

@@ -16,6 +16,7 @@ RSVD_ERR_PRECISION = -3
 RSVD_ERR_WORKSPACE = -4
 RSVD_ERR_LAUNCH = -5
 RSVD_ERR_NONFINITE = -6
+RSVD_ERR_SCRATCH_LIMIT = -7
 RSVD_WARN_NOCONV = 1
 
 RSVD_PATH_EXACT = 1
@@ -36,6 +37,8 @@ EXPORTED = (
     "rsvd_profile_enable",
     "rsvd_profile_collect",
     "rsvd_profile_class_name",
+    "rsvd_truncate_noalloc",
+    "rsvd_noalloc_scratch_bytes",
 )
 
 
@@ -98,10 +101,13 @@ def load():
     lib.rsvd_status_string.restype = ctypes.c_char_p
     lib.rsvd_profile_enable.argtypes = [i]
     lib.rsvd_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ip, i]
+    lib.rsvd_truncate_noalloc.argtypes = [i, i, vp, i, par, vp, vp, i, vp, i, vp, vp]
+    lib.rsvd_noalloc_scratch_bytes.argtypes = []
+    lib.rsvd_noalloc_scratch_bytes.restype = ctypes.c_size_t
     lib.rsvd_profile_class_name.argtypes = [i]
     lib.rsvd_profile_class_name.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("rsvd_status_string", "rsvd_profile_class_name"):
+        if name not in ("rsvd_status_string", "rsvd_profile_class_name", "rsvd_noalloc_scratch_bytes"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

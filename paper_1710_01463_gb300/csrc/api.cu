@@ -275,6 +275,7 @@ const char* rsvd_status_string(int status) {
     case RSVD_ERR_LAUNCH: return cudaGetErrorString(last_cuda_error());
     case RSVD_ERR_NONFINITE: return "non-finite value in the input";
     case RSVD_WARN_NOCONV: return "Jacobi SVD reached its sweep cap";
+    case RSVD_ERR_SCRATCH_LIMIT: return "matrix needs more scratch than the fixed no-allocation array holds";
     default: return "unknown status";
   }
 }
@@ -497,3 +498,64 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- no-allocation entry point
+// Some callers cannot hand the library a workspace: code that runs where
+// device allocation is forbidden or unavailable after start-up (a host
+// framework that owns and pre-reserves all device memory, a real-time loop with
+// a fixed memory budget, a plain C caller without any allocator).  For them,
+// rsvd_truncate_noalloc runs the same computation as rsvd_truncate with its
+// scratch in a fixed array that lives in this library's device image.
+#include <mutex>
+
+namespace rsvd {
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB, held by every GPU that loads the library
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxScratchDevices = 64;
+void* g_scratch_dev_ptr[kMaxScratchDevices] = {};
+std::mutex g_scratch_mutex;
+
+// Device address of g_static_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device (with that device current) and cached.
+int static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    last_cuda_error() = e;
+    return RSVD_ERR_LAUNCH;
+  }
+  if (dev < 0 || dev >= kMaxScratchDevices) return RSVD_ERR_INVALID_SIZE;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_dev_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      last_cuda_error() = e;
+      return RSVD_ERR_LAUNCH;
+    }
+    g_scratch_dev_ptr[dev] = ptr;
+  }
+  *out = g_scratch_dev_ptr[dev];
+  return RSVD_OK;
+}
+
+}  // namespace
+}  // namespace rsvd
+
+extern "C" int rsvd_truncate_noalloc(int m, int n, const void* A, int lda, const rsvd_params* p, double* S, void* U,
+                                     int ldu, void* Vt, int ldvt, rsvd_info* info, void* cuda_stream) {
+  size_t need = 0;
+  int rc = rsvd_workspace_size(m, n, p, &need);
+  if (rc != RSVD_OK) return rc;
+  if (need > kStaticScratchBytes) return RSVD_ERR_SCRATCH_LIMIT;
+  void* scratch = nullptr;
+  rc = static_scratch(&scratch);
+  if (rc != RSVD_OK) return rc;
+  return rsvd_truncate(m, n, A, lda, p, S, U, ldu, Vt, ldvt, scratch, kStaticScratchBytes, info, cuda_stream);
+}
+
+extern "C" size_t rsvd_noalloc_scratch_bytes(void) { return kStaticScratchBytes; }
