@@ -54,6 +54,7 @@ extern "C" {
 #define RSVD_ERR_NONFINITE     -6   /* device: NaN or Inf met in the input (info.status) */
 #define RSVD_ERR_SCRATCH_LIMIT -7   /* rsvd_truncate_noalloc: the matrix needs more scratch than its fixed array */
 #define RSVD_WARN_NOCONV        1   /* device: the Jacobi SVD hit its sweep cap (info.status) */
+#define RSVD_WARN_CG            2   /* device (backward): a conjugate-gradient column did not converge (info.status) */
 
 /* Paths recorded in rsvd_info.path (bit set). */
 #define RSVD_PATH_EXACT         1   /* m <= l: Q = I, B = A (the sample covers the range) */
@@ -186,6 +187,49 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond,
                      double* B, size_t tensor_stride, double* lam, size_t lam_stride,
                      const double* gate, const rsvd_params* p, double* trunc_err,
                      void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
+ * rsvd_backward_workspace_size - workspace bytes of rsvd_truncate_backward_batched.
+ */
+int rsvd_backward_workspace_size(int batch, const int* m, const int* n, const int* k, int prec, size_t* bytes);
+
+/*
+ * rsvd_truncate_backward_batched - derivative of the rank-k truncated
+ * factorization A ~ U diag(S) V^T (the differentiable form of the compression
+ * step; the paper itself has no derivative).  Given the factors of each matrix
+ * and the cotangents (Ubar, Sbar, Vbar) of a scalar loss with respect to them,
+ * writes Abar = d loss / d A:
+ *   Abar = U [ (F o (U^T Ubar - Ubar^T U)) S + diag(Sbar) + S (F o (V^T Vbar - Vbar^T V)) ] V^T
+ *        + Z S V^T + U Z^T A + U S Y^T + A Y V^T,
+ *   F_ij = 1 / (s_j^2 - s_i^2) (i != j, the retained block),
+ *   z_i = (s_i^2 I - P A A^T P)^-1 P ubar_i,  y_i = (s_i^2 I - Q A^T A Q)^-1 Q vbar_i,
+ *   P = I - U U^T, Q = I - V V^T.
+ * The z / y terms carry the coupling to the discarded singular triplets without
+ * forming them; they are solved by conjugate gradients on the device (all k
+ * columns at once, up to max_iter iterations, a column stopping when its
+ * residual is below tol times its right-hand side).  This equals the adjoint
+ * of the full SVD with zero cotangents on the discarded triplets, and requires
+ * the retained singular values to be distinct and above every discarded one.
+ *   prec: RSVD_F64 (all double) or RSVD_F32 (A, U, Vt, cotangents and Abar float,
+ *         products in FP32).
+ *   A[b] m x n (lda), S[b] k doubles, U[b] m x k (ldu), Vt[b] k x n (ldvt): the
+ *         factors (e.g. from rsvd_truncate_batched).
+ *   Ubar, Sbar, Vtbar: HOST arrays of device pointers (m x k with ldub, k
+ *         doubles, k x n with ldvb - the cotangent of Vt); a NULL array means a
+ *         zero cotangent for every matrix.
+ *   Abar[b] [out] m x n (ldab).
+ *   info: DEVICE array of batch records; status RSVD_WARN_CG when a column did
+ *         not converge or met non-positive curvature.
+ * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_PRECISION,
+ * RSVD_ERR_WORKSPACE, RSVD_ERR_LAUNCH.
+ */
+int rsvd_truncate_backward_batched(int batch, const int* m, const int* n, const int* k, int prec,
+                                   const void* const* A, const int* lda, const double* const* S,
+                                   const void* const* U, const int* ldu, const void* const* Vt, const int* ldvt,
+                                   const void* const* Ubar, const int* ldub, const double* const* Sbar,
+                                   const void* const* Vtbar, const int* ldvb,
+                                   void* const* Abar, const int* ldab, int max_iter, double tol,
+                                   void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
 
 /*
  * rsvd_truncate_noalloc - rsvd_truncate for callers that cannot allocate or

@@ -18,6 +18,7 @@ RSVD_ERR_LAUNCH = -5
 RSVD_ERR_NONFINITE = -6
 RSVD_ERR_SCRATCH_LIMIT = -7
 RSVD_WARN_NOCONV = 1
+RSVD_WARN_CG = 2
 
 RSVD_PATH_EXACT = 1
 RSVD_PATH_HOUSEHOLDER = 2
@@ -37,6 +38,8 @@ EXPORTED = (
     "rsvd_profile_enable",
     "rsvd_profile_collect",
     "rsvd_profile_class_name",
+    "rsvd_backward_workspace_size",
+    "rsvd_truncate_backward_batched",
     "rsvd_truncate_noalloc",
     "rsvd_noalloc_scratch_bytes",
 )
@@ -101,6 +104,9 @@ def load():
     lib.rsvd_status_string.restype = ctypes.c_char_p
     lib.rsvd_profile_enable.argtypes = [i]
     lib.rsvd_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ip, i]
+    lib.rsvd_backward_workspace_size.argtypes = [i, ip, ip, ip, i, ctypes.POINTER(sz)]
+    lib.rsvd_truncate_backward_batched.argtypes = [i, ip, ip, ip, i, pp, ip, pp, pp, ip, pp, ip, pp, ip, pp, pp, ip,
+                                                   pp, ip, i, ctypes.c_double, vp, sz, vp, vp]
     lib.rsvd_truncate_noalloc.argtypes = [i, i, vp, i, par, vp, vp, i, vp, i, vp, vp]
     lib.rsvd_noalloc_scratch_bytes.argtypes = []
     lib.rsvd_noalloc_scratch_bytes.restype = ctypes.c_size_t

@@ -135,3 +135,62 @@ def rsvd_truncate_batched(As, ks, p=8, q=2, seed=0, stream=0, chi_global=0, max_
                        max_sweeps, chi_global)
     U, S, Vt = plan.run(As)
     return U, S, Vt, plan.k_out, plan.info
+
+
+def rsvd_truncate_backward_batched(As, Us, Ss, Vts, Ubars=None, Sbars=None, Vtbars=None, max_iter=300, tol=None):
+    """Abar for each matrix from its factors and the cotangents (see include/rsvd.h)."""
+    lib = _lib.load()
+    B = len(As)
+    dtype = As[0].dtype
+    prec = _DTYPE_PREC[dtype]
+    if tol is None:
+        tol = 1e-12 if dtype == torch.float64 else 1e-6
+    ms = [A.shape[0] for A in As]
+    ns = [A.shape[1] for A in As]
+    ks = [S.numel() for S in Ss]
+    m_a, n_a, k_a = _lib.int_array(ms), _lib.int_array(ns), _lib.int_array(ks)
+    sz = ctypes.c_size_t(0)
+    _lib.check(lib.rsvd_backward_workspace_size(B, m_a, n_a, k_a, prec, ctypes.byref(sz)), "rsvd_backward_workspace_size")
+    dev = As[0].device
+    work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=dev)
+    Abars = [torch.empty_like(A) for A in As]
+    info = torch.zeros((B, _lib.INFO_INTS), dtype=torch.int32, device=dev)
+    for t in list(As) + list(Us) + list(Vts):
+        _require_cuda(t)
+        if t.dtype != dtype or t.stride(1) != 1:
+            raise ValueError("factors must share the dtype of A and be row-major")
+
+    def arr(ts):
+        return None if ts is None else _lib.ptr_array([t.data_ptr() for t in ts])
+
+    def lds(ts):
+        return None if ts is None else _lib.int_array([t.stride(0) for t in ts])
+
+    rc = lib.rsvd_truncate_backward_batched(
+        B, m_a, n_a, k_a, prec, arr(As), lds(As), arr(Ss), arr(Us), lds(Us), arr(Vts), lds(Vts),
+        arr(Ubars), lds(Ubars), arr(Sbars), arr(Vtbars), lds(Vtbars), arr(Abars), lds(Abars),
+        int(max_iter), float(tol), ctypes.c_void_p(work.data_ptr()), work.numel(),
+        ctypes.c_void_p(info.data_ptr()), _stream_handle())
+    _lib.check(rc, "rsvd_truncate_backward_batched")
+    return Abars, info
+
+
+class RSVDTrunc(torch.autograd.Function):
+    """(U, S, Vt) = rank-k RSVD of A (forward: rsvd_truncate), with the
+    derivative of the truncated factorization (backward: the library's
+    rsvd_truncate_backward_batched)."""
+
+    @staticmethod
+    def forward(ctx, A, k, p=8, q=2, seed=0, stream=0):
+        U, S, Vt, info = rsvd_truncate(A.contiguous(), k, p, q, seed, stream)
+        ctx.save_for_backward(A.contiguous(), U, S, Vt)
+        return U, S, Vt
+
+    @staticmethod
+    def backward(ctx, gU, gS, gVt):
+        A, U, S, Vt = ctx.saved_tensors
+        Ub = None if gU is None else [gU.contiguous().to(A.dtype)]
+        Sb = None if gS is None else [gS.contiguous().to(torch.float64)]
+        Vb = None if gVt is None else [gVt.contiguous().to(A.dtype)]
+        Abar, _ = rsvd_truncate_backward_batched([A], [U], [S], [Vt], Ub, Sb, Vb)
+        return Abar[0], None, None, None, None, None

@@ -14,6 +14,11 @@
 
 namespace rsvd {
 
+cudaError_t& last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -91,10 +96,6 @@ inline int sample_width(int m, int n, int k, int p) { return std::min(k + p, std
     }                                            \
   } while (0)
 
-cudaError_t& last_cuda_error() {
-  static thread_local cudaError_t e = cudaSuccess;
-  return e;
-}
 
 template <typename T>
 OrthBatch<T> orth_batch(const std::vector<Prob*>& ps, bool onY) {

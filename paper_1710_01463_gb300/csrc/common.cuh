@@ -29,6 +29,8 @@ struct GemmJob {
   const double* div;   // optional: divide C by *div
   const int* gate;     // optional: run only if *gate == gate_val
   int gate_val;
+  double alpha = 1.0;  // C = alpha op(A) op(X) (+ C when accumulate)
+  int accumulate = 0;
 };
 
 template <typename Tin, typename Tout>
@@ -169,10 +171,56 @@ struct TebdFinBatch {
   TebdFinJob job[kMaxJobs];
 };
 
+// ---- backward (CG on the discarded space) ---------------------------------
+template <typename T>
+struct BwJob {
+  int rows, k;
+  T *p, *r, *w, *z, *t;     // rows x k (ld = k)
+  const T* bvec;            // right-hand sides, rows x k
+  const double* s;          // k singular values
+  double *pw, *rho, *rho_new, *rho0, *beta;  // k each
+  int* active;              // k
+  int* flags;               // bit 0: a column met a non-positive curvature
+  double tol2;
+};
+template <typename T>
+struct BwBatch {
+  int count;
+  BwJob<T> job[kMaxJobs];
+};
+template <typename T>
+struct BwCoreJob {
+  int k;
+  const T* X;               // U^T Ubar (k x k) or nullptr
+  const T* Yv;              // V^T Vbar (k x k) or nullptr
+  const double* s;
+  const double* sbar;       // or nullptr
+  T* core;                  // k x k
+};
+template <typename T>
+struct BwCoreBatch {
+  int count;
+  BwCoreJob<T> job[kMaxJobs];
+};
+template <typename T>
+struct BwScaleJob {
+  int rows, k;              // out is rows x k (ld = k)
+  const T* in;
+  int ldin;
+  const double* s;          // nullptr: plain copy
+  int transpose;            // 1: out[r, c] = in[c * ldin + r]
+  T* out;
+};
+template <typename T>
+struct BwScaleBatch {
+  int count;
+  BwScaleJob<T> job[kMaxJobs];
+};
+
 // ---- optional per-kernel timing (CUDA events around launches) -------------
 enum KernelClass {
   KC_PREP = 0, KC_OMEGA, KC_GEMM, KC_GRAM, KC_CHOL, KC_HOUSEHOLDER, KC_JACOBI, KC_SIGN, KC_SELECT, KC_TEBD,
-  KC_COUNT
+  KC_BACKWARD, KC_COUNT
 };
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s);
@@ -195,6 +243,17 @@ cudaError_t launch_sign(const SignBatch<T>& b, cudaStream_t s);
 cudaError_t launch_select(const SelectBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_theta(const TebdBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_bw_coldot(const BwBatch<T>& b, int which, cudaStream_t s);
+template <typename T>
+cudaError_t launch_bw_elementwise(const BwBatch<T>& b, int op, cudaStream_t s);
+template <typename T>
+cudaError_t launch_bw_core(const BwCoreBatch<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_bw_colscale(const BwScaleBatch<T>& b, cudaStream_t s);
+
+// last CUDA error seen by a launch of this library (per host thread)
+cudaError_t& last_cuda_error();
 
 // shared-memory budget of the Jacobi kernel for given sizes (bytes), and the
 // cluster size chosen for them

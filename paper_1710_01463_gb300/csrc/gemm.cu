@@ -157,7 +157,9 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
       const int gj = n0 + tx + 16 * j;
       if (gj < J.N) {
         Tout v = J.div ? (Tout)((double)acc[i][j] * scale) : (Tout)acc[i][j];
-        J.C[(long long)gi * J.ldc + gj] = v;
+        if (J.alpha != 1.0) v = (Tout)(J.alpha * (double)v);
+        Tout* c = J.C + (long long)gi * J.ldc + gj;
+        *c = J.accumulate ? (Tout)(*c + v) : v;
       }
     }
   }

@@ -380,6 +380,266 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
   cluster.sync();  // no CTA leaves while others may read its shared memory
 }
 
+// ---------------------------------------------------------------- blocked Householder QR
+// Same factorization as householder_kernel, blocked by panels of kNb columns
+// (compact WY form, H_j0 ... H_j1-1 = I - V T V^T): rank 0 of the cluster
+// gathers the panel's rows through distributed shared memory and factors it
+// alone (block-level barriers only), every CTA then applies I - V T^T V^T to
+// its rows of the trailing columns with one cluster exchange of V^T Y.  Q is
+// accumulated backwards panel by panel, one exchange per panel.  Three cluster
+// barriers per panel instead of three per column.
+constexpr int kNb = 16;
+
+struct PanelLayout {
+  size_t ys, vo, wp, ws, alpha, total;  // shared-memory offsets in doubles
+};
+
+// Shared memory: own rows of Y (then Q) and of V, one V^T Y buffer, T^T W and
+// the reflector scalars.  The panel (rank 0 only) and the T matrices of all
+// panels live in the matrix's global scratch (hw, hq), which stays in L2.
+__host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) {
+  const int rs = (rows + csize - 1) / csize;
+  PanelLayout L;
+  size_t o = 0;
+  L.ys = o; o += (size_t)rs * l;
+  L.vo = o; o += (size_t)rs * l;
+  L.wp = o; o += (size_t)kNb * l;
+  L.ws = o; o += (size_t)kNb * l;
+  L.alpha = o; o += (size_t)l;
+  L.total = o;
+  return L;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __grid_constant__ OrthBatch<T> b, int csize) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const OrthJob<T>& J = b.job[blockIdx.y];
+  if (*J.flag == 0) return;  // cluster-uniform
+  const int C = csize;
+  const int rank = (int)cluster.block_rank();
+  const int rows = J.rows, l = J.l;
+  const int rs = (rows + C - 1) / C;
+  const int r0 = rank * rs;
+  const int nr = max(0, min(rows, r0 + rs) - r0);
+  const PanelLayout L = panel_layout(rows, l, C);
+  extern __shared__ double sm[];
+  double* Ys = sm + L.ys;      // own rows of Y, later of Q   (rs x l)
+  double* Vo = sm + L.vo;      // own rows of V              (rs x l)
+  double* Wp = sm + L.wp;      // partial V^T Y               (kNb x l)
+  double* Ws = sm + L.ws;      // summed V^T Y, then T^T W    (kNb x l)
+  double* alpha = sm + L.alpha;
+  double* Pn = J.hw;           // rank 0: the panel, rows x kNb (global scratch, L2)
+  double* Tall = J.hq;         // T of every panel, npanel x kNb x kNb (global scratch)
+  __shared__ double red[kHhThreads / 32][2];
+  __shared__ double sc[2];
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = kHhThreads / 32;
+
+  for (int e = tid; e < nr * l; e += kHhThreads) {
+    Ys[e] = (double)J.Y[(size_t)r0 * l + e];
+    Vo[e] = 0.0;
+  }
+  __syncthreads();
+  const int npanel = (l + kNb - 1) / kNb;
+  for (int p = 0; p < npanel; ++p) {
+    const int j0 = p * kNb, nb = min(kNb, l - j0);
+    const int R = rows - j0;  // panel rows j0 .. rows-1
+    double* Tp = Tall + (size_t)p * kNb * kNb;
+    cluster.sync();  // trailing updates of the previous panel are complete everywhere
+    if (rank == 0) {
+      // gather the panel
+      for (int e = tid; e < R * nb; e += kHhThreads) {
+        const int rr = e / nb, c = e % nb;
+        const int r = j0 + rr, owner = r / rs;
+        Pn[rr * kNb + c] = cluster.map_shared_rank(Ys, owner)[(r - owner * rs) * l + j0 + c];
+      }
+      __syncthreads();
+      for (int jj = 0; jj < nb; ++jj) {
+        double a = 0.0;
+        for (int rr = jj + tid; rr < R; rr += kHhThreads) a = fma(Pn[rr * kNb + jj], Pn[rr * kNb + jj], a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) red[warp][0] = a;
+        __syncthreads();
+        if (tid == 0) {
+          double nrm2 = 0.0;
+          for (int q = 0; q < nw; ++q) nrm2 += red[q][0];
+          const double x0 = Pn[jj * kNb + jj];
+          double al = 0.0, inv = 0.0;
+          if (nrm2 > 0.0) {
+            al = x0 >= 0.0 ? -sqrt(nrm2) : sqrt(nrm2);
+            const double v0 = x0 - al;
+            const double vn2 = nrm2 - x0 * x0 + v0 * v0;
+            inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
+          }
+          alpha[j0 + jj] = al;
+          sc[0] = inv;
+          sc[1] = x0 - al;
+        }
+        __syncthreads();
+        const double inv = sc[0], v0 = sc[1];
+        for (int rr = tid; rr < R; rr += kHhThreads) {
+          double v = 0.0;
+          if (rr == jj) v = v0 * inv;
+          else if (rr > jj) v = Pn[rr * kNb + jj] * inv;
+          Pn[rr * kNb + jj] = v;  // V's column (zero above the diagonal)
+        }
+        __syncthreads();
+        for (int c = jj + 1 + warp; c < nb; c += nw) {
+          double d = 0.0;
+          for (int rr = jj + lane; rr < R; rr += 32) d = fma(Pn[rr * kNb + jj], Pn[rr * kNb + c], d);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+          const double m2d = -2.0 * d;
+          for (int rr = jj + lane; rr < R; rr += 32) Pn[rr * kNb + c] = fma(m2d, Pn[rr * kNb + jj], Pn[rr * kNb + c]);
+        }
+        __syncthreads();
+      }
+      // T (upper triangular): T_jj = 2, T[0:j, j] = -2 T[0:j, 0:j] (V[:, 0:j]^T v_j)
+      double* G = Ws;  // V^T V scratch (nb x nb)
+      for (int e = warp; e < nb * nb; e += nw) {
+        const int i = e / nb, j = e % nb;
+        double d = 0.0;
+        if (i < j)
+          for (int rr = j + lane; rr < R; rr += 32) d = fma(Pn[rr * kNb + i], Pn[rr * kNb + j], d);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) G[e] = d;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int e = 0; e < kNb * kNb; ++e) Tp[e] = 0.0;
+        for (int j = 0; j < nb; ++j) {
+          for (int i = 0; i < j; ++i) {
+            double s = 0.0;
+            for (int t = i; t < j; ++t) s = fma(Tp[i * kNb + t], G[t * nb + j], s);
+            Tp[i * kNb + j] = -2.0 * s;
+          }
+          Tp[j * kNb + j] = 2.0;
+          for (int i = j + 1; i < kNb; ++i) Tp[i * kNb + j] = 0.0;
+        }
+      }
+    }
+    cluster.sync();  // panel factored: V and T readable from rank 0
+    if (rank != 0 && tid < nb) alpha[j0 + tid] = cluster.map_shared_rank(alpha, 0)[j0 + tid];
+    {
+      const double* Pn0 = Pn;
+      for (int e = tid; e < nr * nb; e += kHhThreads) {
+        const int rr = e / nb, c = e % nb;
+        const int r = r0 + rr;
+        Vo[rr * l + j0 + c] = (r >= j0) ? Pn0[(r - j0) * kNb + c] : 0.0;
+      }
+    }
+    __syncthreads();
+    // trailing update of columns j0 + nb .. l-1: Y <- Y - V T^T (V^T Y)
+    const int c1 = j0 + nb, wcols = l - c1;
+    double* Wb = Wp;
+    if (wcols > 0) {
+      for (int e = tid; e < nb * wcols; e += kHhThreads) {
+        const int jj = e / wcols, c = c1 + e % wcols;
+        double d = 0.0;
+        for (int rr = 0; rr < nr; ++rr) d = fma(Vo[rr * l + j0 + jj], Ys[rr * l + c], d);
+        Wb[jj * l + c] = d;
+      }
+    }
+    cluster.sync();
+    if (wcols > 0) {
+      // W = sum over ranks of the partials, one (jj, c) entry per thread
+      for (int e = tid; e < nb * wcols; e += kHhThreads) {
+        const int jj = e / wcols, c = c1 + e % wcols;
+        double d = 0.0;
+        for (int r = 0; r < C; ++r) d += cluster.map_shared_rank(Wb, r)[jj * l + c];
+        Ws[jj * l + c] = d;
+      }
+      __syncthreads();
+      // M = T^T W, (T^T W)_jj = sum_{ii <= jj} T[ii][jj] W_ii; kept in registers across the barrier
+      double mreg[(kNb * 256 + kHhThreads - 1) / kHhThreads];
+      int cnt = 0;
+      for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {
+        const int jj = e / wcols, c = c1 + e % wcols;
+        double m = 0.0;
+        for (int ii = 0; ii <= jj; ++ii) m = fma(Tp[ii * kNb + jj], Ws[ii * l + c], m);
+        mreg[cnt] = m;
+      }
+      __syncthreads();
+      cnt = 0;
+      for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {
+        const int jj = e / wcols, c = c1 + e % wcols;
+        Ws[jj * l + c] = mreg[cnt];
+      }
+      __syncthreads();
+      for (int e = tid; e < nr * wcols; e += kHhThreads) {
+        const int rr = e / wcols, c = c1 + e % wcols;
+        double y = Ys[rr * l + c];
+        for (int jj = 0; jj < nb; ++jj) y = fma(-Vo[rr * l + j0 + jj], Ws[jj * l + c], y);
+        Ys[rr * l + c] = y;
+      }
+    }
+    __syncthreads();
+  }
+  // Q = (I - V_0 T_0 V_0^T) ... (I - V_last T_last V_last^T) [I; 0], accumulated backwards
+  cluster.sync();  // every remote read of Ys / Wp above is done
+  for (int e = tid; e < nr * l; e += kHhThreads) {
+    const int rr = e / l, c = e % l;
+    Ys[e] = (r0 + rr == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int p = npanel - 1; p >= 0; --p) {
+    const int j0 = p * kNb, nb = min(kNb, l - j0);
+    const double* Tp = Tall + (size_t)p * kNb * kNb;
+    const int wcols = l - j0;
+    double* Wb = Wp;
+    cluster.sync();  // the previous panel's remote reads of Wp are done
+    for (int e = tid; e < nb * wcols; e += kHhThreads) {
+      const int jj = e / wcols, c = j0 + e % wcols;
+      double d = 0.0;
+      for (int rr = 0; rr < nr; ++rr) d = fma(Vo[rr * l + j0 + jj], Ys[rr * l + c], d);
+      Wb[jj * l + c] = d;
+    }
+    cluster.sync();
+    for (int e = tid; e < nb * wcols; e += kHhThreads) {
+      const int jj = e / wcols, c = j0 + e % wcols;
+      double d = 0.0;
+      for (int r = 0; r < C; ++r) d += cluster.map_shared_rank(Wb, r)[jj * l + c];
+      Ws[jj * l + c] = d;
+    }
+    __syncthreads();
+    {
+      double mreg[(kNb * 256 + kHhThreads - 1) / kHhThreads];
+      int cnt = 0;
+      for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {  // (T W)_jj = sum_{ii >= jj} T[jj][ii] W_ii
+        const int jj = e / wcols, c = j0 + e % wcols;
+        double m = 0.0;
+        for (int ii = jj; ii < nb; ++ii) m = fma(Tp[jj * kNb + ii], Ws[ii * l + c], m);
+        mreg[cnt] = m;
+      }
+      __syncthreads();
+      cnt = 0;
+      for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {
+        const int jj = e / wcols, c = j0 + e % wcols;
+        Ws[jj * l + c] = mreg[cnt];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * wcols; e += kHhThreads) {
+      const int rr = e / wcols, c = j0 + e % wcols;
+      double q = Ys[rr * l + c];
+      for (int jj = 0; jj < nb; ++jj) q = fma(-Vo[rr * l + j0 + jj], Ws[jj * l + c], q);
+      Ys[rr * l + c] = q;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nr * l; e += kHhThreads) {
+    const int c = e % l;
+    const double sg = alpha[c] < 0.0 ? -1.0 : 1.0;
+    J.Y[(size_t)r0 * l + e] = (T)(sg * Ys[e]);
+  }
+  if (rank == 0 && tid == 0) {
+    if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
+    atomicOr(&J.info->path, RSVD_PATH_HOUSEHOLDER);
+  }
+  cluster.sync();  // no CTA leaves while others may read its shared memory
+}
+
 }  // namespace
 
 template <typename T>
@@ -454,15 +714,54 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   // fallback for flagged matrices: Householder QR of the original sample
-  // Householder for flagged matrices, grouped by cluster size / storage
-  {
+  // Householder for flagged matrices: the blocked kernel for matrices with
+  // l >= kNb whose shared-memory slices fit, the column kernel for the rest
+  OrthBatch<T> pb, cb;
+  pb.count = cb.count = 0;
+  pb.max_chunks = cb.max_chunks = b.max_chunks;
+  pb.max_tilepairs = cb.max_tilepairs = b.max_tilepairs;
+  for (int i = 0; i < b.count; ++i) {
+    const OrthJob<T>& J = b.job[i];
+    const int cs = min(8, max(1, ceil_div(J.rows, 32)));
+    const bool fits = panel_layout(J.rows, J.l, cs).total * sizeof(double) <= 110 * 1024;
+    if (J.l >= kNb && J.l <= 256 && fits) pb.job[pb.count++] = J;
+    else cb.job[cb.count++] = J;
+  }
+  if (pb.count > 0) {
     int maxrows = 1;
-    for (int i = 0; i < b.count; ++i) maxrows = max(maxrows, b.job[i].rows);
+    for (int i = 0; i < pb.count; ++i) maxrows = max(maxrows, pb.job[i].rows);
+    const int pcs = min(8, max(1, ceil_div(maxrows, 32)));
+    size_t psmem = 0;
+    for (int i = 0; i < pb.count; ++i)
+      psmem = max(psmem, panel_layout(pb.job[i].rows, pb.job[i].l, pcs).total * sizeof(double));
+    e = cudaFuncSetAttribute(householder_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pcs, pb.count, 1);
+    cfg.blockDim = dim3(kHhThreads, 1, 1);
+    cfg.dynamicSmemBytes = psmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pcs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    prof_begin(KC_HOUSEHOLDER, s);
+    e = cudaLaunchKernelEx(&cfg, householder_panel_kernel<T>, pb, pcs);
+    prof_end(KC_HOUSEHOLDER, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (cb.count > 0) {
+    const OrthBatch<T>& b2 = cb;
+    int maxrows = 1;
+    for (int i = 0; i < b2.count; ++i) maxrows = max(maxrows, b2.job[i].rows);
     int csize = min(8, max(1, ceil_div(maxrows, 32)));
     auto bytes = [&](int cs) {
       size_t mx = 0;
-      for (int i = 0; i < b.count; ++i) {
-        const int rs = ceil_div(b.job[i].rows, cs), l = b.job[i].l;
+      for (int i = 0; i < b2.count; ++i) {
+        const int rs = ceil_div(b2.job[i].rows, cs), l = b2.job[i].l;
         mx = max(mx, (hh_small_doubles(l) + 2 * (size_t)rs * l) * sizeof(double));
       }
       return mx;
@@ -471,7 +770,7 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
     const int use_global = bytes(csize) > 200 * 1024 ? 1 : 0;
     size_t hsmem = 0;
     if (use_global) {
-      for (int i = 0; i < b.count; ++i) hsmem = max(hsmem, hh_small_doubles(b.job[i].l) * sizeof(double));
+      for (int i = 0; i < b2.count; ++i) hsmem = max(hsmem, hh_small_doubles(b2.job[i].l) * sizeof(double));
     } else {
       hsmem = bytes(csize);
     }
@@ -482,7 +781,7 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
       if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(csize, b.count, 1);
+    cfg.gridDim = dim3(csize, b2.count, 1);
     cfg.blockDim = dim3(kHhThreads, 1, 1);
     cfg.dynamicSmemBytes = hsmem;
     cfg.stream = s;
@@ -494,7 +793,7 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     prof_begin(KC_HOUSEHOLDER, s);
-    e = cudaLaunchKernelEx(&cfg, householder_kernel<T>, b, csize, use_global);
+    e = cudaLaunchKernelEx(&cfg, householder_kernel<T>, b2, csize, use_global);
     prof_end(KC_HOUSEHOLDER, s);
     if (e != cudaSuccess) return e;
   }

@@ -28,7 +28,7 @@ Prof& prof() {
 }
 
 const char* kNames[KC_COUNT] = {"prep", "omega", "gemm", "gram", "cholesky", "householder",
-                                "jacobi", "sign", "select", "tebd"};
+                                "jacobi", "sign", "select", "tebd", "backward"};
 
 }  // namespace
 
