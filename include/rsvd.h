@@ -65,7 +65,9 @@ extern "C" {
  * always computed in FP64. */
 typedef enum {
   RSVD_F64 = 0,   /* A, U, V^T are double; every product in FP64 */
-  RSVD_F32 = 1    /* A, U, V^T are float; products in FP32 (FFMA) */
+  RSVD_F32 = 1,   /* A, U, V^T are float; products in FP32 (FFMA) */
+  RSVD_TF32 = 2,  /* A float; products with A on tensor cores as TF32, FP32 accumulation */
+  RSVD_BF16 = 3   /* A bfloat16; products with A on tensor cores in BF16, FP32 accumulation */
 } rsvd_prec;
 
 typedef struct {
@@ -187,6 +189,20 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond,
                      double* B, size_t tensor_stride, double* lam, size_t lam_stride,
                      const double* gate, const rsvd_params* p, double* trunc_err,
                      void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
+ * rsvd_gemm_tc - the tensor-core product of the mixed-precision path (exposed
+ * so that it can be verified on its own): C = A B^T with A (M x K, lda) and B
+ * (N x K, ldb) row-major device matrices of bfloat16 (RSVD_BF16) or float read
+ * as TF32 (RSVD_TF32), C (M x N, ldc) float.  tcgen05.mma with TMEM
+ * accumulation, TMA-fed; N <= 256.  A, B must be 16-byte aligned with
+ * lda * element size and ldb * element size multiples of 16 bytes.  err
+ * (device int, may be NULL) is set to 1 if a pipeline wait timed out.
+ * Errors: RSVD_ERR_PRECISION, RSVD_ERR_INVALID_SIZE (also for a layout TMA
+ * cannot describe), RSVD_ERR_NULL_POINTER, RSVD_ERR_LAUNCH.
+ */
+int rsvd_gemm_tc(int M, int N, int K, int prec, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
+                 int* err, void* cuda_stream);
 
 /*
  * rsvd_backward_workspace_size - workspace bytes of rsvd_truncate_backward_batched.

@@ -25,6 +25,8 @@ RSVD_PATH_HOUSEHOLDER = 2
 
 RSVD_F64 = 0
 RSVD_F32 = 1
+RSVD_TF32 = 2
+RSVD_BF16 = 3
 
 EXPORTED = (
     "rsvd_gaussian",
@@ -38,6 +40,7 @@ EXPORTED = (
     "rsvd_profile_enable",
     "rsvd_profile_collect",
     "rsvd_profile_class_name",
+    "rsvd_gemm_tc",
     "rsvd_backward_workspace_size",
     "rsvd_truncate_backward_batched",
     "rsvd_truncate_noalloc",
@@ -104,6 +107,7 @@ def load():
     lib.rsvd_status_string.restype = ctypes.c_char_p
     lib.rsvd_profile_enable.argtypes = [i]
     lib.rsvd_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ip, i]
+    lib.rsvd_gemm_tc.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp, vp]
     lib.rsvd_backward_workspace_size.argtypes = [i, ip, ip, ip, i, ctypes.POINTER(sz)]
     lib.rsvd_truncate_backward_batched.argtypes = [i, ip, ip, ip, i, pp, ip, pp, pp, ip, pp, ip, pp, ip, pp, pp, ip,
                                                    pp, ip, i, ctypes.c_double, vp, sz, vp, vp]

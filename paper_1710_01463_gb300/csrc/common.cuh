@@ -4,6 +4,7 @@
 // and every launch sequence can be captured in a CUDA graph.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -217,10 +218,28 @@ struct BwScaleBatch {
   BwScaleJob<T> job[kMaxJobs];
 };
 
+// ---- tensor-core GEMM (tcgen05, TMA) --------------------------------------
+// C[M x N] (FP32) = A[M x K] B[N x K]^T, both operands K-major (row-major).
+constexpr int kMaxTcJobs = 16;
+struct TcJob {
+  CUtensorMap ta;  // A, box 128 rows x 128 bytes
+  CUtensorMap tb;  // B, box Npad rows x 128 bytes
+  float* C;
+  int* err;        // optional: set to 1 when a wait timed out
+  int M, N, Npad, K, ldc;
+};
+struct TcBatch {
+  int count;
+  TcJob job[kMaxTcJobs];
+};
+bool make_tmap(CUtensorMap* map, const void* base, int rows, int cols, int ld, int elem_bytes, int box_rows);
+size_t tc_smem_bytes(int Npad, int stages);
+int tc_stages(int Npad);
+
 // ---- optional per-kernel timing (CUDA events around launches) -------------
 enum KernelClass {
   KC_PREP = 0, KC_OMEGA, KC_GEMM, KC_GRAM, KC_CHOL, KC_HOUSEHOLDER, KC_JACOBI, KC_SIGN, KC_SELECT, KC_TEBD,
-  KC_BACKWARD, KC_COUNT
+  KC_BACKWARD, KC_TCGEMM, KC_CONVERT, KC_COUNT
 };
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s);
@@ -243,6 +262,8 @@ cudaError_t launch_sign(const SignBatch<T>& b, cudaStream_t s);
 cudaError_t launch_select(const SelectBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_theta(const TebdBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s);
+template <typename TIn>
+cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bw_coldot(const BwBatch<T>& b, int which, cudaStream_t s);
 template <typename T>

@@ -438,13 +438,49 @@ __global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __g
     Ys[e] = (double)J.Y[(size_t)r0 * l + e];
     Vo[e] = 0.0;
   }
+  // every CTA must apply the same column signs: columns left unfactored by an
+  // early end keep alpha = 0 (sign +1) everywhere
+  for (int c = tid; c < l; c += kHhThreads) alpha[c] = 0.0;
   __syncthreads();
+  __shared__ double trail_part;  // this CTA's sum of squares of the trailing block
+  __shared__ double trail_sum;
+  __shared__ double fro0;
   const int npanel = (l + kNb - 1) / kNb;
+  int npanel_used = npanel;
   for (int p = 0; p < npanel; ++p) {
     const int j0 = p * kNb, nb = min(kNb, l - j0);
     const int R = rows - j0;  // panel rows j0 .. rows-1
     double* Tp = Tall + (size_t)p * kNb * kNb;
+    {  // sum of squares of the trailing block Y[j0:, j0:] over own rows
+      double a = 0.0;
+      for (int e = tid; e < nr * (l - j0); e += kHhThreads) {
+        const int rr = e / (l - j0), c = j0 + e % (l - j0);
+        if (r0 + rr >= j0) a = fma(Ys[rr * l + c], Ys[rr * l + c], a);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) red[warp][0] = a;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int q = 0; q < nw; ++q) t += red[q][0];
+        trail_part = t;
+      }
+    }
     cluster.sync();  // trailing updates of the previous panel are complete everywhere
+    if (tid == 0) {
+      double t = 0.0;
+      for (int r = 0; r < C; ++r) t += *cluster.map_shared_rank(&trail_part, r);
+      trail_sum = t;
+      if (p == 0) fro0 = t;
+    }
+    __syncthreads();
+    // early end: the rest of Y is rounding noise (below 2^-52 of ||Y||_F); the
+    // remaining columns of Q are completed by the reflectors applied so far
+    if (p > 0 && !(trail_sum > fro0 * 0x1.0p-104)) {
+      npanel_used = p;
+      break;  // identical decision in every CTA of the cluster
+    }
     if (rank == 0) {
       // gather the panel
       for (int e = tid; e < R * nb; e += kHhThreads) {
@@ -583,7 +619,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __g
     Ys[e] = (r0 + rr == c) ? 1.0 : 0.0;
   }
   __syncthreads();
-  for (int p = npanel - 1; p >= 0; --p) {
+  for (int p = npanel_used - 1; p >= 0; --p) {
     const int j0 = p * kNb, nb = min(kNb, l - j0);
     const double* Tp = Tall + (size_t)p * kNb * kNb;
     const int wcols = l - j0;

@@ -28,7 +28,7 @@ Prof& prof() {
 }
 
 const char* kNames[KC_COUNT] = {"prep", "omega", "gemm", "gram", "cholesky", "householder",
-                                "jacobi", "sign", "select", "tebd", "backward"};
+                                "jacobi", "sign", "select", "tebd", "backward", "tcgemm", "convert"};
 
 }  // namespace
 
