@@ -52,6 +52,7 @@ extern "C" {
 #define RSVD_ERR_WORKSPACE     -4   /* workspace smaller than the size query returned */
 #define RSVD_ERR_LAUNCH        -5   /* a CUDA launch failed (message via rsvd_status_string) */
 #define RSVD_ERR_NONFINITE     -6   /* device: NaN or Inf met in the input (info.status) */
+#define RSVD_ERR_TIMEOUT       -8   /* device: a tensor-core pipeline wait timed out (info.status) */
 #define RSVD_ERR_SCRATCH_LIMIT -7   /* rsvd_truncate_noalloc: the matrix needs more scratch than its fixed array */
 #define RSVD_WARN_NOCONV        1   /* device: the Jacobi SVD hit its sweep cap (info.status) */
 #define RSVD_WARN_CG            2   /* device (backward): a conjugate-gradient column did not converge (info.status) */
@@ -62,7 +63,9 @@ extern "C" {
 
 /* Arithmetic of the products with A (the sketch, the power iteration and the
  * projection).  The Gram matrix, the Cholesky factor and the SVD of B are
- * always computed in FP64. */
+ * always computed in FP64.  With RSVD_TF32 / RSVD_BF16 the samples are FP32,
+ * U and V^T are float, and the call needs l <= 256, m > l, a 16-byte aligned
+ * A and lda * element size a multiple of 16 bytes (else RSVD_ERR_INVALID_SIZE). */
 typedef enum {
   RSVD_F64 = 0,   /* A, U, V^T are double; every product in FP64 */
   RSVD_F32 = 1,   /* A, U, V^T are float; products in FP32 (FFMA) */
@@ -111,10 +114,11 @@ int rsvd_workspace_size(int m, int n, const rsvd_params* p, size_t* bytes);
 /*
  * rsvd_truncate - Alg. RSVD (Sec. II.B) returning the rank-k truncated SVD
  * A ~ U diag(S) V^T of one m-by-n matrix.
- *   A    [in]  device, m x n, lda >= n; double (RSVD_F64) or float (RSVD_F32)
+ *   A    [in]  device, m x n, lda >= n; double (RSVD_F64), float (RSVD_F32,
+ *              RSVD_TF32) or bfloat16 (RSVD_BF16)
  *   S    [out] device, k doubles, descending
- *   U    [out] device, m x k, ldu >= k, same type as A; orthonormal columns
- *   Vt   [out] device, k x n, ldvt >= n, same type as A; orthonormal rows,
+ *   U    [out] device, m x k, ldu >= k, double for RSVD_F64 else float; orthonormal columns
+ *   Vt   [out] device, k x n, ldvt >= n, type of U; orthonormal rows,
  *        except that rows of numerically negligible singular values
  *        (sigma_i <= 2^-52 sigma_1, below the rounding level of any FP64
  *        method) are orthogonal to the other rows but not to each other;

@@ -17,6 +17,7 @@ RSVD_ERR_WORKSPACE = -4
 RSVD_ERR_LAUNCH = -5
 RSVD_ERR_NONFINITE = -6
 RSVD_ERR_SCRATCH_LIMIT = -7
+RSVD_ERR_TIMEOUT = -8
 RSVD_WARN_NOCONV = 1
 RSVD_WARN_CG = 2
 

@@ -10,7 +10,19 @@ import torch
 
 from . import _lib
 
-_DTYPE_PREC = {torch.float64: _lib.RSVD_F64, torch.float32: _lib.RSVD_F32}
+_DTYPE_PREC = {torch.float64: _lib.RSVD_F64, torch.float32: _lib.RSVD_F32, torch.bfloat16: _lib.RSVD_BF16}
+
+
+def _prec_of(A, tf32=False):
+    if tf32:
+        if A.dtype != torch.float32:
+            raise ValueError("TF32 products need a float32 A")
+        return _lib.RSVD_TF32
+    return _DTYPE_PREC[A.dtype]
+
+
+def _out_dtype(A):
+    return torch.float64 if A.dtype == torch.float64 else torch.float32
 
 
 def _stream_handle(stream=None):
@@ -55,22 +67,26 @@ def rsvd_workspace_size(m, n, k, p=8, q=2, dtype=torch.float64):
     return sz.value
 
 
-def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None):
-    """Rank-k RSVD of one matrix: returns (U, S, Vt, info) as CUDA tensors."""
+def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf32=False):
+    """Rank-k RSVD of one matrix: returns (U, S, Vt, info) as CUDA tensors.
+
+    A float64 -> FP64 products; float32 -> FP32 (tf32=True: TF32 tensor cores);
+    bfloat16 -> BF16 tensor cores.  U and Vt are float64 for float64 A, else float32.
+    """
     lib = _lib.load()
     _require_cuda(A)
     if A.dim() != 2 or A.stride(1) != 1:
         raise ValueError("A must be a row-major 2-D tensor")
-    prec = _DTYPE_PREC[A.dtype]
+    prec = _prec_of(A, tf32)
     m, n = A.shape
     par = _params(k, p, q, prec, seed, stream, max_sweeps)
     sz = ctypes.c_size_t(0)
     _lib.check(lib.rsvd_workspace_size(m, n, ctypes.byref(par), ctypes.byref(sz)), "rsvd_workspace_size")
     if work is None or work.numel() < sz.value:
         work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=A.device)
-    U = torch.empty((m, k), dtype=A.dtype, device=A.device)
+    U = torch.empty((m, k), dtype=_out_dtype(A), device=A.device)
     S = torch.empty((k,), dtype=torch.float64, device=A.device)
-    Vt = torch.empty((k, n), dtype=A.dtype, device=A.device)
+    Vt = torch.empty((k, n), dtype=_out_dtype(A), device=A.device)
     info = torch.zeros((1, _lib.INFO_INTS), dtype=torch.int32, device=A.device)
     rc = lib.rsvd_truncate(m, n, ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.byref(par),
                            ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(U.data_ptr()), U.stride(0),
@@ -84,13 +100,15 @@ class BatchedPlan:
     """Preallocated outputs and workspace of rsvd_truncate_batched for fixed shapes."""
 
     def __init__(self, shapes, ks, p=8, q=2, seed=0, stream=0, dtype=torch.float64, device="cuda",
-                 max_sweeps=0, chi_global=0):
+                 max_sweeps=0, chi_global=0, tf32=False):
         lib = _lib.load()
         self.shapes = [(int(m), int(n)) for m, n in shapes]
         self.ks = [int(k) for k in ks]
         self.dtype = dtype
         self.chi_global = int(chi_global)
-        self.par = _params(self.ks[0], p, q, _DTYPE_PREC[dtype], seed, stream, max_sweeps)
+        prec = _lib.RSVD_TF32 if tf32 else _DTYPE_PREC[dtype]
+        out = torch.float64 if dtype == torch.float64 else torch.float32
+        self.par = _params(self.ks[0], p, q, prec, seed, stream, max_sweeps)
         B = len(self.shapes)
         self.m_arr = _lib.int_array([s[0] for s in self.shapes])
         self.n_arr = _lib.int_array([s[1] for s in self.shapes])
@@ -99,9 +117,9 @@ class BatchedPlan:
         _lib.check(lib.rsvd_batched_workspace_size(B, self.m_arr, self.n_arr, self.k_arr, ctypes.byref(self.par),
                                                    ctypes.byref(sz)), "rsvd_batched_workspace_size")
         self.work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=device)
-        self.U = [torch.empty((m, k), dtype=dtype, device=device) for (m, _), k in zip(self.shapes, self.ks)]
+        self.U = [torch.empty((m, k), dtype=out, device=device) for (m, _), k in zip(self.shapes, self.ks)]
         self.S = [torch.empty((k,), dtype=torch.float64, device=device) for k in self.ks]
-        self.Vt = [torch.empty((k, n), dtype=dtype, device=device) for (_, n), k in zip(self.shapes, self.ks)]
+        self.Vt = [torch.empty((k, n), dtype=out, device=device) for (_, n), k in zip(self.shapes, self.ks)]
         self.info = torch.zeros((B, _lib.INFO_INTS), dtype=torch.int32, device=device)
         self.k_out = torch.zeros((B,), dtype=torch.int32, device=device)
         self.S_ptr = _lib.ptr_array([t.data_ptr() for t in self.S])
@@ -129,10 +147,10 @@ class BatchedPlan:
         return self.U, self.S, self.Vt
 
 
-def rsvd_truncate_batched(As, ks, p=8, q=2, seed=0, stream=0, chi_global=0, max_sweeps=0):
+def rsvd_truncate_batched(As, ks, p=8, q=2, seed=0, stream=0, chi_global=0, max_sweeps=0, tf32=False):
     """Alg. RSVD on a list of matrices; returns (U list, S list, Vt list, k_out, info)."""
     plan = BatchedPlan([tuple(A.shape) for A in As], ks, p, q, seed, stream, As[0].dtype, As[0].device,
-                       max_sweeps, chi_global)
+                       max_sweeps, chi_global, tf32)
     U, S, Vt = plan.run(As)
     return U, S, Vt, plan.k_out, plan.info
 

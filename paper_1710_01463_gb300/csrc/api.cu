@@ -10,6 +10,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace rsvd {
@@ -45,10 +47,17 @@ struct Prob {
   double *G, *part, *hw, *hq, *Bm, *Bg, *Pg, *sig;
   int* flag;
   int csize, use_global;
+  // tensor-core path: A^T, Omega^T / Z^T, Q^T in the operand precision
+  void *At, *WT, *QT;
+  int ldAt, ldWT, ldQT;
 };
 
+inline int pad8(int x) { return (x + 7) / 8 * 8; }
+
 // Workspace of one matrix (bytes), with the buffer offsets when `p` is given.
-size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base) {
+// tc_bytes > 0 (the operand size of the tensor-core precisions) adds A^T
+// (n x m), Omega^T / Z^T (l x n) and Q^T (l x m) with 8-element-aligned rows.
+size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int tc_bytes = 0) {
   const int mx = std::max(m, n);
   const int nchunk = ceil_div(mx, kGramChunk);
   const int cs = jacobi_cluster_size(l, n);
@@ -74,7 +83,13 @@ size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base) {
   void* Pg = take(glob ? (size_t)l * (l + 16) * 8 : 0);
   void* sig = take((size_t)l * 8);
   void* flag = take(sizeof(int) * 4);
+  const size_t lop = 2 * (size_t)((l + 15) / 16 * 16);  // rows of a split (hi + lo) operand
+  void* At = take(tc_bytes ? (size_t)n * pad8(m) * tc_bytes : 0);
+  void* WT = take(tc_bytes ? lop * pad8(n) * tc_bytes : 0);
+  void* QT = take(tc_bytes ? lop * pad8(m) * tc_bytes : 0);
   if (p) {
+    p->At = At; p->WT = WT; p->QT = QT;
+    p->ldAt = pad8(m); p->ldWT = pad8(n); p->ldQT = pad8(m);
     p->Y0 = Y0; p->Y1 = Y1; p->Z0 = Z0; p->Z1 = Z1; p->Rinv = Rinv; p->Ps = Ps;
     p->G = (double*)G; p->part = (double*)part; p->hw = (double*)hw; p->hq = (double*)hq;
     p->Bm = (double*)Bm; p->Bg = (double*)Bg; p->Pg = (double*)Pg; p->sig = (double*)sig;
@@ -233,27 +248,189 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
   return RSVD_OK;
 }
 
+// Alg. RSVD with the products of A on tensor cores (operands TIn = bf16 or
+// float read as TF32, FP32 accumulation); orthonormalisation, SVD of B and the
+// lift as in the FP32 path.
+template <typename TIn>
+int run_chunk_tc(std::vector<Prob>& probs, int q, cudaStream_t s) {
+  const int cnt = (int)probs.size();
+  const int eb = (int)sizeof(TIn);
+  {
+    PrepBatch<float> b;
+    b.count = cnt;
+    for (int i = 0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      b.job[i] = PrepJob<float>{p.m, p.n, p.l, 0, nullptr, p.lda, (float*)p.Y0, p.Bm, p.flag, p.info};
+    }
+    RSVD_TRY(launch_prep<float>(b, s));
+  }
+  {  // A^T, once per call
+    XposeBatch x;
+    x.count = cnt;
+    for (int i = 0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      x.job[i] = XposeJob{p.m, p.n, p.lda, p.ldAt, p.A, p.At};
+    }
+    RSVD_TRY((launch_transpose<TIn, TIn>(x, s)));
+  }
+  // The thin operands (Omega, Z, Q) go to the tensor cores split into a high
+  // and a low part in the operand precision, stacked as 2 lp rows (lp = l
+  // rounded up to 16); the GEMM adds the two halves of its accumulator, so the
+  // product carries the thin operand to about FP32 accuracy while A is read
+  // once.  Samples wider than 128 columns use the plain (unsplit) operand.
+  std::vector<int> lp(cnt), splitv(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    lp[i] = (probs[i].l + 15) / 16 * 16;
+    splitv[i] = 2 * lp[i] <= 256 ? 1 : 0;
+  }
+  {  // Omega (n x l, FP32) into Z0
+    OmegaBatch<float> b;
+    b.count = cnt;
+    for (int i = 0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      b.job[i] = OmegaJob<float>{p.n, p.l, p.l, (float*)p.Z0, p.seed, p.stream, 0};
+    }
+    RSVD_TRY(launch_omega<float>(b, s));
+  }
+  std::vector<Prob*> all;
+  for (auto& p : probs) all.push_back(&p);
+  // C (rows x l, FP32) = Aop (rows x K) * Bop (l x K)^T
+  auto tc = [&](bool transposedA, bool fromQ, bool toZ) -> int {
+    TcBatch b;
+    b.count = 0;
+    for (int i = 0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      TcJob& J = b.job[b.count++];
+      const int rows = transposedA ? p.n : p.m;
+      const int K = transposedA ? p.m : p.n;
+      const void* Aop = transposedA ? p.At : p.A;
+      const int ldA = transposedA ? p.ldAt : p.lda;
+      const void* Bop = fromQ ? p.QT : p.WT;
+      const int ldB = fromQ ? p.ldQT : p.ldWT;
+      J.fold = splitv[i] ? lp[i] : 0;
+      J.Npad = splitv[i] ? 2 * lp[i] : lp[i];
+      if (!make_tmap(&J.ta, Aop, rows, K, ldA, eb, 128) || !make_tmap(&J.tb, Bop, J.Npad, K, ldB, eb, J.Npad))
+        return RSVD_ERR_INVALID_SIZE;
+      J.C = (float*)(toZ ? p.Z0 : p.Y0);
+      J.err = p.flag + 1;
+      J.M = rows;
+      J.N = p.l;
+      J.K = K;
+      J.ldc = p.l;
+    }
+    RSVD_TRY(launch_tc_gemm<TIn>(b, s));
+    return RSVD_OK;
+  };
+  // thin operand: Q^T from Y0 (m x l) or Omega^T / Z^T from Z0 (n x l)
+  auto xpose_to_op = [&](bool fromZ) -> int {
+    XposeBatch xs, xp;
+    xs.count = xp.count = 0;
+    for (int i = 0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      XposeJob j = fromZ ? XposeJob{p.n, p.l, p.l, p.ldWT, p.Z0, p.WT} : XposeJob{p.m, p.l, p.l, p.ldQT, p.Y0, p.QT};
+      j.fold = lp[i];
+      if (splitv[i]) xs.job[xs.count++] = j;
+      else xp.job[xp.count++] = j;
+    }
+    RSVD_TRY(launch_split_transpose<TIn>(xs, 0, s));
+    RSVD_TRY((launch_transpose<float, TIn>(xp, s)));
+    return RSVD_OK;
+  };
+  int rc;
+  if ((rc = xpose_to_op(true))) return rc;  // Omega^T
+  if ((rc = tc(false, false, false))) return rc;  // Y = A Omega
+  RSVD_TRY(launch_orth<float>(orth_batch<float>(all, true), s));
+  for (int it = 0; it < q; ++it) {
+    if ((rc = xpose_to_op(false))) return rc;
+    if ((rc = tc(true, true, true))) return rc;   // Z = A^T Q
+    RSVD_TRY(launch_orth<float>(orth_batch<float>(all, false), s));
+    if ((rc = xpose_to_op(true))) return rc;
+    if ((rc = tc(false, false, false))) return rc;  // Y = A Z
+    RSVD_TRY(launch_orth<float>(orth_batch<float>(all, true), s));
+  }
+  if ((rc = xpose_to_op(false))) return rc;
+  if ((rc = tc(true, true, true))) return rc;  // B^T = A^T Q (n x l)
+  {
+    XposeBatch x;
+    x.count = cnt;
+    for (int i = 0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      x.job[i] = XposeJob{p.n, p.l, p.l, p.n, p.Z0, p.Bm};
+    }
+    RSVD_TRY((launch_transpose<float, double>(x, s)));
+  }
+  {
+    std::vector<int> done(cnt, 0);
+    for (int i0 = 0; i0 < cnt; ++i0) {
+      if (done[i0]) continue;
+      JacobiBatch<float> b;
+      b.count = 0;
+      b.csize = probs[i0].csize;
+      b.use_global = probs[i0].use_global;
+      for (int i = i0; i < cnt; ++i) {
+        Prob& p = probs[i];
+        if (done[i] || p.csize != b.csize || p.use_global != b.use_global) continue;
+        done[i] = 1;
+        JacobiJob<float>& J = b.job[b.count++];
+        J.l = p.l; J.n = p.n; J.k = p.k;
+        J.Bm = p.Bm; J.Bg = p.Bg; J.Pg = p.Pg;
+        J.S = p.S; J.sig = p.sig;
+        J.Vt = (float*)p.Vt; J.ldvt = p.ldvt;
+        J.Ps = (float*)p.Ps;
+        J.info = p.info;
+        J.max_sweeps = p.max_sweeps;
+        J.want_vt = 1;
+        J.pipe_err = p.flag + 1;
+      }
+      RSVD_TRY(launch_jacobi<float>(b, s));
+    }
+  }
+  {
+    GemmBatch<float, float> g;
+    g.count = 0;
+    SignBatch<float> sb;
+    sb.count = 0;
+    for (auto& p : probs) {
+      g.job[g.count++] = GemmJob<float, float>{p.m, p.k, p.l, p.l, p.l, p.ldu, (const float*)p.Y0, (const float*)p.Ps,
+                                               (float*)p.U, nullptr, nullptr, 0};
+      sb.job[sb.count++] = SignJob<float>{p.m, p.n, p.k, (float*)p.U, p.ldu, (float*)p.Vt, p.ldvt};
+    }
+    RSVD_TRY((launch_gemm<float, float, false, true>(g, s)));
+    RSVD_TRY(launch_sign<float>(sb, s));
+  }
+  return RSVD_OK;
+}
+
 int check_params(const rsvd_params* p) {
   if (!p) return RSVD_ERR_NULL_POINTER;
   if (p->p < 0 || p->q < 0 || p->q > 64 || p->max_sweeps < 0 || p->flags != 0) return RSVD_ERR_INVALID_SIZE;
-  if (p->prec != RSVD_F64 && p->prec != RSVD_F32) return RSVD_ERR_PRECISION;
+  if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_TF32 && p->prec != RSVD_BF16)
+    return RSVD_ERR_PRECISION;
   return RSVD_OK;
 }
 
 size_t tsize_of(int prec) { return prec == RSVD_F64 ? 8 : 4; }
+bool is_tc(int prec) { return prec == RSVD_TF32 || prec == RSVD_BF16; }
+int tc_bytes_of(int prec) { return prec == RSVD_BF16 ? 2 : prec == RSVD_TF32 ? 4 : 0; }
 
 int run_batched(std::vector<Prob>& probs, const rsvd_params* p, char* work, size_t work_bytes, cudaStream_t s) {
   const size_t ts = tsize_of(p->prec);
+  const int tcb = tc_bytes_of(p->prec);
   size_t need = 0;
-  for (auto& pr : probs) need += layout(nullptr, pr.m, pr.n, pr.k, pr.l, ts, nullptr);
+  for (auto& pr : probs) need += layout(nullptr, pr.m, pr.n, pr.k, pr.l, ts, nullptr, tcb);
   if (need > work_bytes) return RSVD_ERR_WORKSPACE;
   size_t off = 0;
   for (auto& pr : probs) {
-    off += layout(&pr, pr.m, pr.n, pr.k, pr.l, ts, work + off);
+    off += layout(&pr, pr.m, pr.n, pr.k, pr.l, ts, work + off, tcb);
   }
-  for (size_t c0 = 0; c0 < probs.size(); c0 += kMaxJobs) {
-    std::vector<Prob> chunk(probs.begin() + c0, probs.begin() + std::min(probs.size(), c0 + kMaxJobs));
-    int rc = p->prec == RSVD_F64 ? run_chunk<double>(chunk, p->q, s) : run_chunk<float>(chunk, p->q, s);
+  const size_t step = is_tc(p->prec) ? (size_t)kMaxTcJobs : (size_t)kMaxJobs;
+  for (size_t c0 = 0; c0 < probs.size(); c0 += step) {
+    std::vector<Prob> chunk(probs.begin() + c0, probs.begin() + std::min(probs.size(), c0 + step));
+    int rc;
+    if (p->prec == RSVD_F64) rc = run_chunk<double>(chunk, p->q, s);
+    else if (p->prec == RSVD_F32) rc = run_chunk<float>(chunk, p->q, s);
+    else if (p->prec == RSVD_BF16) rc = run_chunk_tc<__nv_bfloat16>(chunk, p->q, s);
+    else rc = run_chunk_tc<float>(chunk, p->q, s);
     if (rc != RSVD_OK) return rc;
   }
   return RSVD_OK;
@@ -276,6 +453,7 @@ const char* rsvd_status_string(int status) {
     case RSVD_ERR_LAUNCH: return cudaGetErrorString(last_cuda_error());
     case RSVD_ERR_NONFINITE: return "non-finite value in the input";
     case RSVD_WARN_NOCONV: return "Jacobi SVD reached its sweep cap";
+    case RSVD_ERR_TIMEOUT: return "a device pipeline wait timed out (results invalid)";
     case RSVD_ERR_SCRATCH_LIMIT: return "matrix needs more scratch than the fixed no-allocation array holds";
     default: return "unknown status";
   }
@@ -299,7 +477,8 @@ int rsvd_batched_workspace_size(int batch, const int* m, const int* n, const int
     if (m[b] < 1 || n[b] < 1 || k[b] < 1 || k[b] > std::min(m[b], n[b])) return RSVD_ERR_INVALID_SIZE;
     const int l = sample_width(m[b], n[b], k[b], p->p);
     if (l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
-    tot += layout(nullptr, m[b], n[b], k[b], l, tsize_of(p->prec), nullptr);
+    if (is_tc(p->prec) && (l > 256 || m[b] <= l)) return RSVD_ERR_INVALID_SIZE;
+    tot += layout(nullptr, m[b], n[b], k[b], l, tsize_of(p->prec), nullptr, tc_bytes_of(p->prec));
   }
   *bytes = tot;
   return RSVD_OK;
@@ -332,6 +511,12 @@ int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* con
     pr.m = m[b]; pr.n = n[b]; pr.k = k[b];
     pr.l = sample_width(m[b], n[b], k[b], p->p);
     if (pr.l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+    if (is_tc(p->prec)) {
+      // tensor-core operands: l <= 256, a sample narrower than A, TMA-describable rows
+      const size_t eb = (size_t)tc_bytes_of(p->prec);
+      if (pr.l > 256 || m[b] <= pr.l) return RSVD_ERR_INVALID_SIZE;
+      if (((uintptr_t)A[b]) % 16 || ((size_t)lda[b] * eb) % 16) return RSVD_ERR_INVALID_SIZE;
+    }
     pr.exact = pr.m <= pr.l ? 1 : 0;
     pr.want_u = 1;
     pr.A = A[b]; pr.lda = lda[b];

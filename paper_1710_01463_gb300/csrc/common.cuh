@@ -47,6 +47,7 @@ struct OmegaJob {
   int n, l, ld;
   T* out;
   unsigned long long seed, stream;
+  int transposed = 0;  // 1: write Omega^T (l x n, ld) instead of Omega (n x l, ld)
 };
 template <typename T>
 struct OmegaBatch {
@@ -92,6 +93,7 @@ struct JacobiJob {
   rsvd_info* info;
   int max_sweeps;
   int want_vt;
+  const int* pipe_err = nullptr;  // optional: nonzero when an earlier tensor-core pipeline wait timed out
 };
 template <typename T>
 struct JacobiBatch {
@@ -218,6 +220,24 @@ struct BwScaleBatch {
   BwScaleJob<T> job[kMaxJobs];
 };
 
+// ---- transposes with precision change ------------------------------------
+struct XposeJob {
+  int rows, cols;      // of the input
+  int ldin, ldout;
+  const void* in;
+  void* out;           // cols x rows
+  int fold = 0;        // split transposes: row offset of the low parts
+};
+struct XposeBatch {
+  int count;
+  XposeJob job[kMaxJobs];
+};
+template <typename Tin, typename Tout>
+cudaError_t launch_transpose(const XposeBatch& b, cudaStream_t s);
+// out (2 * fold rows): rows c = hi(in[:, c]), rows fold + c = in[:, c] - hi(in[:, c])
+template <typename Tout>
+cudaError_t launch_split_transpose(const XposeBatch& b, int fold_rows_of_job0_unused, cudaStream_t s);
+
 // ---- tensor-core GEMM (tcgen05, TMA) --------------------------------------
 // C[M x N] (FP32) = A[M x K] B[N x K]^T, both operands K-major (row-major).
 constexpr int kMaxTcJobs = 16;
@@ -227,6 +247,7 @@ struct TcJob {
   float* C;
   int* err;        // optional: set to 1 when a wait timed out
   int M, N, Npad, K, ldc;
+  int fold;        // > 0: B holds [B_hi; B_lo] with B_lo starting at row `fold`; C = acc[:, c] + acc[:, fold + c]
 };
 struct TcBatch {
   int count;

@@ -258,7 +258,9 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const __grid_con
     if (tid == 0) {
       J.info->jacobi_sweeps = sweeps;
       J.info->rotations = (int)min(total_rot, (long long)0x7fffffff);
-      if (nonfinite)
+      if (J.pipe_err && *J.pipe_err)
+        J.info->status = RSVD_ERR_TIMEOUT;
+      else if (nonfinite)
         J.info->status = RSVD_ERR_NONFINITE;
       else if (!converged && J.info->status == RSVD_OK)
         J.info->status = RSVD_WARN_NOCONV;

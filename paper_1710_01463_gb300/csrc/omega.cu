@@ -6,6 +6,8 @@
 // (words 0,1 -> cos, sin; words 2,3 -> cos, sin).  One thread per Philox
 // block; stores are scattered by row (Omega is row-major n x l) but Omega is
 // tiny next to A (n*l elements against m*n).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace rsvd {
@@ -64,7 +66,10 @@ __device__ __forceinline__ void omega_block(const OmegaJob<T>& J, long long blk,
     if (e < total) {
       const long long c = e / J.n;
       const long long r = e - c * J.n;
-      J.out[r * J.ld + c] = (T)z[s];
+      if (J.transposed)
+        J.out[c * J.ld + r] = (T)z[s];
+      else
+        J.out[r * J.ld + c] = (T)z[s];
     }
   }
 }
@@ -102,11 +107,12 @@ cudaError_t launch_omega_f64_single(int n, int l, int ld, double* out, unsigned 
                                     unsigned long long stream, cudaStream_t s) {
   OmegaBatch<double> b;
   b.count = 1;
-  b.job[0] = OmegaJob<double>{n, l, ld, out, seed, stream};
+  b.job[0] = OmegaJob<double>{n, l, ld, out, seed, stream, 0};
   return launch_omega<double>(b, s);
 }
 
 template cudaError_t launch_omega<double>(const OmegaBatch<double>&, cudaStream_t);
 template cudaError_t launch_omega<float>(const OmegaBatch<float>&, cudaStream_t);
+template cudaError_t launch_omega<__nv_bfloat16>(const OmegaBatch<__nv_bfloat16>&, cudaStream_t);
 
 }  // namespace rsvd

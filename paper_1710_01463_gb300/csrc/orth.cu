@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepB
     J.info->jacobi_sweeps = 0;
     J.info->l = J.l;
     J.info->rotations = 0;
-    *J.flag = 0;
+    J.flag[0] = 0;
+    J.flag[1] = 0;
   }
   if (!J.exact) return;
   // Q = I (m x l, l = m) and B = A (l x n, FP64)

@@ -216,9 +216,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
     if (!ok) atomicExch(&err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int row = m0 + q * 32 + lane;
-    for (int c0 = 0; c0 < N; c0 += 16) {
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+    const int cend = J.fold > 0 ? J.fold : N;
+    for (int c0 = 0; c0 < cend; c0 += 16) {
       float v[16];
-      ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+      ld16(tl + (uint32_t)c0, v);
+      if (J.fold > 0) {  // hi and lo parts of the B operand: add the two halves
+        float w[16];
+        ld16(tl + (uint32_t)(J.fold + c0), w);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += w[i];
+      }
       if (ok && row < J.M) {
         float* dst = J.C + (size_t)row * J.ldc + c0;
 #pragma unroll
@@ -315,6 +323,7 @@ extern "C" int rsvd_gemm_tc(int M, int N, int K, int prec, const void* A, int ld
     return RSVD_ERR_INVALID_SIZE;
   J.C = C;
   J.err = err;
+  J.fold = 0;
   J.M = M;
   J.N = N;
   J.K = K;
