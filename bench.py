@@ -29,6 +29,7 @@ L_SITES, CHI, D_LOC, H_FIELD, DT, P_OVER, Q_POW, SEED = 64, 128, 2, 1.0, 0.01, 1
 PREP_STEPS, PREP_DT = 20, 0.1
 WORKLOAD = "tebd_tfim_L64_chi128_d2_dt0.01_p10_q2_fp64"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 
 
 def base_config():
@@ -360,6 +361,325 @@ def cpu_leg(ch):
                       f"BLAS threads = all host cores, Philox in pure Python"}
 
 
+# ------------------------------------------------------------------ other workloads
+# `--workload dense|mixed|sectors|grad`: the other configurations of the path,
+# each as its own JSON line (same contract; the default run is the TEBD one).
+HBM_PEAK_GBS = None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def profile_classes(lib):
+    import ctypes
+    nclass = 16
+    ms_c = (ctypes.c_double * nclass)()
+    cnt_c = (ctypes.c_int * nclass)()
+    ncls = lib.rsvd_profile_collect(ms_c, cnt_c, nclass)
+    lib.rsvd_profile_enable(0)
+    return {lib.rsvd_profile_class_name(c).decode(): (ms_c[c], cnt_c[c]) for c in range(ncls)}
+
+
+def rsvd_flops(m, n, k, l, q, sweeps, rots, prec):
+    """Algorithmic flops of one RSVD by kernel class (see step_flops), plus the
+    tensor-core bytes of the BF16 / TF32 forms."""
+    f = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "tcgemm": 0.0}
+    exact = m <= l
+    prod = (2 * q + 2) * 2.0 * m * n * l
+    if not exact:
+        f["tcgemm" if prec in ("bf16", "tf32") else "gemm"] += prod
+        for it in range(2 * q + 1):
+            rows = m if it % 2 == 0 else n
+            if 3 * l > rows:
+                f["householder"] += 2 * (2.0 * rows * l * l - 2.0 * l ** 3 / 3.0)
+            else:
+                f["gram"] += 2 * rows * l * l
+                f["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
+                f["gemm"] += 2 * rows * l * l
+    f["gemm"] += 2.0 * m * l * k  # lift
+    f["jacobi"] += sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * (6.0 * n + 6.0 * l) + (sweeps + 1) * 2.0 * n * l
+    return f
+
+
+def tc_bytes(m, n, l, q, eb):
+    """HBM bytes of the tensor-core products of one RSVD: every product reads A
+    (or A^T) once, the split thin operand (2 lp rows) and writes the FP32 sample."""
+    lp = (l + 15) // 16 * 16
+    npad = 2 * lp if 2 * lp <= 256 else lp
+    tot = 0.0
+    for it in range(2 * q + 2):
+        rows, K = (m, n) if it % 2 == 0 else (n, m)
+        tot += rows * K * eb + npad * K * eb + rows * l * 4
+    return tot
+
+
+def run_workload(args):
+    import numpy as np
+    import torch
+    from paper_1710_01463_gb300 import _lib, api, inputs
+    from oracle import rsvd as orsvd
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = _lib.load()
+    peaks = measured_peaks()
+    dev = torch.device("cuda", local)
+    wl = args.workload
+    q = 2
+    g = torch.Generator(device="cpu").manual_seed(1234 + rank)
+
+    def ortho(nn, seed):
+        G = torch.from_numpy(np.random.default_rng(seed).standard_normal((nn, nn))).to(dev)
+        Q, R = torch.linalg.qr(G)
+        return Q * torch.sign(torch.diagonal(R))[None, :]
+
+    if wl == "dense":
+        m = n = 256
+        k, p, B = 32, 8, 1024
+        s = torch.from_numpy(inputs.exp_spectrum(256)).to(dev)
+        U0, V0 = ortho(256, 202), ortho(256, 203)
+        As = []
+        for j in range(B):
+            rp, cp = torch.randperm(256, generator=g).to(dev), torch.randperm(256, generator=g).to(dev)
+            As.append(((U0[rp] * s[None, :]) @ V0[cp].T).contiguous())
+        dtype = torch.float64
+        ks = [k] * B
+        prec = "f64"
+        config = {"workload": "dense_fp64_256x256_k32_p8_q2_batch1024", "m": 256, "n": 256, "k": k, "p": p, "q": q,
+                  "batch": B, "spectrum": "s_i = exp(-i/16)", "l2": "inputs (512 MB) larger than L2"}
+    elif wl == "mixed":
+        m = n = 4096
+        k, p, B = 64, 16, 16
+        s = torch.from_numpy(inputs.power_spectrum(n, 1.5)).to(dev)
+        U0, V0 = ortho(n, 206), ortho(n, 207)
+        As = []
+        for j in range(B):
+            rp, cp = torch.randperm(n, generator=g).to(dev), torch.randperm(n, generator=g).to(dev)
+            As.append(((U0[rp] * s[None, :]) @ V0[cp].T).to(torch.bfloat16 if args.precision == "bf16" else torch.float32).contiguous())
+        del U0, V0
+        dtype = As[0].dtype
+        ks = [k] * B
+        prec = args.precision
+        config = {"workload": f"ttn_{prec}_4096x4096_k64_p16_q2_batch16", "m": m, "n": n, "k": k, "p": p, "q": q,
+                  "batch": B, "spectrum": "s_i = i^-1.5", "l2": "inputs (16 x 4096^2) larger than L2"}
+    elif wl == "sectors":
+        shapes, f = inputs.sector_shapes(N=32, lo=64, hi=2048, seed=104)
+        k, p, B = 512, 16, 32
+        As = []
+        for b, ((mb, nb), fb) in enumerate(zip(shapes, f)):
+            r = min(mb, nb)
+            s = torch.from_numpy(inputs.power_spectrum(r, 1.2, fb)).to(dev)
+            Ub = ortho(mb, 3000 + 2 * b)[:, :r]
+            Vb = ortho(nb, 3001 + 2 * b)[:, :r]
+            As.append(((Ub * s[None, :]) @ Vb.T).float().contiguous())
+        dtype = torch.float32
+        ks = [min(k, *A.shape) for A in As]
+        prec = "f32"
+        config = {"workload": "sectors32_64to2048_chi512_fp32_p16_q2", "blocks": 32, "chi_global": 512, "p": p,
+                  "q": q, "policy": "maximal k_b = min(chi, m_b, n_b)", "spectrum": "s_i = f_b i^-1.2",
+                  "elements": int(sum(A.numel() for A in As)), "l2": "flushed (512 MB write) before every timed step"}
+    elif wl == "grad":
+        m = n = 1024
+        k, p, B = 128, 16, 64
+        s = torch.from_numpy(inputs.harmonic_spectrum(n)).to(dev)
+        U0, V0 = ortho(n, 208), ortho(n, 209)
+        As = []
+        for j in range(B):
+            rp, cp = torch.randperm(n, generator=g).to(dev), torch.randperm(n, generator=g).to(dev)
+            As.append(((U0[rp] * s[None, :]) @ V0[cp].T).float().contiguous())
+        rng = np.random.default_rng(105)
+        w = torch.from_numpy(rng.uniform(0, 1, size=k)).to(dev)
+        W = torch.from_numpy(rng.standard_normal((n, 8))).float().to(dev)
+        dtype = torch.float32
+        ks = [k] * B
+        prec = "f32"
+        config = {"workload": "grad_fp32_1024x1024_k128_p16_q2_batch64", "m": m, "n": n, "k": k, "p": p, "q": q,
+                  "batch": B, "spectrum": "s_i = 1/(1+0.05 i)", "loss": "sum w_i s_i + ||W^T U_k||_F^2, W 1024x8",
+                  "l2": "inputs (256 MB) larger than L2"}
+    else:
+        raise ValueError(wl)
+
+    plan = api.BatchedPlan([tuple(A.shape) for A in As], ks, p, q, 103 + 1000 * rank, 0, dtype, dev,
+                           chi_global=(512 if wl == "sectors" else 0), tf32=(prec == "tf32"))
+
+    def step():
+        plan.run(As)
+        if wl == "grad":
+            Ub = [2.0 * (W @ (W.T @ U)) for U in plan.U]
+            Sb = [w.clone() for _ in plan.S]
+            api.rsvd_truncate_backward_batched(As, plan.U, plan.S, plan.Vt, Ub, Sb, None, max_iter=120, tol=1e-6)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    lib.rsvd_profile_enable(400000)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    infos = []
+    for i in range(args.steps):
+        if wl == "sectors":
+            flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        infos.append(plan.info.clone())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    classes = profile_classes(lib)
+    tot_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    units_per_step = 1 if wl == "sectors" else B
+    value = ws * units_per_step / (ms_per_step / 1e3)
+
+    # algorithmic work
+    fl = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "tcgemm": 0.0}
+    tcb = 0.0
+    for inf in infos:
+        rec = inf.cpu().numpy()
+        for j, A in enumerate(As):
+            mm, nn = A.shape
+            kk = ks[j]
+            ll = min(kk + p, mm, nn)
+            f = rsvd_flops(mm, nn, kk, ll, q, int(rec[j][3]), int(rec[j][5]), prec)
+            for key in fl:
+                fl[key] += f[key]
+            if prec in ("bf16", "tf32"):
+                tcb += tc_bytes(mm, nn, ll, q, 2 if prec == "bf16" else 4)
+            if wl == "grad":  # backward: retained block + 120 CG iterations + the coupling terms (GEMMs)
+                fl["gemm"] += 2.0 * mm * kk * kk * 2 + 2.0 * mm * nn * kk
+                fl["gemm"] += 120 * (2 * 2.0 * mm * nn * kk + 4 * 2.0 * mm * kk * kk)
+                fl["gemm"] += 3 * 2.0 * mm * nn * kk
+    total_kernel_ms = sum(v[0] for v in classes.values())
+    kernels = {}
+    for name, (ms, cnt) in classes.items():
+        if cnt == 0:
+            continue
+        e = {"launch_groups": cnt, "ms_total": round(ms, 3), "share": round(ms / total_kernel_ms, 4)}
+        if name == "tcgemm" and ms > 0:
+            e["gbs"] = round(tcb / (ms / 1e3) / 1e9, 1)
+            e["frac_hbm_peak"] = round(tcb / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)
+            e["tflops"] = round(fl["tcgemm"] / (ms / 1e3) / 1e12, 3)
+        elif name in fl and ms > 0 and fl[name] > 0:
+            e["tflops"] = round(fl[name] / (ms / 1e3) / 1e12, 4)
+            if prec == "f64" or name in ("gram", "cholesky", "householder", "jacobi"):
+                e["frac_fp64_peak"] = round(fl[name] / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4)
+            else:
+                e["frac_fp32_peak"] = round(fl[name] / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS, 4)
+        kernels[name] = e
+    dom = max(kernels, key=lambda x: kernels[x]["ms_total"])
+    dms = classes[dom][0] / 1e3
+    if dom == "tcgemm":
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(tcb / dms / 1e9, 1), "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(tcb / dms / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        fp64 = prec == "f64" or dom in ("gram", "cholesky", "householder", "jacobi")
+        pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+        ach = fl.get(dom, 0.0) / dms / 1e12 if dms > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": round(pk, 3), "unit": "TFLOP/s",
+                    "frac": round(ach / pk, 4), "traffic": None,
+                    "peak_source": ("FP64 DFMA 152 SMs x 2/clk x 2 flop x 2.07 GHz" if fp64 else
+                                    "FP32 FFMA 152 SMs x 128/clk x 2 flop x 2.07 GHz") + " (derived)"}
+    launches = sum(cnt * {"gram": 2, "select": 2}.get(name, 1) for name, (ms, cnt) in classes.items())
+    stat = torch.stack(infos).cpu().numpy()
+    result = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16",
+                                                                "tf32": "tf32"}[prec],
+              "data": "synthetic", "config": dict(config, parallelism=f"replicas{ws}"),
+              "tflops": round(ws * sum(fl.values()) / (tot_ms / 1e3) / 1e12, 4), "roofline": roofline,
+              "kernels": kernels, "gpu_launches": launches, "clocks": clk,
+              "device_status": {"max_jacobi_sweeps": int(stat[..., 3].max()),
+                                "mean_jacobi_sweeps": round(float(stat[..., 3].mean()), 3),
+                                "nonzero_status": int((stat[..., 0] != 0).sum())}}
+    if rank == 0 and not args.no_extras:
+        # e2e: inputs from pinned host memory, results back to the host, every step
+        hA = [A.cpu().pin_memory() for A in As]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nst = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nst):
+            for A, h in zip(As, hA):
+                A.copy_(h, non_blocking=True)
+            step()
+            outs = [t.to("cpu", non_blocking=True) for t in plan.S]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / nst
+        result["e2e"] = {"value": round(units_per_step / (ems / 1e3), 3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hA)),
+                         "d2h_bytes_per_step": int(sum(t.numel() * 8 for t in plan.S)), "ms_per_step": round(ems, 3)}
+        # error against the exact truncated SVD on matrix 0
+        A0 = As[0].double().cpu().numpy()
+        k0 = ks[0]
+        sv = np.linalg.svd(A0, compute_uv=False)
+        s_gpu = plan.S[0].cpu().numpy()
+        big = sv[:k0] > 1e-8 * sv[0]
+        u0, v0 = plan.U[0].double().cpu().numpy(), plan.Vt[0].double().cpu().numpy()
+        err = np.linalg.norm(A0 - (u0 * s_gpu) @ v0)
+        dtr = np.sqrt(np.sum(sv[k0:] ** 2))
+        _, so, _ = orsvd.rsvd(A0, k0, p, q, 103, 0)
+        result["error"] = {"matrix": 0, "fro_err_over_delta_trunc": float(err / dtr) if dtr > 0 else None,
+                           "max_rel_sigma_err_vs_exact": float(np.max(np.abs(s_gpu[big] - sv[:k0][big]) / sv[:k0][big])),
+                           "max_abs_sigma_err_vs_fp64_oracle_rsvd_over_sigma1": float(np.max(np.abs(s_gpu - so)) / so[0])}
+        if wl == "sectors":
+            result["error"]["k_out"] = plan.k_out.cpu().tolist()
+        # comparator: full SVD + truncate (cuSOLVER via torch) on matrix 0..3
+        cd = torch.float64 if prec == "f64" else torch.float32
+        Ac = [A.to(cd) for A in As[:(1 if wl == "mixed" else 4)]]
+        torch.linalg.svd(Ac[0], full_matrices=False)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        for A in Ac:
+            Uf, Sf, Vf = torch.linalg.svd(A, full_matrices=False)
+        c1.record()
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / len(Ac)
+        result["comparator"] = {"kind": f"torch.linalg.svd (cuSOLVER) {cd} + slice, per matrix",
+                                "ms_per_matrix": round(cms, 3),
+                                "matrices_per_s": round(1e3 / cms, 3)}
+        # CPU oracle on a bounded sample: oracle RSVD of matrix 0 (and more while under ~10 s)
+        t0 = time.time()
+        nrun = 0
+        while True:
+            orsvd.rsvd(As[nrun % len(As)].double().cpu().numpy(), ks[nrun % len(As)], p, q, 103, nrun)
+            nrun += 1
+            if time.time() - t0 > 10.0:
+                break
+        el = time.time() - t0
+        per = el / nrun
+        cpu_value = (1.0 / (per * len(As))) if wl == "sectors" else 1.0 / per
+        result["cpu_baseline"] = {"value": round(cpu_value, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                  "sample": f"{nrun} oracle RSVD(s) of the workload's matrices (numpy FP64, BLAS threads = all host cores)"
+                                            + ("; sectors: per-block time x 32" if wl == "sectors" else "")}
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
 # ------------------------------------------------------------------ reference arm (the oracle)
 def run_reference(args):
     ws, rank, _ = dist_env()
@@ -405,6 +725,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / error / comparator / CPU legs")
+    ap.add_argument("--workload", default="tebd", choices=["tebd", "dense", "mixed", "sectors", "grad"],
+                    help="tebd (default): the TEBD bond-update workload; the others time the remaining configurations")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32"], help="mixed workload: operand precision")
     ap.add_argument("--chain-length", type=int, default=64,
                     help="L (default 64); a shorter chain keeps the 256 x 256 central bonds (profiling case)")
     args = ap.parse_args()
@@ -416,6 +739,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "tebd":
+        run_workload(args)
     else:
         run_ours(args)
 

@@ -50,6 +50,10 @@ struct Prob {
   // tensor-core path: A^T, Omega^T / Z^T, Q^T in the operand precision
   void *At, *WT, *QT;
   int ldAt, ldWT, ldQT;
+  // wide B (n >= 4 l): B^T = Q_b R first, Jacobi on M = B Q_b (l x l)
+  int wide;
+  double *Bt, *Bt2, *Mb, *RinvD;
+  void *Wb, *Qbt;
 };
 
 inline int pad8(int x) { return (x + 7) / 8 * 8; }
@@ -60,8 +64,10 @@ inline int pad8(int x) { return (x + 7) / 8 * 8; }
 size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int tc_bytes = 0) {
   const int mx = std::max(m, n);
   const int nchunk = ceil_div(mx, kGramChunk);
-  const int cs = jacobi_cluster_size(l, n);
-  const int glob = jacobi_fits_smem(l, n, cs) ? 0 : 1;
+  const int wide = n >= 4 * l ? 1 : 0;
+  const int jn = wide ? l : n;  // columns of the matrix the Jacobi SVD works on
+  const int cs = jacobi_cluster_size(l, jn);
+  const int glob = jacobi_fits_smem(l, jn, cs) ? 0 : 1;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -79,7 +85,7 @@ size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int
   void* hw = take((size_t)(mx + 16) * l * 8);
   void* hq = take((size_t)(mx + 16) * l * 8);
   void* Bm = take((size_t)l * n * 8);
-  void* Bg = take(glob ? (size_t)l * (n + 16) * 8 : 0);
+  void* Bg = take(glob ? (size_t)l * (jn + 16) * 8 : 0);
   void* Pg = take(glob ? (size_t)l * (l + 16) * 8 : 0);
   void* sig = take((size_t)l * 8);
   void* flag = take(sizeof(int) * 4);
@@ -87,6 +93,12 @@ size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int
   void* At = take(tc_bytes ? (size_t)n * pad8(m) * tc_bytes : 0);
   void* WT = take(tc_bytes ? lop * pad8(n) * tc_bytes : 0);
   void* QT = take(tc_bytes ? lop * pad8(m) * tc_bytes : 0);
+  void* Bt = take(wide ? (size_t)n * l * 8 : 0);
+  void* Bt2 = take(wide ? (size_t)n * l * 8 : 0);
+  void* Mb = take(wide ? (size_t)l * l * 8 : 0);
+  void* RinvD = take(wide ? (size_t)l * l * 8 : 0);
+  void* Wb = take(wide ? (size_t)std::max(k, 1) * l * tsize : 0);
+  void* Qbt = take(wide ? (size_t)l * n * tsize : 0);
   if (p) {
     p->At = At; p->WT = WT; p->QT = QT;
     p->ldAt = pad8(m); p->ldWT = pad8(n); p->ldQT = pad8(m);
@@ -96,6 +108,9 @@ size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int
     p->flag = (int*)flag;
     p->csize = cs;
     p->use_global = glob;
+    p->wide = wide;
+    p->Bt = (double*)Bt; p->Bt2 = (double*)Bt2; p->Mb = (double*)Mb; p->RinvD = (double*)RinvD;
+    p->Wb = Wb; p->Qbt = Qbt;
   }
   return off;
 }
@@ -137,6 +152,99 @@ OrthBatch<T> orth_batch(const std::vector<Prob*>& ps, bool onY) {
     J.hh_first = 3 * J.l > J.rows ? 1 : 0;
   }
   return b;
+}
+
+// Rank-k SVD of B (l x n, FP64, in Bm) for every matrix: one-sided Jacobi on
+// B itself, or - for wide B (n >= 4 l) - on the l x l matrix M = B Q_b where
+// B^T = Q_b R is an FP64 orthonormalisation of B^T (same CholeskyQR2 /
+// Householder machinery as the samples); then B = M Q_b^T and the rows of V^T
+// are the Jacobi's normalised rows times Q_b^T.  Writes S, V^T and the sorted
+// rotations Ps (U~ = Ps^T).
+template <typename T>
+int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
+  const int cnt = (int)probs.size();
+  std::vector<Prob*> wide;
+  for (auto& p : probs)
+    if (p.wide) wide.push_back(&p);
+  if (!wide.empty()) {
+    const int wc = (int)wide.size();
+    {  // B^T (n x l)
+      XposeBatch x;
+      x.count = wc;
+      for (int i = 0; i < wc; ++i) {
+        Prob& p = *wide[i];
+        x.job[i] = XposeJob{p.l, p.n, p.n, p.l, p.Bm, p.Bt};
+      }
+      RSVD_TRY((launch_transpose<double, double>(x, s)));
+    }
+    {  // Q_b = orth(B^T) in FP64
+      OrthBatch<double> ob;
+      ob.count = wc;
+      ob.max_chunks = 0;
+      ob.max_tilepairs = 0;
+      for (int i = 0; i < wc; ++i) {
+        Prob& p = *wide[i];
+        OrthJob<double>& J = ob.job[i];
+        J.rows = p.n; J.l = p.l; J.Y = p.Bt; J.Y1 = p.Bt2; J.part = p.part; J.G = p.G; J.Rinv = p.RinvD;
+        J.hw = p.hw; J.hq = p.hq; J.flag = p.flag; J.info = p.info; J.hh_first = 3 * p.l > p.n ? 1 : 0;
+      }
+      RSVD_TRY(launch_orth<double>(ob, s));
+    }
+    {  // M = B Q_b (l x l)
+      GemmBatch<double, double> g;
+      g.count = wc;
+      for (int i = 0; i < wc; ++i) {
+        Prob& p = *wide[i];
+        g.job[i] = GemmJob<double, double>{p.l, p.l, p.n, p.n, p.l, p.l, p.Bm, p.Bt, p.Mb, nullptr, nullptr, 0};
+      }
+      RSVD_TRY((launch_gemm<double, double, false, false>(g, s)));
+    }
+    {  // Q_b^T (l x n) in the output precision
+      XposeBatch x;
+      x.count = wc;
+      for (int i = 0; i < wc; ++i) {
+        Prob& p = *wide[i];
+        x.job[i] = XposeJob{p.n, p.l, p.l, p.n, p.Bt, p.Qbt};
+      }
+      RSVD_TRY((launch_transpose<double, T>(x, s)));
+    }
+  }
+  std::vector<int> done(cnt, 0);
+  for (int i0 = 0; i0 < cnt; ++i0) {
+    if (done[i0]) continue;
+    JacobiBatch<T> b;
+    b.count = 0;
+    b.csize = probs[i0].csize;
+    b.use_global = probs[i0].use_global;
+    for (int i = i0; i < cnt; ++i) {
+      Prob& p = probs[i];
+      if (done[i] || p.csize != b.csize || p.use_global != b.use_global) continue;
+      done[i] = 1;
+      JacobiJob<T>& J = b.job[b.count++];
+      J.l = p.l; J.n = p.wide ? p.l : p.n; J.k = p.k;
+      J.Bm = p.wide ? p.Mb : p.Bm; J.Bg = p.Bg; J.Pg = p.Pg;
+      J.S = p.S; J.sig = p.sig;
+      J.Vt = p.wide ? (T*)p.Wb : (T*)p.Vt;
+      J.ldvt = p.wide ? p.l : p.ldvt;
+      J.Ps = (T*)p.Ps;
+      J.info = p.info;
+      J.max_sweeps = p.max_sweeps;
+      J.want_vt = 1;
+      J.pipe_err = tc_err ? p.flag + 1 : nullptr;
+    }
+    RSVD_TRY(launch_jacobi<T>(b, s));
+  }
+  if (!wide.empty()) {  // V^T = W Q_b^T
+    GemmBatch<T, T> g;
+    g.count = 0;
+    for (auto* pp : wide) {
+      Prob& p = *pp;
+      g.job[g.count++] = GemmJob<T, T>{p.k, p.n, p.l, p.l, p.n, p.ldvt, (const T*)p.Wb, (const T*)p.Qbt, (T*)p.Vt,
+                                       nullptr, nullptr, 0};
+    }
+    RSVD_TRY((launch_gemm<T, T, false, false>(g, s)));
+  }
+  return RSVD_OK;
 }
 
 // Alg. RSVD for up to kMaxJobs matrices of one precision.
@@ -204,31 +312,10 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
       RSVD_TRY((launch_gemm<T, double, true, false>(g, s)));
     }
   }
-  // SVD of B by one-sided Jacobi; matrices grouped by cluster size / storage
+  // SVD of B
   {
-    std::vector<int> done(cnt, 0);
-    for (int i0 = 0; i0 < cnt; ++i0) {
-      if (done[i0]) continue;
-      JacobiBatch<T> b;
-      b.count = 0;
-      b.csize = probs[i0].csize;
-      b.use_global = probs[i0].use_global;
-      for (int i = i0; i < cnt; ++i) {
-        Prob& p = probs[i];
-        if (done[i] || p.csize != b.csize || p.use_global != b.use_global) continue;
-        done[i] = 1;
-        JacobiJob<T>& J = b.job[b.count++];
-        J.l = p.l; J.n = p.n; J.k = p.k;
-        J.Bm = p.Bm; J.Bg = p.Bg; J.Pg = p.Pg;
-        J.S = p.S; J.sig = p.sig;
-        J.Vt = (T*)p.Vt; J.ldvt = p.ldvt;
-        J.Ps = (T*)p.Ps;
-        J.info = p.info;
-        J.max_sweeps = p.max_sweeps;
-        J.want_vt = 1;
-      }
-      RSVD_TRY(launch_jacobi<T>(b, s));
-    }
+    int rc = svd_of_B<T>(probs, s, false);
+    if (rc != RSVD_OK) return rc;
   }
   // lift U = Q U~ and fix the signs
   {
@@ -360,30 +447,8 @@ int run_chunk_tc(std::vector<Prob>& probs, int q, cudaStream_t s) {
     RSVD_TRY((launch_transpose<float, double>(x, s)));
   }
   {
-    std::vector<int> done(cnt, 0);
-    for (int i0 = 0; i0 < cnt; ++i0) {
-      if (done[i0]) continue;
-      JacobiBatch<float> b;
-      b.count = 0;
-      b.csize = probs[i0].csize;
-      b.use_global = probs[i0].use_global;
-      for (int i = i0; i < cnt; ++i) {
-        Prob& p = probs[i];
-        if (done[i] || p.csize != b.csize || p.use_global != b.use_global) continue;
-        done[i] = 1;
-        JacobiJob<float>& J = b.job[b.count++];
-        J.l = p.l; J.n = p.n; J.k = p.k;
-        J.Bm = p.Bm; J.Bg = p.Bg; J.Pg = p.Pg;
-        J.S = p.S; J.sig = p.sig;
-        J.Vt = (float*)p.Vt; J.ldvt = p.ldvt;
-        J.Ps = (float*)p.Ps;
-        J.info = p.info;
-        J.max_sweeps = p.max_sweeps;
-        J.want_vt = 1;
-        J.pipe_err = p.flag + 1;
-      }
-      RSVD_TRY(launch_jacobi<float>(b, s));
-    }
+    int rc2 = svd_of_B<float>(probs, s, true);
+    if (rc2 != RSVD_OK) return rc2;
   }
   {
     GemmBatch<float, float> g;

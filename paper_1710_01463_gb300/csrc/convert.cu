@@ -118,5 +118,7 @@ template cudaError_t launch_transpose<__nv_bfloat16, __nv_bfloat16>(const XposeB
 template cudaError_t launch_transpose<float, float>(const XposeBatch&, cudaStream_t);
 template cudaError_t launch_transpose<float, __nv_bfloat16>(const XposeBatch&, cudaStream_t);
 template cudaError_t launch_transpose<float, double>(const XposeBatch&, cudaStream_t);
+template cudaError_t launch_transpose<double, double>(const XposeBatch&, cudaStream_t);
+template cudaError_t launch_transpose<double, float>(const XposeBatch&, cudaStream_t);
 
 }  // namespace rsvd

@@ -4,26 +4,29 @@
 // the lift U = Q U~.
 //
 // SIMT kernel (FFMA for float, DFMA for double): on GB300 FP64 has no tensor
-// core path, so the FP64 products are bound by the DFMA pipe.  64 x 64 output
-// tile per CTA, K staged through shared memory in slices of 16, a 4 x 4
-// register tile per thread with a stride-16 layout (conflict-free shared
-// reads, 16-wide coalesced stores).  Register double-buffering of the next K
-// slice overlaps the global loads with the FMAs.
+// core path, so the FP64 products are bound by the DFMA pipe.  Conflict-free
+// shared reads and 16-wide coalesced stores through a stride-16 register-tile
+// layout; register double-buffering of the next K slice overlaps the global
+// loads with the FMAs.
 #include "common.cuh"
 
 namespace rsvd {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int NT = 256;  // threads per CTA (a 16 x 16 grid)
 
-template <typename Tin, bool TA>
-__device__ __forceinline__ void load_a(const Tin* __restrict__ A, int lda, int M, int K,
-                                       int m0, int k0, Tin (&ra)[4]) {
+// BM x BN output tile, K slices of BK through shared memory (double
+// buffered via registers), a TM x TM register tile per thread with a stride-16
+// layout: 64 x 64 / 4 x 4 / BK 16 for FP64 (DFMA-bound), 128 x 128 / 8 x 8 /
+// BK 8 for FP32 (four FFMAs per shared-memory load).
+template <typename Tin, bool TA, int BM, int BK>
+__device__ __forceinline__ void load_a(const Tin* __restrict__ A, int lda, int M, int K, int m0, int k0,
+                                       Tin (&ra)[BM * BK / NT]) {
   const int t = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int idx = t + q * NT;  // 0..1023 over a 64 x 16 tile
+  for (int q = 0; q < BM * BK / NT; ++q) {
+    const int idx = t + q * NT;
     int i, kk;
     if (!TA) {  // A is M x K: k fastest
       kk = idx % BK;
@@ -39,11 +42,11 @@ __device__ __forceinline__ void load_a(const Tin* __restrict__ A, int lda, int M
   }
 }
 
-template <typename Tin, bool TA>
-__device__ __forceinline__ void store_a(Tin (*As)[BM + 1], const Tin (&ra)[4]) {
+template <typename Tin, bool TA, int BM, int BK>
+__device__ __forceinline__ void store_a(Tin (*As)[BM + 1], const Tin (&ra)[BM * BK / NT]) {
   const int t = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < BM * BK / NT; ++q) {
     const int idx = t + q * NT;
     int i, kk;
     if (!TA) {
@@ -57,11 +60,12 @@ __device__ __forceinline__ void store_a(Tin (*As)[BM + 1], const Tin (&ra)[4]) {
   }
 }
 
-template <typename Tin, bool TX>
-__device__ __forceinline__ void load_x(const Tin* __restrict__ X, int ldx, int N, int K, int n0, int k0, Tin (&rx)[4]) {
+template <typename Tin, bool TX, int BN, int BK>
+__device__ __forceinline__ void load_x(const Tin* __restrict__ X, int ldx, int N, int K, int n0, int k0,
+                                       Tin (&rx)[BN * BK / NT]) {
   const int t = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < BN * BK / NT; ++q) {
     const int idx = t + q * NT;
     int j, kk;
     if (!TX) {  // X is K x N: n fastest
@@ -78,11 +82,11 @@ __device__ __forceinline__ void load_x(const Tin* __restrict__ X, int ldx, int N
   }
 }
 
-template <typename Tin, bool TX>
-__device__ __forceinline__ void store_x(Tin (*Xs)[BN + 1], const Tin (&rx)[4]) {
+template <typename Tin, bool TX, int BN, int BK>
+__device__ __forceinline__ void store_x(Tin (*Xs)[BN + 1], const Tin (&rx)[BN * BK / NT]) {
   const int t = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < BN * BK / NT; ++q) {
     const int idx = t + q * NT;
     int j, kk;
     if (!TX) {
@@ -96,8 +100,9 @@ __device__ __forceinline__ void store_x(Tin (*Xs)[BN + 1], const Tin (&rx)[4]) {
   }
 }
 
-template <typename Tin, typename Tout, bool TA, bool TX>
+template <typename Tin, typename Tout, bool TA, bool TX, int BM, int BK>
 __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBatch<Tin, Tout> b) {
+  constexpr int BN = BM, TM = BM / 16;
   const GemmJob<Tin, Tout>& J = b.job[blockIdx.z];
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (m0 >= J.M || n0 >= J.N) return;
@@ -107,41 +112,41 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
   __shared__ Tin Xs[2][BK][BN + 1];
 
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  Tin acc[4][4];
+  Tin acc[TM][TM];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (Tin)0;
+    for (int j = 0; j < TM; ++j) acc[i][j] = (Tin)0;
 
-  Tin ra[4], rx[4];
-  load_a<Tin, TA>(J.A, J.lda, J.M, J.K, m0, 0, ra);
-  load_x<Tin, TX>(J.X, J.ldx, J.N, J.K, n0, 0, rx);
-  store_a<Tin, TA>(As[0], ra);
-  store_x<Tin, TX>(Xs[0], rx);
+  Tin ra[BM * BK / NT], rx[BN * BK / NT];
+  load_a<Tin, TA, BM, BK>(J.A, J.lda, J.M, J.K, m0, 0, ra);
+  load_x<Tin, TX, BN, BK>(J.X, J.ldx, J.N, J.K, n0, 0, rx);
+  store_a<Tin, TA, BM, BK>(As[0], ra);
+  store_x<Tin, TX, BN, BK>(Xs[0], rx);
   __syncthreads();
 
   const int nk = (J.K + BK - 1) / BK;
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
     if (kt + 1 < nk) {
-      load_a<Tin, TA>(J.A, J.lda, J.M, J.K, m0, (kt + 1) * BK, ra);
-      load_x<Tin, TX>(J.X, J.ldx, J.N, J.K, n0, (kt + 1) * BK, rx);
+      load_a<Tin, TA, BM, BK>(J.A, J.lda, J.M, J.K, m0, (kt + 1) * BK, ra);
+      load_x<Tin, TX, BN, BK>(J.X, J.ldx, J.N, J.K, n0, (kt + 1) * BK, rx);
     }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      Tin av[4], xv[4];
+      Tin av[TM], xv[TM];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[cur][kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) av[i] = As[cur][kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) xv[j] = Xs[cur][kk][tx + 16 * j];
+      for (int j = 0; j < TM; ++j) xv[j] = Xs[cur][kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], xv[j], acc[i][j]);
+        for (int j = 0; j < TM; ++j) acc[i][j] = fma(av[i], xv[j], acc[i][j]);
     }
     if (kt + 1 < nk) {
-      store_a<Tin, TA>(As[cur ^ 1], ra);
-      store_x<Tin, TX>(Xs[cur ^ 1], rx);
+      store_a<Tin, TA, BM, BK>(As[cur ^ 1], ra);
+      store_x<Tin, TX, BN, BK>(Xs[cur ^ 1], rx);
     }
     __syncthreads();
   }
@@ -149,11 +154,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
   double scale = 1.0;
   if (J.div) scale = 1.0 / *J.div;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int gi = m0 + ty + 16 * i;
     if (gi >= J.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TM; ++j) {
       const int gj = n0 + tx + 16 * j;
       if (gj < J.N) {
         Tout v = J.div ? (Tout)((double)acc[i][j] * scale) : (Tout)acc[i][j];
@@ -165,18 +170,28 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
   }
 }
 
+template <typename Tin>
+struct GemmTile {
+  static constexpr int BM = 64, BK = 16;
+};
+template <>
+struct GemmTile<float> {
+  static constexpr int BM = 128, BK = 8;
+};
+
 }  // namespace
 
 template <typename Tin, typename Tout, bool TA, bool TX>
 cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
   if (b.count <= 0) return cudaSuccess;
+  constexpr int BM = GemmTile<Tin>::BM, BK = GemmTile<Tin>::BK;
   int tm = 1, tn = 1;
   for (int i = 0; i < b.count; ++i) {
     tm = max(tm, ceil_div(b.job[i].M, BM));
-    tn = max(tn, ceil_div(b.job[i].N, BN));
+    tn = max(tn, ceil_div(b.job[i].N, BM));
   }
   prof_begin(KC_GEMM, s);
-  gemm_kernel<Tin, Tout, TA, TX><<<dim3(tn, tm, b.count), NT, 0, s>>>(b);
+  gemm_kernel<Tin, Tout, TA, TX, BM, BK><<<dim3(tn, tm, b.count), NT, 0, s>>>(b);
   prof_end(KC_GEMM, s);
   return cudaGetLastError();
 }
