@@ -44,6 +44,19 @@ def truncations_per_step():
     return 2 * a + b
 
 
+def job_ms(local_ms):
+    """Timed-region duration of the whole job: the maximum over ranks (any
+    torch.distributed backend; the local value when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_ms)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -201,11 +214,7 @@ def run_ours(args):
     ncls = lib.rsvd_profile_collect(ms_c, cnt_c, nclass)
     lib.rsvd_profile_enable(0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = job_ms(sum(step_ms))
     ms_per_step = tot_ms / args.steps
     value = ws * truncations_per_step() / (ms_per_step / 1e3)
 
@@ -388,22 +397,30 @@ def profile_classes(lib):
 
 def rsvd_flops(m, n, k, l, q, sweeps, rots, prec):
     """Algorithmic flops of one RSVD by kernel class (see step_flops), plus the
-    tensor-core bytes of the BF16 / TF32 forms."""
+    tensor-core products of the BF16 / TF32 forms.  Wide B (n >= 4l): the SVD
+    of B runs on the l x l factor of an orthonormalisation of B^T."""
     f = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "tcgemm": 0.0}
     exact = m <= l
-    prod = (2 * q + 2) * 2.0 * m * n * l
+
+    def orth(rows):
+        if 3 * l > rows:
+            f["householder"] += 2 * (2.0 * rows * l * l - 2.0 * l ** 3 / 3.0)
+        else:
+            f["gram"] += 2 * rows * l * l
+            f["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
+            f["gemm"] += 2 * rows * l * l
+
     if not exact:
-        f["tcgemm" if prec in ("bf16", "tf32") else "gemm"] += prod
+        f["tcgemm" if prec in ("bf16", "tf32") else "gemm"] += (2 * q + 2) * 2.0 * m * n * l
         for it in range(2 * q + 1):
-            rows = m if it % 2 == 0 else n
-            if 3 * l > rows:
-                f["householder"] += 2 * (2.0 * rows * l * l - 2.0 * l ** 3 / 3.0)
-            else:
-                f["gram"] += 2 * rows * l * l
-                f["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
-                f["gemm"] += 2 * rows * l * l
+            orth(m if it % 2 == 0 else n)
     f["gemm"] += 2.0 * m * l * k  # lift
-    f["jacobi"] += sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * (6.0 * n + 6.0 * l) + (sweeps + 1) * 2.0 * n * l
+    jn = n
+    if n >= 4 * l:  # B^T = Q_b R, M = B Q_b, V^T = W Q_b^T
+        orth(n)
+        f["gemm"] += 2.0 * l * n * l + 2.0 * k * l * n
+        jn = l
+    f["jacobi"] += sweeps * (l * (l - 1) / 2.0) * 2.0 * jn + rots * (6.0 * jn + 6.0 * l) + (sweeps + 1) * 2.0 * jn * l
     return f
 
 
@@ -510,6 +527,16 @@ def run_workload(args):
 
     plan = api.BatchedPlan([tuple(A.shape) for A in As], ks, p, q, 103 + 1000 * rank, 0, dtype, dev,
                            chi_global=(512 if wl == "sectors" else 0), tf32=(prec == "tf32"))
+    if wl == "sectors" and args.policy == "estimate":
+        # trial ranks from the previous step's selection plus a margin of 16
+        # (the paper: estimates from previous iterations plus oversampling)
+        plan.run(As)
+        torch.cuda.synchronize()
+        kprev = plan.k_out.cpu().tolist()
+        ks = [min(min(A.shape), kp + 16) for A, kp in zip(As, kprev)]
+        config["policy"] = "previous step's kept count + 16 (first step: maximal)"
+        plan = api.BatchedPlan([tuple(A.shape) for A in As], ks, p, q, 103 + 1000 * rank, 0, dtype, dev,
+                               chi_global=512)
 
     def step():
         plan.run(As)
@@ -541,11 +568,7 @@ def run_workload(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     classes = profile_classes(lib)
-    tot_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = job_ms(sum(a.elapsed_time(b) for a, b in ev))
     ms_per_step = tot_ms / args.steps
     units_per_step = 1 if wl == "sectors" else B
     value = ws * units_per_step / (ms_per_step / 1e3)
@@ -643,7 +666,11 @@ def run_workload(args):
                            "max_rel_sigma_err_vs_exact": float(np.max(np.abs(s_gpu[big] - sv[:k0][big]) / sv[:k0][big])),
                            "max_abs_sigma_err_vs_fp64_oracle_rsvd_over_sigma1": float(np.max(np.abs(s_gpu - so)) / so[0])}
         if wl == "sectors":
-            result["error"]["k_out"] = plan.k_out.cpu().tolist()
+            ko = plan.k_out.cpu().tolist()
+            result["error"]["k_out"] = ko
+            # a trial rank is adequate when the block's last trial value was not selected
+            result["error"]["trial_ranks_adequate"] = bool(all(kk < kt or kt == min(A.shape)
+                                                               for kk, kt, A in zip(ko, ks, As)))
         # comparator: full SVD + truncate (cuSOLVER via torch) on matrix 0..3
         cd = torch.float64 if prec == "f64" else torch.float32
         Ac = [A.to(cd) for A in As[:(1 if wl == "mixed" else 4)]]
@@ -728,6 +755,8 @@ def main():
     ap.add_argument("--workload", default="tebd", choices=["tebd", "dense", "mixed", "sectors", "grad"],
                     help="tebd (default): the TEBD bond-update workload; the others time the remaining configurations")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32"], help="mixed workload: operand precision")
+    ap.add_argument("--policy", default="estimate", choices=["estimate", "maximal"],
+                    help="sectors workload: per-block trial ranks")
     ap.add_argument("--chain-length", type=int, default=64,
                     help="L (default 64); a shorter chain keeps the 256 x 256 central bonds (profiling case)")
     args = ap.parse_args()

@@ -201,12 +201,15 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond,
  * as TF32 (RSVD_TF32), C (M x N, ldc) float.  tcgen05.mma with TMEM
  * accumulation, TMA-fed; N <= 256.  A, B must be 16-byte aligned with
  * lda * element size and ldb * element size multiples of 16 bytes.  err
- * (device int, may be NULL) is set to 1 if a pipeline wait timed out.
+ * (device int, may be NULL) is set to 1 if a pipeline wait timed out (every
+ * wait gives up after about one second; the kernel then finishes and C is
+ * invalid).  test_flags: 0, or 1 to issue no loads at all - the waits run out
+ * and err reports it (a test of that failure path; nothing faults or hangs).
  * Errors: RSVD_ERR_PRECISION, RSVD_ERR_INVALID_SIZE (also for a layout TMA
  * cannot describe), RSVD_ERR_NULL_POINTER, RSVD_ERR_LAUNCH.
  */
 int rsvd_gemm_tc(int M, int N, int K, int prec, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
-                 int* err, void* cuda_stream);
+                 int* err, int test_flags, void* cuda_stream);
 
 /*
  * rsvd_backward_workspace_size - workspace bytes of rsvd_truncate_backward_batched.

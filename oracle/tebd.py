@@ -121,11 +121,11 @@ def mps_energy(B, L, h):
     """<psi|H|psi> / <psi|psi> by exact contraction of psi = B[0] B[1] ... B[L-1]."""
     left = [np.ones((1, 1))]
     for i in range(L):
-        left.append(np.einsum("ab,asc,bsd->cd", left[i], B[i], B[i]))
+        left.append(np.einsum("ab,asc,bsd->cd", left[i], B[i], B[i], optimize=True))
     right = [None] * (L + 1)
     right[L] = np.ones((1, 1))
     for i in range(L - 1, -1, -1):
-        right[i] = np.einsum("asc,bsd,cd->ab", B[i], B[i], right[i + 1])
+        right[i] = np.einsum("asc,bsd,cd->ab", B[i], B[i], right[i + 1], optimize=True)
     norm = float(left[L][0, 0])
     e = 0.0
     d = B[0].shape[1]
@@ -133,7 +133,7 @@ def mps_energy(B, L, h):
         two = np.einsum("atb,buc->atuc", B[i], B[i + 1])
         hb = bond_hamiltonian(i, L, h).reshape(d, d, d, d)
         htwo = np.einsum("stxy,axyc->astc", hb, two)
-        e += float(np.einsum("ab,astc,bstd,cd->", left[i], htwo, two, right[i + 2]))
+        e += float(np.einsum("ab,astc,bstd,cd->", left[i], htwo, two, right[i + 2], optimize=True))
     return e / norm
 
 

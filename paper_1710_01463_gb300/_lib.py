@@ -108,7 +108,7 @@ def load():
     lib.rsvd_status_string.restype = ctypes.c_char_p
     lib.rsvd_profile_enable.argtypes = [i]
     lib.rsvd_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ip, i]
-    lib.rsvd_gemm_tc.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp, vp]
+    lib.rsvd_gemm_tc.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp, i, vp]
     lib.rsvd_backward_workspace_size.argtypes = [i, ip, ip, ip, i, ctypes.POINTER(sz)]
     lib.rsvd_truncate_backward_batched.argtypes = [i, ip, ip, ip, i, pp, ip, pp, pp, ip, pp, ip, pp, ip, pp, pp, ip,
                                                    pp, ip, i, ctypes.c_double, vp, sz, vp, vp]

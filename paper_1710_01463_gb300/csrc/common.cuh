@@ -284,7 +284,7 @@ cudaError_t launch_select(const SelectBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_theta(const TebdBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s);
 template <typename TIn>
-cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s);
+cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s, int skip_loads = 0);
 template <typename T>
 cudaError_t launch_bw_coldot(const BwBatch<T>& b, int which, cudaStream_t s);
 template <typename T>

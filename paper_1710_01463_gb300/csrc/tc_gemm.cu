@@ -25,7 +25,6 @@ namespace {
 
 constexpr int kTcThreads = 192;
 constexpr int kTcM = 128;
-constexpr unsigned kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -37,10 +36,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// bounded wait for the given phase parity; returns false on timeout
+// bounded wait for the given phase parity: gives up after about one second
+// of SM clock cycles and returns false
+constexpr long long kWaitCycles = 2LL << 30;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
-  for (unsigned it = 0; it < kSpinLimit; ++it) {
+  const long long t0 = clock64();
+  for (;;) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -48,8 +50,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -131,7 +133,8 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 template <typename TIn>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_constant__ TcBatch b, int stages) {
+__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_constant__ TcBatch b, int stages,
+                                                                int skip_loads) {
   const TcJob& J = b.job[blockIdx.y];
   const int m0 = blockIdx.x * kTcM;
   if (m0 >= J.M) return;  // whole CTA, before any barrier or TMEM use
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
   const uint32_t tmem = *tmem_slot;
   const int nk = (J.K + BK - 1) / BK;
 
-  if (warp == 0 && lane == 0) {
+  if (warp == 0 && lane == 0 && !skip_loads) {
     // producer
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % stages;
@@ -286,7 +289,7 @@ bool make_tmap(CUtensorMap* map, const void* base, int rows, int cols, int ld, i
 }
 
 template <typename TIn>
-cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s) {
+cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s, int skip_loads) {
   if (b.count <= 0) return cudaSuccess;
   int maxM = 1, maxN = 16;
   for (int i = 0; i < b.count; ++i) {
@@ -298,18 +301,18 @@ cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   prof_begin(KC_TCGEMM, s);
-  tc_gemm_kernel<TIn><<<dim3(ceil_div(maxM, kTcM), b.count), kTcThreads, smem, s>>>(b, stages);
+  tc_gemm_kernel<TIn><<<dim3(ceil_div(maxM, kTcM), b.count), kTcThreads, smem, s>>>(b, stages, skip_loads);
   prof_end(KC_TCGEMM, s);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_tc_gemm<__nv_bfloat16>(const TcBatch&, cudaStream_t);
-template cudaError_t launch_tc_gemm<float>(const TcBatch&, cudaStream_t);
+template cudaError_t launch_tc_gemm<__nv_bfloat16>(const TcBatch&, cudaStream_t, int);
+template cudaError_t launch_tc_gemm<float>(const TcBatch&, cudaStream_t, int);
 
 }  // namespace rsvd
 
 extern "C" int rsvd_gemm_tc(int M, int N, int K, int prec, const void* A, int lda, const void* B, int ldb, float* C,
-                            int ldc, int* err, void* cuda_stream) {
+                            int ldc, int* err, int test_flags, void* cuda_stream) {
   using namespace rsvd;
   if (prec != RSVD_BF16 && prec != RSVD_TF32) return RSVD_ERR_PRECISION;
   if (M < 1 || N < 1 || N > 256 || K < 1 || lda < K || ldb < K || ldc < N) return RSVD_ERR_INVALID_SIZE;
@@ -328,8 +331,10 @@ extern "C" int rsvd_gemm_tc(int M, int N, int K, int prec, const void* A, int ld
   J.N = N;
   J.K = K;
   J.ldc = ldc;
-  cudaError_t e = prec == RSVD_BF16 ? launch_tc_gemm<__nv_bfloat16>(b, (cudaStream_t)cuda_stream)
-                                    : launch_tc_gemm<float>(b, (cudaStream_t)cuda_stream);
+  if (test_flags & ~1) return RSVD_ERR_INVALID_SIZE;
+  const int skip = test_flags & 1;
+  cudaError_t e = prec == RSVD_BF16 ? launch_tc_gemm<__nv_bfloat16>(b, (cudaStream_t)cuda_stream, skip)
+                                    : launch_tc_gemm<float>(b, (cudaStream_t)cuda_stream, skip);
   if (e != cudaSuccess) {
     last_cuda_error() = e;
     return RSVD_ERR_LAUNCH;

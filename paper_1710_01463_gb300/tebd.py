@@ -125,3 +125,19 @@ class TebdChain:
     def state_from_host(self, B, lam):
         self.B.copy_(torch.from_numpy(np.asarray(B)))
         self.lam.copy_(torch.from_numpy(np.asarray(lam)))
+
+    def save(self, path, step):
+        """Checkpoint: B tensors, Schmidt values, bond dimensions, step and dt (.npz)."""
+        B, lam = self.state_to_host()
+        np.savez(path, B=B, lam=lam, D=np.asarray(self.D), L=self.L, chi=self.chi, h=self.h,
+                 step=int(step), dt=float(self.dt if self.dt is not None else 0.0))
+
+    def load(self, path):
+        """Restore a checkpoint written by save(); returns the step to continue from."""
+        z = np.load(path)
+        if int(z["L"]) != self.L or int(z["chi"]) != self.chi or list(z["D"]) != self.D:
+            raise ValueError("checkpoint does not match this chain")
+        self.state_from_host(z["B"], z["lam"])
+        if float(z["dt"]) > 0:
+            self.set_dt(float(z["dt"]))
+        return int(z["step"])

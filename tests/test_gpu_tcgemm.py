@@ -30,7 +30,7 @@ def run(_lib, A, B, prec):
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     rc = _lib.load().rsvd_gemm_tc(M, N, K, prec, ctypes.c_void_p(A.data_ptr()), A.stride(0),
                                   ctypes.c_void_p(B.data_ptr()), B.stride(0), ctypes.c_void_p(C.data_ptr()),
-                                  C.stride(0), ctypes.c_void_p(err.data_ptr()),
+                                  C.stride(0), ctypes.c_void_p(err.data_ptr()), 0,
                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0
     torch.cuda.synchronize()
@@ -63,5 +63,24 @@ def test_tc_gemm_rejects_unaligned_stride(lib):
     B = torch.zeros(16, 100, dtype=torch.bfloat16, device="cuda")
     C = torch.zeros(64, 16, dtype=torch.float32, device="cuda")
     rc = lib.load().rsvd_gemm_tc(64, 16, 100, lib.RSVD_BF16, ctypes.c_void_p(A.data_ptr()), 100,
-                                 ctypes.c_void_p(B.data_ptr()), 100, ctypes.c_void_p(C.data_ptr()), 16, None, None)
+                                 ctypes.c_void_p(B.data_ptr()), 100, ctypes.c_void_p(C.data_ptr()), 16, None, 0, None)
     assert rc == lib.RSVD_ERR_INVALID_SIZE
+
+
+def test_pipeline_wait_limit_reports_error(lib):
+    # no loads are issued, so the MMA thread's wait runs out (about one second);
+    # the kernel finishes, reports the timeout, and the context stays usable
+    A = torch.zeros(128, 64, dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros(16, 64, dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros(128, 16, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.load().rsvd_gemm_tc(128, 16, 64, lib.RSVD_BF16, ctypes.c_void_p(A.data_ptr()), 64,
+                                 ctypes.c_void_p(B.data_ptr()), 64, ctypes.c_void_p(C.data_ptr()), 16,
+                                 ctypes.c_void_p(err.data_ptr()), 1, None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 1
+    # the device still works
+    A2 = torch.ones(128, 64, dtype=torch.bfloat16, device="cuda")
+    C2 = run(lib, A2, torch.ones(16, 64, dtype=torch.bfloat16, device="cuda"), lib.RSVD_BF16)
+    assert torch.allclose(C2, torch.full_like(C2, 64.0))

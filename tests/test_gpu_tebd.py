@@ -56,3 +56,23 @@ def test_tebd_converges_small_chain(mods):
     e = otebd.mps_energy(ch.tensors(), L, 1.0)
     e0 = otebd.exact_ground_energy_ed(L, 1.0)
     assert 0 < e - e0 < 3e-5
+
+
+def test_checkpoint_resume_is_exact(mods, tmp_path):
+    L, chi = 10, 16
+    a = mods.TebdChain(L, chi, seed=4)
+    a.set_product_state(inputs.product_state_vectors(L, 2, 102))
+    a.set_dt(0.05)
+    for s in range(6):
+        a.step(s)
+    path = str(tmp_path / "state.npz")
+    a.save(path, 6)
+    for s in range(6, 10):
+        a.step(s)
+    b = mods.TebdChain(L, chi, seed=4)
+    start = b.load(path)
+    for s in range(start, 10):
+        b.step(s)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.B.cpu().numpy(), b.B.cpu().numpy())
+    np.testing.assert_array_equal(a.lam.cpu().numpy(), b.lam.cpu().numpy())
