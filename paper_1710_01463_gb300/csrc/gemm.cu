@@ -18,8 +18,7 @@ constexpr int NT = 256;  // threads per CTA (a 16 x 16 grid)
 
 // BM x BN output tile, K slices of BK through shared memory (double
 // buffered via registers), a TM x TM register tile per thread with a stride-16
-// layout: 64 x 64 / 4 x 4 / BK 16 for FP64 (DFMA-bound), 128 x 128 / 8 x 8 /
-// BK 8 for FP32 (four FFMAs per shared-memory load).
+// layout: 64 x 64 / 4 x 4 / BK 16.
 template <typename Tin, bool TA, int BM, int BK>
 __device__ __forceinline__ void load_a(const Tin* __restrict__ A, int lda, int M, int K, int m0, int k0,
                                        Tin (&ra)[BM * BK / NT]) {
@@ -100,9 +99,9 @@ __device__ __forceinline__ void store_x(Tin (*Xs)[BN + 1], const Tin (&rx)[BN * 
   }
 }
 
-template <typename Tin, typename Tout, bool TA, bool TX, int BM, int BK>
+template <typename Tin, typename Tout, bool TA, bool TX, int BM, int BN, int BK>
 __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBatch<Tin, Tout> b) {
-  constexpr int BN = BM, TM = BM / 16;
+  constexpr int TM = BM / 16, TN = BN / 16;
   const GemmJob<Tin, Tout>& J = b.job[blockIdx.z];
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (m0 >= J.M || n0 >= J.N) return;
@@ -112,11 +111,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
   __shared__ Tin Xs[2][BK][BN + 1];
 
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  Tin acc[TM][TM];
+  Tin acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TM; ++j) acc[i][j] = (Tin)0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = (Tin)0;
 
   Tin ra[BM * BK / NT], rx[BN * BK / NT];
   load_a<Tin, TA, BM, BK>(J.A, J.lda, J.M, J.K, m0, 0, ra);
@@ -134,15 +133,15 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
     }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      Tin av[TM], xv[TM];
+      Tin av[TM], xv[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) av[i] = As[cur][kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < TM; ++j) xv[j] = Xs[cur][kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) xv[j] = Xs[cur][kk][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TM; ++j) acc[i][j] = fma(av[i], xv[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], xv[j], acc[i][j]);
     }
     if (kt + 1 < nk) {
       store_a<Tin, TA, BM, BK>(As[cur ^ 1], ra);
@@ -158,7 +157,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
     const int gi = m0 + ty + 16 * i;
     if (gi >= J.M) continue;
 #pragma unroll
-    for (int j = 0; j < TM; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int gj = n0 + tx + 16 * j;
       if (gj < J.N) {
         Tout v = J.div ? (Tout)((double)acc[i][j] * scale) : (Tout)acc[i][j];
@@ -170,30 +169,38 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
   }
 }
 
-template <typename Tin>
-struct GemmTile {
-  static constexpr int BM = 64, BK = 16;
-};
-template <>
-struct GemmTile<float> {
-  static constexpr int BM = 128, BK = 8;
-};
-
 }  // namespace
 
-template <typename Tin, typename Tout, bool TA, bool TX>
-cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
-  if (b.count <= 0) return cudaSuccess;
-  constexpr int BM = GemmTile<Tin>::BM, BK = GemmTile<Tin>::BK;
+template <typename Tin, typename Tout, bool TA, bool TX, int BM, int BN>
+cudaError_t launch_tile(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
   int tm = 1, tn = 1;
   for (int i = 0; i < b.count; ++i) {
     tm = max(tm, ceil_div(b.job[i].M, BM));
-    tn = max(tn, ceil_div(b.job[i].N, BM));
+    tn = max(tn, ceil_div(b.job[i].N, BN));
   }
   prof_begin(KC_GEMM, s);
-  gemm_kernel<Tin, Tout, TA, TX, BM, BK><<<dim3(tn, tm, b.count), NT, 0, s>>>(b);
+  gemm_kernel<Tin, Tout, TA, TX, BM, BN, 16><<<dim3(tn, tm, b.count), NT, 0, s>>>(b);
   prof_end(KC_GEMM, s);
   return cudaGetLastError();
+}
+
+// Tile shape per launch: 64 x 64, 64 x 48 or 48 x 64, whichever computes the
+// fewest padded outputs over the batch (the sample widths l are not multiples
+// of 64: l = 138 fills 144 of a 48-wide tiling and only 138 of 192 otherwise).
+template <typename Tin, typename Tout, bool TA, bool TX>
+cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  long long w[3] = {0, 0, 0};
+  const int bm[3] = {64, 64, 48}, bn[3] = {64, 48, 64};
+  for (int i = 0; i < b.count; ++i)
+    for (int t = 0; t < 3; ++t)
+      w[t] += (long long)ceil_div(b.job[i].M, bm[t]) * bm[t] * ceil_div(b.job[i].N, bn[t]) * bn[t];
+  int best = 0;
+  for (int t = 1; t < 3; ++t)
+    if (w[t] < w[best]) best = t;
+  if (best == 1) return launch_tile<Tin, Tout, TA, TX, 64, 48>(b, s);
+  if (best == 2) return launch_tile<Tin, Tout, TA, TX, 48, 64>(b, s);
+  return launch_tile<Tin, Tout, TA, TX, 64, 64>(b, s);
 }
 
 #define INST(Tin, Tout)                                                                           \

@@ -70,7 +70,7 @@ __host__ __device__ inline size_t jsmem_small(int l, const JLayout& L) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const __grid_constant__ JacobiBatch<T> b) {
+__global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_constant__ JacobiBatch<T> b) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = b.csize;
   const int rank = (int)cluster.block_rank();

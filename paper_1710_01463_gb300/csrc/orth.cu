@@ -395,24 +395,48 @@ struct PanelLayout {
   size_t ys, vo, wp, ws, alpha, total;  // shared-memory offsets in doubles
 };
 
+constexpr int kPanStride = kNb + 1;  // panel rows in shared memory, padded against bank conflicts
+
 // Shared memory: own rows of Y (then Q) and of V, one V^T Y buffer, T^T W and
-// the reflector scalars.  The panel (rank 0 only) and the T matrices of all
-// panels live in the matrix's global scratch (hw, hq), which stays in L2.
+// the reflector scalars.  Rank 0 factors the panel (one row per thread) in the
+// region of the two V^T Y buffers, which are idle at that point; the T
+// matrices of all panels are kept in the matrix's global scratch (hq,
+// L2-resident) for the accumulation of Q.
 __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) {
   const int rs = (rows + csize - 1) / csize;
   PanelLayout L;
   size_t o = 0;
   L.ys = o; o += (size_t)rs * l;
   L.vo = o; o += (size_t)rs * l;
-  L.wp = o; o += (size_t)kNb * l;
-  L.ws = o; o += (size_t)kNb * l;
+  L.wp = o;
+  L.ws = o + (size_t)kNb * l;
+  const size_t wbuf = 2 * (size_t)kNb * l, pan = (size_t)rows * kPanStride;
+  o += wbuf > pan ? wbuf : pan;
   L.alpha = o; o += (size_t)l;
   L.total = o;
   return L;
 }
 
+// Sums kNb = 16 per-lane values over a warp by recursive halving (16 shuffles
+// instead of 80): lanes 2i and 2i + 1 return the warp's sum of value i.
+__device__ __forceinline__ double warp_reduce_scatter16(double (&a)[kNb], int lane) {
+  static_assert(kNb == 16, "the halving schedule assumes 16 values");
+#pragma unroll
+  for (int lev = 0; lev < 4; ++lev) {
+    const int off = 16 >> lev, half = 8 >> lev;
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const double send = up ? a[k] : a[k + half];
+      const double keep = up ? a[k + half] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __grid_constant__ OrthBatch<T> b, int csize) {
+__global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const __grid_constant__ OrthBatch<T> b, int csize) {
   cg::cluster_group cluster = cg::this_cluster();
   const OrthJob<T>& J = b.job[blockIdx.y];
   if (*J.flag == 0) return;  // cluster-uniform
@@ -429,10 +453,13 @@ __global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __g
   double* Wp = sm + L.wp;      // partial V^T Y               (kNb x l)
   double* Ws = sm + L.ws;      // summed V^T Y, then T^T W    (kNb x l)
   double* alpha = sm + L.alpha;
-  double* Pn = J.hw;           // rank 0: the panel, rows x kNb (global scratch, L2)
   double* Tall = J.hq;         // T of every panel, npanel x kNb x kNb (global scratch)
   __shared__ double red[kHhThreads / 32][2];
-  __shared__ double sc[2];
+  __shared__ double red1[kHhThreads / 32];
+  __shared__ double red16[kHhThreads / 32][kNb];
+  __shared__ double fin[kNb];
+  __shared__ double Ts[kNb][kNb];  // T of the current panel
+  __shared__ double x0s;
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = kHhThreads / 32;
 
   for (int e = tid; e < nr * l; e += kHhThreads) {
@@ -483,88 +510,81 @@ __global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __g
       break;  // identical decision in every CTA of the cluster
     }
     if (rank == 0) {
-      // gather the panel
-      for (int e = tid; e < R * nb; e += kHhThreads) {
-        const int rr = e / nb, c = e % nb;
-        const int r = j0 + rr, owner = r / rs;
-        Pn[rr * kNb + c] = cluster.map_shared_rank(Ys, owner)[(r - owner * rs) * l + j0 + c];
+      // one panel row per thread (rows <= kHhThreads is a launch condition):
+      // x[c] = Pan[tid][c] = Y[j0 + tid, j0 + c]; columns c < jj are replaced by
+      // the reflectors v_c as they are formed
+      double* x = Wp + (size_t)tid * kPanStride;
+      const int r = j0 + tid;
+      const bool live = tid < R;
+      if (live) {
+        const int owner = r / rs;
+        const double* src = cluster.map_shared_rank(Ys, owner) + (size_t)(r - owner * rs) * l + j0;
+#pragma unroll
+        for (int c = 0; c < kNb; ++c) x[c] = c < nb ? src[c] : 0.0;
       }
-      __syncthreads();
+      if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = 0.0;
       for (int jj = 0; jj < nb; ++jj) {
-        double a = 0.0;
-        for (int rr = jj + tid; rr < R; rr += kHhThreads) a = fma(Pn[rr * kNb + jj], Pn[rr * kNb + jj], a);
+        // squared norm of column jj over panel rows jj .. R-1
+        const double xj = live ? x[jj] : 0.0;
+        double a = (tid >= jj) ? xj * xj : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) red[warp][0] = a;
+        if (lane == 0) red1[warp] = a;
+        if (tid == jj) x0s = xj;
         __syncthreads();
-        if (tid == 0) {
-          double nrm2 = 0.0;
-          for (int q = 0; q < nw; ++q) nrm2 += red[q][0];
-          const double x0 = Pn[jj * kNb + jj];
-          double al = 0.0, inv = 0.0;
-          if (nrm2 > 0.0) {
-            al = x0 >= 0.0 ? -sqrt(nrm2) : sqrt(nrm2);
-            const double v0 = x0 - al;
-            const double vn2 = nrm2 - x0 * x0 + v0 * v0;
-            inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
-          }
-          alpha[j0 + jj] = al;
-          sc[0] = inv;
-          sc[1] = x0 - al;
+        double nrm2 = 0.0;
+        for (int q = 0; q < nw; ++q) nrm2 += red1[q];  // same order in every thread
+        const double x0 = x0s;
+        double al = 0.0, inv = 0.0;
+        if (nrm2 > 0.0) {
+          al = x0 >= 0.0 ? -sqrt(nrm2) : sqrt(nrm2);
+          const double w0 = x0 - al;
+          const double vn2 = nrm2 - x0 * x0 + w0 * w0;
+          inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
         }
-        __syncthreads();
-        const double inv = sc[0], v0 = sc[1];
-        for (int rr = tid; rr < R; rr += kHhThreads) {
-          double v = 0.0;
-          if (rr == jj) v = v0 * inv;
-          else if (rr > jj) v = Pn[rr * kNb + jj] * inv;
-          Pn[rr * kNb + jj] = v;  // V's column (zero above the diagonal)
-        }
-        __syncthreads();
-        for (int c = jj + 1 + warp; c < nb; c += nw) {
-          double d = 0.0;
-          for (int rr = jj + lane; rr < R; rr += 32) d = fma(Pn[rr * kNb + jj], Pn[rr * kNb + c], d);
+        // this row's entry of the unit reflector v (zero above the diagonal)
+        const double v = tid == jj ? (x0 - al) * inv : tid > jj ? xj * inv : 0.0;
+        // one reduction of kNb slots: slot c = sum over rows of x[c] v, which
+        // is v_c^T v (a column of T) for c < jj and v^T Y[:, c] for c > jj
+        double sl[kNb];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-          const double m2d = -2.0 * d;
-          for (int rr = jj + lane; rr < R; rr += 32) Pn[rr * kNb + c] = fma(m2d, Pn[rr * kNb + jj], Pn[rr * kNb + c]);
+        for (int c = 0; c < kNb; ++c) sl[c] = (live && c != jj) ? x[c] * v : 0.0;
+        const double part = warp_reduce_scatter16(sl, lane);
+        if ((lane & 1) == 0) red16[warp][lane >> 1] = part;
+        __syncthreads();
+        if (tid < kNb) {
+          double t = 0.0;
+          for (int q = 0; q < nw; ++q) t += red16[q][tid];
+          fin[tid] = t;
         }
         __syncthreads();
+        if (live) {
+          for (int c = jj + 1; c < nb; ++c) x[c] = fma(-2.0 * fin[c], v, x[c]);
+          x[jj] = v;
+        }
+        // T_jj = 2, T[0:jj, jj] = -2 T[0:jj, 0:jj] (V[:, 0:jj]^T v)
+        if (tid < jj) {
+          double t = 0.0;
+          for (int q = tid; q < jj; ++q) t = fma(Ts[tid][q], fin[q], t);
+          Ts[tid][jj] = -2.0 * t;
+        }
+        if (tid == jj) Ts[jj][jj] = 2.0;
+        if (tid == 0) alpha[j0 + jj] = al;
       }
-      // T (upper triangular): T_jj = 2, T[0:j, j] = -2 T[0:j, 0:j] (V[:, 0:j]^T v_j)
-      double* G = Ws;  // V^T V scratch (nb x nb)
-      for (int e = warp; e < nb * nb; e += nw) {
-        const int i = e / nb, j = e % nb;
-        double d = 0.0;
-        if (i < j)
-          for (int rr = j + lane; rr < R; rr += 32) d = fma(Pn[rr * kNb + i], Pn[rr * kNb + j], d);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        if (lane == 0) G[e] = d;
+      // V's rows go straight to their owners' V slices; T to the global copy
+      // that the accumulation of Q reads back
+      if (live) {
+        const int owner = r / rs;
+        double* dst = cluster.map_shared_rank(Vo, owner) + (size_t)(r - owner * rs) * l + j0;
+        for (int c = 0; c < nb; ++c) dst[c] = x[c];
       }
       __syncthreads();
-      if (tid == 0) {
-        for (int e = 0; e < kNb * kNb; ++e) Tp[e] = 0.0;
-        for (int j = 0; j < nb; ++j) {
-          for (int i = 0; i < j; ++i) {
-            double s = 0.0;
-            for (int t = i; t < j; ++t) s = fma(Tp[i * kNb + t], G[t * nb + j], s);
-            Tp[i * kNb + j] = -2.0 * s;
-          }
-          Tp[j * kNb + j] = 2.0;
-          for (int i = j + 1; i < kNb; ++i) Tp[i * kNb + j] = 0.0;
-        }
-      }
+      if (tid < kNb * kNb) Tp[tid] = Ts[tid / kNb][tid % kNb];
     }
-    cluster.sync();  // panel factored: V and T readable from rank 0
-    if (rank != 0 && tid < nb) alpha[j0 + tid] = cluster.map_shared_rank(alpha, 0)[j0 + tid];
-    {
-      const double* Pn0 = Pn;
-      for (int e = tid; e < nr * nb; e += kHhThreads) {
-        const int rr = e / nb, c = e % nb;
-        const int r = r0 + rr;
-        Vo[rr * l + j0 + c] = (r >= j0) ? Pn0[(r - j0) * kNb + c] : 0.0;
-      }
+    cluster.sync();  // panel factored: V in place everywhere, alpha and T readable from rank 0
+    if (rank != 0) {
+      if (tid < nb) alpha[j0 + tid] = cluster.map_shared_rank(alpha, 0)[j0 + tid];
+      if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = cluster.map_shared_rank(&Ts[0][0], 0)[tid];
     }
     __syncthreads();
     // trailing update of columns j0 + nb .. l-1: Y <- Y - V T^T (V^T Y)
@@ -594,7 +614,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __g
       for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {
         const int jj = e / wcols, c = c1 + e % wcols;
         double m = 0.0;
-        for (int ii = 0; ii <= jj; ++ii) m = fma(Tp[ii * kNb + jj], Ws[ii * l + c], m);
+        for (int ii = 0; ii <= jj; ++ii) m = fma(Ts[ii][jj], Ws[ii * l + c], m);
         mreg[cnt] = m;
       }
       __syncthreads();
@@ -626,6 +646,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __g
     const int wcols = l - j0;
     double* Wb = Wp;
     cluster.sync();  // the previous panel's remote reads of Wp are done
+    if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = Tp[tid];
     for (int e = tid; e < nb * wcols; e += kHhThreads) {
       const int jj = e / wcols, c = j0 + e % wcols;
       double d = 0.0;
@@ -646,7 +667,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_panel_kernel(const __g
       for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {  // (T W)_jj = sum_{ii >= jj} T[jj][ii] W_ii
         const int jj = e / wcols, c = j0 + e % wcols;
         double m = 0.0;
-        for (int ii = jj; ii < nb; ++ii) m = fma(Tp[jj * kNb + ii], Ws[ii * l + c], m);
+        for (int ii = jj; ii < nb; ++ii) m = fma(Ts[jj][ii], Ws[ii * l + c], m);
         mreg[cnt] = m;
       }
       __syncthreads();
@@ -761,7 +782,7 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
     const OrthJob<T>& J = b.job[i];
     const int cs = min(8, max(1, ceil_div(J.rows, 32)));
     const bool fits = panel_layout(J.rows, J.l, cs).total * sizeof(double) <= 110 * 1024;
-    if (J.l >= kNb && J.l <= 256 && fits) pb.job[pb.count++] = J;
+    if (J.l >= kNb && J.l <= 256 && J.rows <= kHhThreads && fits) pb.job[pb.count++] = J;
     else cb.job[cb.count++] = J;
   }
   if (pb.count > 0) {
