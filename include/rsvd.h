@@ -58,7 +58,7 @@ extern "C" {
 #define RSVD_WARN_CG            2   /* device (backward): a conjugate-gradient column did not converge (info.status) */
 
 /* Paths recorded in rsvd_info.path (bit set). */
-#define RSVD_PATH_EXACT         1   /* m <= l: Q = I, B = A (the sample covers the range) */
+#define RSVD_PATH_EXACT         1   /* m <= l and m <= 16: Q = I, B = A (the sample covers the range) */
 #define RSVD_PATH_HOUSEHOLDER   2   /* CholeskyQR2 broke down at least once; Householder QR used */
 
 /* Arithmetic of the products with A (the sketch, the power iteration and the
@@ -92,6 +92,9 @@ typedef struct {
   int jacobi_sweeps;   /* sweeps of the one-sided Jacobi SVD of B */
   int l;               /* sample width used */
   int rotations;       /* plane rotations applied by the Jacobi SVD (all sweeps) */
+  int qr_columns;      /* columns the last Householder QR factored before its trailing block
+                          fell to rounding level (l when it ran to the end; 0 if none ran):
+                          a numerical-rank estimate of the sample, rounded up to 16 */
 } rsvd_info;
 
 /*

@@ -70,6 +70,7 @@ class RsvdInfo(ctypes.Structure):
         ("jacobi_sweeps", ctypes.c_int),
         ("l", ctypes.c_int),
         ("rotations", ctypes.c_int),
+        ("qr_columns", ctypes.c_int),
     ]
 
 

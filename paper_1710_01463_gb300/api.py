@@ -42,9 +42,9 @@ def _require_cuda(*ts):
 
 
 def info_dicts(info):
-    """Decode a (batch, 6) int32 info tensor into a list of dicts."""
+    """Decode a (batch, INFO_INTS) int32 info tensor into a list of dicts."""
     rows = info.view(-1, _lib.INFO_INTS).cpu().tolist()
-    keys = ("status", "path", "chol_fallbacks", "jacobi_sweeps", "l", "rotations")
+    keys = ("status", "path", "chol_fallbacks", "jacobi_sweeps", "l", "rotations", "qr_columns")
     return [dict(zip(keys, r)) for r in rows]
 
 

@@ -117,6 +117,15 @@ size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int
 
 inline int sample_width(int m, int n, int k, int p) { return std::min(k + p, std::min(m, n)); }
 
+// When the sample spans the whole column space (m <= l), a small matrix skips
+// the sampling: Q = I, B = A.  Larger ones keep the sampled path with l = m:
+// Q is then square orthogonal (B = Q^T A has A's singular values) and the
+// power iteration aligns it with the left singular vectors, so the Jacobi SVD
+// of B converges in a few sweeps over its numerically nonzero rows instead of
+// many sweeps over all rows of A.
+constexpr int kExactMaxRows = 16;
+inline int use_exact_path(int m, int l) { return (m <= l && m <= kExactMaxRows) ? 1 : 0; }
+
 #define RSVD_TRY(x)                              \
   do {                                           \
     cudaError_t err__ = (x);                     \
@@ -230,6 +239,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       J.info = p.info;
       J.max_sweeps = p.max_sweeps;
       J.want_vt = 1;
+      J.want_p = p.want_u;
       J.pipe_err = tc_err ? p.flag + 1 : nullptr;
     }
     RSVD_TRY(launch_jacobi<T>(b, s));
@@ -582,7 +592,7 @@ int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* con
       if (pr.l > 256 || m[b] <= pr.l) return RSVD_ERR_INVALID_SIZE;
       if (((uintptr_t)A[b]) % 16 || ((size_t)lda[b] * eb) % 16) return RSVD_ERR_INVALID_SIZE;
     }
-    pr.exact = pr.m <= pr.l ? 1 : 0;
+    pr.exact = use_exact_path(pr.m, pr.l);
     pr.want_u = 1;
     pr.A = A[b]; pr.lda = lda[b];
     pr.S = S[b]; pr.U = U[b]; pr.ldu = ldu[b]; pr.Vt = Vt[b]; pr.ldvt = ldvt[b];
@@ -713,7 +723,7 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     Prob& pr = probs[b];
     std::memset(&pr, 0, sizeof(Prob));
     pr.m = m; pr.n = n; pr.k = k; pr.l = l;
-    pr.exact = m <= l ? 1 : 0;
+    pr.exact = use_exact_path(m, l);
     pr.want_u = 0;
     pr.A = th; pr.lda = n;
     pr.S = (double*)(wb + lay[b].S);

@@ -93,6 +93,7 @@ struct JacobiJob {
   rsvd_info* info;
   int max_sweeps;
   int want_vt;
+  int want_p = 1;                 // accumulate the rotations P (needed only for U~ = P^T)
   const int* pipe_err = nullptr;  // optional: nonzero when an earlier tensor-core pipeline wait timed out
 };
 template <typename T>

@@ -1,7 +1,8 @@
 // Small SVD of B = Q^T A (l x n, FP64): Alg. RSVD step 4 (Sec. II.B), the
 // rank-k TSVD of B.  One-sided Jacobi (Hestenes; Demmel-Veselic) on the ROWS
 // of B: plane rotations P B = W until the rows of W are mutually orthogonal;
-// then sigma_i = ||w_i||, V~ rows = w_i / sigma_i and U~ = P^T.
+// then sigma_i = ||w_i||, V~ rows = w_i / sigma_i and U~ = P^T (P is
+// accumulated only when U is wanted: the TEBD bond update uses S and V only).
 //
 // GB300 layout: one thread-block CLUSTER per matrix.  The n columns of B (and
 // the l columns of the rotation accumulator P) are split across the CTAs of
@@ -10,9 +11,10 @@
 // disjoint pairs per round, one team of 8 lanes per pair.  Per round every CTA
 // forms the partial inner products <b_i, b_j> of its column slice, the cluster
 // exchanges them through distributed shared memory (one cluster barrier per
-// round, double-buffered; lane r of a team reads rank r's partial), and every
-// CTA reduces them with the same shuffle tree - so all CTAs take bit-identical
-// rotation decisions - and rotates its own slice.
+// round, double-buffered), one lane per pair sums them in rank order and forms
+// the rotation - so all CTAs take bit-identical decisions, and the FP64
+// scalar work (square roots, divisions) occupies as few warps as possible -
+// and the teams rotate their own slice.
 //
 // Row norms are recomputed exactly at the start of every sweep and updated by
 // the rotation identities (alpha - t gamma, beta + t gamma) inside it.  A pair
@@ -65,8 +67,9 @@ __host__ __device__ inline JLayout jlayout(int l, int n, int csize) {
 }
 
 __host__ __device__ inline size_t jsmem_small(int l, const JLayout& L) {
-  // norms, nrm_part, gpart[2][npairs], order (int, padded to doubles)
-  return sizeof(double) * ((size_t)2 * l + 2 * (size_t)L.npairs + (size_t)(l + 1) / 2 + 1);
+  // norms, nrm_part, gpart[2][npairs], order (int, padded to doubles),
+  // rotation cosines and sines [npairs] and flags (int, padded)
+  return sizeof(double) * ((size_t)2 * l + 4 * (size_t)L.npairs + (size_t)(l + 1) / 2 + 1 + (size_t)(L.npairs + 1) / 2 + 1);
 }
 
 template <typename T>
@@ -85,6 +88,9 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   double* nrm_part = norms + l;
   double* gpart = nrm_part + l;                 // [2][npairs]
   int* order = (int*)(gpart + 2 * L.npairs);
+  double* rcs = gpart + 2 * L.npairs + (l + 1) / 2 + 1;  // per pair of the round: cos, sin, rotate?
+  double* rsn = rcs + L.npairs;
+  int* rfl = (int*)(rsn + L.npairs);
   double* Bs;
   double* Ps;
   if (b.use_global) {
@@ -107,10 +113,12 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
     const int i = e / L.nc, c = e % L.nc;
     Bs[e] = (c < ncl) ? J.Bm[(size_t)i * n + c0 + c] : 0.0;
   }
-  for (int e = tid; e < l * L.np; e += kJacobiThreads) {
-    const int i = e / L.np, c = e % L.np;
-    Ps[e] = (c < npl && i == p0 + c) ? 1.0 : 0.0;
-  }
+  const bool want_p = J.want_p != 0;
+  if (want_p)
+    for (int e = tid; e < l * L.np; e += kJacobiThreads) {
+      const int i = e / L.np, c = e % L.np;
+      Ps[e] = (c < npl && i == p0 + c) ? 1.0 : 0.0;
+    }
   if (tid == 0) nonfinite = 0;
   __syncthreads();
 
@@ -180,47 +188,52 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         if (tl == 0) gp[s] = g;
       }
       cluster.sync();
-      for (int s = team; s < npl2; s += nteam) {
+      // rotation scalars, one lane per pair, in as few warps as possible (a
+      // warp's FP64 instruction holds the SM's FP64 pipe for 16 cycles whatever
+      // the number of active lanes); every CTA sums the partials in rank order,
+      // so all CTAs of the cluster take bit-identical decisions
+      for (int s = tid; s < npl2; s += kJacobiThreads) {
         int a, bq;
         round_pair(r, s, lpl, a, bq);
-        if (bq >= nlive) continue;
-        const int i = live[a], j = live[bq];
-        const double al = norms[i], be = norms[j];
-        double g = 0.0;
-        for (int rr = tl; rr < C; rr += kTeam) g += cluster.map_shared_rank(gp, rr)[s];
-#pragma unroll
-        for (int o = kTeam / 2; o > 0; o >>= 1) g += __shfl_xor_sync(tmask, g, o, kTeam);
-        // rotation scalars on the team's lane 0 only (FP64 sqrt / divide are costly on this part)
-        double t = 0.0, cs = 1.0, sn = 0.0;
         int rot = 0;
-        if (tl == 0 && al > 0.0 && be > 0.0 && fabs(g) > tol * sqrt(al * be)) {
-          rot = 1;
-          const double zeta = (be - al) / (2.0 * g);
-          // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); 1 / (2 zeta) once zeta^2 would overflow
-          t = fabs(zeta) < 1e150 ? (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)) : 0.5 / zeta;
-          cs = 1.0 / sqrt(1.0 + t * t);
-          sn = cs * t;
+        double cs = 1.0, sn = 0.0;
+        if (bq < nlive) {
+          const int i = live[a], j = live[bq];
+          const double al = norms[i], be = norms[j];
+          double g = 0.0;
+          for (int rr = 0; rr < C; ++rr) g += cluster.map_shared_rank(gp, rr)[s];
+          if (al > 0.0 && be > 0.0 && fabs(g) > tol * sqrt(al * be)) {
+            rot = 1;
+            const double zeta = (be - al) / (2.0 * g);
+            // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); 1 / (2 zeta) once zeta^2 would overflow
+            const double t = fabs(zeta) < 1e150 ? (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)) : 0.5 / zeta;
+            cs = 1.0 / sqrt(1.0 + t * t);
+            sn = cs * t;
+            norms[i] = al - t * g;
+            norms[j] = be + t * g;
+            atomicAdd(&rot_count, 1);
+          }
         }
-        const int tb = (tid % 32) / kTeam * kTeam;
-        rot = __shfl_sync(tmask, rot, tb);
-        if (!rot) continue;
-        t = __shfl_sync(tmask, t, tb);
-        cs = __shfl_sync(tmask, cs, tb);
-        sn = __shfl_sync(tmask, sn, tb);
+        rcs[s] = cs;
+        rsn[s] = sn;
+        rfl[s] = rot;
+      }
+      __syncthreads();
+      for (int s = team; s < npl2; s += nteam) {
+        if (!rfl[s]) continue;  // team-uniform
+        int a, bq;
+        round_pair(r, s, lpl, a, bq);
+        const int i = live[a], j = live[bq];
+        const double cs = rcs[s], sn = rsn[s];
         for (int c = tl; c < ncl; c += kTeam) {
           const double x = Bs[i * L.nc + c], y = Bs[j * L.nc + c];
           Bs[i * L.nc + c] = cs * x - sn * y;
           Bs[j * L.nc + c] = sn * x + cs * y;
         }
-        for (int c = tl; c < npl; c += kTeam) {
+        for (int c = tl; want_p && c < npl; c += kTeam) {
           const double x = Ps[i * L.np + c], y = Ps[j * L.np + c];
           Ps[i * L.np + c] = cs * x - sn * y;
           Ps[j * L.np + c] = sn * x + cs * y;
-        }
-        if (tl == 0) {
-          norms[i] = al - t * g;
-          norms[j] = be + t * g;
-          atomicAdd(&rot_count, 1);
         }
       }
       __syncthreads();
@@ -274,10 +287,11 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
       J.Vt[(size_t)r * J.ldvt + c0 + c] = (T)(v > 0.0 ? Bs[src * L.nc + c] / v : 0.0);
     }
   }
-  for (int e = tid; e < k * npl; e += kJacobiThreads) {
-    const int r = e / npl, c = e % npl;
-    J.Ps[(size_t)r * l + p0 + c] = (T)Ps[order[r] * L.np + c];
-  }
+  if (want_p)
+    for (int e = tid; e < k * npl; e += kJacobiThreads) {
+      const int r = e / npl, c = e % npl;
+      J.Ps[(size_t)r * l + p0 + c] = (T)Ps[order[r] * L.np + c];
+    }
   cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 

@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
   if (rank == 0 && tid == 0) {
     if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
     atomicOr(&J.info->path, RSVD_PATH_HOUSEHOLDER);
+    J.info->qr_columns = l;
   }
   cluster.sync();  // no CTA leaves while others may read its shared memory
 }
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   __shared__ double fin[kNb];
   __shared__ double Ts[kNb][kNb];  // T of the current panel
   __shared__ double x0s;
+  __shared__ double sc[2];
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = kHhThreads / 32;
 
   for (int e = tid; e < nr * l; e += kHhThreads) {
@@ -503,19 +505,28 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       if (p == 0) fro0 = t;
     }
     __syncthreads();
-    // early end: the rest of Y is rounding noise (below 2^-52 of ||Y||_F); the
-    // remaining columns of Q are completed by the reflectors applied so far
-    if (p > 0 && !(trail_sum > fro0 * 0x1.0p-104)) {
+    // early end: the rest of Y is rounding noise.  The trailing block of a
+    // numerically rank-deficient sample settles near 2^-52 ||Y||_F (the
+    // rounding of the products and of the reflections); below 2^-51 ||Y||_F it
+    // is dropped, which moves no singular value by more than 2^-51 sqrt(l)
+    // sigma_1 (< 1e-14 sigma_1 for l <= 256).  The remaining columns of Q are
+    // completed by the reflectors applied so far.
+    if (p > 0 && !(trail_sum > fro0 * 0x1.0p-102)) {
       npanel_used = p;
       break;  // identical decision in every CTA of the cluster
     }
     if (rank == 0) {
       // one panel row per thread (rows <= kHhThreads is a launch condition):
       // x[c] = Pan[tid][c] = Y[j0 + tid, j0 + c]; columns c < jj are replaced by
-      // the reflectors v_c as they are formed
+      // the reflectors v_c as they are formed.  FP64 issue is the scarce
+      // resource (a warp instruction holds the SM's FP64 pipe for 16 cycles):
+      // only the warps that hold panel rows compute, and the reflector scalars
+      // and T's column are formed by warp 0 alone.
       double* x = Wp + (size_t)tid * kPanStride;
       const int r = j0 + tid;
       const bool live = tid < R;
+      const int nlw = (R + 31) / 32;  // warps holding panel rows
+      const bool wlive = warp < nlw;
       if (live) {
         const int owner = r / rs;
         const double* src = cluster.map_shared_rank(Ys, owner) + (size_t)(r - owner * rs) * l + j0;
@@ -524,52 +535,66 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       }
       if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = 0.0;
       for (int jj = 0; jj < nb; ++jj) {
-        // squared norm of column jj over panel rows jj .. R-1
-        const double xj = live ? x[jj] : 0.0;
-        double a = (tid >= jj) ? xj * xj : 0.0;
+        if (wlive) {  // squared norm of column jj over panel rows jj .. R-1
+          const double xj = live ? x[jj] : 0.0;
+          double a = tid >= jj ? xj * xj : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) red1[warp] = a;
-        if (tid == jj) x0s = xj;
-        __syncthreads();
-        double nrm2 = 0.0;
-        for (int q = 0; q < nw; ++q) nrm2 += red1[q];  // same order in every thread
-        const double x0 = x0s;
-        double al = 0.0, inv = 0.0;
-        if (nrm2 > 0.0) {
-          al = x0 >= 0.0 ? -sqrt(nrm2) : sqrt(nrm2);
-          const double w0 = x0 - al;
-          const double vn2 = nrm2 - x0 * x0 + w0 * w0;
-          inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          if (lane == 0) red1[warp] = a;
+          if (tid == jj) x0s = xj;
         }
-        // this row's entry of the unit reflector v (zero above the diagonal)
-        const double v = tid == jj ? (x0 - al) * inv : tid > jj ? xj * inv : 0.0;
-        // one reduction of kNb slots: slot c = sum over rows of x[c] v, which
-        // is v_c^T v (a column of T) for c < jj and v^T Y[:, c] for c > jj
-        double sl[kNb];
-#pragma unroll
-        for (int c = 0; c < kNb; ++c) sl[c] = (live && c != jj) ? x[c] * v : 0.0;
-        const double part = warp_reduce_scatter16(sl, lane);
-        if ((lane & 1) == 0) red16[warp][lane >> 1] = part;
         __syncthreads();
-        if (tid < kNb) {
+        if (warp == 0) {
+          double a = lane < nlw ? red1[lane] : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          if (lane == 0) {
+            const double x0 = x0s;
+            double al = 0.0, inv = 0.0;
+            if (a > 0.0) {
+              al = x0 >= 0.0 ? -sqrt(a) : sqrt(a);
+              const double w0 = x0 - al;
+              const double vn2 = a - x0 * x0 + w0 * w0;
+              inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
+            }
+            sc[0] = inv;
+            sc[1] = (x0 - al) * inv;  // v at row jj
+            alpha[j0 + jj] = al;
+            Ts[jj][jj] = 2.0;
+          }
+        }
+        __syncthreads();
+        double v = 0.0;
+        if (wlive) {
+          // this row's entry of the unit reflector v (zero above the diagonal),
+          // then one reduction of kNb slots: slot c = sum over rows of x[c] v,
+          // which is v_c^T v (a column of T) for c < jj and v^T Y[:, c] for c > jj
+          v = tid == jj ? sc[1] : (live && tid > jj) ? x[jj] * sc[0] : 0.0;
+          double sl[kNb];
+#pragma unroll
+          for (int c = 0; c < kNb; ++c) sl[c] = (live && c != jj) ? x[c] * v : 0.0;
+          const double part = warp_reduce_scatter16(sl, lane);
+          if ((lane & 1) == 0) red16[warp][lane >> 1] = part;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          double f = 0.0;
+          if (lane < kNb)
+            for (int q = 0; q < nlw; ++q) f += red16[q][lane];
+          if (lane < kNb) fin[lane] = lane > jj ? -2.0 * f : f;
+          // T[0:jj, jj] = -2 T[0:jj, 0:jj] (V[:, 0:jj]^T v): lane i sums q = i .. jj-1
           double t = 0.0;
-          for (int q = 0; q < nw; ++q) t += red16[q][tid];
-          fin[tid] = t;
+          for (int q = 0; q < jj; ++q) {
+            const double fq = __shfl_sync(0xffffffffu, f, q);
+            if (lane <= q) t = fma(Ts[lane][q], fq, t);
+          }
+          if (lane < jj) Ts[lane][jj] = -2.0 * t;
         }
         __syncthreads();
         if (live) {
-          for (int c = jj + 1; c < nb; ++c) x[c] = fma(-2.0 * fin[c], v, x[c]);
+          for (int c = jj + 1; c < nb; ++c) x[c] = fma(fin[c], v, x[c]);
           x[jj] = v;
         }
-        // T_jj = 2, T[0:jj, jj] = -2 T[0:jj, 0:jj] (V[:, 0:jj]^T v)
-        if (tid < jj) {
-          double t = 0.0;
-          for (int q = tid; q < jj; ++q) t = fma(Ts[tid][q], fin[q], t);
-          Ts[tid][jj] = -2.0 * t;
-        }
-        if (tid == jj) Ts[jj][jj] = 2.0;
-        if (tid == 0) alpha[j0 + jj] = al;
       }
       // V's rows go straight to their owners' V slices; T to the global copy
       // that the accumulation of Q reads back
@@ -587,14 +612,16 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = cluster.map_shared_rank(&Ts[0][0], 0)[tid];
     }
     __syncthreads();
-    // trailing update of columns j0 + nb .. l-1: Y <- Y - V T^T (V^T Y)
+    // trailing update of columns j0 + nb .. l-1: Y <- Y - V T^T (V^T Y); V is
+    // zero on the rows above j0, which neither contribute nor change
     const int c1 = j0 + nb, wcols = l - c1;
+    const int rr0 = max(0, min(nr, j0 - r0));  // first own row at or below j0
     double* Wb = Wp;
     if (wcols > 0) {
       for (int e = tid; e < nb * wcols; e += kHhThreads) {
         const int jj = e / wcols, c = c1 + e % wcols;
         double d = 0.0;
-        for (int rr = 0; rr < nr; ++rr) d = fma(Vo[rr * l + j0 + jj], Ys[rr * l + c], d);
+        for (int rr = rr0; rr < nr; ++rr) d = fma(Vo[rr * l + j0 + jj], Ys[rr * l + c], d);
         Wb[jj * l + c] = d;
       }
     }
@@ -624,8 +651,8 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
         Ws[jj * l + c] = mreg[cnt];
       }
       __syncthreads();
-      for (int e = tid; e < nr * wcols; e += kHhThreads) {
-        const int rr = e / wcols, c = c1 + e % wcols;
+      for (int e = tid; e < (nr - rr0) * wcols; e += kHhThreads) {
+        const int rr = rr0 + e / wcols, c = c1 + e % wcols;
         double y = Ys[rr * l + c];
         for (int jj = 0; jj < nb; ++jj) y = fma(-Vo[rr * l + j0 + jj], Ws[jj * l + c], y);
         Ys[rr * l + c] = y;
@@ -644,13 +671,14 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     const int j0 = p * kNb, nb = min(kNb, l - j0);
     const double* Tp = Tall + (size_t)p * kNb * kNb;
     const int wcols = l - j0;
+    const int rr0 = max(0, min(nr, j0 - r0));  // rows above j0: V is zero there
     double* Wb = Wp;
     cluster.sync();  // the previous panel's remote reads of Wp are done
     if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = Tp[tid];
     for (int e = tid; e < nb * wcols; e += kHhThreads) {
       const int jj = e / wcols, c = j0 + e % wcols;
       double d = 0.0;
-      for (int rr = 0; rr < nr; ++rr) d = fma(Vo[rr * l + j0 + jj], Ys[rr * l + c], d);
+      for (int rr = rr0; rr < nr; ++rr) d = fma(Vo[rr * l + j0 + jj], Ys[rr * l + c], d);
       Wb[jj * l + c] = d;
     }
     cluster.sync();
@@ -678,8 +706,8 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       }
     }
     __syncthreads();
-    for (int e = tid; e < nr * wcols; e += kHhThreads) {
-      const int rr = e / wcols, c = j0 + e % wcols;
+    for (int e = tid; e < (nr - rr0) * wcols; e += kHhThreads) {
+      const int rr = rr0 + e / wcols, c = j0 + e % wcols;
       double q = Ys[rr * l + c];
       for (int jj = 0; jj < nb; ++jj) q = fma(-Vo[rr * l + j0 + jj], Ws[jj * l + c], q);
       Ys[rr * l + c] = q;
@@ -694,6 +722,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   if (rank == 0 && tid == 0) {
     if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
     atomicOr(&J.info->path, RSVD_PATH_HOUSEHOLDER);
+    J.info->qr_columns = min(l, npanel_used * kNb);
   }
   cluster.sync();  // no CTA leaves while others may read its shared memory
 }
