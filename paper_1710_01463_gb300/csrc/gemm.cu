@@ -17,8 +17,8 @@ namespace {
 constexpr int NT = 256;  // threads per CTA (a 16 x 16 grid)
 
 // BM x BN output tile, K slices of BK through shared memory (double
-// buffered via registers), a TM x TM register tile per thread with a stride-16
-// layout: 64 x 64 / 4 x 4 / BK 16.
+// buffered via registers), a TM x TN register tile per thread with a stride-16
+// layout: BM / 16 x BN / 16 per thread, BK 16.
 template <typename Tin, bool TA, int BM, int BK>
 __device__ __forceinline__ void load_a(const Tin* __restrict__ A, int lda, int M, int K, int m0, int k0,
                                        Tin (&ra)[BM * BK / NT]) {
@@ -184,22 +184,51 @@ cudaError_t launch_tile(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Tile shape per launch: 64 x 64, 64 x 48 or 48 x 64, whichever computes the
-// fewest padded outputs over the batch (the sample widths l are not multiples
-// of 64: l = 138 fills 144 of a 48-wide tiling and only 138 of 192 otherwise).
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+  }
+  return n;
+}
+
+// Tile shape per launch.  The FMA loop of every shape keeps the SM's FP64 pipe
+// busy, so an FP64 launch takes about as long as its most loaded SM:
+// ceil(tiles / SMs) x tile area.  Small batches of narrow products (the sample
+// widths l are not multiples of 64) waste most of that on idle SMs with 64-wide
+// tiles, so FP64 launches also consider 32-row and 32-column tiles.  FP32
+// tiles of 32 would be bound by shared-memory loads (FFMA issues 64 times
+// faster than DFMA); FP32 picks the shape with the fewest padded outputs.
 template <typename Tin, typename Tout, bool TA, bool TX>
 cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
   if (b.count <= 0) return cudaSuccess;
-  long long w[3] = {0, 0, 0};
-  const int bm[3] = {64, 64, 48}, bn[3] = {64, 48, 64};
-  for (int i = 0; i < b.count; ++i)
-    for (int t = 0; t < 3; ++t)
-      w[t] += (long long)ceil_div(b.job[i].M, bm[t]) * bm[t] * ceil_div(b.job[i].N, bn[t]) * bn[t];
+  constexpr bool f64 = sizeof(Tin) == 8;
+  constexpr int ns = f64 ? 6 : 3;
+  const int bm[6] = {64, 64, 48, 48, 32, 32}, bn[6] = {64, 48, 64, 32, 48, 32};
+  long long cost[6];
+  const long long sms = sm_count();
+  for (int t = 0; t < ns; ++t) {
+    long long tiles = 0, padded = 0;
+    for (int i = 0; i < b.count; ++i) {
+      const long long tm = ceil_div(b.job[i].M, bm[t]), tn = ceil_div(b.job[i].N, bn[t]);
+      tiles += tm * tn;
+      padded += tm * bm[t] * tn * bn[t];
+    }
+    cost[t] = f64 ? (tiles + sms - 1) / sms * bm[t] * bn[t] : padded;
+  }
   int best = 0;
-  for (int t = 1; t < 3; ++t)
-    if (w[t] < w[best]) best = t;
-  if (best == 1) return launch_tile<Tin, Tout, TA, TX, 64, 48>(b, s);
-  if (best == 2) return launch_tile<Tin, Tout, TA, TX, 48, 64>(b, s);
+  for (int t = 1; t < ns; ++t)
+    if (cost[t] < cost[best]) best = t;
+  switch (best) {
+    case 1: return launch_tile<Tin, Tout, TA, TX, 64, 48>(b, s);
+    case 2: return launch_tile<Tin, Tout, TA, TX, 48, 64>(b, s);
+    case 3: if constexpr (f64) return launch_tile<Tin, Tout, TA, TX, 48, 32>(b, s); break;
+    case 4: if constexpr (f64) return launch_tile<Tin, Tout, TA, TX, 32, 48>(b, s); break;
+    case 5: if constexpr (f64) return launch_tile<Tin, Tout, TA, TX, 32, 32>(b, s); break;
+    default: break;
+  }
   return launch_tile<Tin, Tout, TA, TX, 64, 64>(b, s);
 }
 
