@@ -36,6 +36,7 @@ namespace rsvd {
 namespace {
 
 constexpr int kJacobiThreads = 512;
+constexpr int kMaxCluster = 16;  // cluster sizes up to 16 (non-portable above 8)
 constexpr int kTeam = 8;   // lanes per row pair; lane t of a team reads the partials of ranks t, t + 8
 constexpr size_t kSmemBudget = 220 * 1024;
 
@@ -200,14 +201,28 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         if (bq < nlive) {
           const int i = live[a], j = live[bq];
           const double al = norms[i], be = norms[j];
+          double pv[kMaxCluster];  // all remote loads in flight at once, summed in rank order
+#pragma unroll
+          for (int rr = 0; rr < kMaxCluster; ++rr) pv[rr] = rr < C ? cluster.map_shared_rank(gp, rr)[s] : 0.0;
           double g = 0.0;
-          for (int rr = 0; rr < C; ++rr) g += cluster.map_shared_rank(gp, rr)[s];
+#pragma unroll
+          for (int rr = 0; rr < kMaxCluster; ++rr)
+            if (rr < C) g += pv[rr];
           if (al > 0.0 && be > 0.0 && fabs(g) > tol * sqrt(al * be)) {
             rot = 1;
-            const double zeta = (be - al) / (2.0 * g);
-            // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); 1 / (2 zeta) once zeta^2 would overflow
-            const double t = fabs(zeta) < 1e150 ? (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)) : 0.5 / zeta;
-            cs = 1.0 / sqrt(1.0 + t * t);
+            // tan of the rotation angle: with zeta = (be - al) / (2g),
+            // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) = 2g sign(h) / (|h| + sqrt(h^2 + 4g^2)),
+            // h = be - al (one square root and one division); the zeta form
+            // (1 / (2 zeta) once zeta^2 would overflow) where h^2 or g^2 could overflow
+            const double h = be - al;
+            double t;
+            if (fabs(h) < 1e150 && fabs(g) < 1e150) {
+              t = (h >= 0.0 ? 2.0 * g : -2.0 * g) / (fabs(h) + sqrt(fma(h, h, 4.0 * g * g)));
+            } else {
+              const double zeta = h / (2.0 * g);
+              t = fabs(zeta) < 1e150 ? (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)) : 0.5 / zeta;
+            }
+            cs = rsqrt(fma(t, t, 1.0));
             sn = cs * t;
             norms[i] = al - t * g;
             norms[j] = be + t * g;

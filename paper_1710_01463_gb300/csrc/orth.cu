@@ -387,10 +387,12 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
 // (compact WY form, H_j0 ... H_j1-1 = I - V T V^T): rank 0 of the cluster
 // gathers the panel's rows through distributed shared memory and factors it
 // alone (block-level barriers only), every CTA then applies I - V T^T V^T to
-// its rows of the trailing columns with one cluster exchange of V^T Y.  Q is
-// accumulated backwards panel by panel, one exchange per panel.  Three cluster
+// its rows of the trailing columns: partial products V^T Y per CTA, each CTA
+// sums and transforms one slice of the columns, and the slices are exchanged.
+// Q is accumulated backwards panel by panel the same way.  Four cluster
 // barriers per panel instead of three per column.
 constexpr int kNb = 16;
+constexpr int kPanelMaxCluster = 8;  // the blocked kernel runs on portable cluster sizes
 
 struct PanelLayout {
   size_t ys, vo, wp, ws, alpha, total;  // shared-memory offsets in doubles
@@ -434,6 +436,58 @@ __device__ __forceinline__ double warp_reduce_scatter16(double (&a)[kNb], int la
     }
   }
   return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
+// After every CTA of the cluster has written its partial V^T Y for columns
+// c0 .. c0 + wcols - 1 into Wb (kNb x l rows), forms W = the sum of the
+// partials and M = T^T W (kTW = false, trailing update) or M = T W (kTW =
+// true, accumulation of Q), and leaves all of M in every CTA's Ws.  Each CTA
+// sums and transforms its own slice of the columns only (no FP64 work is
+// repeated across the cluster) and then gathers the other slices.  Called by
+// every CTA of the cluster (it contains a cluster barrier).
+template <bool kTW>
+__device__ void cluster_sum_apply_t(cg::cluster_group& cluster, int rank, int C, const double* Wb, double* Ws,
+                                    const double (*Ts)[kNb], int nb, int l, int c0, int wcols) {
+  const int tid = threadIdx.x;
+  const int cw = (wcols + C - 1) / C;
+  const int cb = c0 + rank * cw, w = max(0, min(c0 + wcols, cb + cw) - cb);
+  for (int e = tid; e < nb * w; e += kHhThreads) {
+    const int jj = e / w, c = cb + e % w;
+    double pv[kPanelMaxCluster];  // every remote load in flight at once, summed in rank order
+#pragma unroll
+    for (int r = 0; r < kPanelMaxCluster; ++r) pv[r] = r < C ? cluster.map_shared_rank(Wb, r)[jj * l + c] : 0.0;
+    double d = 0.0;
+#pragma unroll
+    for (int r = 0; r < kPanelMaxCluster; ++r)
+      if (r < C) d += pv[r];
+    Ws[jj * l + c] = d;
+  }
+  __syncthreads();
+  double mreg[(kNb * 256 + kHhThreads - 1) / kHhThreads];
+  int cnt = 0;
+  for (int e = tid; e < nb * w; e += kHhThreads, ++cnt) {
+    const int jj = e / w, c = cb + e % w;
+    double m = 0.0;
+    if (kTW) {
+      for (int ii = jj; ii < nb; ++ii) m = fma(Ts[jj][ii], Ws[ii * l + c], m);
+    } else {
+      for (int ii = 0; ii <= jj; ++ii) m = fma(Ts[ii][jj], Ws[ii * l + c], m);
+    }
+    mreg[cnt] = m;
+  }
+  __syncthreads();
+  cnt = 0;
+  for (int e = tid; e < nb * w; e += kHhThreads, ++cnt) {
+    const int jj = e / w, c = cb + e % w;
+    Ws[jj * l + c] = mreg[cnt];
+  }
+  cluster.sync();  // every slice of M is complete
+  for (int e = tid; e < nb * wcols; e += kHhThreads) {
+    const int jj = e / wcols, c = c0 + e % wcols;
+    const int owner = (c - c0) / cw;
+    if (owner != rank) Ws[jj * l + c] = cluster.map_shared_rank(Ws, owner)[jj * l + c];
+  }
+  __syncthreads();
 }
 
 template <typename T>
@@ -555,7 +609,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
               al = x0 >= 0.0 ? -sqrt(a) : sqrt(a);
               const double w0 = x0 - al;
               const double vn2 = a - x0 * x0 + w0 * w0;
-              inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
+              inv = vn2 > 0.0 ? rsqrt(vn2) : 0.0;
             }
             sc[0] = inv;
             sc[1] = (x0 - al) * inv;  // v at row jj
@@ -627,30 +681,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     }
     cluster.sync();
     if (wcols > 0) {
-      // W = sum over ranks of the partials, one (jj, c) entry per thread
-      for (int e = tid; e < nb * wcols; e += kHhThreads) {
-        const int jj = e / wcols, c = c1 + e % wcols;
-        double d = 0.0;
-        for (int r = 0; r < C; ++r) d += cluster.map_shared_rank(Wb, r)[jj * l + c];
-        Ws[jj * l + c] = d;
-      }
-      __syncthreads();
-      // M = T^T W, (T^T W)_jj = sum_{ii <= jj} T[ii][jj] W_ii; kept in registers across the barrier
-      double mreg[(kNb * 256 + kHhThreads - 1) / kHhThreads];
-      int cnt = 0;
-      for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {
-        const int jj = e / wcols, c = c1 + e % wcols;
-        double m = 0.0;
-        for (int ii = 0; ii <= jj; ++ii) m = fma(Ts[ii][jj], Ws[ii * l + c], m);
-        mreg[cnt] = m;
-      }
-      __syncthreads();
-      cnt = 0;
-      for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {
-        const int jj = e / wcols, c = c1 + e % wcols;
-        Ws[jj * l + c] = mreg[cnt];
-      }
-      __syncthreads();
+      cluster_sum_apply_t<false>(cluster, rank, C, Wb, Ws, Ts, nb, l, c1, wcols);
       for (int e = tid; e < (nr - rr0) * wcols; e += kHhThreads) {
         const int rr = rr0 + e / wcols, c = c1 + e % wcols;
         double y = Ys[rr * l + c];
@@ -682,30 +713,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       Wb[jj * l + c] = d;
     }
     cluster.sync();
-    for (int e = tid; e < nb * wcols; e += kHhThreads) {
-      const int jj = e / wcols, c = j0 + e % wcols;
-      double d = 0.0;
-      for (int r = 0; r < C; ++r) d += cluster.map_shared_rank(Wb, r)[jj * l + c];
-      Ws[jj * l + c] = d;
-    }
-    __syncthreads();
-    {
-      double mreg[(kNb * 256 + kHhThreads - 1) / kHhThreads];
-      int cnt = 0;
-      for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {  // (T W)_jj = sum_{ii >= jj} T[jj][ii] W_ii
-        const int jj = e / wcols, c = j0 + e % wcols;
-        double m = 0.0;
-        for (int ii = jj; ii < nb; ++ii) m = fma(Ts[jj][ii], Ws[ii * l + c], m);
-        mreg[cnt] = m;
-      }
-      __syncthreads();
-      cnt = 0;
-      for (int e = tid; e < nb * wcols; e += kHhThreads, ++cnt) {
-        const int jj = e / wcols, c = j0 + e % wcols;
-        Ws[jj * l + c] = mreg[cnt];
-      }
-    }
-    __syncthreads();
+    cluster_sum_apply_t<true>(cluster, rank, C, Wb, Ws, Ts, nb, l, j0, wcols);
     for (int e = tid; e < (nr - rr0) * wcols; e += kHhThreads) {
       const int rr = rr0 + e / wcols, c = j0 + e % wcols;
       double q = Ys[rr * l + c];
@@ -809,7 +817,7 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
   pb.max_tilepairs = cb.max_tilepairs = b.max_tilepairs;
   for (int i = 0; i < b.count; ++i) {
     const OrthJob<T>& J = b.job[i];
-    const int cs = min(8, max(1, ceil_div(J.rows, 32)));
+    const int cs = min(kPanelMaxCluster, max(1, ceil_div(J.rows, 32)));
     const bool fits = panel_layout(J.rows, J.l, cs).total * sizeof(double) <= 110 * 1024;
     if (J.l >= kNb && J.l <= 256 && J.rows <= kHhThreads && fits) pb.job[pb.count++] = J;
     else cb.job[cb.count++] = J;
@@ -817,7 +825,7 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
   if (pb.count > 0) {
     int maxrows = 1;
     for (int i = 0; i < pb.count; ++i) maxrows = max(maxrows, pb.job[i].rows);
-    const int pcs = min(8, max(1, ceil_div(maxrows, 32)));
+    const int pcs = min(kPanelMaxCluster, max(1, ceil_div(maxrows, 32)));
     size_t psmem = 0;
     for (int i = 0; i < pb.count; ++i)
       psmem = max(psmem, panel_layout(pb.job[i].rows, pb.job[i].l, pcs).total * sizeof(double));
