@@ -455,9 +455,8 @@ def run_workload(args):
     g = torch.Generator(device="cpu").manual_seed(1234 + rank)
 
     def ortho(nn, seed):
-        G = torch.from_numpy(np.random.default_rng(seed).standard_normal((nn, nn))).to(dev)
-        Q, R = torch.linalg.qr(G)
-        return Q * torch.sign(torch.diagonal(R))[None, :]
+        # seeded orthogonal factor, formed on the host (no solver library on the device side)
+        return torch.from_numpy(inputs.haar_like_orthogonal(nn, seed)).to(dev)
 
     if wl == "dense":
         m = n = 256

@@ -218,10 +218,14 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       RSVD_TRY((launch_transpose<double, T>(x, s)));
     }
   }
+  // one launch per (cluster size, storage) group; the groups are independent
+  // and run concurrently, the first on s and the others on side streams
   std::vector<int> done(cnt, 0);
+  std::vector<JacobiBatch<T>> groups;
   for (int i0 = 0; i0 < cnt; ++i0) {
     if (done[i0]) continue;
-    JacobiBatch<T> b;
+    groups.emplace_back();
+    JacobiBatch<T>& b = groups.back();
     b.count = 0;
     b.csize = probs[i0].csize;
     b.use_global = probs[i0].use_global;
@@ -242,7 +246,18 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       J.want_p = p.want_u;
       J.pipe_err = tc_err ? p.flag + 1 : nullptr;
     }
-    RSVD_TRY(launch_jacobi<T>(b, s));
+  }
+  {
+    const int ng = (int)groups.size();
+    const int nside = std::min(ng - 1, kSideStreams);
+    SideStreams* ss = nullptr;
+    if (nside > 0) {
+      ss = side_streams();
+      if (!ss) return RSVD_ERR_LAUNCH;
+      RSVD_TRY(fork_side(ss, nside, s));
+    }
+    for (int g = 0; g < ng; ++g) RSVD_TRY(launch_jacobi<T>(groups[g], g == 0 ? s : ss->stream[(g - 1) % kSideStreams]));
+    if (ss) RSVD_TRY(join_side(ss, nside, s));
   }
   if (!wide.empty()) {  // V^T = W Q_b^T
     GemmBatch<T, T> g;

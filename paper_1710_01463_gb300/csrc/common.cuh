@@ -298,6 +298,18 @@ cudaError_t launch_bw_colscale(const BwScaleBatch<T>& b, cudaStream_t s);
 // last CUDA error seen by a launch of this library (per host thread)
 cudaError_t& last_cuda_error();
 
+// Side streams for independent groups of work within one call (streams.cu).
+constexpr int kSideStreams = 4;
+struct SideStreams {
+  bool ready = false;
+  cudaStream_t stream[kSideStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSideStreams] = {};
+};
+SideStreams* side_streams();                               // this thread's, for the current device; null on failure
+cudaError_t fork_side(SideStreams* ss, int n, cudaStream_t s);  // side streams 0..n-1 wait for s's work so far
+cudaError_t join_side(SideStreams* ss, int n, cudaStream_t s);  // s waits for side streams 0..n-1
+
 // shared-memory budget of the Jacobi kernel for given sizes (bytes), and the
 // cluster size chosen for them
 int jacobi_cluster_size(int l, int n);

@@ -312,11 +312,13 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
 
 }  // namespace
 
+// One CTA per 32 columns, up to eight (sixteen when a slice of eight does not
+// fit in shared memory).  Depends on the matrix alone, so no matrix's rounding
+// depends on the rest of its batch.
 int jacobi_cluster_size(int l, int n) {
   int c = n / 32;
   if (c < 1) c = 1;
   if (c > 8) c = 8;
-  // grow to 16 when a slice of 8 would not fit in shared memory
   if (c == 8 && !jacobi_fits_smem(l, n, 8) && jacobi_fits_smem(l, n, 16)) c = 16;
   return c;
 }

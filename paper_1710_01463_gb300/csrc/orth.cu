@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
                                                                   int use_global) {
   cg::cluster_group cluster = cg::this_cluster();
   const OrthJob<T>& J = b.job[blockIdx.y];
-  if (*J.flag == 0) return;  // cluster-uniform: one matrix per cluster
+  if (!J.hh_first && *J.flag == 0) return;  // cluster-uniform: one matrix per cluster
   const int C = csize;
   const int rank = (int)cluster.block_rank();
   const int rows = J.rows, l = J.l;
@@ -494,7 +494,7 @@ template <typename T>
 __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const __grid_constant__ OrthBatch<T> b, int csize) {
   cg::cluster_group cluster = cg::this_cluster();
   const OrthJob<T>& J = b.job[blockIdx.y];
-  if (*J.flag == 0) return;  // cluster-uniform
+  if (!J.hh_first && *J.flag == 0) return;  // cluster-uniform
   const int C = csize;
   const int rank = (int)cluster.block_rank();
   const int rows = J.rows, l = J.l;
@@ -751,7 +751,7 @@ cudaError_t launch_prep(const PrepBatch<T>& b, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
+cudaError_t launch_cholqr2(const OrthBatch<T>& b, cudaStream_t s) {
   if (b.count <= 0) return cudaSuccess;
   int maxl = 1, maxchunk = 1, maxtp = 1;
   long long maxll = 1;
@@ -808,24 +808,27 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
     e = launch_gemm<T, T, false, false>(g, s);
     if (e != cudaSuccess) return e;
   }
-  // fallback for flagged matrices: Householder QR of the original sample
-  // Householder for flagged matrices: the blocked kernel for matrices with
-  // l >= kNb whose shared-memory slices fit, the column kernel for the rest
+  return cudaGetLastError();
+}
+
+// Householder QR of the matrices of b that are flagged (or Householder-first):
+// the blocked kernel for matrices with l >= kNb whose shared-memory slices
+// fit, the column kernel for the rest.
+template <typename T>
+cudaError_t launch_householder(const OrthBatch<T>& b, cudaStream_t s) {
+  cudaError_t e;
   OrthBatch<T> pb, cb;
   pb.count = cb.count = 0;
   pb.max_chunks = cb.max_chunks = b.max_chunks;
   pb.max_tilepairs = cb.max_tilepairs = b.max_tilepairs;
   for (int i = 0; i < b.count; ++i) {
     const OrthJob<T>& J = b.job[i];
-    const int cs = min(kPanelMaxCluster, max(1, ceil_div(J.rows, 32)));
-    const bool fits = panel_layout(J.rows, J.l, cs).total * sizeof(double) <= 110 * 1024;
+    const bool fits = panel_layout(J.rows, J.l, kPanelMaxCluster).total * sizeof(double) <= 110 * 1024;
     if (J.l >= kNb && J.l <= 256 && J.rows <= kHhThreads && fits) pb.job[pb.count++] = J;
     else cb.job[cb.count++] = J;
   }
   if (pb.count > 0) {
-    int maxrows = 1;
-    for (int i = 0; i < pb.count; ++i) maxrows = max(maxrows, pb.job[i].rows);
-    const int pcs = min(kPanelMaxCluster, max(1, ceil_div(maxrows, 32)));
+    const int pcs = kPanelMaxCluster;  // fixed: no matrix's rounding depends on the rest of its batch
     size_t psmem = 0;
     for (int i = 0; i < pb.count; ++i)
       psmem = max(psmem, panel_layout(pb.job[i].rows, pb.job[i].l, pcs).total * sizeof(double));
@@ -893,6 +896,45 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
+}
+
+// Orthonormalisation of a batch of samples (Alg. RSVD steps 2-3).  Nearly
+// square samples go to Householder QR directly (hh_first), the others to
+// CholeskyQR2 with Householder as the fallback on breakdown.  The two groups
+// are independent: the Householder-first group runs on a side stream (forked
+// from and joined back to s by events), concurrently with the CholeskyQR2
+// group, whose short launches would otherwise leave the GPU idle.
+template <typename T>
+cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  OrthBatch<T> hb, cq;
+  hb.count = cq.count = 0;
+  hb.max_chunks = cq.max_chunks = b.max_chunks;
+  hb.max_tilepairs = cq.max_tilepairs = b.max_tilepairs;
+  for (int i = 0; i < b.count; ++i) {
+    if (b.job[i].hh_first) hb.job[hb.count++] = b.job[i];
+    else cq.job[cq.count++] = b.job[i];
+  }
+  cudaError_t e = cudaSuccess;
+  SideStreams* fk = nullptr;
+  if (hb.count > 0 && cq.count > 0) {
+    fk = side_streams();
+    if (!fk) return cudaErrorUnknown;
+    e = fork_side(fk, 1, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (hb.count > 0) {
+    e = launch_householder<T>(hb, fk ? fk->stream[0] : s);
+    if (e != cudaSuccess) return e;
+  }
+  if (cq.count > 0) {
+    e = launch_cholqr2<T>(cq, s);
+    if (e != cudaSuccess) return e;
+    e = launch_householder<T>(cq, s);  // matrices whose Cholesky factorization broke down
+    if (e != cudaSuccess) return e;
+  }
+  if (fk) e = join_side(fk, 1, s);
+  return e;
 }
 
 template cudaError_t launch_prep<double>(const PrepBatch<double>&, cudaStream_t);

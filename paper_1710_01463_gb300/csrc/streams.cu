@@ -1,0 +1,43 @@
+// Side streams for independent groups of work inside one library call: the
+// groups are forked from the caller's stream by an event and joined back to it
+// by one event per side stream, so the call stays ordered on the caller's
+// stream (and capturable into a CUDA graph) while its groups overlap.
+#include "common.cuh"
+
+namespace rsvd {
+
+SideStreams* side_streams() {
+  constexpr int kMaxDevices = 64;
+  thread_local SideStreams ss[kMaxDevices];  // per host thread: concurrent callers never share events
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  SideStreams& x = ss[dev];
+  if (!x.ready) {
+    SideStreams y;
+    if (cudaEventCreateWithFlags(&y.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    for (int i = 0; i < kSideStreams; ++i)
+      if (cudaStreamCreateWithFlags(&y.stream[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&y.join[i], cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    y.ready = true;
+    x = y;
+  }
+  return &x;
+}
+
+cudaError_t fork_side(SideStreams* ss, int n, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(ss->fork, s);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ss->stream[i], ss->fork, 0);
+  return e;
+}
+
+cudaError_t join_side(SideStreams* ss, int n, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(ss->join[i], ss->stream[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ss->join[i], 0);
+  }
+  return e;
+}
+
+}  // namespace rsvd
