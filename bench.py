@@ -29,6 +29,20 @@ L_SITES, CHI, D_LOC, H_FIELD, DT, P_OVER, Q_POW, SEED = 64, 128, 2, 1.0, 0.01, 1
 PREP_STEPS, PREP_DT = 20, 0.1
 WORKLOAD = "tebd_tfim_L64_chi128_d2_dt0.01_p10_q2_fp64"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+# DRAM bytes (read + write) per launch of a workload's dominant kernel, from one
+# ncu capture of that kernel as it stands (summaries under profiles/); a kernel
+# changed since its capture has no entry (traffic null).
+TRAFFIC_PER_LAUNCH = {
+    ("tebd", "householder"): (7.644416e6, "profiles/householder_panel_tebd_L64_chi128.md"),
+    ("mixed", "gram"): (20.98e6, "profiles/gram_and_tc_gemm_mixed_bf16_16x4096.md"),
+    ("mixed", "tcgemm"): (561.69e6 + 16.31e6, "profiles/gram_and_tc_gemm_mixed_bf16_16x4096.md"),
+}
+
+
+def traffic_of(workload, kernel):
+    t = TRAFFIC_PER_LAUNCH.get((workload, kernel))
+    return (t[0], t[1]) if t else (None, None)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 
 
@@ -129,35 +143,46 @@ def bond_shapes():
     return out
 
 
+def hh_flops(rows, l, r):
+    """Householder QR of a rows x l sample stopped after r reflectors (r = l when it
+    runs to the end), and the accumulation of the explicit Q (rows x l) from them:
+    2 (4 rows l r - 2 (rows + l) r^2 + 4 r^3 / 3)."""
+    r = min(r, l)
+    return 2.0 * (4.0 * rows * l * r - 2.0 * (rows + l) * r * r + 4.0 * r ** 3 / 3.0)
+
+
 def step_flops(info):
     """Algorithmic FP64 flops of one Trotter step, split by kernel class.
 
-    GEMMs: sketch / power / projection (2q+2) 2mnl, two-site contraction 2mnk,
-    B update 2mnk.  Each of the 2q+1 orthonormalisations of a rows x l sample:
-    CholeskyQR2 (two passes of Gram rows l^2, Cholesky + triangular inverse
-    2 l^3 / 3, Y R^-1 rows l^2) or, for nearly square samples (3l > rows),
-    Householder QR (factor 2 rows l^2 - 2 l^3 / 3, forming Q the same).  Jacobi
+    Follows the library's path decisions: Q = I, B = A only for m <= 16 (and
+    m <= l); otherwise GEMMs for the sketch / power / projection (2q+2) 2mnl,
+    plus the two-site contraction 2mnk and the B update 2mnk.  Each of the
+    2q+1 orthonormalisations of a rows x l sample: CholeskyQR2 (two passes of
+    Gram rows l^2, Cholesky + triangular inverse 2 l^3 / 3, Y R^-1 rows l^2)
+    or, for nearly square samples (3l > rows), Householder QR stopped after the
+    device-reported number of reflectors (rsvd_info.qr_columns of the last
+    orthonormalisation, taken for all of them) with its explicit Q.  Jacobi
     (from the device counts): every sweep forms the row norms (2nl) and the
     inner products of all l(l-1)/2 pairs (2n each); each applied rotation
-    costs 6n + 6l.
+    costs 6n (the TEBD update does not accumulate the rotations of U).
     """
     flops = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0}
     for j, lay in enumerate(bond_shapes()):
         for b, (m, n, k, l) in enumerate(lay):
+            rec = info[j][b]
+            sweeps, rots, qr_cols = int(rec[3]), int(rec[5]), int(rec[6])
             flops["gemm"] += 2.0 * m * n * k + 2.0 * m * n * k
-            if m > l:
+            if not (m <= l and m <= 16):
                 flops["gemm"] += (2 * Q_POW + 2) * 2.0 * m * n * l
                 for it in range(2 * Q_POW + 1):
                     rows = m if it % 2 == 0 else n
                     if 3 * l > rows:
-                        flops["householder"] += 2 * (2.0 * rows * l * l - 2.0 * l ** 3 / 3.0)
+                        flops["householder"] += hh_flops(rows, l, qr_cols if qr_cols > 0 else l)
                     else:
                         flops["gram"] += 2 * rows * l * l
                         flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
                         flops["gemm"] += 2 * rows * l * l
-            rec = info[j][b]
-            sweeps, rots = int(rec[3]), int(rec[5])
-            flops["jacobi"] += (sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * (6.0 * n + 6.0 * l)
+            flops["jacobi"] += (sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * 6.0 * n
                                 + (sweeps + 1) * 2.0 * n * l)
     return flops
 
@@ -243,7 +268,8 @@ def run_ours(args):
     for name, (ms, cnt) in classes.items():
         launches += cnt * per_group.get(name, 1)
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(dom_ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(dom_ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(dom_ach / FP64_PEAK_TFLOPS, 4),
+                "traffic": traffic_of("tebd", dom)[0], "traffic_source": traffic_of("tebd", dom)[1],
                 "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s; "
                                "DFMA microbenchmark on this GB300: 1.20 TFLOP/s)"}
 
@@ -395,16 +421,16 @@ def profile_classes(lib):
     return {lib.rsvd_profile_class_name(c).decode(): (ms_c[c], cnt_c[c]) for c in range(ncls)}
 
 
-def rsvd_flops(m, n, k, l, q, sweeps, rots, prec):
+def rsvd_flops(m, n, k, l, q, sweeps, rots, prec, qr_cols=0, want_u=True):
     """Algorithmic flops of one RSVD by kernel class (see step_flops), plus the
     tensor-core products of the BF16 / TF32 forms.  Wide B (n >= 4l): the SVD
     of B runs on the l x l factor of an orthonormalisation of B^T."""
     f = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "tcgemm": 0.0}
-    exact = m <= l
+    exact = m <= l and m <= 16
 
     def orth(rows):
         if 3 * l > rows:
-            f["householder"] += 2 * (2.0 * rows * l * l - 2.0 * l ** 3 / 3.0)
+            f["householder"] += hh_flops(rows, l, qr_cols if qr_cols > 0 else l)
         else:
             f["gram"] += 2 * rows * l * l
             f["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
@@ -414,13 +440,15 @@ def rsvd_flops(m, n, k, l, q, sweeps, rots, prec):
         f["tcgemm" if prec in ("bf16", "tf32") else "gemm"] += (2 * q + 2) * 2.0 * m * n * l
         for it in range(2 * q + 1):
             orth(m if it % 2 == 0 else n)
-    f["gemm"] += 2.0 * m * l * k  # lift
+    if want_u:
+        f["gemm"] += 2.0 * m * l * k  # lift
     jn = n
     if n >= 4 * l:  # B^T = Q_b R, M = B Q_b, V^T = W Q_b^T
         orth(n)
         f["gemm"] += 2.0 * l * n * l + 2.0 * k * l * n
         jn = l
-    f["jacobi"] += sweeps * (l * (l - 1) / 2.0) * 2.0 * jn + rots * (6.0 * jn + 6.0 * l) + (sweeps + 1) * 2.0 * jn * l
+    f["jacobi"] += (sweeps * (l * (l - 1) / 2.0) * 2.0 * jn + rots * (6.0 * jn + (6.0 * l if want_u else 0.0))
+                    + (sweeps + 1) * 2.0 * jn * l)
     return f
 
 
@@ -581,7 +609,7 @@ def run_workload(args):
             mm, nn = A.shape
             kk = ks[j]
             ll = min(kk + p, mm, nn)
-            f = rsvd_flops(mm, nn, kk, ll, q, int(rec[j][3]), int(rec[j][5]), prec)
+            f = rsvd_flops(mm, nn, kk, ll, q, int(rec[j][3]), int(rec[j][5]), prec, int(rec[j][6]))
             for key in fl:
                 fl[key] += f[key]
             if prec in ("bf16", "tf32"):
@@ -611,14 +639,16 @@ def run_workload(args):
     dms = classes[dom][0] / 1e3
     if dom == "tcgemm":
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(tcb / dms / 1e9, 1), "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": round(tcb / dms / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
+                    "unit": "GB/s", "frac": round(tcb / dms / 1e9 / peaks["hbm_gbs"], 4),
+                    "traffic": traffic_of(wl, dom)[0], "traffic_source": traffic_of(wl, dom)[1],
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     else:
         fp64 = prec == "f64" or dom in ("gram", "cholesky", "householder", "jacobi")
         pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
         ach = fl.get(dom, 0.0) / dms / 1e12 if dms > 0 else 0.0
         roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": round(pk, 3), "unit": "TFLOP/s",
-                    "frac": round(ach / pk, 4), "traffic": None,
+                    "frac": round(ach / pk, 4), "traffic": traffic_of(wl, dom)[0],
+                    "traffic_source": traffic_of(wl, dom)[1],
                     "peak_source": ("FP64 DFMA 152 SMs x 2/clk x 2 flop x 2.07 GHz" if fp64 else
                                     "FP32 FFMA 152 SMs x 128/clk x 2 flop x 2.07 GHz") + " (derived)"}
     launches = sum(cnt * {"gram": 2, "select": 2}.get(name, 1) for name, (ms, cnt) in classes.items())
