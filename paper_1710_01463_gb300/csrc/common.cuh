@@ -15,7 +15,7 @@ namespace rsvd {
 
 constexpr int kMaxJobs = 64;       // jobs per launch (larger batches are chunked)
 constexpr int kGramChunk = 256;    // rows of Y per Gram partial
-constexpr int kGramTile = 32;      // Gram tile edge
+constexpr int kGramTile = 16;      // Gram tile edge
 
 // ---- batched GEMM: C = op(A) * op(X) [/ *div] ----------------------------
 // op(A) is M x K, op(X) is K x N, C is M x N; all row-major.

@@ -64,9 +64,13 @@ __device__ __forceinline__ void tilepair(int idx, int T, int& ti, int& tj) {
   tj = ti + idx;
 }
 
-// partial G over one chunk of rows for one 32 x 32 tile (ti <= tj)
+// partial G over one chunk of rows for one kGramTile x kGramTile tile (ti <= tj),
+// one output per thread.  16-wide tiles: the FMA loop is FP64-bound at any
+// tile size, so the small tile loses nothing and pads less (l = 80 computes
+// 15 x 256 outputs instead of 6 x 1024; l = 138, 45 x 256 instead of 15 x 1024).
 template <typename T>
 __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ OrthBatch<T> b, int gated, int src1) {
+  static_assert(kGramTile == 16, "one output per thread of a 16 x 16 tile");
   const OrthJob<T>& J = b.job[blockIdx.z];
   if (J.hh_first || (gated && *J.flag != 0)) return;
   const int l = J.l;
@@ -79,38 +83,27 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ OrthB
   tilepair(blockIdx.x, nt, ti, tj);
   const T* Y = src1 ? J.Y1 : J.Y;
 
-  __shared__ double Si[32][33], Sj[32][33];
+  constexpr int kRows = 32;  // rows of Y staged per step
+  __shared__ double Si[kRows][kGramTile + 1], Sj[kRows][kGramTile + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  double acc = 0.0;
   const int r_begin = c * kGramChunk;
   const int r_end = min(J.rows, r_begin + kGramChunk);
-  for (int r0 = r_begin; r0 < r_end; r0 += 32) {
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-      const int rr = e / 32, cc = e % 32;
+  for (int r0 = r_begin; r0 < r_end; r0 += kRows) {
+    for (int e = threadIdx.x; e < kRows * kGramTile; e += 256) {
+      const int rr = e / kGramTile, cc = e % kGramTile;
       const int r = r0 + rr;
-      const int ci = ti * 32 + cc, cj = tj * 32 + cc;
+      const int ci = ti * kGramTile + cc, cj = tj * kGramTile + cc;
       Si[rr][cc] = (r < r_end && ci < l) ? (double)Y[(long long)r * l + ci] : 0.0;
       Sj[rr][cc] = (r < r_end && cj < l) ? (double)Y[(long long)r * l + cj] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) {
-      const double a0 = Si[rr][ty], a1 = Si[rr][ty + 16];
-      const double b0 = Sj[rr][tx], b1 = Sj[rr][tx + 16];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
-    }
+    for (int rr = 0; rr < kRows; ++rr) acc = fma(Si[rr][ty], Sj[rr][tx], acc);
     __syncthreads();
   }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int bb = 0; bb < 2; ++bb) {
-      const int i = ti * 32 + ty + 16 * a, j = tj * 32 + tx + 16 * bb;
-      if (i < l && j < l) J.part[((long long)c * l + i) * l + j] = acc[a][bb];
-    }
+  const int i = ti * kGramTile + ty, j = tj * kGramTile + tx;
+  if (i < l && j < l) J.part[((long long)c * l + i) * l + j] = acc;
 }
 
 template <typename T>
@@ -134,7 +127,12 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant_
 // One CTA per matrix.  R (upper, R^T R = G) is built in shared memory when l is
 // small enough, else in place in G.  Breakdown (a pivot that is not above
 // kPivotTol times its original diagonal entry) sets the flag; the matrix then
-// takes the Householder path.
+// takes the Householder path.  Right-looking: per column j, one lane forms the
+// pivot, the scaled row j is staged, and the trailing upper triangle is updated
+// with rows spread over warps and columns over lanes (no index division).
+// R^-1 then overwrites R column by column (X[0:j, j] = -X[0:j, 0:j] R[0:j, j] /
+// R_jj), a team of four lanes per row, and is written out with zeros below
+// the diagonal.
 template <typename T>
 __global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ OrthBatch<T> b, int pass, int use_smem) {
   const OrthJob<T>& J = b.job[blockIdx.x];
@@ -145,52 +143,67 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ Or
   if (pass == 1 && *J.flag != 0) return;
   extern __shared__ double sm[];
   const int l = J.l;
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = blockDim.x / 32;
   double* diag0 = sm;
-  double* R = use_smem ? sm + l : J.G;
+  double* srow = sm + l;  // scaled row j of R
+  double* R = use_smem ? sm + 2 * l : J.G;
   __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const double g = J.G[e];
-    if (use_smem) R[e] = g;
-    if (e / l == e % l) diag0[e / l] = g;
-  }
+  __shared__ double inv_rjj;
+  if (tid == 0) bad = 0;
+  if (use_smem)
+    for (int e = tid; e < l * l; e += blockDim.x) R[e] = J.G[e];
+  for (int i = tid; i < l; i += blockDim.x) diag0[i] = J.G[(long long)i * l + i];
   __syncthreads();
   for (int j = 0; j < l; ++j) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       const double d = R[j * l + j];
       if (!(d > kPivotTol * diag0[j]) || !(diag0[j] > 0.0)) {
         bad = 1;
       } else {
-        R[j * l + j] = sqrt(d);
+        const double rjj = sqrt(d);
+        R[j * l + j] = rjj;
+        inv_rjj = 1.0 / rjj;
       }
     }
     __syncthreads();
     if (bad) break;
-    const double rjj = R[j * l + j];
-    for (int c = j + 1 + threadIdx.x; c < l; c += blockDim.x) R[j * l + c] /= rjj;
+    for (int c = j + 1 + tid; c < l; c += blockDim.x) srow[c] = R[j * l + c] * inv_rjj;
     __syncthreads();
-    const int w = l - j - 1;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      const int r = j + 1 + e / w, c = j + 1 + e % w;
-      if (c >= r) R[r * l + c] = fma(-R[j * l + r], R[j * l + c], R[r * l + c]);
+    for (int c = j + 1 + tid; c < l; c += blockDim.x) R[j * l + c] = srow[c];
+    for (int r = j + 1 + warp; r < l; r += nw) {
+      const double sr = srow[r];
+      for (int c = r + lane; c < l; c += 32) R[r * l + c] = fma(-sr, srow[c], R[r * l + c]);
     }
     __syncthreads();
   }
-  if (pass == 0 && threadIdx.x == 0) *J.flag = bad;  // every orthonormalisation starts afresh
+  if (pass == 0 && tid == 0) *J.flag = bad;  // every orthonormalisation starts afresh
   if (bad) {
-    if (threadIdx.x == 0) *J.flag = 1;
+    if (tid == 0) *J.flag = 1;
     return;
   }
-  // X = R^-1 (upper): column j by back substitution, one thread per column
-  for (int j = threadIdx.x; j < l; j += blockDim.x) {
-    for (int i = l - 1; i > j; --i) J.Rinv[(long long)i * l + j] = (T)0;
-    const double xj = 1.0 / R[j * l + j];
-    J.Rinv[(long long)j * l + j] = (T)xj;
-    for (int i = j - 1; i >= 0; --i) {
-      double s = R[i * l + j] * xj;
-      for (int t = i + 1; t < j; ++t) s = fma(R[i * l + t], (double)J.Rinv[(long long)t * l + j], s);
-      J.Rinv[(long long)i * l + j] = (T)(-s / R[i * l + i]);
+  // X = R^-1 in place: column j needs X[0:j, 0:j] (done) and R[0:j, j] (still R);
+  // the new column is staged in srow until every read of the old one is done
+  constexpr int kTeam = 4;
+  const int team = tid / kTeam, tl = tid % kTeam, nteam = blockDim.x / kTeam;
+  for (int j = 0; j < l; ++j) {
+    const double xjj = 1.0 / R[j * l + j];
+    for (int i0 = 0; i0 < j; i0 += nteam) {  // team-uniform trip count: the shuffles see full teams
+      const int i = i0 + team;
+      double s = 0.0;
+      if (i < j)
+        for (int t = i + tl; t < j; t += kTeam) s = fma(R[i * l + t], R[t * l + j], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (i < j && tl == 0) srow[i] = -s * xjj;
     }
+    __syncthreads();  // every read of column j is done
+    for (int i = tid; i < j; i += blockDim.x) R[i * l + j] = srow[i];
+    if (tid == 0) R[j * l + j] = xjj;
+    __syncthreads();
+  }
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e / l, jcol = e - i * l;
+    J.Rinv[e] = (T)(i <= jcol ? R[e] : 0.0);
   }
 }
 
@@ -764,9 +777,9 @@ cudaError_t launch_cholqr2(const OrthBatch<T>& b, cudaStream_t s) {
     maxtp = max(maxtp, nt * (nt + 1) / 2);
   }
   // shared-memory Cholesky when R fits (l <= 160)
-  const size_t smem_full = (size_t)(maxl + (size_t)maxl * maxl) * sizeof(double);
+  const size_t smem_full = (size_t)(2 * maxl + (size_t)maxl * maxl) * sizeof(double);
   const int use_smem = smem_full <= 210 * 1024 ? 1 : 0;
-  const size_t smem = use_smem ? smem_full : (size_t)maxl * sizeof(double);
+  const size_t smem = use_smem ? smem_full : (size_t)2 * maxl * sizeof(double);
   cudaError_t e;
   e = cudaFuncSetAttribute(cholinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
