@@ -159,6 +159,11 @@ OrthBatch<T> orth_batch(const std::vector<Prob*>& ps, bool onY) {
     // nearly square samples: Householder QR directly (CholeskyQR2 has no flop
     // advantage there and such samples are often numerically rank deficient)
     J.hh_first = 3 * J.l > J.rows ? 1 : 0;
+    // without U, Q only has to span the sampled range: a Householder QR that
+    // ends early forms just its leading columns, and the later products skip
+    // the rest (their operands are zero there)
+    J.rank_eff = p.flag + 2;
+    J.trunc_q = p.want_u ? 0 : 1;
   }
   return b;
 }
@@ -306,6 +311,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
       for (int i = 0; i < rc; ++i) {
         Prob& p = *rs[i];
         g.job[i] = GemmJob<T, T>{p.m, p.l, p.n, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Z0, (T*)p.Y0, nullptr, nullptr, 0};
+        if (!p.want_u) g.job[i].n_eff = p.flag + 2;
       }
       return launch_gemm<T, T, false, false>(g, s);
     };
@@ -315,6 +321,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
       for (int i = 0; i < rc; ++i) {
         Prob& p = *rs[i];
         g.job[i] = GemmJob<T, T>{p.n, p.l, p.m, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Y0, (T*)p.Z0, nullptr, nullptr, 0};
+        if (!p.want_u) g.job[i].n_eff = p.flag + 2;
       }
       return launch_gemm<T, T, true, false>(g, s);
     };
@@ -333,6 +340,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
       for (int i = 0; i < rc; ++i) {
         Prob& p = *rs[i];
         g.job[i] = GemmJob<T, double>{p.l, p.n, p.m, p.l, p.lda, p.n, (const T*)p.Y0, (const T*)p.A, p.Bm, nullptr, nullptr, 0};
+        if (!p.want_u) g.job[i].m_eff = p.flag + 2;
       }
       RSVD_TRY((launch_gemm<T, double, true, false>(g, s)));
     }

@@ -32,6 +32,11 @@ struct GemmJob {
   int gate_val;
   double alpha = 1.0;  // C = alpha op(A) op(X) (+ C when accumulate)
   int accumulate = 0;
+  // optional device counts: rows m >= *m_eff / columns n >= *n_eff of C are
+  // exact zeros (the operand's rows / columns there are zero) and are written
+  // without the product
+  const int* m_eff = nullptr;
+  const int* n_eff = nullptr;
 };
 
 template <typename Tin, typename Tout>
@@ -69,6 +74,11 @@ struct OrthJob {
   int* flag;         // breakdown flag
   rsvd_info* info;
   int hh_first;      // 1: skip CholeskyQR2, use Householder QR directly
+  // leading columns of Q that carry the sample's range (device); with trunc_q
+  // a Householder QR that ends early forms only those columns (the rest of Q
+  // is left zero) and records their number here
+  int* rank_eff = nullptr;
+  int trunc_q = 0;
 };
 template <typename T>
 struct OrthBatch {

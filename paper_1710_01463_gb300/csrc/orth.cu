@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepB
     J.info->rotations = 0;
     J.flag[0] = 0;
     J.flag[1] = 0;
+    J.flag[2] = J.l;  // columns of Q that carry the sampled range
   }
   if (!J.exact) return;
   // Q = I (m x l, l = m) and B = A (l x n, FP64)
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ Or
     if (tid == 0) *J.flag = 1;
     return;
   }
+  if (pass == 1 && J.rank_eff && tid == 0) *J.rank_eff = l;  // CholeskyQR2 succeeded: full column rank
   // X = R^-1 in place: column j needs X[0:j, 0:j] (done) and R[0:j, j] (still R);
   // the new column is staged in srow until every read of the old one is done
   constexpr int kTeam = 4;
@@ -206,6 +208,9 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ Or
     J.Rinv[e] = (T)(i <= jcol ? R[e] : 0.0);
   }
 }
+
+// CTA size of cholinv_kernel: small factors synchronise fewer warps per column
+inline int chol_threads(int l) { return l <= 64 ? 128 : (l <= 128 ? 256 : 512); }
 
 // ---------------------------------------------------------------- Householder QR
 // Householder QR of Y (rows x l) by one thread-block CLUSTER per matrix: the
@@ -391,6 +396,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
     if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
     atomicOr(&J.info->path, RSVD_PATH_HOUSEHOLDER);
     J.info->qr_columns = l;
+    if (J.trunc_q && J.rank_eff) *J.rank_eff = l;
   }
   cluster.sync();  // no CTA leaves while others may read its shared memory
 }
@@ -704,7 +710,10 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     }
     __syncthreads();
   }
-  // Q = (I - V_0 T_0 V_0^T) ... (I - V_last T_last V_last^T) [I; 0], accumulated backwards
+  // Q = (I - V_0 T_0 V_0^T) ... (I - V_last T_last V_last^T) [I; 0], accumulated backwards.
+  // With trunc_q and an early end, only the leading qc columns (those that
+  // carry the sample's range) are formed; the others are written as zeros.
+  const int qc = (J.trunc_q && npanel_used < npanel) ? min(l, npanel_used * kNb) : l;
   cluster.sync();  // every remote read of Ys / Wp above is done
   for (int e = tid; e < nr * l; e += kHhThreads) {
     const int rr = e / l, c = e % l;
@@ -714,7 +723,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   for (int p = npanel_used - 1; p >= 0; --p) {
     const int j0 = p * kNb, nb = min(kNb, l - j0);
     const double* Tp = Tall + (size_t)p * kNb * kNb;
-    const int wcols = l - j0;
+    const int wcols = qc - j0;
     const int rr0 = max(0, min(nr, j0 - r0));  // rows above j0: V is zero there
     double* Wb = Wp;
     cluster.sync();  // the previous panel's remote reads of Wp are done
@@ -738,12 +747,13 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   for (int e = tid; e < nr * l; e += kHhThreads) {
     const int c = e % l;
     const double sg = alpha[c] < 0.0 ? -1.0 : 1.0;
-    J.Y[(size_t)r0 * l + e] = (T)(sg * Ys[e]);
+    J.Y[(size_t)r0 * l + e] = c < qc ? (T)(sg * Ys[e]) : (T)0;
   }
   if (rank == 0 && tid == 0) {
     if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
     atomicOr(&J.info->path, RSVD_PATH_HOUSEHOLDER);
     J.info->qr_columns = min(l, npanel_used * kNb);
+    if (J.trunc_q && J.rank_eff) *J.rank_eff = qc;
   }
   cluster.sync();  // no CTA leaves while others may read its shared memory
 }
@@ -791,7 +801,7 @@ cudaError_t launch_cholqr2(const OrthBatch<T>& b, cudaStream_t s) {
   gram_reduce_kernel<T><<<dim3(rgx, b.count), 256, 0, s>>>(b, 0);
   prof_end(KC_GRAM, s);
   prof_begin(KC_CHOL, s);
-  cholinv_kernel<T><<<b.count, 512, smem, s>>>(b, 0, use_smem);
+  cholinv_kernel<T><<<b.count, chol_threads(maxl), smem, s>>>(b, 0, use_smem);
   prof_end(KC_CHOL, s);
   {
     GemmBatch<T, T> g;
@@ -809,7 +819,7 @@ cudaError_t launch_cholqr2(const OrthBatch<T>& b, cudaStream_t s) {
   gram_reduce_kernel<T><<<dim3(rgx, b.count), 256, 0, s>>>(b, 1);
   prof_end(KC_GRAM, s);
   prof_begin(KC_CHOL, s);
-  cholinv_kernel<T><<<b.count, 512, smem, s>>>(b, 1, use_smem);
+  cholinv_kernel<T><<<b.count, chol_threads(maxl), smem, s>>>(b, 1, use_smem);
   prof_end(KC_CHOL, s);
   {
     GemmBatch<T, T> g;
