@@ -775,6 +775,10 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     // B_i <- theta_B V / ||S||   (V^T now stored in B_{i+1})
     g3.job[b] = GemmJob<double, double>{m, k, n, n, n, k, (double*)(wb + lay[b].thetaB), B + tensor_stride * (i + 1),
                                         B + tensor_stride * i, nrm, nullptr, 0};
+    // B = Q^T A has at most rank_eff nonzero rows, so V^T has at most that many
+    // nonzero rows (zero singular values sort last): the columns of B_i beyond
+    // them are exact zeros
+    g3.job[b].n_eff = probs[b].flag + 2;
   }
   RSVD_TRY(launch_tebd_finish(fb, s));
   RSVD_TRY((launch_gemm<double, double, false, true>(g3, s)));

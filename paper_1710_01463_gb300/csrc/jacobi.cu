@@ -73,6 +73,20 @@ __host__ __device__ inline size_t jsmem_small(int l, const JLayout& L) {
   return sizeof(double) * ((size_t)2 * l + 4 * (size_t)L.npairs + (size_t)(l + 1) / 2 + 1 + (size_t)(L.npairs + 1) / 2 + 1);
 }
 
+// Sum over the CTAs of the cluster of v[i] in their shared memory: every
+// remote load in flight at once, then a fixed pairwise tree (so every CTA gets
+// the same bits, and the dependent FP64 adds are log2 C deep, not C).
+__device__ __forceinline__ double cluster_tree_sum(cg::cluster_group& cluster, const double* v, int i, int C) {
+  double pv[kMaxCluster];
+#pragma unroll
+  for (int r = 0; r < kMaxCluster; ++r) pv[r] = r < C ? cluster.map_shared_rank(v, r)[i] : 0.0;
+#pragma unroll
+  for (int w = 1; w < kMaxCluster; w <<= 1)
+#pragma unroll
+    for (int r = 0; r + w < kMaxCluster; r += 2 * w) pv[r] += pv[r + w];
+  return pv[0];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_constant__ JacobiBatch<T> b) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -107,7 +121,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   __shared__ double rowmax;
   int* live = order;  // live-row list during the sweeps; the sort order afterwards
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int team = tid / kTeam, tl = tid % kTeam, nteam = kJacobiThreads / kTeam;
   const unsigned tmask = 0xffu << ((tid % 32) / kTeam * kTeam);  // this team's lanes
   for (int e = tid; e < l * L.nc; e += kJacobiThreads) {
@@ -124,49 +138,64 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   __syncthreads();
 
   const double tol = (double)max(n, 1) * 0x1.0p-53;
+  const double tol2 = tol * tol;
   const int max_sweeps = J.max_sweeps;
   int sweeps = 0;
   long long total_rot = 0;
   bool converged = false;
   for (;;) {
-    // exact row norms of this sweep
+    // exact row norms of this sweep (four independent partial sums: a dependent
+    // FP64 operation costs about 64 cycles on this part)
     for (int i = tid; i < l; i += kJacobiThreads) {
-      double s = 0.0;
-      for (int c = 0; c < ncl; ++c) s = fma(Bs[i * L.nc + c], Bs[i * L.nc + c], s);
-      nrm_part[i] = s;
+      const double* row = Bs + (size_t)i * L.nc;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int c = 0;
+      for (; c + 3 < ncl; c += 4) {
+        s0 = fma(row[c], row[c], s0);
+        s1 = fma(row[c + 1], row[c + 1], s1);
+        s2 = fma(row[c + 2], row[c + 2], s2);
+        s3 = fma(row[c + 3], row[c + 3], s3);
+      }
+      for (; c < ncl; ++c) s0 = fma(row[c], row[c], s0);
+      nrm_part[i] = (s0 + s1) + (s2 + s3);
     }
     cluster.sync();
-    for (int i = tid; i < l; i += kJacobiThreads) {
-      double s = 0.0;
-      for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(nrm_part, r)[i];
-      norms[i] = s;
-    }
+    for (int i = tid; i < l; i += kJacobiThreads) norms[i] = cluster_tree_sum(cluster, nrm_part, i, C);
     if (tid == 0) rot_count = 0;
     __syncthreads();
+    // norms are >= +0, so finiteness, maxima and comparisons with non-negative
+    // thresholds are integer operations on the bit patterns
     for (int i = tid; i < l; i += kJacobiThreads)
-      if (!isfinite(norms[i])) nonfinite = 1;
+      if (((__double_as_longlong(norms[i]) >> 52) & 0x7ff) == 0x7ff) nonfinite = 1;
     __syncthreads();
     if (nonfinite) break;  // identical in every CTA of the cluster
-    if (tid < 32) {
-      double mx = 0.0;
-      for (int i = tid; i < l; i += 32) mx = fmax(mx, norms[i]);
+    if (warp == 0) {
+      long long mx = 0;
+      for (int i = lane; i < l; i += 32) mx = max(mx, __double_as_longlong(norms[i]));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (tid == 0) rowmax = mx;
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) rowmax = __longlong_as_double(mx);
     }
     __syncthreads();
     {
-      const double floor_ = rowmax * 0x1.0p-104;  // (2^-52)^2 of the largest squared row norm
+      // (2^-52)^2 of the largest squared row norm
+      const long long floor_bits = __double_as_longlong(rowmax * 0x1.0p-104);
       for (int e = tid; e < l * L.nc; e += kJacobiThreads)
-        if (!(norms[e / L.nc] > floor_)) Bs[e] = 0.0;
+        if (!(__double_as_longlong(norms[e / L.nc]) > floor_bits)) Bs[e] = 0.0;
       __syncthreads();
       for (int i = tid; i < l; i += kJacobiThreads)
-        if (!(norms[i] > floor_)) norms[i] = 0.0;
-      if (tid == 0) {
+        if (!(__double_as_longlong(norms[i]) > floor_bits)) norms[i] = 0.0;
+      __syncthreads();  // every norm is final before the live list is built
+      if (warp == 0) {  // live rows in index order, by ballots
         int nl = 0;
-        for (int i = 0; i < l; ++i)
-          if (norms[i] > 0.0) live[nl++] = i;
-        nlive = nl;
+        for (int b0 = 0; b0 < l; b0 += 32) {
+          const int i = b0 + lane;
+          const bool lv = i < l && __double_as_longlong(norms[i]) > 0;
+          const unsigned m = __ballot_sync(0xffffffffu, lv);
+          if (lv) live[nl + __popc(m & ((1u << lane) - 1u))] = i;
+          nl += __popc(m);
+        }
+        if (lane == 0) nlive = nl;
       }
       __syncthreads();
     }
@@ -201,27 +230,29 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         if (bq < nlive) {
           const int i = live[a], j = live[bq];
           const double al = norms[i], be = norms[j];
-          double pv[kMaxCluster];  // all remote loads in flight at once, summed in rank order
-#pragma unroll
-          for (int rr = 0; rr < kMaxCluster; ++rr) pv[rr] = rr < C ? cluster.map_shared_rank(gp, rr)[s] : 0.0;
-          double g = 0.0;
-#pragma unroll
-          for (int rr = 0; rr < kMaxCluster; ++rr)
-            if (rr < C) g += pv[rr];
-          if (al > 0.0 && be > 0.0 && fabs(g) > tol * sqrt(al * be)) {
+          const double g = cluster_tree_sum(cluster, gp, s, C);
+          // al, be > 0 and g^2 > tol^2 al be, compared as bit patterns (all >= +0)
+          if (__double_as_longlong(al) > 0 && __double_as_longlong(be) > 0 &&
+              __double_as_longlong(g * g) > __double_as_longlong(tol2 * (al * be))) {
             rot = 1;
-            // tan of the rotation angle: with zeta = (be - al) / (2g),
-            // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) = 2g sign(h) / (|h| + sqrt(h^2 + 4g^2)),
-            // h = be - al (one square root and one division); the zeta form
-            // (1 / (2 zeta) once zeta^2 would overflow) where h^2 or g^2 could overflow
-            const double h = be - al;
-            double t;
-            if (fabs(h) < 1e150 && fabs(g) < 1e150) {
-              t = (h >= 0.0 ? 2.0 * g : -2.0 * g) / (fabs(h) + sqrt(fma(h, h, 4.0 * g * g)));
-            } else {
-              const double zeta = h / (2.0 * g);
-              t = fabs(zeta) < 1e150 ? (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)) : 0.5 / zeta;
-            }
+            // tangent of the annihilating angle, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+            // zeta = (be - al) / (2g), formed in FP32 (a dependent FP64 chain of
+            // square roots and divisions would hold the round for microseconds).
+            // Any angle gives an exactly orthogonal rotation once cs, sn come from
+            // the same t in FP64; the FP32 angle leaves |g| at about 1e-7 of its
+            // value instead of 0, and the FP64 stopping test above decides
+            // convergence, so the result keeps FP64 accuracy.
+            // h and 2g are scaled by a power of two (from the exponent bits) into
+            // FP32 range; live rows differ by at most 2^104 in squared norm
+            // (deflation), so |zeta| < 1e29 and only zeta^2 needs the guard
+            const double h = be - al, g2 = 2.0 * g;
+            const double mx = fmax(fabs(h), fabs(g2));
+            const long long ex = min(((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023, 1022LL);
+            const double sc = __longlong_as_double((1023 - ex) << 52);  // 2^-ex
+            const float zf = (float)(h * sc) / (float)(g2 * sc);
+            const float tf = fabsf(zf) < 1e18f ? copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)))
+                                               : 0.5f / zf;
+            const double t = (double)tf;
             cs = rsqrt(fma(t, t, 1.0));
             sn = cs * t;
             norms[i] = al - t * g;
@@ -263,14 +294,20 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   for (int i = tid; i < l; i += kJacobiThreads) {
     const double v = sqrt(norms[i]);
     sig[i] = v;
-    if (!isfinite(v)) nonfinite = 1;
+    if (((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff) nonfinite = 1;
   }
   __syncthreads();
+  // descending order, lower index first on ties; the keys are the bit
+  // patterns of the (non-negative) values, -1 for a non-finite one
+  auto key = [&](int j) {
+    const long long b = __double_as_longlong(sig[j]);
+    return ((b >> 52) & 0x7ff) == 0x7ff ? -1LL : b;
+  };
   for (int i = tid; i < l; i += kJacobiThreads) {
-    const double ki = isfinite(sig[i]) ? sig[i] : -1.0;
+    const long long ki = key(i);
     int rk = 0;
     for (int j = 0; j < l; ++j) {
-      const double kj = isfinite(sig[j]) ? sig[j] : -1.0;
+      const long long kj = key(j);
       rk += (kj > ki) || (kj == ki && j < i);
     }
     order[rk] = i;

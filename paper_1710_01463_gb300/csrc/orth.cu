@@ -157,13 +157,18 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ Or
   __syncthreads();
   for (int j = 0; j < l; ++j) {
     if (tid == 0) {
+      // pivot test on bit patterns (d > tol diag0 >= +0; d itself may have gone
+      // negative by cancellation, which the signed compare rejects), and one
+      // reciprocal square root for both R_jj and its inverse
       const double d = R[j * l + j];
-      if (!(d > kPivotTol * diag0[j]) || !(diag0[j] > 0.0)) {
+      if (!(__double_as_longlong(d) > __double_as_longlong(kPivotTol * diag0[j])) ||
+          !(__double_as_longlong(diag0[j]) > 0)) {
         bad = 1;
       } else {
-        const double rjj = sqrt(d);
-        R[j * l + j] = rjj;
-        inv_rjj = 1.0 / rjj;
+        const double ir = rsqrt(d);
+        R[j * l + j] = d * ir;
+        inv_rjj = ir;
+        srow[j] = ir;  // kept for the inverse below (srow[c] for c > j is written later in this column)
       }
     }
     __syncthreads();
@@ -188,12 +193,19 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ Or
   constexpr int kTeam = 4;
   const int team = tid / kTeam, tl = tid % kTeam, nteam = blockDim.x / kTeam;
   for (int j = 0; j < l; ++j) {
-    const double xjj = 1.0 / R[j * l + j];
+    const double xjj = srow[j];  // 1 / R_jj from the factorization (srow[i], i < j, is reused below)
     for (int i0 = 0; i0 < j; i0 += nteam) {  // team-uniform trip count: the shuffles see full teams
       const int i = i0 + team;
-      double s = 0.0;
-      if (i < j)
-        for (int t = i + tl; t < j; t += kTeam) s = fma(R[i * l + t], R[t * l + j], s);
+      double s = 0.0, s1 = 0.0;  // two chains per lane
+      if (i < j) {
+        int t = i + tl;
+        for (; t + kTeam < j; t += 2 * kTeam) {
+          s = fma(R[i * l + t], R[t * l + j], s);
+          s1 = fma(R[i * l + t + kTeam], R[(t + kTeam) * l + j], s1);
+        }
+        if (t < j) s = fma(R[i * l + t], R[t * l + j], s);
+      }
+      s += s1;
       s += __shfl_xor_sync(0xffffffffu, s, 1);
       s += __shfl_xor_sync(0xffffffffu, s, 2);
       if (i < j && tl == 0) srow[i] = -s * xjj;
@@ -457,6 +469,34 @@ __device__ __forceinline__ double warp_reduce_scatter16(double (&a)[kNb], int la
   return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
 }
 
+// sum over own rows rr0 .. nr-1 of a[rr * ld] * b[rr * ld] (a column of V
+// times a column of Y), four independent chains: a dependent FP64 FMA costs
+// about 64 cycles on this part
+__device__ __forceinline__ double dot_rows(const double* a, const double* b, int ld, int rr0, int nr) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int rr = rr0;
+  for (; rr + 3 < nr; rr += 4) {
+    s0 = fma(a[rr * ld], b[rr * ld], s0);
+    s1 = fma(a[(rr + 1) * ld], b[(rr + 1) * ld], s1);
+    s2 = fma(a[(rr + 2) * ld], b[(rr + 2) * ld], s2);
+    s3 = fma(a[(rr + 3) * ld], b[(rr + 3) * ld], s3);
+  }
+  for (; rr < nr; ++rr) s0 = fma(a[rr * ld], b[rr * ld], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// sum over jj < nb of v[jj] * w[jj * ld] (a row of V times a column of M), two chains
+__device__ __forceinline__ double dot_panel(const double* v, const double* w, int ld, int nb) {
+  double s0 = 0.0, s1 = 0.0;
+  int jj = 0;
+  for (; jj + 1 < nb; jj += 2) {
+    s0 = fma(v[jj], w[jj * ld], s0);
+    s1 = fma(v[jj + 1], w[(jj + 1) * ld], s1);
+  }
+  if (jj < nb) s0 = fma(v[jj], w[jj * ld], s0);
+  return s0 + s1;
+}
+
 // After every CTA of the cluster has written its partial V^T Y for columns
 // c0 .. c0 + wcols - 1 into Wb (kNb x l rows), forms W = the sum of the
 // partials and M = T^T W (kTW = false, trailing update) or M = T W (kTW =
@@ -472,27 +512,37 @@ __device__ void cluster_sum_apply_t(cg::cluster_group& cluster, int rank, int C,
   const int cb = c0 + rank * cw, w = max(0, min(c0 + wcols, cb + cw) - cb);
   for (int e = tid; e < nb * w; e += kHhThreads) {
     const int jj = e / w, c = cb + e % w;
-    double pv[kPanelMaxCluster];  // every remote load in flight at once, summed in rank order
+    double pv[kPanelMaxCluster];  // every remote load in flight at once, summed by a fixed tree
 #pragma unroll
     for (int r = 0; r < kPanelMaxCluster; ++r) pv[r] = r < C ? cluster.map_shared_rank(Wb, r)[jj * l + c] : 0.0;
-    double d = 0.0;
 #pragma unroll
-    for (int r = 0; r < kPanelMaxCluster; ++r)
-      if (r < C) d += pv[r];
-    Ws[jj * l + c] = d;
+    for (int w2 = 1; w2 < kPanelMaxCluster; w2 <<= 1)
+#pragma unroll
+      for (int r = 0; r + w2 < kPanelMaxCluster; r += 2 * w2) pv[r] += pv[r + w2];
+    Ws[jj * l + c] = pv[0];
   }
   __syncthreads();
   double mreg[(kNb * 256 + kHhThreads - 1) / kHhThreads];
   int cnt = 0;
   for (int e = tid; e < nb * w; e += kHhThreads, ++cnt) {
     const int jj = e / w, c = cb + e % w;
-    double m = 0.0;
+    double m0 = 0.0, m1 = 0.0;  // two chains: a dependent FP64 FMA costs about 64 cycles
     if (kTW) {
-      for (int ii = jj; ii < nb; ++ii) m = fma(Ts[jj][ii], Ws[ii * l + c], m);
+      int ii = jj;
+      for (; ii + 1 < nb; ii += 2) {
+        m0 = fma(Ts[jj][ii], Ws[ii * l + c], m0);
+        m1 = fma(Ts[jj][ii + 1], Ws[(ii + 1) * l + c], m1);
+      }
+      if (ii < nb) m0 = fma(Ts[jj][ii], Ws[ii * l + c], m0);
     } else {
-      for (int ii = 0; ii <= jj; ++ii) m = fma(Ts[ii][jj], Ws[ii * l + c], m);
+      int ii = 0;
+      for (; ii + 1 <= jj; ii += 2) {
+        m0 = fma(Ts[ii][jj], Ws[ii * l + c], m0);
+        m1 = fma(Ts[ii + 1][jj], Ws[(ii + 1) * l + c], m1);
+      }
+      if (ii <= jj) m0 = fma(Ts[ii][jj], Ws[ii * l + c], m0);
     }
-    mreg[cnt] = m;
+    mreg[cnt] = m0 + m1;
   }
   __syncthreads();
   cnt = 0;
@@ -622,13 +672,16 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
           if (lane == 0) {
+            // a >= +0: sign tests on the bit patterns (an FP64 compare-and-branch
+            // costs hundreds of cycles on this part), ||x|| = a rsqrt(a)
             const double x0 = x0s;
             double al = 0.0, inv = 0.0;
-            if (a > 0.0) {
-              al = x0 >= 0.0 ? -sqrt(a) : sqrt(a);
+            if (__double_as_longlong(a) > 0) {
+              const double nx = a * rsqrt(a);
+              al = __double_as_longlong(x0) >= 0 ? -nx : nx;
               const double w0 = x0 - al;
-              const double vn2 = a - x0 * x0 + w0 * w0;
-              inv = vn2 > 0.0 ? rsqrt(vn2) : 0.0;
+              const double vn2 = fma(w0, w0, fma(-x0, x0, a));
+              inv = __double_as_longlong(vn2) > 0 ? rsqrt(vn2) : 0.0;
             }
             sc[0] = inv;
             sc[1] = (x0 - al) * inv;  // v at row jj
@@ -651,17 +704,28 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
         }
         __syncthreads();
         if (warp == 0) {
-          double f = 0.0;
-          if (lane < kNb)
-            for (int q = 0; q < nlw; ++q) f += red16[q][lane];
+          double pw[kHhThreads / 32];  // the warps' partials, summed by a fixed tree
+#pragma unroll
+          for (int q = 0; q < kHhThreads / 32; ++q) pw[q] = (lane < kNb && q < nlw) ? red16[q][lane] : 0.0;
+#pragma unroll
+          for (int w2 = 1; w2 < kHhThreads / 32; w2 <<= 1)
+#pragma unroll
+            for (int q = 0; q + w2 < kHhThreads / 32; q += 2 * w2) pw[q] += pw[q + w2];
+          const double f = pw[0];
           if (lane < kNb) fin[lane] = lane > jj ? -2.0 * f : f;
-          // T[0:jj, jj] = -2 T[0:jj, 0:jj] (V[:, 0:jj]^T v): lane i sums q = i .. jj-1
-          double t = 0.0;
-          for (int q = 0; q < jj; ++q) {
-            const double fq = __shfl_sync(0xffffffffu, f, q);
-            if (lane <= q) t = fma(Ts[lane][q], fq, t);
+          // T[0:jj, jj] = -2 T[0:jj, 0:jj] (V[:, 0:jj]^T v): lane i sums q = i .. jj-1, two chains
+          double t0 = 0.0, t1 = 0.0;
+          int q = 0;
+          for (; q + 1 < jj; q += 2) {
+            const double fq0 = __shfl_sync(0xffffffffu, f, q), fq1 = __shfl_sync(0xffffffffu, f, q + 1);
+            if (lane <= q) t0 = fma(Ts[lane][q], fq0, t0);
+            if (lane <= q + 1) t1 = fma(Ts[lane][q + 1], fq1, t1);
           }
-          if (lane < jj) Ts[lane][jj] = -2.0 * t;
+          if (q < jj) {
+            const double fq0 = __shfl_sync(0xffffffffu, f, q);
+            if (lane <= q) t0 = fma(Ts[lane][q], fq0, t0);
+          }
+          if (lane < jj) Ts[lane][jj] = -2.0 * (t0 + t1);
         }
         __syncthreads();
         if (live) {
@@ -693,9 +757,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     if (wcols > 0) {
       for (int e = tid; e < nb * wcols; e += kHhThreads) {
         const int jj = e / wcols, c = c1 + e % wcols;
-        double d = 0.0;
-        for (int rr = rr0; rr < nr; ++rr) d = fma(Vo[rr * l + j0 + jj], Ys[rr * l + c], d);
-        Wb[jj * l + c] = d;
+        Wb[jj * l + c] = dot_rows(Vo + j0 + jj, Ys + c, l, rr0, nr);
       }
     }
     cluster.sync();
@@ -703,9 +765,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       cluster_sum_apply_t<false>(cluster, rank, C, Wb, Ws, Ts, nb, l, c1, wcols);
       for (int e = tid; e < (nr - rr0) * wcols; e += kHhThreads) {
         const int rr = rr0 + e / wcols, c = c1 + e % wcols;
-        double y = Ys[rr * l + c];
-        for (int jj = 0; jj < nb; ++jj) y = fma(-Vo[rr * l + j0 + jj], Ws[jj * l + c], y);
-        Ys[rr * l + c] = y;
+        Ys[rr * l + c] -= dot_panel(Vo + rr * l + j0, Ws + c, l, nb);
       }
     }
     __syncthreads();
@@ -730,17 +790,13 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = Tp[tid];
     for (int e = tid; e < nb * wcols; e += kHhThreads) {
       const int jj = e / wcols, c = j0 + e % wcols;
-      double d = 0.0;
-      for (int rr = rr0; rr < nr; ++rr) d = fma(Vo[rr * l + j0 + jj], Ys[rr * l + c], d);
-      Wb[jj * l + c] = d;
+      Wb[jj * l + c] = dot_rows(Vo + j0 + jj, Ys + c, l, rr0, nr);
     }
     cluster.sync();
     cluster_sum_apply_t<true>(cluster, rank, C, Wb, Ws, Ts, nb, l, j0, wcols);
     for (int e = tid; e < (nr - rr0) * wcols; e += kHhThreads) {
       const int rr = rr0 + e / wcols, c = j0 + e % wcols;
-      double q = Ys[rr * l + c];
-      for (int jj = 0; jj < nb; ++jj) q = fma(-Vo[rr * l + j0 + jj], Ws[jj * l + c], q);
-      Ys[rr * l + c] = q;
+      Ys[rr * l + c] -= dot_panel(Vo + rr * l + j0, Ws + c, l, nb);
     }
     __syncthreads();
   }
