@@ -621,11 +621,16 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       }
     }
     cluster.sync();  // trailing updates of the previous panel are complete everywhere
-    if (tid == 0) {
-      double t = 0.0;
-      for (int r = 0; r < C; ++r) t += *cluster.map_shared_rank(&trail_part, r);
-      trail_sum = t;
-      if (p == 0) fro0 = t;
+    if (tid == 0) {  // every remote load in flight at once, summed by a fixed tree
+      double pv[kPanelMaxCluster];
+#pragma unroll
+      for (int r = 0; r < kPanelMaxCluster; ++r) pv[r] = r < C ? *cluster.map_shared_rank(&trail_part, r) : 0.0;
+#pragma unroll
+      for (int w2 = 1; w2 < kPanelMaxCluster; w2 <<= 1)
+#pragma unroll
+        for (int r = 0; r + w2 < kPanelMaxCluster; r += 2 * w2) pv[r] += pv[r + w2];
+      trail_sum = pv[0];
+      if (p == 0) fro0 = pv[0];
     }
     __syncthreads();
     // early end: the rest of Y is rounding noise.  The trailing block of a
