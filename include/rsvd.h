@@ -198,6 +198,26 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond,
                      void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
 
 /*
+ * rsvd_gemm_f64_tc - the FP64 tensor-core product of the FP64 path (exposed so
+ * that it can be verified on its own): C = A B^T with A (M x K, lda), B (N x K,
+ * ldb) and C (M x N, ldc) row-major FP64 device matrices, N <= 256, K <= 256.
+ * Every row of A and of B is split exactly into nine BF16 slices of 6-bit
+ * integers relative to the row's power-of-two exponent (only bits below
+ * 2^-54 of the row's largest magnitude are dropped); the slice products are
+ * summed exactly by tcgen05.mma in FP32 tensor memory, level by level, and
+ * the levels in FP64.  Error: at most about 2.3 K 2^-53 max|A_r| max|B_c| per
+ * entry (the normwise class of an FP64 GEMM).  A row holding Inf or NaN gives
+ * NaN.
+ * work: device workspace of rsvd_gemm_f64_tc_workspace_size(M, N, K) bytes
+ * (256-byte aligned).  err (device int, may be NULL) as for rsvd_gemm_tc.
+ * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_WORKSPACE,
+ * RSVD_ERR_LAUNCH.
+ */
+size_t rsvd_gemm_f64_tc_workspace_size(int M, int N, int K);
+int rsvd_gemm_f64_tc(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                     void* work, size_t work_bytes, int* err, void* cuda_stream);
+
+/*
  * rsvd_gemm_tc - the tensor-core product of the mixed-precision path (exposed
  * so that it can be verified on its own): C = A B^T with A (M x K, lda) and B
  * (N x K, ldb) row-major device matrices of bfloat16 (RSVD_BF16) or float read

@@ -42,6 +42,8 @@ EXPORTED = (
     "rsvd_profile_collect",
     "rsvd_profile_class_name",
     "rsvd_gemm_tc",
+    "rsvd_gemm_f64_tc_workspace_size",
+    "rsvd_gemm_f64_tc",
     "rsvd_backward_workspace_size",
     "rsvd_truncate_backward_batched",
     "rsvd_truncate_noalloc",
@@ -110,6 +112,9 @@ def load():
     lib.rsvd_profile_enable.argtypes = [i]
     lib.rsvd_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ip, i]
     lib.rsvd_gemm_tc.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp, i, vp]
+    lib.rsvd_gemm_f64_tc_workspace_size.argtypes = [i, i, i]
+    lib.rsvd_gemm_f64_tc_workspace_size.restype = sz
+    lib.rsvd_gemm_f64_tc.argtypes = [i, i, i, vp, i, vp, i, vp, i, vp, sz, vp, vp]
     lib.rsvd_backward_workspace_size.argtypes = [i, ip, ip, ip, i, ctypes.POINTER(sz)]
     lib.rsvd_truncate_backward_batched.argtypes = [i, ip, ip, ip, i, pp, ip, pp, pp, ip, pp, ip, pp, ip, pp, pp, ip,
                                                    pp, ip, i, ctypes.c_double, vp, sz, vp, vp]

@@ -23,10 +23,8 @@ cudaError_t& last_cuda_error() {
 
 namespace {
 
-constexpr size_t kAlign = 256;
 constexpr int kMaxSample = 1024;  // largest sample width l supported
 
-inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Prob {
   int m, n, k, l;

@@ -6,6 +6,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -265,13 +266,53 @@ struct TcBatch {
   TcJob job[kMaxTcJobs];
 };
 bool make_tmap(CUtensorMap* map, const void* base, int rows, int cols, int ld, int elem_bytes, int box_rows);
+
+// FP64 products on the tensor cores by exact slicing (oz_gemm.cu): every FP64
+// value x of a row r is 2^e_r * sum_{i=1..9} p_i 2^-6i + (truncation below
+// 2^(e_r - 54)) with integer p_i in [-63, 63] held exactly in BF16; the slice
+// products of one level L = i + j <= 11 are summed exactly in an FP32
+// accumulator (|sum| <= 9 * 256 * 63^2 < 2^24 for K <= 256) and the levels in
+// FP64.
+constexpr int kOzSlices = 9;
+constexpr int kOzMaxK = 256;
+constexpr int kMaxOzJobs = 32;
+struct OzJob {
+  CUtensorMap tp;    // slices of P: kOzSlices blocks of M rows, row length Kp, box 128 rows x 64
+  CUtensorMap ts;    // slices of S^T: kOzSlices blocks of Npad rows, box ntile rows x 64
+  double* C;         // C = P S: M x N (ldc), or its transpose N x M when trans_c
+  const int* ep;     // M row exponents of P
+  const int* es;     // N column exponents of S
+  const int* n_eff;  // optional: columns >= *n_eff are exact zeros
+  int* err;          // optional: set to 1 when a pipeline wait timed out
+  int M, N, Npad, K, ldc, trans_c;
+};
+struct OzBatch {
+  int count;
+  int ntile;  // columns per CTA (multiple of 16, at most 64)
+  OzJob job[kMaxOzJobs];
+};
+// one row (or, with xt, one column) of X split into slices per job
+struct OzSplitJob {
+  const double* X;
+  int rows, K, ldx, xt;  // xt: row r is column r of X (X is K x rows)
+  int rows_blk, Kp;      // slice block: rows_blk rows (rows .. rows_blk-1 zero) of Kp entries (K .. Kp-1 zero)
+  __nv_bfloat16* S;      // kOzSlices blocks of rows_blk x Kp
+  int* e;                // rows_blk exponents (0 for zero rows)
+};
+struct OzSplitBatch {
+  int count;
+  OzSplitJob job[kMaxJobs];
+};
+cudaError_t launch_oz_split(const OzSplitBatch& b, cudaStream_t s);
+cudaError_t launch_oz_gemm(const OzBatch& b, cudaStream_t s);
+int oz_ntile(int Npad);
 size_t tc_smem_bytes(int Npad, int stages);
 int tc_stages(int Npad);
 
 // ---- optional per-kernel timing (CUDA events around launches) -------------
 enum KernelClass {
   KC_PREP = 0, KC_OMEGA, KC_GEMM, KC_GRAM, KC_CHOL, KC_HOUSEHOLDER, KC_JACOBI, KC_SIGN, KC_SELECT, KC_TEBD,
-  KC_BACKWARD, KC_TCGEMM, KC_CONVERT, KC_COUNT
+  KC_BACKWARD, KC_TCGEMM, KC_CONVERT, KC_OZGEMM, KC_OZSPLIT, KC_COUNT
 };
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s);
@@ -327,5 +368,8 @@ size_t jacobi_smem_bytes(int l, int n, int csize);
 bool jacobi_fits_smem(int l, int n, int csize);
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+constexpr size_t kAlign = 256;  // workspace buffer alignment
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 }  // namespace rsvd

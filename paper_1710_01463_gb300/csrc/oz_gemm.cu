@@ -1,0 +1,354 @@
+// FP64 products C = P S on the tcgen05 tensor cores, for the products with A
+// of Alg. RSVD (Sec. II.B) - the sketch A Omega, the power-iteration products
+// A^T Q and A Z, and the projection (as B^T = A^T Q) - when K <= 256.
+//
+// Exact slicing (an error-free splitting of each FP64 row into small
+// integers, in the spirit of Ozaki's scheme): a row r of P with largest
+// magnitude below 2^e_r is written as |x| = 2^(e_r - 54) n with a 54-bit
+// integer n = floor(|x| 2^(54 - e_r)) read off the FP64 bit pattern, and n is
+// cut into nine 6-bit pieces, x = 2^e_r sum_{i=1..9} p_i 2^-6i exactly (only
+// the bits of x below 2^(e_r - 54) are dropped; integer operations only).
+// Each p_i in [-63, 63] is exact in BF16.  With the columns of S sliced the
+// same way (q_j, exponents f_c):
+//
+//   C[r][c] = 2^(e_r + f_c) sum_L 2^-6L T_L[r][c],   T_L = sum_{i+j=L} P_i S_j^T
+//
+// Every product p_i q_j is an integer below 2^12 and |T_L| <= 9 * 256 * 63^2
+// < 2^24, so the tcgen05 BF16 MMA accumulates each level exactly in FP32 in
+// tensor memory (K <= 256).  Levels L = 2 .. 11 are kept (53 slice products).
+// Error per entry, with 2^e_r <= 2 max|P_r| and 2^f_c <= 2 max|S_c|: the bits
+// cut off by the slicing add at most 2 K 2^-53 max|P_r| max|S_c|, the dropped
+// levels L >= 12 at most 0.25 K 2^-53 max|P_r| max|S_c| - the normwise class
+// of an FP64 GEMM (K 2^-53 |P_r| |S_c|).  The ten level sums are combined in
+// FP64 in the epilogue.
+//
+// One CTA computes a 128 x ntile tile (ntile <= 64: the epilogue keeps one
+// FP64 accumulator per column in registers).  Warp 0 issues the TMA loads of
+// the P and S slice tiles, warp 1 issues the MMAs into two TMEM accumulators
+// (levels alternate, so the epilogue of one level overlaps the MMAs of the
+// next), warps 2-5 read each finished level back and add it in FP64.  Every
+// mbarrier wait is bounded; on a timeout the kernel records an error and
+// finishes without further work.
+#include "common.cuh"
+#include "tcgen05.cuh"
+
+namespace rsvd {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kOzThreads = 192;
+constexpr int kOzM = 128;
+constexpr int kOzBK = 64;     // BF16 elements of K per stage (128 bytes)
+constexpr int kOzMmaK = 16;   // K per MMA
+constexpr int kOzMaxNt = 64;  // columns per CTA
+
+// ---------------------------------------------------------------- slicing
+// One warp per row of the slice block: the row's exponent from the largest
+// magnitude (integer maximum of the bit patterns), then the nine slices of
+// every entry.  Rows of a block past `rows` and entries past K are zero; a
+// row holding Inf or NaN gets NaN slices, so that the product is NaN there.
+__global__ void __launch_bounds__(256) oz_split_kernel(const __grid_constant__ OzSplitBatch b) {
+  const OzSplitJob& J = b.job[blockIdx.y];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int r = blockIdx.x * (blockDim.x / 32) + warp;
+  if (r >= J.rows_blk) return;
+  const size_t blk = (size_t)J.rows_blk * J.Kp;
+  __nv_bfloat16* S = J.S + (size_t)r * J.Kp;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  if (r >= J.rows) {
+    for (int k = lane; k < J.Kp; k += 32)
+#pragma unroll
+      for (int i = 0; i < kOzSlices; ++i) S[i * blk + k] = zero;
+    if (lane == 0) J.e[r] = 0;
+    return;
+  }
+  auto at = [&](int k) { return J.xt ? J.X[(size_t)k * J.ldx + r] : J.X[(size_t)r * J.ldx + k]; };
+  long long mx = 0;
+  for (int k = lane; k < J.K; k += 32) mx = max(mx, __double_as_longlong(at(k)) & 0x7fffffffffffffffLL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int emax = (int)((mx >> 52) & 0x7ff);
+  const bool nonfinite = emax == 0x7ff;
+  const int e = mx == 0 ? 0 : max(emax, 1) - 1022;  // every |x| of the row is below 2^e
+  if (lane == 0) J.e[r] = nonfinite ? 0 : e;
+  const __nv_bfloat16 nan = __float2bfloat16_rn(__int_as_float(0x7fc00000));
+  for (int k = lane; k < J.Kp; k += 32) {
+    long long n = 0;
+    bool neg = false;
+    if (k < J.K && mx != 0 && !nonfinite) {
+      const long long bits = __double_as_longlong(at(k));
+      neg = bits < 0;
+      const int E = (int)((bits >> 52) & 0x7ff);
+      const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (E ? (1LL << 52) : 0LL);
+      const int sh = max(E, 1) - 1021 - e;  // n = floor(|x| 2^(54 - e)) = mant 2^sh, sh <= 1
+      n = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0LL);
+    }
+#pragma unroll
+    for (int i = 0; i < kOzSlices; ++i) {
+      const int p = (int)((n >> (48 - 6 * i)) & 63);
+      S[i * blk + k] = nonfinite ? nan : __float2bfloat16_rn((float)(neg ? -p : p));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- product
+__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_constant__ OzBatch b, int stages) {
+  const OzJob& J = b.job[blockIdx.z];
+  const int NT = b.ntile;
+  const int m0 = blockIdx.x * kOzM, n0 = blockIdx.y * NT;
+  if (m0 >= J.M || n0 >= J.N) return;  // whole CTA, before any barrier or TMEM use
+  if (J.n_eff && n0 >= *J.n_eff) {     // a tile of exact zeros
+    for (int e = threadIdx.x; e < kOzM * NT; e += kOzThreads) {
+      const int r = m0 + e / NT, c = n0 + e % NT;
+      if (r < J.M && c < J.N) J.C[J.trans_c ? (size_t)c * J.ldc + r : (size_t)r * J.ldc + c] = 0.0;
+    }
+    return;
+  }
+  const uint32_t a_bytes = kOzM * 128;
+  const uint32_t b_bytes = (uint32_t)NT * 128;
+  const uint32_t stage_bytes = (a_bytes + b_bytes + 1023) / 1024 * 1024;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) / 1024 * 1024);
+  uint64_t* full = (uint64_t*)(smem + (size_t)stages * stage_bytes);
+  uint64_t* empty = full + stages;
+  uint64_t* tfull = empty + stages;  // [2]: a level's accumulator is complete
+  uint64_t* tfree = tfull + 2;       // [2]: the epilogue has read it
+  uint32_t* tmem_slot = (uint32_t*)(tfree + 2);
+  __shared__ int err;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t ncols = 2 * NT <= 32 ? 32 : (2 * NT <= 64 ? 64 : 128);
+
+  if (threadIdx.x == 0) {
+    err = 0;
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int t = 0; t < 2; ++t) {
+      mbar_init(&tfull[t], 1);
+      mbar_init(&tfree[t], 4);  // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int nk = (J.K + kOzBK - 1) / kOzBK;
+  constexpr int L0 = 2, L1 = kOzSlices + 2;  // levels L = i + j kept (slices numbered from 1)
+
+  if (warp == 0 && lane == 0) {
+    // producer: the slice tiles of every (level, i, k-tile) step, in MMA order
+    int step = 0;
+    for (int L = L0; L <= L1 && !*(volatile int*)&err; ++L)
+      for (int i = max(1, L - kOzSlices); i <= min(kOzSlices, L - 1) && !*(volatile int*)&err; ++i)
+        for (int kt = 0; kt < nk; ++kt, ++step) {
+          const int s = step % stages;
+          if (step >= stages && !mbar_wait(&empty[s], ((step / stages) & 1) ^ 1)) {
+            atomicExch(&err, 1);
+            break;
+          }
+          uint8_t* sa = smem + (size_t)s * stage_bytes;
+          mbar_expect_tx(&full[s], a_bytes + b_bytes);
+          tma_load_2d(sa, &J.tp, &full[s], kt * kOzBK, (i - 1) * J.M + m0);
+          tma_load_2d(sa + a_bytes, &J.ts, &full[s], kt * kOzBK, (L - i - 1) * J.Npad + n0);
+        }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: level L accumulates in TMEM buffer L & 1
+    const uint32_t id = idesc<__nv_bfloat16>(kOzM, NT);
+    int step = 0;
+    for (int L = L0; L <= L1 && !*(volatile int*)&err; ++L) {
+      const int bf = L & 1, use = (L - L0) >> 1;
+      if (use > 0) {
+        if (!mbar_wait(&tfree[bf], (use - 1) & 1)) {
+          atomicExch(&err, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+      const uint32_t td = tmem + (uint32_t)(bf * NT);
+      bool first = true;
+      for (int i = max(1, L - kOzSlices); i <= min(kOzSlices, L - 1) && !*(volatile int*)&err; ++i)
+        for (int kt = 0; kt < nk; ++kt, ++step) {
+          const int s = step % stages;
+          if (!mbar_wait(&full[s], (step / stages) & 1)) {
+            atomicExch(&err, 1);
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+          const uint32_t sb = sa + a_bytes;
+#pragma unroll
+          for (int kk = 0; kk < kOzBK / kOzMmaK; ++kk) {
+            const uint32_t off = kk * kOzMmaK * 2;  // 32 bytes per MMA step
+            mma<__nv_bfloat16>(td, smem_desc(sa + off), smem_desc(sb + off), id, (first && kk == 0) ? 0u : 1u);
+          }
+          first = false;
+          mma_commit(&empty[s]);
+        }
+      mma_commit(&tfull[bf]);
+    }
+  } else if (warp >= 2) {
+    // epilogue: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31
+    const int q = warp % 4;
+    const int row = m0 + q * 32 + lane;
+    double acc[kOzMaxNt];
+#pragma unroll
+    for (int c = 0; c < kOzMaxNt; ++c) acc[c] = 0.0;
+    bool ok = true;
+    for (int L = L0; L <= L1; ++L) {
+      const int bf = L & 1, use = (L - L0) >> 1;
+      if (!mbar_wait(&tfull[bf], use & 1)) {
+        ok = false;
+        atomicExch(&err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const double w = __longlong_as_double((long long)(1023 - 6 * L) << 52);  // 2^-6L
+      const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(bf * NT);
+#pragma unroll
+      for (int c0 = 0; c0 < kOzMaxNt; c0 += 16)
+        if (c0 < NT) {
+          float t[16];
+          ld16(tl + (uint32_t)c0, t);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc[c0 + u] = fma((double)t[u], w, acc[c0 + u]);
+        }
+      // this level's buffer is free again (the MMAs of level L + 1 run in the other one meanwhile)
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tfree[bf]);
+    }
+    if (ok && !err && row < J.M) {
+      const int er = J.ep[row];
+#pragma unroll
+      for (int c = 0; c < kOzMaxNt; ++c) {
+        const int col = n0 + c;
+        if (c < NT && col < J.N) {
+          const double x = ldexp(acc[c], er + J.es[col]);
+          J.C[J.trans_c ? (size_t)col * J.ldc + row : (size_t)row * J.ldc + col] = x;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+  if (threadIdx.x == 0 && err && J.err) atomicExch(J.err, 1);
+}
+
+size_t oz_smem_bytes(int ntile, int stages) {
+  const size_t stage = ((size_t)kOzM * 128 + (size_t)ntile * 128 + 1023) / 1024 * 1024;
+  return 1024 + stage * stages + (2 * (size_t)stages + 4) * 8 + 16;
+}
+
+}  // namespace
+
+// columns per CTA: the fewest tiles of at most 64 columns, as even as multiples of 16 allow
+int oz_ntile(int Npad) {
+  const int nt = (Npad + kOzMaxNt - 1) / kOzMaxNt;
+  return ((Npad + nt - 1) / nt + 15) / 16 * 16;
+}
+
+cudaError_t launch_oz_split(const OzSplitBatch& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  int mr = 1;
+  for (int i = 0; i < b.count; ++i) mr = max(mr, b.job[i].rows_blk);
+  prof_begin(KC_OZSPLIT, s);
+  oz_split_kernel<<<dim3(ceil_div(mr, 8), b.count), 256, 0, s>>>(b);
+  prof_end(KC_OZSPLIT, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gemm(const OzBatch& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  int maxM = 1, maxN = 1;
+  for (int i = 0; i < b.count; ++i) {
+    maxM = max(maxM, b.job[i].M);
+    maxN = max(maxN, b.job[i].N);
+  }
+  int stages = 6;
+  while (stages > 2 && oz_smem_bytes(b.ntile, stages) > 200 * 1024) --stages;
+  const size_t smem = oz_smem_bytes(b.ntile, stages);
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  prof_begin(KC_OZGEMM, s);
+  oz_gemm_kernel<<<dim3(ceil_div(maxM, kOzM), ceil_div(maxN, b.ntile), b.count), kOzThreads, smem, s>>>(b, stages);
+  prof_end(KC_OZGEMM, s);
+  return cudaGetLastError();
+}
+
+}  // namespace rsvd
+
+// C = A B^T in FP64 through the sliced tensor-core product (the verification
+// entry point declared in rsvd.h).
+extern "C" size_t rsvd_gemm_f64_tc_workspace_size(int M, int N, int K) {
+  using namespace rsvd;
+  if (M < 1 || N < 1 || K < 1) return 0;
+  const size_t Kp = (size_t)(K + 7) / 8 * 8, Npad = (size_t)(N + 15) / 16 * 16;
+  const size_t sa = align_up((size_t)kOzSlices * M * Kp * 2), sb = align_up((size_t)kOzSlices * Npad * Kp * 2);
+  return sa + sb + align_up((size_t)M * 4) + align_up(Npad * 4);
+}
+
+extern "C" int rsvd_gemm_f64_tc(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                                int ldc, void* work, size_t work_bytes, int* err, void* cuda_stream) {
+  using namespace rsvd;
+  if (M < 1 || N < 1 || N > 256 || K < 1 || K > kOzMaxK || lda < K || ldb < K || ldc < N) return RSVD_ERR_INVALID_SIZE;
+  if (!A || !B || !C || !work) return RSVD_ERR_NULL_POINTER;
+  if (work_bytes < rsvd_gemm_f64_tc_workspace_size(M, N, K)) return RSVD_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int Kp = (K + 7) / 8 * 8, Npad = (N + 15) / 16 * 16;
+  char* w = (char*)work;
+  __nv_bfloat16* SA = (__nv_bfloat16*)w;
+  w += align_up((size_t)kOzSlices * M * Kp * 2);
+  __nv_bfloat16* SB = (__nv_bfloat16*)w;
+  w += align_up((size_t)kOzSlices * Npad * Kp * 2);
+  int* eA = (int*)w;
+  w += align_up((size_t)M * 4);
+  int* eB = (int*)w;
+  OzSplitBatch sp;
+  sp.count = 2;
+  sp.job[0] = OzSplitJob{A, M, K, lda, 0, M, Kp, SA, eA};
+  sp.job[1] = OzSplitJob{B, N, K, ldb, 0, Npad, Kp, SB, eB};
+  cudaError_t e = launch_oz_split(sp, s);
+  if (e != cudaSuccess) {
+    last_cuda_error() = e;
+    return RSVD_ERR_LAUNCH;
+  }
+  OzBatch b;
+  b.count = 1;
+  b.ntile = oz_ntile(Npad);
+  OzJob& J = b.job[0];
+  if (!make_tmap(&J.tp, SA, kOzSlices * M, Kp, Kp, 2, 128) || !make_tmap(&J.ts, SB, kOzSlices * Npad, Kp, Kp, 2, b.ntile))
+    return RSVD_ERR_INVALID_SIZE;
+  J.C = C;
+  J.ep = eA;
+  J.es = eB;
+  J.n_eff = nullptr;
+  J.err = err;
+  J.M = M;
+  J.N = N;
+  J.Npad = Npad;
+  J.K = K;
+  J.ldc = ldc;
+  J.trans_c = 0;
+  e = launch_oz_gemm(b, s);
+  if (e != cudaSuccess) {
+    last_cuda_error() = e;
+    return RSVD_ERR_LAUNCH;
+  }
+  return RSVD_OK;
+}

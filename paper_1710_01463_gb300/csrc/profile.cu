@@ -28,7 +28,7 @@ Prof& prof() {
 }
 
 const char* kNames[KC_COUNT] = {"prep", "omega", "gemm", "gram", "cholesky", "householder",
-                                "jacobi", "sign", "select", "tebd", "backward", "tcgemm", "convert"};
+                                "jacobi", "sign", "select", "tebd", "backward", "tcgemm", "convert", "ozgemm", "ozsplit"};
 
 }  // namespace
 
