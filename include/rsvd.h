@@ -57,6 +57,12 @@ extern "C" {
 #define RSVD_WARN_NOCONV        1   /* device: the Jacobi SVD hit its sweep cap (info.status) */
 #define RSVD_WARN_CG            2   /* device (backward): a conjugate-gradient column did not converge (info.status) */
 
+/* rsvd_params.flags.  By default the FP64 products with A (the sketch, the
+ * power iteration and the projection) of matrices with m, n <= 256 and
+ * l <= 256 run on the tensor cores by exact slicing (see rsvd_gemm_f64_tc:
+ * FP64-class error); RSVD_FLAG_F64_SIMT computes them with FP64 FMAs instead. */
+#define RSVD_FLAG_F64_SIMT      1
+
 /* Paths recorded in rsvd_info.path (bit set). */
 #define RSVD_PATH_EXACT         1   /* m <= l and m <= 16: Q = I, B = A (the sample covers the range) */
 #define RSVD_PATH_HOUSEHOLDER   2   /* CholeskyQR2 broke down at least once; Householder QR used */
@@ -81,7 +87,7 @@ typedef struct {
   uint64_t seed;    /* Philox key word 0 */
   uint64_t stream;  /* Philox key word 1 of the first matrix; matrix b uses stream + b */
   int max_sweeps;   /* Jacobi sweep cap (0 = default 40) */
-  int flags;        /* reserved, must be 0 */
+  int flags;        /* 0, or RSVD_FLAG_F64_SIMT */
 } rsvd_params;
 
 /* Device-written record, one per matrix. */

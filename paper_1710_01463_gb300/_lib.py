@@ -28,6 +28,7 @@ RSVD_F64 = 0
 RSVD_F32 = 1
 RSVD_TF32 = 2
 RSVD_BF16 = 3
+RSVD_FLAG_F64_SIMT = 1
 
 EXPORTED = (
     "rsvd_gaussian",

@@ -30,9 +30,11 @@ def _stream_handle(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _params(k, p, q, prec, seed, stream, max_sweeps=0):
+def _params(k, p, q, prec, seed, stream, max_sweeps=0, simt=False):
+    """rsvd_params; simt=True sets RSVD_FLAG_F64_SIMT (FP64 products with A on FP64 FMAs
+    instead of the tensor cores by exact slicing)."""
     return _lib.RsvdParams(int(k), int(p), int(q), int(prec), int(seed) & ((1 << 64) - 1),
-                           int(stream) & ((1 << 64) - 1), int(max_sweeps), 0)
+                           int(stream) & ((1 << 64) - 1), int(max_sweeps), _lib.RSVD_FLAG_F64_SIMT if simt else 0)
 
 
 def _require_cuda(*ts):
@@ -67,11 +69,12 @@ def rsvd_workspace_size(m, n, k, p=8, q=2, dtype=torch.float64):
     return sz.value
 
 
-def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf32=False):
+def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf32=False, simt=False):
     """Rank-k RSVD of one matrix: returns (U, S, Vt, info) as CUDA tensors.
 
-    A float64 -> FP64 products; float32 -> FP32 (tf32=True: TF32 tensor cores);
-    bfloat16 -> BF16 tensor cores.  U and Vt are float64 for float64 A, else float32.
+    A float64 -> FP64 products (tensor cores by exact slicing where m, n, l <= 256,
+    unless simt=True); float32 -> FP32 (tf32=True: TF32 tensor cores); bfloat16 -> BF16
+    tensor cores.  U and Vt are float64 for float64 A, else float32.
     """
     lib = _lib.load()
     _require_cuda(A)
@@ -79,7 +82,7 @@ def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf3
         raise ValueError("A must be a row-major 2-D tensor")
     prec = _prec_of(A, tf32)
     m, n = A.shape
-    par = _params(k, p, q, prec, seed, stream, max_sweeps)
+    par = _params(k, p, q, prec, seed, stream, max_sweeps, simt)
     sz = ctypes.c_size_t(0)
     _lib.check(lib.rsvd_workspace_size(m, n, ctypes.byref(par), ctypes.byref(sz)), "rsvd_workspace_size")
     if work is None or work.numel() < sz.value:
@@ -100,7 +103,7 @@ class BatchedPlan:
     """Preallocated outputs and workspace of rsvd_truncate_batched for fixed shapes."""
 
     def __init__(self, shapes, ks, p=8, q=2, seed=0, stream=0, dtype=torch.float64, device="cuda",
-                 max_sweeps=0, chi_global=0, tf32=False):
+                 max_sweeps=0, chi_global=0, tf32=False, simt=False):
         lib = _lib.load()
         self.shapes = [(int(m), int(n)) for m, n in shapes]
         self.ks = [int(k) for k in ks]
@@ -108,7 +111,7 @@ class BatchedPlan:
         self.chi_global = int(chi_global)
         prec = _lib.RSVD_TF32 if tf32 else _DTYPE_PREC[dtype]
         out = torch.float64 if dtype == torch.float64 else torch.float32
-        self.par = _params(self.ks[0], p, q, prec, seed, stream, max_sweeps)
+        self.par = _params(self.ks[0], p, q, prec, seed, stream, max_sweeps, simt)
         B = len(self.shapes)
         self.m_arr = _lib.int_array([s[0] for s in self.shapes])
         self.n_arr = _lib.int_array([s[1] for s in self.shapes])

@@ -52,6 +52,12 @@ struct Prob {
   int wide;
   double *Bt, *Bt2, *Mb, *RinvD;
   void *Wb, *Qbt;
+  // FP64 products with A on the tensor cores (exact slicing): slices of A
+  // (m rows, K = n), of A^T (n rows, K = m) and of the thin operand's columns
+  int oz;
+  __nv_bfloat16 *SA, *SAt, *SS;
+  int *eA, *eAt, *eS;
+  int KpA, KpAt, KpS, Npad;
 };
 
 inline int pad8(int x) { return (x + 7) / 8 * 8; }
@@ -59,7 +65,7 @@ inline int pad8(int x) { return (x + 7) / 8 * 8; }
 // Workspace of one matrix (bytes), with the buffer offsets when `p` is given.
 // tc_bytes > 0 (the operand size of the tensor-core precisions) adds A^T
 // (n x m), Omega^T / Z^T (l x n) and Q^T (l x m) with 8-element-aligned rows.
-size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int tc_bytes = 0) {
+size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int tc_bytes = 0, int oz = 0) {
   const int mx = std::max(m, n);
   const int nchunk = ceil_div(mx, kGramChunk);
   const int wide = n >= 4 * l ? 1 : 0;
@@ -97,7 +103,18 @@ size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int
   void* RinvD = take(wide ? (size_t)l * l * 8 : 0);
   void* Wb = take(wide ? (size_t)std::max(k, 1) * l * tsize : 0);
   void* Qbt = take(wide ? (size_t)l * n * tsize : 0);
+  const int KpA = pad8(n), KpAt = pad8(m), KpS = pad8(std::max(m, n)), Npad = (l + 15) / 16 * 16;
+  void* SA = take(oz ? (size_t)kOzSlices * m * KpA * 2 : 0);
+  void* SAt = take(oz ? (size_t)kOzSlices * n * KpAt * 2 : 0);
+  void* SS = take(oz ? (size_t)kOzSlices * Npad * KpS * 2 : 0);
+  void* eA = take(oz ? (size_t)m * 4 : 0);
+  void* eAt = take(oz ? (size_t)n * 4 : 0);
+  void* eS = take(oz ? (size_t)Npad * 4 : 0);
   if (p) {
+    p->oz = oz;
+    p->SA = (__nv_bfloat16*)SA; p->SAt = (__nv_bfloat16*)SAt; p->SS = (__nv_bfloat16*)SS;
+    p->eA = (int*)eA; p->eAt = (int*)eAt; p->eS = (int*)eS;
+    p->KpA = KpA; p->KpAt = KpAt; p->KpS = KpS; p->Npad = Npad;
     p->At = At; p->WT = WT; p->QT = QT;
     p->ldAt = pad8(m); p->ldWT = pad8(n); p->ldQT = pad8(m);
     p->Y0 = Y0; p->Y1 = Y1; p->Z0 = Z0; p->Z1 = Z1; p->Rinv = Rinv; p->Ps = Ps;
@@ -123,6 +140,14 @@ inline int sample_width(int m, int n, int k, int p) { return std::min(k + p, std
 // many sweeps over all rows of A.
 constexpr int kExactMaxRows = 16;
 inline int use_exact_path(int m, int l) { return (m <= l && m <= kExactMaxRows) ? 1 : 0; }
+
+// FP64 products with A on the tensor cores: exact level sums need K <= 256
+// (K = n for A Z, m for A^T Y) and the thin operand fits one CTA row (l <= 256)
+inline int use_oz(int m, int n, int l, int exact, const rsvd_params* p) {
+  return (p->prec == RSVD_F64 && !(p->flags & RSVD_FLAG_F64_SIMT) && !exact && m <= kOzMaxK && n <= kOzMaxK && l <= 256)
+             ? 1
+             : 0;
+}
 
 #define RSVD_TRY(x)                              \
   do {                                           \
@@ -303,21 +328,93 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
       }
       RSVD_TRY(launch_omega<T>(b, s));
     }
-    auto gemm_AZ = [&]() {  // Y0 = A Z0
+    // products with A: on the tensor cores by exact slicing for the eligible
+    // matrices (the slices of A and A^T are made once per call), FP64 FMAs for
+    // the others
+    std::vector<Prob*> rsd, oz;
+    for (auto* pp : rs) (pp->oz ? oz : rsd).push_back(pp);
+    struct OzMaps {
+      CUtensorMap tpA, tpAt, tsN, tsM;
+    };
+    std::vector<OzMaps> maps(oz.size());
+    int ntile = 16;
+    if (!oz.empty()) {
+      int npad = 16;
+      for (auto* pp : oz) npad = std::max(npad, pp->Npad);
+      ntile = oz_ntile(npad);
+      OzSplitBatch sb;
+      sb.count = 0;
+      for (size_t i = 0; i < oz.size(); ++i) {
+        Prob& p = *oz[i];
+        if (sb.count + 2 > kMaxJobs) {
+          RSVD_TRY(launch_oz_split(sb, s));
+          sb.count = 0;
+        }
+        sb.job[sb.count++] = OzSplitJob{(const double*)p.A, p.m, p.n, p.lda, 0, p.m, p.KpA, p.SA, p.eA};
+        sb.job[sb.count++] = OzSplitJob{(const double*)p.A, p.n, p.m, p.lda, 1, p.n, p.KpAt, p.SAt, p.eAt};
+        if (!make_tmap(&maps[i].tpA, p.SA, kOzSlices * p.m, p.n, p.KpA, 2, 128) ||
+            !make_tmap(&maps[i].tpAt, p.SAt, kOzSlices * p.n, p.m, p.KpAt, 2, 128) ||
+            !make_tmap(&maps[i].tsN, p.SS, kOzSlices * p.Npad, p.n, p.KpS, 2, ntile) ||
+            !make_tmap(&maps[i].tsM, p.SS, kOzSlices * p.Npad, p.m, p.KpS, 2, ntile))
+          return RSVD_ERR_LAUNCH;
+      }
+      RSVD_TRY(launch_oz_split(sb, s));
+    }
+    // C = P S with P = A (K = n) or A^T (K = m), S = the thin operand X (K x l,
+    // ld l); C row-major (ldc = l) or, for B = Q^T A, written transposed
+    enum { kAZ, kAtY, kQtA };
+    auto oz_product = [&](int kind) -> int {
+      OzSplitBatch sb;
+      sb.count = 0;
+      for (auto* pp : oz) {
+        Prob& p = *pp;
+        const bool onA = kind == kAZ;
+        sb.job[sb.count++] = OzSplitJob{(const double*)(onA ? p.Z0 : p.Y0), p.l, onA ? p.n : p.m, p.l, 1, p.Npad,
+                                        p.KpS, p.SS, p.eS};
+      }
+      RSVD_TRY(launch_oz_split(sb, s));
+      for (size_t c0 = 0; c0 < oz.size(); c0 += kMaxOzJobs) {
+        OzBatch b;
+        b.count = 0;
+        b.ntile = ntile;
+        for (size_t i = c0; i < std::min(oz.size(), c0 + kMaxOzJobs); ++i) {
+          Prob& p = *oz[i];
+          OzJob& J = b.job[b.count++];
+          J.tp = kind == kAZ ? maps[i].tpA : maps[i].tpAt;
+          J.ts = kind == kAZ ? maps[i].tsN : maps[i].tsM;
+          J.ep = kind == kAZ ? p.eA : p.eAt;
+          J.es = p.eS;
+          J.M = kind == kAZ ? p.m : p.n;
+          J.N = p.l;
+          J.Npad = p.Npad;
+          J.K = kind == kAZ ? p.n : p.m;
+          J.C = kind == kAZ ? (double*)p.Y0 : kind == kAtY ? (double*)p.Z0 : p.Bm;
+          J.ldc = kind == kQtA ? p.n : p.l;
+          J.trans_c = kind == kQtA ? 1 : 0;
+          J.n_eff = p.want_u ? nullptr : p.flag + 2;
+          J.err = p.flag + 1;  // a timed-out pipeline wait is reported by the Jacobi SVD's status
+        }
+        RSVD_TRY(launch_oz_gemm(b, s));
+      }
+      return RSVD_OK;
+    };
+    auto gemm_AZ = [&]() -> cudaError_t {  // Y0 = A Z0
+      if (!oz.empty() && oz_product(kAZ) != RSVD_OK) return last_cuda_error();
       GemmBatch<T, T> g;
-      g.count = rc;
-      for (int i = 0; i < rc; ++i) {
-        Prob& p = *rs[i];
+      g.count = (int)rsd.size();
+      for (int i = 0; i < g.count; ++i) {
+        Prob& p = *rsd[i];
         g.job[i] = GemmJob<T, T>{p.m, p.l, p.n, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Z0, (T*)p.Y0, nullptr, nullptr, 0};
         if (!p.want_u) g.job[i].n_eff = p.flag + 2;
       }
       return launch_gemm<T, T, false, false>(g, s);
     };
-    auto gemm_AtY = [&]() {  // Z0 = A^T Y0
+    auto gemm_AtY = [&]() -> cudaError_t {  // Z0 = A^T Y0
+      if (!oz.empty() && oz_product(kAtY) != RSVD_OK) return last_cuda_error();
       GemmBatch<T, T> g;
-      g.count = rc;
-      for (int i = 0; i < rc; ++i) {
-        Prob& p = *rs[i];
+      g.count = (int)rsd.size();
+      for (int i = 0; i < g.count; ++i) {
+        Prob& p = *rsd[i];
         g.job[i] = GemmJob<T, T>{p.n, p.l, p.m, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Y0, (T*)p.Z0, nullptr, nullptr, 0};
         if (!p.want_u) g.job[i].n_eff = p.flag + 2;
       }
@@ -333,19 +430,22 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
       RSVD_TRY(launch_orth<T>(orth_batch<T>(rs, true), s));
     }
     {  // step 4: B = Q^T A (l x n) in FP64
+      if (!oz.empty() && oz_product(kQtA) != RSVD_OK) return RSVD_ERR_LAUNCH;
       GemmBatch<T, double> g;
-      g.count = rc;
-      for (int i = 0; i < rc; ++i) {
-        Prob& p = *rs[i];
+      g.count = (int)rsd.size();
+      for (int i = 0; i < g.count; ++i) {
+        Prob& p = *rsd[i];
         g.job[i] = GemmJob<T, double>{p.l, p.n, p.m, p.l, p.lda, p.n, (const T*)p.Y0, (const T*)p.A, p.Bm, nullptr, nullptr, 0};
         if (!p.want_u) g.job[i].m_eff = p.flag + 2;
       }
       RSVD_TRY((launch_gemm<T, double, true, false>(g, s)));
     }
   }
-  // SVD of B
+  // SVD of B (a timed-out wait of the tensor-core products is reported through its status)
   {
-    int rc = svd_of_B<T>(probs, s, false);
+    bool any_oz = false;
+    for (auto& pr : probs) any_oz = any_oz || (pr.oz && !pr.exact);
+    int rc = svd_of_B<T>(probs, s, any_oz);
     if (rc != RSVD_OK) return rc;
   }
   // lift U = Q U~ and fix the signs
@@ -499,7 +599,8 @@ int run_chunk_tc(std::vector<Prob>& probs, int q, cudaStream_t s) {
 
 int check_params(const rsvd_params* p) {
   if (!p) return RSVD_ERR_NULL_POINTER;
-  if (p->p < 0 || p->q < 0 || p->q > 64 || p->max_sweeps < 0 || p->flags != 0) return RSVD_ERR_INVALID_SIZE;
+  if (p->p < 0 || p->q < 0 || p->q > 64 || p->max_sweeps < 0 || (p->flags & ~RSVD_FLAG_F64_SIMT) != 0)
+    return RSVD_ERR_INVALID_SIZE;
   if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_TF32 && p->prec != RSVD_BF16)
     return RSVD_ERR_PRECISION;
   return RSVD_OK;
@@ -513,11 +614,11 @@ int run_batched(std::vector<Prob>& probs, const rsvd_params* p, char* work, size
   const size_t ts = tsize_of(p->prec);
   const int tcb = tc_bytes_of(p->prec);
   size_t need = 0;
-  for (auto& pr : probs) need += layout(nullptr, pr.m, pr.n, pr.k, pr.l, ts, nullptr, tcb);
+  for (auto& pr : probs) need += layout(nullptr, pr.m, pr.n, pr.k, pr.l, ts, nullptr, tcb, use_oz(pr.m, pr.n, pr.l, pr.exact, p));
   if (need > work_bytes) return RSVD_ERR_WORKSPACE;
   size_t off = 0;
   for (auto& pr : probs) {
-    off += layout(&pr, pr.m, pr.n, pr.k, pr.l, ts, work + off, tcb);
+    off += layout(&pr, pr.m, pr.n, pr.k, pr.l, ts, work + off, tcb, use_oz(pr.m, pr.n, pr.l, pr.exact, p));
   }
   const size_t step = is_tc(p->prec) ? (size_t)kMaxTcJobs : (size_t)kMaxJobs;
   for (size_t c0 = 0; c0 < probs.size(); c0 += step) {
@@ -574,7 +675,8 @@ int rsvd_batched_workspace_size(int batch, const int* m, const int* n, const int
     const int l = sample_width(m[b], n[b], k[b], p->p);
     if (l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
     if (is_tc(p->prec) && (l > 256 || m[b] <= l)) return RSVD_ERR_INVALID_SIZE;
-    tot += layout(nullptr, m[b], n[b], k[b], l, tsize_of(p->prec), nullptr, tc_bytes_of(p->prec));
+    tot += layout(nullptr, m[b], n[b], k[b], l, tsize_of(p->prec), nullptr, tc_bytes_of(p->prec),
+                  use_oz(m[b], n[b], l, use_exact_path(m[b], l), p));
   }
   *bytes = tot;
   return RSVD_OK;
@@ -653,7 +755,7 @@ namespace {
 struct TebdLayout {
   size_t t2, thetaB, theta, S, nrm, fro2, rsvd;
 };
-size_t tebd_bond_bytes(int m, int n, int k, int l, TebdLayout* o) {
+size_t tebd_bond_bytes(int m, int n, int k, int l, int oz, TebdLayout* o) {
   size_t off = 0;
   auto take = [&](size_t b) {
     size_t x = off;
@@ -668,7 +770,7 @@ size_t tebd_bond_bytes(int m, int n, int k, int l, TebdLayout* o) {
   L.nrm = take(8);
   L.fro2 = take(64 * 8);
   L.rsvd = off;
-  off += layout(nullptr, m, n, k, l, 8, nullptr);
+  off += layout(nullptr, m, n, k, l, 8, nullptr, 0, oz);
   if (o) *o = L;
   return off;
 }
@@ -684,7 +786,8 @@ int tebd_workspace_size(int L, int d, const int* D, int nb, const rsvd_params* p
     const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
     if (k < 1 || k > std::min(m, n)) return RSVD_ERR_INVALID_SIZE;
     if (sample_width(m, n, k, p->p) > kMaxSample) return RSVD_ERR_INVALID_SIZE;
-    mx = std::max(mx, tebd_bond_bytes(m, n, k, sample_width(m, n, k, p->p), nullptr));
+    const int l = sample_width(m, n, k, p->p);
+    mx = std::max(mx, tebd_bond_bytes(m, n, k, l, use_oz(m, n, l, use_exact_path(m, l), p), nullptr));
   }
   *bytes = mx * (size_t)nb;
   return RSVD_OK;
@@ -714,7 +817,8 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
   size_t per = 0;
   for (int i = 0; i + 1 < L; ++i) {
     const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
-    per = std::max(per, tebd_bond_bytes(m, n, k, sample_width(m, n, k, p->p), nullptr));
+    const int l = sample_width(m, n, k, p->p);
+    per = std::max(per, tebd_bond_bytes(m, n, k, l, use_oz(m, n, l, use_exact_path(m, l), p), nullptr));
   }
   if (per * (size_t)nb > work_bytes) return RSVD_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -731,7 +835,8 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     const int m = Dl * d, n = d * Dr, k = Dm;
     const int l = sample_width(m, n, k, p->p);
     char* wb = base + per * b;
-    tebd_bond_bytes(m, n, k, l, &lay[b]);
+    const int oz = use_oz(m, n, l, use_exact_path(m, l), p);
+    tebd_bond_bytes(m, n, k, l, oz, &lay[b]);
     double* T2 = (double*)(wb + lay[b].t2);
     double* thB = (double*)(wb + lay[b].thetaB);
     double* th = (double*)(wb + lay[b].theta);
@@ -753,7 +858,7 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     pr.seed = p->seed; pr.stream = p->stream + (uint64_t)i;
     pr.info = info + b;
     pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
-    layout(&pr, m, n, k, l, 8, wb + lay[b].rsvd);
+    layout(&pr, m, n, k, l, 8, wb + lay[b].rsvd, 0, oz);
   }
   RSVD_TRY((launch_gemm<double, double, false, false>(g2, s)));
   RSVD_TRY(launch_tebd_theta(tb, s));

@@ -40,11 +40,11 @@ def bond_gate(hb, tau):
 class TebdChain:
     """MPS of an L-site chain with right-canonical tensors B[i] and Schmidt values lam[j]."""
 
-    def __init__(self, L, chi, h=1.0, p=10, q=2, seed=0, device="cuda", max_sweeps=0):
+    def __init__(self, L, chi, h=1.0, p=10, q=2, seed=0, device="cuda", max_sweeps=0, simt=False):
         if L < 2:
             raise ValueError("L >= 2 required")
         self.L, self.d, self.chi, self.h = L, 2, chi, h
-        self.p, self.q, self.seed, self.max_sweeps = p, q, seed, max_sweeps
+        self.p, self.q, self.seed, self.max_sweeps, self.simt = p, q, seed, max_sweeps, simt
         self.device = torch.device(device)
         d = self.d
         self.D = [int(min(d ** min(j, L - j), chi)) for j in range(L + 1)]
@@ -56,7 +56,7 @@ class TebdChain:
         self.D_arr = _lib.int_array(self.D)
         nb = max(len(x) for x in self.layers)
         lib = _lib.load()
-        par = _params(1, p, q, _lib.RSVD_F64, seed, 0)
+        par = _params(1, p, q, _lib.RSVD_F64, seed, 0, 0, simt)
         sz = ctypes.c_size_t(0)
         _lib.check(lib.tebd_workspace_size(L, d, self.D_arr, nb, ctypes.byref(par), ctypes.byref(sz)),
                    "tebd_workspace_size")
@@ -99,7 +99,7 @@ class TebdChain:
             if not bonds:
                 continue
             par = _params(1, self.p, self.q, _lib.RSVD_F64, self.seed, (3 * step_index + j) * self.L,
-                          self.max_sweeps)
+                          self.max_sweeps, self.simt)
             rc = lib.tebd_bond_update(self.L, self.d, self.D_arr, len(bonds), self.bond_arr[layer],
                                       ctypes.c_void_p(self.B.data_ptr()), self.tensor_stride,
                                       ctypes.c_void_p(self.lam.data_ptr()), self.lam_stride,

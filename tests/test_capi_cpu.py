@@ -39,17 +39,39 @@ def test_status_strings(lib):
         assert len(lib.rsvd_status_string(code)) > 0
 
 
-def params(k=32, p=8, q=2, prec=0):
+def params(k=32, p=8, q=2, prec=0, flags=0):
     from paper_1710_01463_gb300 import _lib
-    return _lib.RsvdParams(k, p, q, prec, 201, 0, 0, 0)
+    return _lib.RsvdParams(k, p, q, prec, 201, 0, 0, flags)
+
+
+def wsize(m, n, **kw):
+    sz = ctypes.c_size_t(0)
+    assert lib_global().rsvd_workspace_size(m, n, ctypes.byref(params(**kw)), ctypes.byref(sz)) == 0
+    return sz.value
+
+
+def lib_global():
+    from paper_1710_01463_gb300 import _lib
+    return _lib.load()
 
 
 def test_workspace_size_grows_with_size(lib):
-    sz1, sz2 = ctypes.c_size_t(0), ctypes.c_size_t(0)
-    assert lib.rsvd_workspace_size(256, 256, ctypes.byref(params()), ctypes.byref(sz1)) == 0
-    assert lib.rsvd_workspace_size(1024, 1024, ctypes.byref(params()), ctypes.byref(sz2)) == 0
-    assert 0 < sz1.value < sz2.value
-    assert sz1.value % 256 == 0
+    # within one product path (FP64 FMAs, or tensor-core slices for m, n <= 256)
+    assert 0 < wsize(256, 256, flags=1) < wsize(1024, 1024) < wsize(2048, 2048)
+    assert 0 < wsize(128, 128) < wsize(256, 256)
+    assert wsize(256, 256) % 256 == 0
+
+
+def test_workspace_holds_the_fp64_slices(lib):
+    # nine BF16 slices of A and of A^T (256 x 256) and of the thin operand (48 x 256), exponents
+    extra = wsize(256, 256) - wsize(256, 256, flags=1)
+    assert extra >= 9 * 2 * (256 * 256 + 256 * 256 + 48 * 256)
+    assert extra < 4 * 1024 * 1024
+
+
+def test_unknown_flags_rejected(lib):
+    sz = ctypes.c_size_t(0)
+    assert lib.rsvd_workspace_size(64, 64, ctypes.byref(params(flags=2)), ctypes.byref(sz)) == -1
 
 
 @pytest.mark.parametrize("m,n,k,p,q,prec,code", [

@@ -124,3 +124,24 @@ def test_sweep_cap_reported(api):
     torch.cuda.synchronize()
     st = api.info_dicts(info)[0]
     assert st["status"] == 1 and st["jacobi_sweeps"] == 1
+
+
+@pytest.mark.parametrize("m,n,k", [(256, 256, 32), (200, 150, 20), (256, 96, 40)])
+def test_fp64_product_paths_agree(api, m, n, k):
+    # the products with A on the tensor cores by exact slicing (default for m, n <= 256)
+    # and on FP64 FMAs (flag) give the oracle's factorization within the FP64 bar
+    A = inputs.spectral_matrix(m, n, inputs.exp_spectrum(min(m, n), 12.0), 31 + m)
+    At = torch.from_numpy(A).cuda()
+    Uo, So, Vto = orsvd.rsvd(A, k, 8, 2, 5, 9)
+    out = {}
+    for simt in (False, True):
+        U, S, Vt, info = api.rsvd_truncate(At, k, 8, 2, 5, 9, simt=simt)
+        torch.cuda.synchronize()
+        s = S.cpu().numpy()
+        assert np.all(np.abs(s - So) <= sigma_tol(So))
+        assert api.info_dicts(info)[0]["status"] == 0
+        out[simt] = (s, U.cpu().numpy(), Vt.cpu().numpy())
+    np.testing.assert_allclose(out[False][0], out[True][0], rtol=1e-11, atol=1e-14 * So[0])
+    u0, u1 = out[False][1], out[True][1]
+    np.testing.assert_allclose(u0.T @ u0, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(np.abs(np.sum(u0 * u1, axis=0))[:k // 2], 1.0, atol=1e-9)

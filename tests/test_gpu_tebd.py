@@ -76,3 +76,25 @@ def test_checkpoint_resume_is_exact(mods, tmp_path):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(a.B.cpu().numpy(), b.B.cpu().numpy())
     np.testing.assert_array_equal(a.lam.cpu().numpy(), b.lam.cpu().numpy())
+
+
+def test_tebd_fp64_product_paths_agree():
+    # a few Trotter steps with the products on the tensor cores (default) and on FP64 FMAs
+    need_gpu()
+    from paper_1710_01463_gb300.tebd import TebdChain
+    from paper_1710_01463_gb300 import inputs as inp
+    from oracle import tebd as ot
+    L, chi = 12, 16
+    res = []
+    for simt in (False, True):
+        ch = TebdChain(L, chi, h=1.0, p=6, q=2, seed=3, simt=simt)
+        ch.set_product_state(inp.product_state_vectors(L, 2, 7))
+        ch.set_dt(0.05)
+        for s in range(6):
+            ch.step(s)
+        torch.cuda.synchronize()
+        assert int((ch.info[..., 0] != 0).sum()) == 0
+        res.append((ot.mps_energy(ch.tensors(), L, 1.0), ch.schmidt_values()))
+    assert abs(res[0][0] - res[1][0]) <= 1e-10 * abs(res[1][0])
+    for a, b in zip(res[0][1], res[1][1]):
+        np.testing.assert_allclose(a, b, atol=1e-10)
