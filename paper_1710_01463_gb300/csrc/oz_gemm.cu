@@ -22,13 +22,15 @@
 // of an FP64 GEMM (K 2^-53 |P_r| |S_c|).  The ten level sums are combined in
 // FP64 in the epilogue.
 //
-// One CTA computes a 128 x ntile tile (ntile <= 64: the epilogue keeps one
-// FP64 accumulator per column in registers).  Warp 0 issues the TMA loads of
-// the P and S slice tiles, warp 1 issues the MMAs into two TMEM accumulators
-// (levels alternate, so the epilogue of one level overlaps the MMAs of the
-// next), warps 2-5 read each finished level back and add it in FP64.  Every
-// mbarrier wait is bounded; on a timeout the kernel records an error and
-// finishes without further work.
+// One CTA computes a 128 x ntile tile (ntile <= 48).  Slice i of P (all of K,
+// at most 64 KB) stays in shared memory, double-buffered, while every slice j
+// of S that it pairs with streams through a ring of stages; each product goes
+// to the TMEM accumulator of its level (ten levels x ntile <= 480 columns).
+// Level L receives its last product with i = L - 1 (L <= 10) or i = 9, so the
+// epilogue warps read level L back and add it in FP64 while the MMAs of later
+// slices run.  Warp 0 issues the TMA loads, warp 1 (one elected thread) the
+// MMAs, warps 2-5 the epilogue.  Every mbarrier wait is bounded; on a timeout
+// the kernel records an error and finishes without further work.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -42,7 +44,8 @@ constexpr int kOzThreads = 192;
 constexpr int kOzM = 128;
 constexpr int kOzBK = 64;     // BF16 elements of K per stage (128 bytes)
 constexpr int kOzMmaK = 16;   // K per MMA
-constexpr int kOzMaxNt = 64;  // columns per CTA
+constexpr int kOzMaxNt = 48;  // columns per CTA (ten level accumulators fit 512 TMEM columns)
+constexpr int kOzMaxKt = kOzMaxK / 64;    // K tiles of one P slice
 
 // ---------------------------------------------------------------- slicing
 // One warp per row of the slice block: the row's exponent from the largest
@@ -106,32 +109,38 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
     }
     return;
   }
-  const uint32_t a_bytes = kOzM * 128;
-  const uint32_t b_bytes = (uint32_t)NT * 128;
-  const uint32_t stage_bytes = (a_bytes + b_bytes + 1023) / 1024 * 1024;
+  const int nk = (J.K + kOzBK - 1) / kOzBK;  // K tiles (<= kOzMaxKt)
+  constexpr uint32_t kTileA = kOzM * 128;    // one K tile of a P slice: 128 rows x 128 bytes
+  const uint32_t p_bytes = (uint32_t)nk * kTileA;
+  const uint32_t s_bytes = (uint32_t)NT * 128;
+  const uint32_t s_stage = (s_bytes + 1023) / 1024 * 1024;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) / 1024 * 1024);
-  uint64_t* full = (uint64_t*)(smem + (size_t)stages * stage_bytes);
-  uint64_t* empty = full + stages;
-  uint64_t* tfull = empty + stages;  // [2]: a level's accumulator is complete
-  uint64_t* tfree = tfull + 2;       // [2]: the epilogue has read it
-  uint32_t* tmem_slot = (uint32_t*)(tfree + 2);
+  uint8_t* pbuf = smem;                                   // [2][kOzMaxKt] P tiles
+  uint8_t* sbuf = smem + 2 * (size_t)kOzMaxKt * kTileA;  // [stages] S tiles
+  uint64_t* pfull = (uint64_t*)(sbuf + (size_t)stages * s_stage);
+  uint64_t* pempty = pfull + 2;
+  uint64_t* sfull = pempty + 2;
+  uint64_t* sempty = sfull + stages;
+  uint64_t* ifull = sempty + stages;  // [kOzSlices]: the products of slice i are complete
+  uint32_t* tmem_slot = (uint32_t*)(ifull + kOzSlices);
   __shared__ int err;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const uint32_t ncols = 2 * NT <= 32 ? 32 : (2 * NT <= 64 ? 64 : 128);
+  constexpr uint32_t ncols = 512;
 
   if (threadIdx.x == 0) {
     err = 0;
-    for (int s = 0; s < stages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
     for (int t = 0; t < 2; ++t) {
-      mbar_init(&tfull[t], 1);
-      mbar_init(&tfree[t], 4);  // one arrival per epilogue warp
+      mbar_init(&pfull[t], 1);
+      mbar_init(&pempty[t], 1);
     }
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&sfull[s], 1);
+      mbar_init(&sempty[s], 1);
+    }
+    for (int i = 0; i < kOzSlices; ++i) mbar_init(&ifull[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -144,92 +153,100 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int nk = (J.K + kOzBK - 1) / kOzBK;
-  constexpr int L0 = 2, L1 = kOzSlices + 2;  // levels L = i + j kept (slices numbered from 1)
+  volatile int* errv = &err;
+  // slices are numbered 1 .. kOzSlices; products (i, j) with i + j <= kOzSlices + 2 are kept
+  auto jmax = [](int i) { return min(kOzSlices, kOzSlices + 2 - i); };
 
   if (warp == 0 && lane == 0) {
-    // producer: the slice tiles of every (level, i, k-tile) step, in MMA order
+    // producer: slice i of P (all K tiles), then the S tiles of every j it pairs with
     int step = 0;
-    for (int L = L0; L <= L1 && !*(volatile int*)&err; ++L)
-      for (int i = max(1, L - kOzSlices); i <= min(kOzSlices, L - 1) && !*(volatile int*)&err; ++i)
+    for (int i = 1; i <= kOzSlices && !*errv; ++i) {
+      const int pb = (i - 1) & 1, use = (i - 1) >> 1;
+      if (use > 0 && !mbar_wait(&pempty[pb], (use - 1) & 1)) {
+        atomicExch(&err, 1);
+        break;
+      }
+      mbar_expect_tx(&pfull[pb], p_bytes);
+      for (int kt = 0; kt < nk; ++kt)
+        tma_load_2d(pbuf + ((size_t)pb * kOzMaxKt + kt) * kTileA, &J.tp, &pfull[pb], kt * kOzBK, (i - 1) * J.M + m0);
+      for (int j = 1; j <= jmax(i) && !*errv; ++j)
         for (int kt = 0; kt < nk; ++kt, ++step) {
           const int s = step % stages;
-          if (step >= stages && !mbar_wait(&empty[s], ((step / stages) & 1) ^ 1)) {
+          if (step >= stages && !mbar_wait(&sempty[s], ((step / stages) & 1) ^ 1)) {
             atomicExch(&err, 1);
             break;
           }
-          uint8_t* sa = smem + (size_t)s * stage_bytes;
-          mbar_expect_tx(&full[s], a_bytes + b_bytes);
-          tma_load_2d(sa, &J.tp, &full[s], kt * kOzBK, (i - 1) * J.M + m0);
-          tma_load_2d(sa + a_bytes, &J.ts, &full[s], kt * kOzBK, (L - i - 1) * J.Npad + n0);
+          mbar_expect_tx(&sfull[s], s_bytes);
+          tma_load_2d(sbuf + (size_t)s * s_stage, &J.ts, &sfull[s], kt * kOzBK, (j - 1) * J.Npad + n0);
         }
+    }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: level L accumulates in TMEM buffer L & 1
+    // MMA issuer: product (i, j) accumulates into the TMEM columns of level i + j
     const uint32_t id = idesc<__nv_bfloat16>(kOzM, NT);
     int step = 0;
-    for (int L = L0; L <= L1 && !*(volatile int*)&err; ++L) {
-      const int bf = L & 1, use = (L - L0) >> 1;
-      if (use > 0) {
-        if (!mbar_wait(&tfree[bf], (use - 1) & 1)) {
-          atomicExch(&err, 1);
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (int i = 1; i <= kOzSlices && !*errv; ++i) {
+      const int pb = (i - 1) & 1, use = (i - 1) >> 1;
+      if (!mbar_wait(&pfull[pb], use & 1)) {
+        atomicExch(&err, 1);
+        break;
       }
-      const uint32_t td = tmem + (uint32_t)(bf * NT);
-      bool first = true;
-      for (int i = max(1, L - kOzSlices); i <= min(kOzSlices, L - 1) && !*(volatile int*)&err; ++i)
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t pa = smem_u32(pbuf + (size_t)pb * kOzMaxKt * kTileA);
+      for (int j = 1; j <= jmax(i) && !*errv; ++j) {
+        const int L = i + j;
+        const uint32_t td = tmem + (uint32_t)((L - 2) * NT);
+        const bool first_of_level = i == max(1, L - kOzSlices);
         for (int kt = 0; kt < nk; ++kt, ++step) {
           const int s = step % stages;
-          if (!mbar_wait(&full[s], (step / stages) & 1)) {
+          if (!mbar_wait(&sfull[s], (step / stages) & 1)) {
             atomicExch(&err, 1);
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
-          const uint32_t sb = sa + a_bytes;
+          const uint32_t sa = pa + (uint32_t)kt * kTileA;
+          const uint32_t sb = smem_u32(sbuf + (size_t)s * s_stage);
 #pragma unroll
           for (int kk = 0; kk < kOzBK / kOzMmaK; ++kk) {
             const uint32_t off = kk * kOzMmaK * 2;  // 32 bytes per MMA step
-            mma<__nv_bfloat16>(td, smem_desc(sa + off), smem_desc(sb + off), id, (first && kk == 0) ? 0u : 1u);
+            mma<__nv_bfloat16>(td, smem_desc(sa + off), smem_desc(sb + off), id,
+                               (first_of_level && kt == 0 && kk == 0) ? 0u : 1u);
           }
-          first = false;
-          mma_commit(&empty[s]);
+          mma_commit(&sempty[s]);
         }
-      mma_commit(&tfull[bf]);
+      }
+      mma_commit(&pempty[pb]);
+      mma_commit(&ifull[i - 1]);
     }
   } else if (warp >= 2) {
-    // epilogue: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31
+    // epilogue: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31.
+    // Level L is complete once slice i = min(L - 1, kOzSlices) is done.
     const int q = warp % 4;
     const int row = m0 + q * 32 + lane;
     double acc[kOzMaxNt];
 #pragma unroll
     for (int c = 0; c < kOzMaxNt; ++c) acc[c] = 0.0;
     bool ok = true;
-    for (int L = L0; L <= L1; ++L) {
-      const int bf = L & 1, use = (L - L0) >> 1;
-      if (!mbar_wait(&tfull[bf], use & 1)) {
+    for (int i = 1; i <= kOzSlices && ok; ++i) {
+      if (!mbar_wait(&ifull[i - 1], 0)) {
         ok = false;
         atomicExch(&err, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const double w = __longlong_as_double((long long)(1023 - 6 * L) << 52);  // 2^-6L
-      const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(bf * NT);
+      for (int L = i + 1; L <= (i == kOzSlices ? kOzSlices + 2 : i + 1); ++L) {
+        const double w = __longlong_as_double((long long)(1023 - 6 * L) << 52);  // 2^-6L
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * NT);
 #pragma unroll
-      for (int c0 = 0; c0 < kOzMaxNt; c0 += 16)
-        if (c0 < NT) {
-          float t[16];
-          ld16(tl + (uint32_t)c0, t);
+        for (int c0 = 0; c0 < kOzMaxNt; c0 += 16)
+          if (c0 < NT) {
+            float t[16];
+            ld16(tl + (uint32_t)c0, t);
 #pragma unroll
-          for (int u = 0; u < 16; ++u) acc[c0 + u] = fma((double)t[u], w, acc[c0 + u]);
-        }
-      // this level's buffer is free again (the MMAs of level L + 1 run in the other one meanwhile)
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tfree[bf]);
+            for (int u = 0; u < 16; ++u) acc[c0 + u] = fma((double)t[u], w, acc[c0 + u]);
+          }
+      }
     }
-    if (ok && !err && row < J.M) {
+    if (ok && !*errv && row < J.M) {
       const int er = J.ep[row];
 #pragma unroll
       for (int c = 0; c < kOzMaxNt; ++c) {
@@ -251,13 +268,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
 }
 
 size_t oz_smem_bytes(int ntile, int stages) {
-  const size_t stage = ((size_t)kOzM * 128 + (size_t)ntile * 128 + 1023) / 1024 * 1024;
-  return 1024 + stage * stages + (2 * (size_t)stages + 4) * 8 + 16;
+  const size_t s_stage = ((size_t)ntile * 128 + 1023) / 1024 * 1024;
+  return 1024 + 2 * (size_t)kOzMaxKt * kOzM * 128 + s_stage * stages + (4 + 2 * (size_t)stages + kOzSlices) * 8 + 16;
 }
 
 }  // namespace
 
-// columns per CTA: the fewest tiles of at most 64 columns, as even as multiples of 16 allow
+// columns per CTA: the fewest tiles of at most kOzMaxNt columns, as even as multiples of 16 allow
 int oz_ntile(int Npad) {
   const int nt = (Npad + kOzMaxNt - 1) / kOzMaxNt;
   return ((Npad + nt - 1) / nt + 15) / 16 * 16;
@@ -280,8 +297,8 @@ cudaError_t launch_oz_gemm(const OzBatch& b, cudaStream_t s) {
     maxM = max(maxM, b.job[i].M);
     maxN = max(maxN, b.job[i].N);
   }
-  int stages = 6;
-  while (stages > 2 && oz_smem_bytes(b.ntile, stages) > 200 * 1024) --stages;
+  int stages = 8;
+  while (stages > 2 && oz_smem_bytes(b.ntile, stages) > 210 * 1024) --stages;
   const size_t smem = oz_smem_bytes(b.ntile, stages);
   cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
