@@ -598,16 +598,20 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   __shared__ double trail_part;  // this CTA's sum of squares of the trailing block
   __shared__ double trail_sum;
   __shared__ double fro0;
-  const int npanel = (l + kNb - 1) / kNb;
+  // Without U (trunc_q), the columns of the sample at and beyond the previous
+  // orthonormalisation's rank are exact zeros (the products skip them): the
+  // factorization runs over the leading lc columns only.
+  const int lc = (J.trunc_q && J.rank_eff) ? min(l, max(kNb, *J.rank_eff)) : l;
+  const int npanel = (lc + kNb - 1) / kNb;
   int npanel_used = npanel;
   for (int p = 0; p < npanel; ++p) {
-    const int j0 = p * kNb, nb = min(kNb, l - j0);
+    const int j0 = p * kNb, nb = min(kNb, lc - j0);
     const int R = rows - j0;  // panel rows j0 .. rows-1
     double* Tp = Tall + (size_t)p * kNb * kNb;
     {  // sum of squares of the trailing block Y[j0:, j0:] over own rows
       double a = 0.0;
-      for (int e = tid; e < nr * (l - j0); e += kHhThreads) {
-        const int rr = e / (l - j0), c = j0 + e % (l - j0);
+      for (int e = tid; e < nr * (lc - j0); e += kHhThreads) {
+        const int rr = e / (lc - j0), c = j0 + e % (lc - j0);
         if (r0 + rr >= j0) a = fma(Ys[rr * l + c], Ys[rr * l + c], a);
       }
 #pragma unroll
@@ -756,7 +760,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     __syncthreads();
     // trailing update of columns j0 + nb .. l-1: Y <- Y - V T^T (V^T Y); V is
     // zero on the rows above j0, which neither contribute nor change
-    const int c1 = j0 + nb, wcols = l - c1;
+    const int c1 = j0 + nb, wcols = lc - c1;
     const int rr0 = max(0, min(nr, j0 - r0));  // first own row at or below j0
     double* Wb = Wp;
     if (wcols > 0) {
@@ -778,7 +782,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   // Q = (I - V_0 T_0 V_0^T) ... (I - V_last T_last V_last^T) [I; 0], accumulated backwards.
   // With trunc_q and an early end, only the leading qc columns (those that
   // carry the sample's range) are formed; the others are written as zeros.
-  const int qc = (J.trunc_q && npanel_used < npanel) ? min(l, npanel_used * kNb) : l;
+  const int qc = J.trunc_q ? min(lc, npanel_used * kNb) : l;
   cluster.sync();  // every remote read of Ys / Wp above is done
   for (int e = tid; e < nr * l; e += kHhThreads) {
     const int rr = e / l, c = e % l;
@@ -786,7 +790,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   }
   __syncthreads();
   for (int p = npanel_used - 1; p >= 0; --p) {
-    const int j0 = p * kNb, nb = min(kNb, l - j0);
+    const int j0 = p * kNb, nb = min(kNb, lc - j0);
     const double* Tp = Tall + (size_t)p * kNb * kNb;
     const int wcols = qc - j0;
     const int rr0 = max(0, min(nr, j0 - r0));  // rows above j0: V is zero there
