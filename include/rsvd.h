@@ -194,6 +194,9 @@ int tebd_workspace_size(int L, int d, const int* D, int nb, const rsvd_params* p
  *   B[i+1] <- V^T;  B[i] <- theta_B V / ||S||;  lam[i+1] <- S / ||S||;
  *   trunc_err[b] (device) <- 1 - ||S||^2 / ||theta||_F^2 (discarded weight).
  * Bond b uses Philox stream p->stream + bond[b].  p->prec must be RSVD_F64.
+ * The contraction B[i] B[i+1] runs over the nonzero entries of lam[i+1] only
+ * (sorted, zeros last): in right-canonical form B[i] = Gamma[i] lam[i+1], so
+ * the columns of B[i] that belong to a zero Schmidt value are zero.
  * info: DEVICE array of nb records.
  * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_PRECISION,
  * RSVD_ERR_WORKSPACE, RSVD_ERR_LAUNCH.

@@ -753,7 +753,7 @@ int rsvd_truncate(int m, int n, const void* A, int lda, const rsvd_params* p, do
 // ---------------------------------------------------------------- TEBD
 namespace {
 struct TebdLayout {
-  size_t t2, thetaB, theta, S, nrm, fro2, rsvd;
+  size_t t2, thetaB, theta, S, nrm, fro2, keff, rsvd;
 };
 size_t tebd_bond_bytes(int m, int n, int k, int l, int oz, TebdLayout* o) {
   size_t off = 0;
@@ -769,6 +769,7 @@ size_t tebd_bond_bytes(int m, int n, int k, int l, int oz, TebdLayout* o) {
   L.S = take((size_t)k * 8);
   L.nrm = take(8);
   L.fro2 = take(64 * 8);
+  L.keff = take(sizeof(int));
   L.rsvd = off;
   off += layout(nullptr, m, n, k, l, 8, nullptr, 0, oz);
   if (o) *o = L;
@@ -829,6 +830,8 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
   g2.count = nb;
   TebdBatch tb;
   tb.count = nb;
+  TebdRankBatch rb;
+  rb.count = nb;
   for (int b = 0; b < nb; ++b) {
     const int i = bond[b];
     const int Dl = D[i], Dm = D[i + 1], Dr = D[i + 2];
@@ -842,8 +845,13 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     double* th = (double*)(wb + lay[b].theta);
     double* Bi = B + tensor_stride * i;
     double* Bj = B + tensor_stride * (i + 1);
-    // T2[(a,t1),(t2,c)] = sum_b B_i[(a,t1), b] B_{i+1}[b, (t2,c)]
+    // T2[(a,t1),(t2,c)] = sum_b B_i[(a,t1), b] B_{i+1}[b, (t2,c)]; b runs over the bond's
+    // nonzero Schmidt values only (the rows of B_{i+1} and the columns of B_i of a zero
+    // Schmidt value are zero: they were set so by the truncation and no later update of a
+    // neighbouring bond fills them)
     g2.job[b] = GemmJob<double, double>{m, n, Dm, Dm, n, n, Bi, Bj, T2, nullptr, nullptr, 0};
+    g2.job[b].k_eff = (const int*)(wb + lay[b].keff);
+    rb.job[b] = TebdRankJob{lam + lam_stride * (i + 1), Dm, (int*)(wb + lay[b].keff)};
     tb.job[b] = TebdJob{Dl, Dr, d, T2, gate + (size_t)b * d * d * d * d, lam + lam_stride * i, thB, th,
                         (double*)(wb + lay[b].fro2)};
     Prob& pr = probs[b];
@@ -860,6 +868,7 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
     layout(&pr, m, n, k, l, 8, wb + lay[b].rsvd, 0, oz);
   }
+  RSVD_TRY(launch_tebd_rank(rb, s));
   RSVD_TRY((launch_gemm<double, double, false, false>(g2, s)));
   RSVD_TRY(launch_tebd_theta(tb, s));
   rc = run_chunk<double>(probs, p->q, s);

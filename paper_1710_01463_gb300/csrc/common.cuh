@@ -38,6 +38,9 @@ struct GemmJob {
   // without the product
   const int* m_eff = nullptr;
   const int* n_eff = nullptr;
+  // optional device count: the sum over k stops at *k_eff (op(A)'s columns and
+  // op(X)'s rows beyond it are zero)
+  const int* k_eff = nullptr;
 };
 
 template <typename Tin, typename Tout>
@@ -334,6 +337,17 @@ template <typename T>
 cudaError_t launch_sign(const SignBatch<T>& b, cudaStream_t s);
 cudaError_t launch_select(const SelectBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_theta(const TebdBatch& b, cudaStream_t s);
+// number of nonzero Schmidt values of a bond (they are sorted, zeros last)
+struct TebdRankJob {
+  const double* lam;
+  int D;
+  int* out;
+};
+struct TebdRankBatch {
+  int count;
+  TebdRankJob job[kMaxJobs];
+};
+cudaError_t launch_tebd_rank(const TebdRankBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s);
 template <typename TIn>
 cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s, int skip_loads = 0);

@@ -126,18 +126,19 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
     for (int j = 0; j < TN; ++j) acc[i][j] = (Tin)0;
 
   Tin ra[BM * BK / NT], rx[BN * BK / NT];
-  load_a<Tin, TA, BM, BK>(J.A, J.lda, J.M, J.K, m0, 0, ra);
-  load_x<Tin, TX, BN, BK>(J.X, J.ldx, J.N, J.K, n0, 0, rx);
+  const int K = J.k_eff ? min(J.K, *J.k_eff) : J.K;
+  load_a<Tin, TA, BM, BK>(J.A, J.lda, J.M, K, m0, 0, ra);
+  load_x<Tin, TX, BN, BK>(J.X, J.ldx, J.N, K, n0, 0, rx);
   store_a<Tin, TA, BM, BK>(As[0], ra);
   store_x<Tin, TX, BN, BK>(Xs[0], rx);
   __syncthreads();
 
-  const int nk = (J.K + BK - 1) / BK;
+  const int nk = (K + BK - 1) / BK;
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
     if (kt + 1 < nk) {
-      load_a<Tin, TA, BM, BK>(J.A, J.lda, J.M, J.K, m0, (kt + 1) * BK, ra);
-      load_x<Tin, TX, BN, BK>(J.X, J.ldx, J.N, J.K, n0, (kt + 1) * BK, rx);
+      load_a<Tin, TA, BM, BK>(J.A, J.lda, J.M, K, m0, (kt + 1) * BK, ra);
+      load_x<Tin, TX, BN, BK>(J.X, J.ldx, J.N, K, n0, (kt + 1) * BK, rx);
     }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {

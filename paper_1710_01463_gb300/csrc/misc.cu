@@ -174,6 +174,26 @@ cudaError_t launch_select(const SelectBatch& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+namespace {
+// one warp per bond: Schmidt values are >= +0, so "nonzero" is a test of the bit pattern
+__global__ void tebd_rank_kernel(const __grid_constant__ TebdRankBatch b) {
+  const TebdRankJob& J = b.job[blockIdx.x];
+  int c = 0;
+  for (int j = threadIdx.x; j < J.D; j += 32) c += __double_as_longlong(J.lam[j]) > 0 ? 1 : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (threadIdx.x == 0) *J.out = c;
+}
+}  // namespace
+
+cudaError_t launch_tebd_rank(const TebdRankBatch& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  prof_begin(KC_TEBD, s);
+  tebd_rank_kernel<<<b.count, 32, 0, s>>>(b);
+  prof_end(KC_TEBD, s);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tebd_theta(const TebdBatch& b, cudaStream_t s) {
   if (b.count <= 0) return cudaSuccess;
   prof_begin(KC_TEBD, s);
