@@ -173,15 +173,21 @@ def step_flops(info):
         for b, (m, n, k, l) in enumerate(lay):
             rec = info[j][b]
             sweeps, rots, qr_cols = int(rec[3]), int(rec[5]), int(rec[6])
-            flops["gemm"] += 2.0 * m * n * k + 2.0 * m * n * k
+            # the bond update forms no U: after the first orthonormalisation only the leading
+            # r columns of Q carry the range (r = reported qr_columns, else l), and the products,
+            # the later QRs, the contraction B_i B_{i+1} (over the nonzero Schmidt values,
+            # at most r) and the B update (over the nonzero columns of V) work on r columns
+            r = min(l, qr_cols) if qr_cols > 0 else l
+            flops["gemm"] += 2.0 * m * n * min(k, r) + 2.0 * m * n * min(k, r)
             if not (m <= l and m <= 16):
                 # products with A: on the tensor cores by exact slicing when m, n, l <= 256
                 oz = m <= 256 and n <= 256 and l <= 256
-                flops["ozgemm" if oz else "gemm"] += (2 * Q_POW + 2) * 2.0 * m * n * l
+                flops["ozgemm" if oz else "gemm"] += 2.0 * m * n * l + (2 * Q_POW + 1) * 2.0 * m * n * r
                 for it in range(2 * Q_POW + 1):
                     rows = m if it % 2 == 0 else n
+                    lw = l if it == 0 else r
                     if 3 * l > rows:
-                        flops["householder"] += hh_flops(rows, l, qr_cols if qr_cols > 0 else l)
+                        flops["householder"] += hh_flops(rows, lw, r)
                     else:
                         flops["gram"] += 2 * rows * l * l
                         flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
