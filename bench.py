@@ -26,6 +26,7 @@ sys.path.insert(0, ROOT)
 METRIC = "RSVD truncations/s & TFLOP/s vs full-SVD-truncate, 1 GB300, at stated error"
 UNIT = "truncations/s"
 L_SITES, CHI, D_LOC, H_FIELD, DT, P_OVER, Q_POW, SEED = 64, 128, 2, 1.0, 0.01, 10, 2, 5
+SPIN, WIDTH = 0.5, 0  # model: spin-S chain (d = 2S + 1), or the 2D cylinder of circumference WIDTH (d = 2^WIDTH)
 PREP_STEPS, PREP_DT = 20, 0.1
 WORKLOAD = "tebd_tfim_L64_chi128_d2_dt0.01_p10_q2_fp64"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
@@ -48,10 +49,21 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 
 
 
 def base_config():
-    return {"workload": WORKLOAD, "L": L_SITES, "chi": CHI, "d": D_LOC, "h": H_FIELD, "dt": DT,
+    return {"workload": WORKLOAD, "model": model_name(), "L": L_SITES, "chi": CHI, "d": D_LOC, "h": H_FIELD, "dt": DT,
             "p": P_OVER, "q": Q_POW, "bond_matrix": f"{CHI * D_LOC}x{CHI * D_LOC}",
             "fp64_products_with_A": "tcgen05 tensor cores, exact 9-slice BF16 split, FP64-class error",
             "truncations_per_step": truncations_per_step(), "l2": "flushed (512 MB write) before every timed step"}
+
+
+def model_name():
+    return f"cyl{WIDTH}" if WIDTH else ("tfim" if SPIN == 0.5 else f"spin{SPIN:g}")
+
+
+def bond_term_oracle(otebd, i):
+    """The bond term of the bench's model, from the oracle (CPU legs only)."""
+    if WIDTH:
+        return otebd.cylinder_bond_hamiltonian(i, L_SITES, H_FIELD, WIDTH)
+    return otebd.bond_hamiltonian(i, L_SITES, H_FIELD, SPIN)
 
 
 def truncations_per_step():
@@ -213,7 +225,7 @@ def run_ours(args):
     from paper_1710_01463_gb300.tebd import TebdChain
 
     lib = _lib.load()
-    ch = TebdChain(L_SITES, CHI, h=H_FIELD, p=P_OVER, q=Q_POW, seed=SEED + 1000 * rank)
+    ch = TebdChain(L_SITES, CHI, h=H_FIELD, p=P_OVER, q=Q_POW, seed=SEED + 1000 * rank, S=SPIN, W=WIDTH or None)
     ch.set_product_state(inputs.product_state_vectors(L_SITES, D_LOC, 102 + rank))
     ch.set_dt(PREP_DT)
     for s in range(PREP_STEPS):
@@ -397,14 +409,15 @@ def cpu_leg(ch):
     n = 0
     while True:
         for i in bonds:
-            G = otebd.gate(otebd.bond_hamiltonian(i, L_SITES, H_FIELD), DT / 2)
+            G = otebd.gate(bond_term_oracle(otebd, i), DT / 2)
             otebd.bond_update(B, lam, i, G, comp, 7 * L_SITES + i)
             n += 1
         if time.time() - t0 > 10.0:
             break
     el = time.time() - t0
     return {"value": round(n / el, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} central 256x256 bond updates (RSVD k=128, p=10, q=2) of the L=64 chain, numpy FP64, "
+            "sample": f"{n} central {CHI * D_LOC}x{CHI * D_LOC} bond updates (RSVD k={CHI}, p={P_OVER}, q={Q_POW}) "
+                      f"of the L={L_SITES} {model_name()} chain, numpy FP64, "
                       f"BLAS threads = all host cores, Philox in pure Python"}
 
 
@@ -775,7 +788,7 @@ def run_reference(args):
 
     def one(step):
         for i in bonds:
-            G = otebd.gate(otebd.bond_hamiltonian(i, L_SITES, H_FIELD), DT / 2)
+            G = otebd.gate(bond_term_oracle(otebd, i), DT / 2)
             otebd.bond_update(B, lam, i, G, comp, (3 * step) * L_SITES + i)
 
     for s in range(args.warmup):
@@ -811,11 +824,20 @@ def main():
                     help="sectors workload: per-block trial ranks")
     ap.add_argument("--chain-length", type=int, default=64,
                     help="L (default 64); a shorter chain keeps the 256 x 256 central bonds (profiling case)")
+    ap.add_argument("--spin", type=float, default=0.5, help="TEBD: spin S of the chain (d = 2S + 1; Sec. III.B)")
+    ap.add_argument("--cylinder-width", type=int, default=0,
+                    help="TEBD: circumference W of the 2D cylinder mapped onto a chain of rings (d = 2^W)")
+    ap.add_argument("--field", type=float, default=None,
+                    help="TEBD: field h (default 1 for S = 1/2, 1.5 for S > 1/2, 3.044 for the cylinder)")
     args = ap.parse_args()
-    global L_SITES, WORKLOAD
+    global L_SITES, WORKLOAD, SPIN, WIDTH, D_LOC, H_FIELD
     if args.chain_length != L_SITES:
         L_SITES = args.chain_length
-        WORKLOAD = WORKLOAD.replace("L64", f"L{L_SITES}")
+    SPIN, WIDTH = args.spin, args.cylinder_width
+    D_LOC = 2 ** WIDTH if WIDTH else int(round(2 * SPIN)) + 1
+    H_FIELD = args.field if args.field is not None else (3.044 if WIDTH else (1.0 if SPIN == 0.5 else 1.5))
+    WORKLOAD = (f"tebd_{model_name()}_L{L_SITES}_chi{CHI}_d{D_LOC}_dt{DT:g}_p{P_OVER}_q{Q_POW}_fp64"
+                + (f"_h{H_FIELD:g}" if args.field is not None else ""))
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -2,11 +2,12 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Model (Sec. III.B, Eq. for H_chain at S = 1/2): the paper writes
-H = -sum X_j X_{j+1} + h sum Z_j with Pauli X, Z; this build uses the unitarily
-equivalent form H = -sum Z_j Z_{j+1} - h sum X_j (exchange the x and z axes,
-then rotate by pi about x to flip the field's sign), which has the same
-spectrum.  Open boundaries; critical point h = 1.
+Models (Sec. III.B): the spin-S chain of Eq. ising_chain and the 2D cylinder of
+Eq. ising_cylinder mapped onto a chain of rings (d = 2^W).  The paper writes the
+couplings in x and the field in z; this build uses the unitarily equivalent form
+with the axes exchanged (rotate x <-> z, then by pi about x to flip the field's
+sign), which has the same spectrum: at S = 1/2, H = -sum Z_j Z_{j+1} - h sum X_j.
+Open boundaries; the spin-1/2 chain is critical at h = 1.
 
 TEBD (Sec. III.A "block update (B)", Sec. III.C protocol), readings where the
 paper is silent:
@@ -38,16 +39,67 @@ PAULI_Z = np.array([[1.0, 0.0], [0.0, -1.0]])
 EYE2 = np.eye(2)
 
 
+def spin_ops(S):
+    """Spin-S operators (S^x, S^z), d = 2S + 1, basis m = S, S-1, ..., -S (Sec. III.B).
+
+    <m|S^z|m> = m and <m+1|S^x|m> = <m|S^x|m+1> = sqrt(S(S+1) - m(m+1)) / 2, the
+    standard ladder-operator elements (the paper's printed X element is garbled:
+    its radicand is negative at S = 1/2; for S = 1/2 these are Pauli / 2, as
+    the paper states they must be).
+    """
+    d = int(round(2 * S)) + 1
+    m = S - np.arange(d)
+    sz = np.diag(m)
+    sx = np.zeros((d, d))
+    for a in range(d - 1):  # rows a (m = S - a) and a + 1 (m - 1)
+        mm = m[a + 1]
+        v = 0.5 * np.sqrt(S * (S + 1) - mm * (mm + 1))
+        sx[a, a + 1] = sx[a + 1, a] = v
+    return sx, sz
+
+
 def bond_dims(L, d, chi):
     """D[j] = min(d^j, d^(L-j), chi), j = 0..L."""
     return [int(min(d ** min(j, L - j), chi)) for j in range(L + 1)]
 
 
-def bond_hamiltonian(i, L, h):
-    """Two-site term of bond (i, i+1) as a 4x4 matrix on (s_i, s_{i+1})."""
+def bond_hamiltonian(i, L, h, S=0.5):
+    """Two-site term of bond (i, i+1), d^2 x d^2 on (s_i, s_{i+1}), of the spin-S chain
+    H = -(1/S^2) sum S^z_j S^z_{j+1} - (h/S) sum S^x_j (Eq. ising_chain with x and z
+    exchanged, a unitary change of basis); S = 1/2 is -sum Z Z - h sum X (Pauli)."""
+    sx, sz = spin_ops(S)
+    one = np.eye(sx.shape[0])
     fl = 1.0 if i == 0 else 0.5
     fr = 1.0 if i + 1 == L - 1 else 0.5
-    return -np.kron(PAULI_Z, PAULI_Z) - h * (fl * np.kron(PAULI_X, EYE2) + fr * np.kron(EYE2, PAULI_X))
+    return -np.kron(sz, sz) / S ** 2 - (h / S) * (fl * np.kron(sx, one) + fr * np.kron(one, sx))
+
+
+def ring_ops(W):
+    """One ring of the W-site circumference of the 2D cylinder (Eq. ising_cylinder) as a
+    site of dimension d = 2^W: Z_j, X_j (Pauli on spin j of the ring), the ring's own
+    coupling sum_j Z_j Z_{j+1 mod W} and sum_j X_j (x and z exchanged as for the chain)."""
+    def on(op, j):
+        out = np.ones((1, 1))
+        for t in range(W):
+            out = np.kron(out, op if t == j else EYE2)
+        return out
+    Z = [on(PAULI_Z, j) for j in range(W)]
+    X = [on(PAULI_X, j) for j in range(W)]
+    ring = sum(Z[j] @ Z[(j + 1) % W] for j in range(W))
+    return Z, X, ring, sum(X)
+
+
+def cylinder_bond_hamiltonian(i, L, h, W):
+    """Two-site term of rings (i, i+1) of the cylinder mapped onto a chain of L rings:
+    -sum_j Z_{i,j} Z_{i+1,j}, plus each ring's own terms -ring - h sum_j X_j shared between
+    its bonds like the chain's field (interior rings half to each bond, edge rings all)."""
+    Z, X, ring, xsum = ring_ops(W)
+    one = np.eye(2 ** W)
+    fl = 1.0 if i == 0 else 0.5
+    fr = 1.0 if i + 1 == L - 1 else 0.5
+    onsite = -ring - h * xsum
+    inter = -sum(np.kron(Z[j], Z[j]) for j in range(W))
+    return inter + fl * np.kron(onsite, one) + fr * np.kron(one, onsite)
 
 
 def gate(hb, tau):
@@ -106,19 +158,34 @@ def layers(L):
     return list(range(0, L - 1, 2)), list(range(1, L - 1, 2))
 
 
-def trotter_step(B, lam, L, h, dt, compress, step):
-    """One second-order Trotter step; returns the summed discarded weight."""
+def chain_bond_terms(L, h, S=0.5):
+    """The L - 1 bond terms of the spin-S chain."""
+    return [bond_hamiltonian(i, L, h, S) for i in range(L - 1)]
+
+
+def cylinder_bond_terms(L, h, W):
+    """The L - 1 bond terms of the W-wide cylinder mapped onto a chain of rings."""
+    return [cylinder_bond_hamiltonian(i, L, h, W) for i in range(L - 1)]
+
+
+def trotter_step(B, lam, L, h, dt, compress, step, terms=None):
+    """One second-order Trotter step; returns the summed discarded weight.  terms: the
+    bond terms (default: the spin-1/2 chain at field h)."""
+    if terms is None:
+        terms = chain_bond_terms(L, h)
     la, lb = layers(L)
     err = 0.0
     for layer, (bonds, tau) in enumerate(((la, dt / 2), (lb, dt), (la, dt / 2))):
         for i in bonds:
-            G = gate(bond_hamiltonian(i, L, h), tau)
+            G = gate(terms[i], tau)
             err += bond_update(B, lam, i, G, compress, (3 * step + layer) * L + i)
     return err
 
 
-def mps_energy(B, L, h):
+def mps_energy(B, L, h, terms=None):
     """<psi|H|psi> / <psi|psi> by exact contraction of psi = B[0] B[1] ... B[L-1]."""
+    if terms is None:
+        terms = chain_bond_terms(L, h)
     left = [np.ones((1, 1))]
     for i in range(L):
         left.append(np.einsum("ab,asc,bsd->cd", left[i], B[i], B[i], optimize=True))
@@ -131,7 +198,7 @@ def mps_energy(B, L, h):
     d = B[0].shape[1]
     for i in range(L - 1):
         two = np.einsum("atb,buc->atuc", B[i], B[i + 1])
-        hb = bond_hamiltonian(i, L, h).reshape(d, d, d, d)
+        hb = terms[i].reshape(d, d, d, d)
         htwo = np.einsum("stxy,axyc->astc", hb, two)
         e += float(np.einsum("ab,astc,bstd,cd->", left[i], htwo, two, right[i + 2], optimize=True))
     return e / norm
@@ -143,6 +210,45 @@ def mps_to_dense(B):
     for t in B[1:]:
         psi = np.einsum("xa,asb->xsb", psi, t).reshape(-1, t.shape[2])
     return psi.reshape(-1)
+
+
+def dense_chain_hamiltonian(L, h, S=0.5):
+    """Spin-S chain as a dense d^L x d^L matrix, built site by site (brute force)."""
+    sx, sz = spin_ops(S)
+    d = sx.shape[0]
+
+    def site_op(op, j):
+        out = np.ones((1, 1))
+        for t in range(L):
+            out = np.kron(out, op if t == j else np.eye(d))
+        return out
+    H = np.zeros((d ** L, d ** L))
+    for j in range(L - 1):
+        H -= site_op(sz, j) @ site_op(sz, j + 1) / S ** 2
+    for j in range(L):
+        H -= (h / S) * site_op(sx, j)
+    return H
+
+
+def dense_cylinder_hamiltonian(L, h, W):
+    """Cylinder of L rings of W spins, dense 2^(LW) matrix, from the single-spin terms of
+    Eq. ising_cylinder (x and z exchanged): -sum Z Z around and along, -h sum X."""
+    n = L * W
+
+    def op_at(op, k):
+        out = np.ones((1, 1))
+        for t in range(n):
+            out = np.kron(out, op if t == k else EYE2)
+        return out
+    H = np.zeros((2 ** n, 2 ** n))
+    for i in range(L):
+        for j in range(W):
+            k = i * W + j
+            H -= op_at(PAULI_Z, k) @ op_at(PAULI_Z, i * W + (j + 1) % W)
+            if i + 1 < L:
+                H -= op_at(PAULI_Z, k) @ op_at(PAULI_Z, k + W)
+            H -= h * op_at(PAULI_X, k)
+    return H
 
 
 def dense_hamiltonian(L, h):

@@ -1,15 +1,19 @@
 """Imaginary-time TEBD driver on a device-resident MPS (Sec. III.A, III.C).
 
-The open spin-1/2 transverse-field Ising chain H = -sum Z_j Z_{j+1} - h sum X_j
-(unitarily equivalent to the paper's spin-1/2 H_chain, Sec. III.B) evolved by
-second-order Trotter steps exp(-dt/2 H_A) exp(-dt H_B) exp(-dt/2 H_A), layer A
-holding the bonds (0,1), (2,3), ... and layer B the bonds (1,2), (3,4), ...
-Each layer is ONE call of tebd_bond_update over all of its bonds, which are
-independent.  Bond dimensions are fixed at min(d^j, d^(L-j), chi); an interior
-site gives half of its field to each of its two bonds, an edge site all of it.
+Models (Sec. III.B), with the coupling and field axes exchanged (a unitary change of
+basis, same spectrum):
+  * the spin-S chain of Eq. ising_chain, H = -(1/S^2) sum S^z_j S^z_{j+1} - (h/S) sum S^x_j,
+    d = 2S + 1 (S = 1/2: H = -sum Z Z - h sum X with Pauli matrices);
+  * the 2D cylinder of Eq. ising_cylinder with circumference W mapped onto a chain of
+    rings, d = 2^W: -sum Z Z around each ring and between neighbouring rings, -h sum X.
+Evolution by second-order Trotter steps exp(-dt/2 H_A) exp(-dt H_B) exp(-dt/2 H_A), layer A
+holding the bonds (0,1), (2,3), ... and layer B the bonds (1,2), (3,4), ...  Each layer is
+ONE call of tebd_bond_update over all of its bonds, which are independent.  Bond dimensions
+are fixed at min(d^j, d^(L-j), chi); an interior site (ring) gives half of its on-site terms
+to each of its two bonds, an edge site all of them.
 
-The gates (4 x 4 matrix exponentials of the bond Hamiltonians) are inputs of
-the bond update and are formed once on the host.
+The gates (d^2 x d^2 matrix exponentials of the bond Hamiltonians) are inputs of the bond
+update and are formed once on the host.
 """
 import ctypes
 
@@ -24,11 +28,42 @@ _Z = np.array([[1.0, 0.0], [0.0, -1.0]])
 _I = np.eye(2)
 
 
-def bond_hamiltonian(i, L, h):
-    """Two-site term of bond (i, i+1), 4 x 4 on (s_i, s_{i+1})."""
+def spin_matrices(S):
+    """(S^x, S^z) of spin S in the basis m = S, S-1, ..., -S: <m|S^z|m> = m and
+    <m+1|S^x|m> = sqrt(S(S+1) - m(m+1)) / 2 (the standard ladder elements)."""
+    d = int(round(2 * S)) + 1
+    m = S - np.arange(d)
+    sx = np.zeros((d, d))
+    for a in range(d - 1):
+        v = 0.5 * np.sqrt(S * (S + 1) - m[a + 1] * (m[a + 1] + 1))
+        sx[a, a + 1] = sx[a + 1, a] = v
+    return sx, np.diag(m)
+
+
+def bond_hamiltonian(i, L, h, S=0.5):
+    """Two-site term of bond (i, i+1) of the spin-S chain, d^2 x d^2 on (s_i, s_{i+1})."""
+    sx, sz = spin_matrices(S)
+    one = np.eye(sx.shape[0])
     fl = 1.0 if i == 0 else 0.5
     fr = 1.0 if i + 1 == L - 1 else 0.5
-    return -np.kron(_Z, _Z) - h * (fl * np.kron(_X, _I) + fr * np.kron(_I, _X))
+    return -np.kron(sz, sz) / S ** 2 - (h / S) * (fl * np.kron(sx, one) + fr * np.kron(one, sx))
+
+
+def ring_bond_hamiltonian(i, L, h, W):
+    """Two-site term of rings (i, i+1) of the W-wide cylinder, 4^W x 4^W."""
+    def on(op, j):
+        out = np.ones((1, 1))
+        for t in range(W):
+            out = np.kron(out, op if t == j else _I)
+        return out
+    Z = [on(_Z, j) for j in range(W)]
+    X = [on(_X, j) for j in range(W)]
+    onsite = -sum(Z[j] @ Z[(j + 1) % W] for j in range(W)) - h * sum(X)
+    one = np.eye(2 ** W)
+    fl = 1.0 if i == 0 else 0.5
+    fr = 1.0 if i + 1 == L - 1 else 0.5
+    inter = -sum(np.kron(Z[j], Z[j]) for j in range(W))
+    return inter + fl * np.kron(onsite, one) + fr * np.kron(one, onsite)
 
 
 def bond_gate(hb, tau):
@@ -40,10 +75,14 @@ def bond_gate(hb, tau):
 class TebdChain:
     """MPS of an L-site chain with right-canonical tensors B[i] and Schmidt values lam[j]."""
 
-    def __init__(self, L, chi, h=1.0, p=10, q=2, seed=0, device="cuda", max_sweeps=0, simt=False):
+    def __init__(self, L, chi, h=1.0, p=10, q=2, seed=0, device="cuda", max_sweeps=0, simt=False, S=0.5, W=None):
+        """S: spin of the chain (d = 2S + 1); W: circumference of the 2D cylinder (d = 2^W;
+        overrides S)."""
         if L < 2:
             raise ValueError("L >= 2 required")
-        self.L, self.d, self.chi, self.h = L, 2, chi, h
+        self.S, self.W = S, W
+        d = 2 ** W if W else int(round(2 * S)) + 1
+        self.L, self.d, self.chi, self.h = L, d, chi, h
         self.p, self.q, self.seed, self.max_sweeps, self.simt = p, q, seed, max_sweeps, simt
         self.device = torch.device(device)
         d = self.d
@@ -71,9 +110,15 @@ class TebdChain:
         self.dt = float(dt)
         gates = []
         for layer, tau in ((0, dt / 2), (1, dt), (0, dt / 2)):
-            g = [bond_gate(bond_hamiltonian(i, self.L, self.h), tau).ravel() for i in self.layers[layer]]
+            g = [bond_gate(self.bond_term(i), tau).ravel() for i in self.layers[layer]]
             gates.append(torch.tensor(np.stack(g), dtype=torch.float64, device=self.device))
         self.gates = gates
+
+    def bond_term(self, i):
+        """The Hamiltonian term of bond (i, i+1) of this chain's model."""
+        if self.W:
+            return ring_bond_hamiltonian(i, self.L, self.h, self.W)
+        return bond_hamiltonian(i, self.L, self.h, self.S)
 
     def set_product_state(self, vectors):
         """B[i][0, :, 0] = vectors[i] / |vectors[i]|, lam[j] = (1, 0, ...)."""
@@ -129,14 +174,16 @@ class TebdChain:
     def save(self, path, step):
         """Checkpoint: B tensors, Schmidt values, bond dimensions, step and dt (.npz)."""
         B, lam = self.state_to_host()
-        np.savez(path, B=B, lam=lam, D=np.asarray(self.D), L=self.L, chi=self.chi, h=self.h,
-                 step=int(step), dt=float(self.dt if self.dt is not None else 0.0))
+        np.savez(path, B=B, lam=lam, D=np.asarray(self.D), L=self.L, chi=self.chi, h=self.h, d=self.d,
+                 S=float(self.S), W=int(self.W or 0), step=int(step), dt=float(self.dt if self.dt is not None else 0.0))
 
     def load(self, path):
         """Restore a checkpoint written by save(); returns the step to continue from."""
         z = np.load(path)
         if int(z["L"]) != self.L or int(z["chi"]) != self.chi or list(z["D"]) != self.D:
             raise ValueError("checkpoint does not match this chain")
+        if "d" in z and (int(z["d"]) != self.d or float(z["S"]) != float(self.S) or int(z["W"]) != int(self.W or 0)):
+            raise ValueError("checkpoint is of another model")
         self.state_from_host(z["B"], z["lam"])
         if float(z["dt"]) > 0:
             self.set_dt(float(z["dt"]))

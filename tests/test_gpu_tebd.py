@@ -98,3 +98,50 @@ def test_tebd_fp64_product_paths_agree():
     assert abs(res[0][0] - res[1][0]) <= 1e-10 * abs(res[1][0])
     for a, b in zip(res[0][1], res[1][1]):
         np.testing.assert_allclose(a, b, atol=1e-10)
+
+
+def run_model(tebd, L, chi, dt, steps, S=0.5, W=None, h=1.0, p=6, q=2, seed=4):
+    d = 2 ** W if W else int(2 * S) + 1
+    ch = tebd.TebdChain(L, chi, h=h, p=p, q=q, seed=seed, S=S, W=W)
+    vec = inputs.product_state_vectors(L, d, 77)
+    ch.set_product_state(vec)
+    ch.set_dt(dt)
+    terms = otebd.cylinder_bond_terms(L, h, W) if W else otebd.chain_bond_terms(L, h, S)
+    D = otebd.bond_dims(L, d, chi)
+    B, lam = otebd.product_state(vec, D)
+    comp = otebd.make_compressor("rsvd", p=p, q=q, seed=seed)
+    for s in range(steps):
+        ch.step(s)
+        otebd.trotter_step(B, lam, L, h, dt, comp, s, terms)
+    torch.cuda.synchronize()
+    return ch, B, lam, terms
+
+
+@pytest.mark.parametrize("S,W,L,chi,h", [(1.0, None, 8, 9, 1.2), (1.5, None, 6, 12, 1.5), (None, 2, 6, 16, 3.0)])
+def test_large_d_models_match_oracle(mods, S, W, L, chi, h):
+    # spin-S chains (d = 2S + 1) and the 2D cylinder (d = 2^W), Sec. III.B: the same bond
+    # update with larger local dimension
+    ch, B, lam, terms = run_model(mods, L, chi, 0.05, 4, S=S or 0.5, W=W, h=h)
+    assert int((ch.info[..., 0] != 0).sum()) == 0
+    lam_g = ch.schmidt_values()
+    for j in range(1, L):
+        np.testing.assert_allclose(lam_g[j], lam[j], atol=1e-10 * np.max(lam[j]) + 1e-14)
+    e_g = otebd.mps_energy(ch.tensors(), L, h, terms)
+    e_o = otebd.mps_energy(B, L, h, terms)
+    assert e_g == pytest.approx(e_o, rel=1e-10)
+
+
+def test_spin1_chain_reaches_ed_ground_energy(mods):
+    S, L, h = 1.0, 6, 1.2
+    ch = mods.TebdChain(L, 27, h=h, p=10, q=2, seed=8, S=S)
+    ch.set_product_state(inputs.product_state_vectors(L, 3, 5))
+    step = 0
+    for dt, n in ((0.1, 60), (0.02, 60), (0.005, 60)):
+        ch.set_dt(dt)
+        for _ in range(n):
+            ch.step(step)
+            step += 1
+    torch.cuda.synchronize()
+    e = otebd.mps_energy(ch.tensors(), L, h, otebd.chain_bond_terms(L, h, S))
+    e0 = float(np.linalg.eigvalsh(otebd.dense_chain_hamiltonian(L, h, S))[0])
+    assert abs(e - e0) <= 1e-4 * abs(e0)

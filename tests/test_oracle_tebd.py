@@ -95,3 +95,79 @@ def test_schmidt_values_normalised_and_entropy():
         assert np.sum(lam[j] ** 2) == pytest.approx(1.0, rel=1e-12)
     assert tebd.entanglement_entropy([1.0]) == 0.0
     assert tebd.entanglement_entropy([2 ** -0.5, 2 ** -0.5]) == pytest.approx(np.log(2.0))
+
+
+# ---- spin-S chain and 2D cylinder (Sec. III.B)
+
+@pytest.mark.parametrize("S", [0.5, 1.0, 1.5, 2.0, 3.5])
+def test_spin_ops_obey_the_spin_algebra(S):
+    # pins the S^x elements (the paper's printed formula is garbled) by the algebra alone:
+    # S^+ = 2 triu(S^x) raises m by one, [S^+, S^-] = 2 S^z and S.S = S(S+1)
+    sx, sz = tebd.spin_ops(S)
+    d = sx.shape[0]
+    assert d == int(2 * S) + 1
+    sp = 2.0 * np.triu(sx, 1)
+    sm = sp.T
+    np.testing.assert_allclose(sz @ sp - sp @ sz, sp, atol=1e-13)
+    np.testing.assert_allclose(sp @ sm - sm @ sp, 2.0 * sz, atol=1e-12)
+    casimir = sx @ sx - (sp - sm) @ (sp - sm) / 4.0 + sz @ sz
+    np.testing.assert_allclose(casimir, S * (S + 1) * np.eye(d), atol=1e-12)
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(sx)), np.sort(np.diag(sz)), atol=1e-12)
+
+
+def test_spin_half_chain_is_the_pauli_chain():
+    L, h = 6, 0.8
+    for i in range(L - 1):
+        fl = 1.0 if i == 0 else 0.5
+        fr = 1.0 if i + 1 == L - 1 else 0.5
+        ref = -np.kron(tebd.PAULI_Z, tebd.PAULI_Z) - h * (fl * np.kron(tebd.PAULI_X, tebd.EYE2)
+                                                          + fr * np.kron(tebd.EYE2, tebd.PAULI_X))
+        np.testing.assert_allclose(tebd.bond_hamiltonian(i, L, h, 0.5), ref, atol=1e-14)
+    np.testing.assert_allclose(tebd.dense_chain_hamiltonian(4, h, 0.5), tebd.dense_hamiltonian(4, h), atol=1e-13)
+
+
+def embed(terms, d, L):
+    H = np.zeros((d ** L, d ** L))
+    for i, t in enumerate(terms):
+        H += np.kron(np.kron(np.eye(d ** i), t), np.eye(d ** (L - i - 2)))
+    return H
+
+
+@pytest.mark.parametrize("S,L", [(1.0, 4), (1.5, 3), (2.0, 3)])
+def test_spin_chain_bond_terms_sum_to_the_hamiltonian(S, L):
+    h = 1.3
+    d = int(2 * S) + 1
+    np.testing.assert_allclose(embed(tebd.chain_bond_terms(L, h, S), d, L), tebd.dense_chain_hamiltonian(L, h, S),
+                               atol=1e-11)
+
+
+@pytest.mark.parametrize("W,L", [(2, 3), (3, 2)])
+def test_cylinder_bond_terms_sum_to_the_hamiltonian(W, L):
+    h = 3.0
+    np.testing.assert_allclose(embed(tebd.cylinder_bond_terms(L, h, W), 2 ** W, L),
+                               tebd.dense_cylinder_hamiltonian(L, h, W), atol=1e-11)
+
+
+def test_cylinder_of_width_one_is_the_chain_shifted():
+    # one spin per ring: the ring coupling Z_j Z_{j+1 mod 1} = 1 adds -1 per ring
+    L, h = 5, 0.7
+    np.testing.assert_allclose(tebd.dense_cylinder_hamiltonian(L, h, 1), tebd.dense_hamiltonian(L, h) - L * np.eye(2 ** L),
+                               atol=1e-12)
+
+
+def test_spin1_imaginary_tebd_reaches_the_ed_ground_energy():
+    S, L, h = 1.0, 5, 1.2
+    d = 3
+    e0 = float(np.linalg.eigvalsh(tebd.dense_chain_hamiltonian(L, h, S))[0])
+    terms = tebd.chain_bond_terms(L, h, S)
+    D = tebd.bond_dims(L, d, 27)
+    vec = np.ones((L, d)) + 0.1 * np.arange(L * d).reshape(L, d)
+    B, lam = tebd.product_state(vec, D)
+    comp = tebd.make_compressor("tsvd")
+    step = 0
+    for dt, n in ((0.1, 60), (0.02, 60), (0.005, 60)):
+        for _ in range(n):
+            tebd.trotter_step(B, lam, L, h, dt, comp, step, terms)
+            step += 1
+    e = tebd.mps_energy(B, L, h, terms)
+    assert abs(e - e0) <= 1e-4 * abs(e0)
