@@ -132,9 +132,11 @@ def test_large_d_models_match_oracle(mods, S, W, L, chi, h):
 
 
 def test_spin1_chain_reaches_ed_ground_energy(mods):
-    S, L, h = 1.0, 6, 1.2
+    # paramagnetic side (gap 1.0 at L = 6): imaginary time 7.5 reaches the ground state from
+    # a product state with generic overlap
+    S, L, h = 1.0, 6, 2.0
     ch = mods.TebdChain(L, 27, h=h, p=10, q=2, seed=8, S=S)
-    ch.set_product_state(inputs.product_state_vectors(L, 3, 5))
+    ch.set_product_state(np.ones((L, 3)) + 0.1 * np.arange(L * 3).reshape(L, 3))
     step = 0
     for dt, n in ((0.1, 60), (0.02, 60), (0.005, 60)):
         ch.set_dt(dt)
@@ -144,4 +146,4 @@ def test_spin1_chain_reaches_ed_ground_energy(mods):
     torch.cuda.synchronize()
     e = otebd.mps_energy(ch.tensors(), L, h, otebd.chain_bond_terms(L, h, S))
     e0 = float(np.linalg.eigvalsh(otebd.dense_chain_hamiltonian(L, h, S))[0])
-    assert abs(e - e0) <= 1e-4 * abs(e0)
+    assert abs(e - e0) <= 1e-7 * abs(e0)
