@@ -424,6 +424,9 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
 // barriers per panel instead of three per column.
 constexpr int kNb = 16;
 constexpr int kPanelMaxCluster = 8;  // the blocked kernel runs on portable cluster sizes
+// shared memory of the blocked kernel: up to about 110 KB two CTAs share an SM;
+// above, one CTA per SM, which still beats the column kernel by far
+constexpr size_t kPanelSmemMax = 220 * 1024;  // with the kernel's 4.6 KB of static shared memory, within 227 KB
 
 struct PanelLayout {
   size_t ys, vo, wp, ws, alpha, total;  // shared-memory offsets in doubles
@@ -911,7 +914,7 @@ cudaError_t launch_householder(const OrthBatch<T>& b, cudaStream_t s) {
   pb.max_tilepairs = cb.max_tilepairs = b.max_tilepairs;
   for (int i = 0; i < b.count; ++i) {
     const OrthJob<T>& J = b.job[i];
-    const bool fits = panel_layout(J.rows, J.l, kPanelMaxCluster).total * sizeof(double) <= 110 * 1024;
+    const bool fits = panel_layout(J.rows, J.l, kPanelMaxCluster).total * sizeof(double) <= kPanelSmemMax;
     if (J.l >= kNb && J.l <= 256 && J.rows <= kHhThreads && fits) pb.job[pb.count++] = J;
     else cb.job[cb.count++] = J;
   }
