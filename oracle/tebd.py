@@ -26,6 +26,11 @@ paper is silent:
     theta = lam[i][a] * theta_B, reshaped (D[i] d) x (d D[i+2])
     (U, S, V^T) = rank-D[i+1] truncated factorization of theta
     B[i+1] <- V^T,  B[i] <- theta_B V / ||S||,  lam[i+1] <- S / ||S||
+* Product update (Sec. III.A, "product update (P)"): the gate as a sum of K
+  Kronecker products of single-site operators, theta = X Y with X of K D[i+1]
+  columns; the cylinder's bonds as W gates of K = 2 (its commuting couplings),
+  the rings' own terms folded into the first and last (see
+  cylinder_product_gates).
 * Philox stream of a bond update: (3 * step + layer) * L + i, layer in {0,1,2}.
 * Energy: exact contraction <psi|H|psi> / <psi|psi> (no canonical-form
   assumption).
@@ -142,6 +147,117 @@ def bond_update(B, lam, i, G, compress, stream):
     lam[i + 1] = S / nrm
     tot = float(np.sum(M * M))
     return max(0.0, 1.0 - nrm * nrm / tot) if tot > 0 else 0.0
+
+
+def product_update(B, lam, i, uL, uR, compress, stream):
+    """One TEBD product update (Sec. III.A, "product update (P)") on sites (i, i+1)
+    with the two-site gate sum_k uL[k] (x) uR[k] (K terms of d x d operators);
+    returns the discarded weight.
+
+    Each side takes its K single-site operators, which widens the bond to K D[i+1]:
+      XB[(a,s1),(k,b)] = sum_t uL[k][s1,t] B[i][a,t,b],   X = lam[i][a] XB
+      Y[(k,b),(s2,c)]  = sum_t uR[k][s2,t] B[i+1][b,t,c]
+    so theta = X Y and theta_B = XB Y, (D[i] d) x (d D[i+2]) of rank <= K D[i+1].
+    The bond is compressed from theta = X Y exactly as in the block update.  With
+    X = Q_X R (thin QR), theta and the (K D[i+1]) x (d D[i+2]) matrix R Y of the
+    paper's P update have the same singular values and right singular vectors,
+    and Alg. RSVD with the same Omega gives the same B = Q^T A for both (their
+    samples differ by the isometry Q_X)."""
+    Dl, d, k = B[i].shape
+    Dr = B[i + 1].shape[2]
+    K = len(uL)
+    XB = np.einsum("kst,atb->askb", np.asarray(uL), B[i]).reshape(Dl * d, K * k)
+    Y = np.einsum("kst,btc->kbsc", np.asarray(uR), B[i + 1]).reshape(K * k, d * Dr)
+    X = np.repeat(lam[i], d)[:, None] * XB
+    M = X @ Y
+    MB = XB @ Y
+    U, S, Vt = compress(M, k, stream)
+    nrm = float(np.linalg.norm(S))
+    B[i + 1] = Vt.reshape(k, d, Dr).copy()
+    B[i] = (MB @ Vt.T / nrm).reshape(Dl, d, k)
+    lam[i + 1] = S / nrm
+    tot = float(np.sum(M * M))
+    return max(0.0, 1.0 - nrm * nrm / tot) if tot > 0 else 0.0
+
+
+def product_factors(B, lam, i, uL, uR):
+    """(X, Y) of the product update and the paper's (K D[i+1]) x (d D[i+2]) matrix
+    R Y (X = Q_X R, thin QR), for checks of the P form."""
+    Dl, d, k = B[i].shape
+    Dr = B[i + 1].shape[2]
+    K = len(uL)
+    XB = np.einsum("kst,atb->askb", np.asarray(uL), B[i]).reshape(Dl * d, K * k)
+    Y = np.einsum("kst,btc->kbsc", np.asarray(uR), B[i + 1]).reshape(K * k, d * Dr)
+    X = np.repeat(lam[i], d)[:, None] * XB
+    R = np.linalg.qr(X, mode="r") if X.shape[0] >= X.shape[1] else X
+    return X, Y, R @ Y
+
+
+def gate_terms(G, d, tol=1e-14):
+    """Operator-Schmidt form of a two-site gate: G[(s1 s2),(t1 t2)] = sum_k
+    uL[k][s1,t1] uR[k][s2,t2], from the SVD of G regrouped as ((s1 t1),(s2 t2));
+    terms below tol times the largest are dropped.  Returns (uL, uR), K x d x d."""
+    R = np.asarray(G).reshape(d, d, d, d).transpose(0, 2, 1, 3).reshape(d * d, d * d)
+    U, s, Vt = np.linalg.svd(R)
+    K = max(1, int(np.sum(s > tol * s[0]))) if s[0] > 0 else 1
+    w = np.sqrt(s[:K])
+    uL = (U[:, :K] * w).T.reshape(K, d, d)
+    uR = (Vt[:K].T * w).T.reshape(K, d, d)
+    return uL, uR
+
+
+def cylinder_product_gates(i, L, h, W, tau):
+    """The bond (i, i+1) of the W-wide cylinder as W gates of K = 2 terms each, the
+    form in which the product update pays (K = 2 < d = 2^W).
+
+    The bond term is C + A with C = -sum_j Z_{i,j} Z_{i+1,j} (W commuting couplings)
+    and A its share of the two rings' own terms (a sum of single-ring operators).
+    exp(-tau (A + C)) is split symmetrically as exp(-tau A / 2) prod_j exp(-tau C_j)
+    exp(-tau A / 2) (error O(tau^3), the order of the layer splitting), with
+    exp(-tau C_j) = cosh(tau) 1 (x) 1 + sinh(tau) Z_j (x) Z_j and exp(-tau A / 2) =
+    gL (x) gR folded into the first and the last coupling.  Returns W pairs
+    (uL, uR), applied in list order."""
+    Z, X, ring, xsum = ring_ops(W)
+    fl = 1.0 if i == 0 else 0.5
+    fr = 1.0 if i + 1 == L - 1 else 0.5
+    onsite = -ring - h * xsum
+    gL = gate_1site(fl * onsite, tau / 2)
+    gR = gate_1site(fr * onsite, tau / 2)
+    one = np.eye(2 ** W)
+    ch, sh = np.cosh(tau), np.sinh(tau)
+    out = []
+    for j in range(W):
+        aL, aR = [ch * one, sh * Z[j]], [one, Z[j]]
+        if j == 0:  # exp(-tau A / 2) acts first
+            aL = [u @ gL for u in aL]
+            aR = [u @ gR for u in aR]
+        if j == W - 1:  # and last
+            aL = [gL @ u for u in aL]
+            aR = [gR @ u for u in aR]
+        out.append((np.array(aL), np.array(aR)))
+    return out
+
+
+def gate_1site(h1, tau):
+    """exp(-tau h1) of a symmetric single-site operator, through its eigenbasis."""
+    w, V = np.linalg.eigh(h1)
+    return (V * np.exp(-tau * w)[None, :]) @ V.T
+
+
+def trotter_step_product(B, lam, L, h, W, dt, compress, step):
+    """One second-order Trotter step of the W-wide cylinder with product updates: the
+    layers of trotter_step, each bond applied as its W gates of cylinder_product_gates
+    (one compression per gate).  Philox stream of gate j of bond i in layer t of the
+    step: ((3 step + t) W + j) L + i.  Returns the summed discarded weight."""
+    la, lb = layers(L)
+    err = 0.0
+    for layer, (bonds, tau) in enumerate(((la, dt / 2), (lb, dt), (la, dt / 2))):
+        gates = {i: cylinder_product_gates(i, L, h, W, tau) for i in bonds}
+        for j in range(W):
+            for i in bonds:
+                uL, uR = gates[i][j]
+                err += product_update(B, lam, i, uL, uR, compress, ((3 * step + layer) * W + j) * L + i)
+    return err
 
 
 def make_compressor(kind, p=10, q=2, seed=0):

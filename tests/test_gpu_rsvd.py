@@ -145,3 +145,14 @@ def test_fp64_product_paths_agree(api, m, n, k):
     u0, u1 = out[False][1], out[True][1]
     np.testing.assert_allclose(u0.T @ u0, np.eye(k), atol=1e-12)
     np.testing.assert_allclose(np.abs(np.sum(u0 * u1, axis=0))[:k // 2], 1.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("m", [384, 512])
+def test_blocked_householder_tall_samples(api, m):
+    # the bond-matrix heights of the spin-1 chain (3 * 128) and the two-leg cylinder
+    # (4 * 128): a spectrum falling through the FP64 floor within l = 138 columns makes
+    # CholeskyQR2 fail, so the samples are orthonormalised by the blocked Householder
+    # kernel with m rows in shared memory
+    A = inputs.spectral_matrix(m, m, inputs.exp_spectrum(m, 4.0), 41 + m)
+    s, u, vt, st = check_rsvd(api, A, 128, 10, 2, seed=7, stream=m)
+    assert st["status"] == 0 and st["path"] & 2 and st["l"] == 138

@@ -171,3 +171,109 @@ def test_spin1_imaginary_tebd_reaches_the_ed_ground_energy():
             step += 1
     e = tebd.mps_energy(B, L, h, terms)
     assert abs(e - e0) <= 1e-4 * abs(e0)
+
+
+def random_bond(rng, Dl, d, Dm, Dr):
+    B = [rng.standard_normal((Dl, d, Dm)), rng.standard_normal((Dm, d, Dr))]
+    lam = [np.sort(rng.uniform(0.1, 1.0, Dl))[::-1], np.ones(Dm), np.ones(Dr)]
+    return B, lam
+
+
+def test_product_update_is_the_block_update_of_the_kronecker_sum():
+    # P update with terms (uL_k, uR_k) == B update with G = sum_k uL_k (x) uR_k: pins the
+    # index placement of X and Y (the random terms are neither symmetric nor equal)
+    rng = np.random.default_rng(61)
+    Dl, d, Dm, Dr, K = 4, 3, 5, 6, 3
+    uL = rng.standard_normal((K, d, d))
+    uR = rng.standard_normal((K, d, d))
+    G = sum(np.kron(uL[k], uR[k]) for k in range(K))
+    comp = tebd.make_compressor("tsvd")
+    Bp, lp = random_bond(rng, Dl, d, Dm, Dr)
+    Bb = [t.copy() for t in Bp]
+    lb = [v.copy() for v in lp]
+    ep = tebd.product_update(Bp, lp, 0, uL, uR, comp, 0)
+    eb = tebd.bond_update(Bb, lb, 0, G, comp, 0)
+    assert ep == pytest.approx(eb, rel=1e-12, abs=1e-15)
+    np.testing.assert_allclose(lp[1], lb[1], atol=1e-13)
+    # singular vectors up to the shared sign rule
+    np.testing.assert_allclose(Bp[1], Bb[1], atol=1e-11)
+    np.testing.assert_allclose(Bp[0], Bb[0], atol=1e-11)
+
+
+def test_product_matrix_has_the_spectrum_of_theta():
+    # the paper's (K D) x (d D') matrix R Y and theta = X Y share singular values and right
+    # singular vectors
+    rng = np.random.default_rng(62)
+    Dl, d, Dm, Dr, K = 6, 4, 5, 7, 2
+    B, lam = random_bond(rng, Dl, d, Dm, Dr)
+    uL = rng.standard_normal((K, d, d))
+    uR = rng.standard_normal((K, d, d))
+    X, Y, RY = tebd.product_factors(B, lam, 0, uL, uR)
+    assert RY.shape == (K * Dm, d * Dr)
+    s1 = np.linalg.svd(X @ Y, compute_uv=False)[:K * Dm]
+    s2 = np.linalg.svd(RY, compute_uv=False)
+    np.testing.assert_allclose(s1, s2, rtol=1e-12, atol=1e-13 * s2[0])
+    _, _, v1 = np.linalg.svd(X @ Y)
+    _, _, v2 = np.linalg.svd(RY)
+    np.testing.assert_allclose(np.abs(v1[:4] @ v2[:4].T), np.eye(4), atol=1e-10)
+
+
+def test_gate_terms_reconstruct_the_gate():
+    rng = np.random.default_rng(63)
+    d = 3
+    G = rng.standard_normal((d * d, d * d))
+    uL, uR = tebd.gate_terms(G, d)
+    assert len(uL) == d * d
+    np.testing.assert_allclose(sum(np.kron(a, b) for a, b in zip(uL, uR)), G, atol=1e-12)
+    # the Ising coupling gate has operator-Schmidt rank 2, a product gate rank 1
+    zz = expm(0.3 * np.kron(tebd.PAULI_Z, tebd.PAULI_Z))
+    assert len(tebd.gate_terms(zz, 2)[0]) == 2
+    assert len(tebd.gate_terms(np.kron(rng.standard_normal((2, 2)), rng.standard_normal((2, 2))), 2)[0]) == 1
+
+
+@pytest.mark.parametrize("W,i,L", [(1, 1, 4), (2, 0, 4), (3, 1, 3), (2, 2, 4)])
+def test_cylinder_product_gates_are_the_symmetric_split(W, i, L):
+    # the W gates multiply to exp(-tau A/2) exp(-tau C) exp(-tau A/2) (A: the rings' own
+    # terms, C: the couplings along the cylinder), built here from the bond term by expm
+    h, tau = 3.0, 0.07
+    d = 2 ** W
+    hb = tebd.cylinder_bond_hamiltonian(i, L, h, W)
+    C = -sum(np.kron(z, z) for z in tebd.ring_ops(W)[0])
+    A = hb - C
+    want = expm(-tau / 2 * A) @ expm(-tau * C) @ expm(-tau / 2 * A)
+    got = np.eye(d * d)
+    for uL, uR in tebd.cylinder_product_gates(i, L, h, W, tau):
+        assert len(uL) == 2
+        got = sum(np.kron(a, b) for a, b in zip(uL, uR)) @ got
+    np.testing.assert_allclose(got, want, atol=1e-12)
+    # a second-order split of exp(-tau hb): the error falls by 8 when tau halves
+    errs = []
+    for t in (tau, tau / 2):
+        g = np.eye(d * d)
+        for uL, uR in tebd.cylinder_product_gates(i, L, h, W, t):
+            g = sum(np.kron(a, b) for a, b in zip(uL, uR)) @ g
+        errs.append(np.linalg.norm(g - expm(-t * hb)))
+    if W > 1:
+        assert 6.0 < errs[0] / errs[1] < 10.0
+
+
+def test_product_tebd_reaches_the_cylinder_ground_state_at_second_order():
+    # product-update TEBD of the W = 2 cylinder without truncation (chi = 16 holds L = 4
+    # exactly): the converged state is off by O(dt^2), so its (variational) energy error
+    # falls as dt^4
+    L, W, h = 4, 2, 3.0
+    d = 2 ** W
+    e0 = float(np.linalg.eigvalsh(tebd.dense_cylinder_hamiltonian(L, h, W))[0])
+    terms = tebd.cylinder_bond_terms(L, h, W)
+    comp = tebd.make_compressor("tsvd")
+    errs = []
+    for dts in (((0.2, 40), (0.08, 200)), ((0.2, 40), (0.04, 400))):
+        B, lam = tebd.product_state(np.ones((L, d)) + 0.1 * np.arange(L * d).reshape(L, d), tebd.bond_dims(L, d, 16))
+        step = 0
+        for dt, n in dts:
+            for _ in range(n):
+                tebd.trotter_step_product(B, lam, L, h, W, dt, comp, step)
+                step += 1
+        errs.append(tebd.mps_energy(B, L, h, terms) - e0)
+    assert 0 < errs[1] < errs[0] < 1e-2 * abs(e0)
+    assert 12.0 < errs[0] / errs[1] < 20.0
