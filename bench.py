@@ -183,7 +183,7 @@ def step_flops(info):
     flops = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "ozgemm": 0.0}
     for j, lay in enumerate(bond_shapes()):
         for b, (m, n, k, l) in enumerate(lay):
-            rec = info[j][b]
+            rec = info[j][0][b]  # (layer, compression, bond) records
             sweeps, rots, qr_cols = int(rec[3]), int(rec[5]), int(rec[6])
             # the bond update forms no U: after the first orthonormalisation only the leading
             # r columns of Q carry the range (r = reported qr_columns, else l), and the products,

@@ -207,6 +207,58 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond,
                      void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
 
 /*
+ * tebd_product_workspace_size - workspace bytes of tebd_product_update for up
+ * to nb bonds with K operator pairs per gate.
+ */
+int tebd_product_workspace_size(int L, int d, const int* D, int nb, int K, const rsvd_params* p, size_t* bytes);
+
+/*
+ * tebd_product_update - TEBD "product update" (Sec. III.A, P) of nb
+ * independent bonds, FP64, in place on the MPS of tebd_bond_update (same B,
+ * lam, D, bond layout and rules).  The gate of bond b is the sum of K
+ * Kronecker products of single-site operators, sum_k uL[k] (x) uR[k]:
+ *   uL, uR  device, nb x K x d x d row-major; operator k of bond b starts at
+ *           uL + (b K + k) d^2, element [s, t] acting as s <- t.
+ * Per bond i, with k = D[i+1] and r = K k:
+ *   XB[(a,s1),(k',b)] = sum_t uL[k'][s1,t] B[i][a,t,b];  X = lam[i] (rows) XB
+ *   Y[(k',b),(s2,c)]  = sum_t uR[k'][s2,t] B[i+1][b,t,c]
+ *   theta = X Y ((D[i] d) x (d D[i+2]), never formed: every product of Alg.
+ *   RSVD with theta is two products through an r x l buffer);
+ *   (S, V^T) = RSVD(theta, k, p, q);  B[i+1] <- V^T;  B[i] <- XB (Y V) / ||S||;
+ *   lam[i+1] <- S / ||S||;  trunc_err[b] <- 1 - ||S||^2 / ||theta||_F^2 with
+ *   ||theta||_F^2 = trace((X^T X)(Y Y^T)).
+ * Alg. RSVD of X Y equals Alg. RSVD of the paper's r x (d D[i+2]) matrix R Y
+ * (X = Q_X R) with the same Omega: the samples differ by the isometry Q_X and
+ * B = Q^T A is the same matrix.  Bond b uses Philox stream p->stream + bond[b].
+ * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_PRECISION
+ * (p->prec must be RSVD_F64), RSVD_ERR_WORKSPACE, RSVD_ERR_LAUNCH.
+ */
+int tebd_product_update(int L, int d, const int* D, int nb, const int* bond, double* B, size_t tensor_stride,
+                        double* lam, size_t lam_stride, int K, const double* uL, const double* uR,
+                        const rsvd_params* p, double* trunc_err, void* work, size_t work_bytes, rsvd_info* info,
+                        void* cuda_stream);
+
+/*
+ * rsvd_factored_workspace_size - workspace bytes of rsvd_truncate_factored.
+ */
+int rsvd_factored_workspace_size(int m, int r, int n, const rsvd_params* p, size_t* bytes);
+
+/*
+ * rsvd_truncate_factored - Alg. RSVD of a matrix given as the product A = X Y
+ * (Sec. II.A: A may be the contraction of two tensors), without forming A:
+ * X (m x r, ldx) and Y (r x n, ldy) row-major device matrices of p->prec
+ * (RSVD_F64 or RSVD_F32); every product with A or A^T is two products through
+ * an r x l buffer (cost 2 (m + n) r l instead of 2 m n l).  Outputs as for
+ * rsvd_truncate (S, U m x k, V^T k x n; same sign rule, Philox stream
+ * p->stream).  The sampled path is taken for every m (no Q = I shortcut).
+ * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_PRECISION,
+ * RSVD_ERR_WORKSPACE, RSVD_ERR_LAUNCH.
+ */
+int rsvd_truncate_factored(int m, int r, int n, const void* X, int ldx, const void* Y, int ldy, const rsvd_params* p,
+                           double* S, void* U, int ldu, void* Vt, int ldvt, void* work, size_t work_bytes,
+                           rsvd_info* info, void* cuda_stream);
+
+/*
  * rsvd_gemm_f64_tc - the FP64 tensor-core product of the FP64 path (exposed so
  * that it can be verified on its own): C = A B^T with A (M x K, lda), B (N x K,
  * ldb) and C (M x N, ldc) row-major FP64 device matrices, N <= 256, K <= 256.

@@ -38,6 +38,10 @@ EXPORTED = (
     "rsvd_truncate_batched",
     "tebd_workspace_size",
     "tebd_bond_update",
+    "tebd_product_workspace_size",
+    "tebd_product_update",
+    "rsvd_factored_workspace_size",
+    "rsvd_truncate_factored",
     "rsvd_status_string",
     "rsvd_profile_enable",
     "rsvd_profile_collect",

@@ -99,6 +99,36 @@ def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf3
     return U, S, Vt, info
 
 
+def rsvd_truncate_factored(X, Y, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None):
+    """Rank-k RSVD of A = X Y without forming A (rsvd_truncate_factored): X (m x r) and Y
+    (r x n) float64 or float32 CUDA tensors.  Returns (U, S, Vt, info)."""
+    lib = _lib.load()
+    _require_cuda(X, Y)
+    if X.dim() != 2 or Y.dim() != 2 or X.stride(1) != 1 or Y.stride(1) != 1 or X.shape[1] != Y.shape[0]:
+        raise ValueError("X (m x r) and Y (r x n) must be row-major with matching r")
+    if X.dtype != Y.dtype or X.dtype not in (torch.float64, torch.float32):
+        raise ValueError("X and Y must both be float64 or both float32")
+    m, r = X.shape
+    n = Y.shape[1]
+    par = _params(k, p, q, _DTYPE_PREC[X.dtype], seed, stream, max_sweeps)
+    sz = ctypes.c_size_t(0)
+    _lib.check(lib.rsvd_factored_workspace_size(m, r, n, ctypes.byref(par), ctypes.byref(sz)),
+               "rsvd_factored_workspace_size")
+    if work is None or work.numel() < sz.value:
+        work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=X.device)
+    U = torch.empty((m, k), dtype=X.dtype, device=X.device)
+    S = torch.empty((k,), dtype=torch.float64, device=X.device)
+    Vt = torch.empty((k, n), dtype=X.dtype, device=X.device)
+    info = torch.zeros((1, _lib.INFO_INTS), dtype=torch.int32, device=X.device)
+    rc = lib.rsvd_truncate_factored(m, r, n, ctypes.c_void_p(X.data_ptr()), X.stride(0), ctypes.c_void_p(Y.data_ptr()),
+                                    Y.stride(0), ctypes.byref(par), ctypes.c_void_p(S.data_ptr()),
+                                    ctypes.c_void_p(U.data_ptr()), U.stride(0), ctypes.c_void_p(Vt.data_ptr()),
+                                    Vt.stride(0), ctypes.c_void_p(work.data_ptr()), ctypes.c_size_t(work.numel()),
+                                    ctypes.c_void_p(info.data_ptr()), _stream_handle())
+    _lib.check(rc, "rsvd_truncate_factored")
+    return U, S, Vt, info
+
+
 class BatchedPlan:
     """Preallocated outputs and workspace of rsvd_truncate_batched for fixed shapes."""
 

@@ -58,6 +58,12 @@ struct Prob {
   __nv_bfloat16 *SA, *SAt, *SS;
   int *eA, *eAt, *eS;
   int KpA, KpAt, KpS, Npad;
+  // A given as the product X Y (X m x r, Y r x n; Sec. II.A): every product with A
+  // is two products through W (r x l), and A itself is never formed
+  int r;
+  const void *Xf, *Yf;
+  int ldxf, ldyf;
+  void* Wf;
 };
 
 inline int pad8(int x) { return (x + 7) / 8 * 8; }
@@ -65,7 +71,7 @@ inline int pad8(int x) { return (x + 7) / 8 * 8; }
 // Workspace of one matrix (bytes), with the buffer offsets when `p` is given.
 // tc_bytes > 0 (the operand size of the tensor-core precisions) adds A^T
 // (n x m), Omega^T / Z^T (l x n) and Q^T (l x m) with 8-element-aligned rows.
-size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int tc_bytes = 0, int oz = 0) {
+size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int tc_bytes = 0, int oz = 0, int r = 0) {
   const int mx = std::max(m, n);
   const int nchunk = ceil_div(mx, kGramChunk);
   const int wide = n >= 4 * l ? 1 : 0;
@@ -110,7 +116,9 @@ size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int
   void* eA = take(oz ? (size_t)m * 4 : 0);
   void* eAt = take(oz ? (size_t)n * 4 : 0);
   void* eS = take(oz ? (size_t)Npad * 4 : 0);
+  void* Wf = take(r ? (size_t)r * l * tsize : 0);
   if (p) {
+    p->Wf = Wf;
     p->oz = oz;
     p->SA = (__nv_bfloat16*)SA; p->SAt = (__nv_bfloat16*)SAt; p->SS = (__nv_bfloat16*)SS;
     p->eA = (int*)eA; p->eAt = (int*)eAt; p->eS = (int*)eS;
@@ -398,24 +406,52 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
       }
       return RSVD_OK;
     };
-    auto gemm_AZ = [&]() -> cudaError_t {  // Y0 = A Z0
-      if (!oz.empty() && oz_product(kAZ) != RSVD_OK) return last_cuda_error();
-      GemmBatch<T, T> g;
-      g.count = (int)rsd.size();
-      for (int i = 0; i < g.count; ++i) {
-        Prob& p = *rsd[i];
-        g.job[i] = GemmJob<T, T>{p.m, p.l, p.n, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Z0, (T*)p.Y0, nullptr, nullptr, 0};
-        if (!p.want_u) g.job[i].n_eff = p.flag + 2;
+    // W = X^T Y0 (r x l) for the factored matrices: the first half of A^T Y0 and of Q^T A
+    auto gemm_XtY = [&]() -> cudaError_t {
+      GemmBatch<T, T> f;
+      f.count = 0;
+      for (auto* pp : rsd) {
+        Prob& p = *pp;
+        if (!p.r) continue;
+        f.job[f.count] = GemmJob<T, T>{p.r, p.l, p.m, p.ldxf, p.l, p.l, (const T*)p.Xf, (const T*)p.Y0, (T*)p.Wf, nullptr, nullptr, 0};
+        if (!p.want_u) f.job[f.count].n_eff = p.flag + 2;
+        ++f.count;
       }
+      return launch_gemm<T, T, true, false>(f, s);
+    };
+    auto gemm_AZ = [&]() -> cudaError_t {  // Y0 = A Z0 (factored: W = Y Z0, Y0 = X W)
+      if (!oz.empty() && oz_product(kAZ) != RSVD_OK) return last_cuda_error();
+      GemmBatch<T, T> g, f;
+      g.count = f.count = 0;
+      for (auto* pp : rsd) {
+        Prob& p = *pp;
+        if (p.r) {
+          f.job[f.count] = GemmJob<T, T>{p.r, p.l, p.n, p.ldyf, p.l, p.l, (const T*)p.Yf, (const T*)p.Z0, (T*)p.Wf, nullptr, nullptr, 0};
+          if (!p.want_u) f.job[f.count].n_eff = p.flag + 2;
+          ++f.count;
+          g.job[g.count] = GemmJob<T, T>{p.m, p.l, p.r, p.ldxf, p.l, p.l, (const T*)p.Xf, (const T*)p.Wf, (T*)p.Y0, nullptr, nullptr, 0};
+        } else {
+          g.job[g.count] = GemmJob<T, T>{p.m, p.l, p.n, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Z0, (T*)p.Y0, nullptr, nullptr, 0};
+        }
+        if (!p.want_u) g.job[g.count].n_eff = p.flag + 2;
+        ++g.count;
+      }
+      cudaError_t e = launch_gemm<T, T, false, false>(f, s);
+      if (e != cudaSuccess) return e;
       return launch_gemm<T, T, false, false>(g, s);
     };
-    auto gemm_AtY = [&]() -> cudaError_t {  // Z0 = A^T Y0
+    auto gemm_AtY = [&]() -> cudaError_t {  // Z0 = A^T Y0 (factored: Z0 = Y^T (X^T Y0))
       if (!oz.empty() && oz_product(kAtY) != RSVD_OK) return last_cuda_error();
+      cudaError_t e = gemm_XtY();
+      if (e != cudaSuccess) return e;
       GemmBatch<T, T> g;
       g.count = (int)rsd.size();
       for (int i = 0; i < g.count; ++i) {
         Prob& p = *rsd[i];
-        g.job[i] = GemmJob<T, T>{p.n, p.l, p.m, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Y0, (T*)p.Z0, nullptr, nullptr, 0};
+        if (p.r)
+          g.job[i] = GemmJob<T, T>{p.n, p.l, p.r, p.ldyf, p.l, p.l, (const T*)p.Yf, (const T*)p.Wf, (T*)p.Z0, nullptr, nullptr, 0};
+        else
+          g.job[i] = GemmJob<T, T>{p.n, p.l, p.m, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Y0, (T*)p.Z0, nullptr, nullptr, 0};
         if (!p.want_u) g.job[i].n_eff = p.flag + 2;
       }
       return launch_gemm<T, T, true, false>(g, s);
@@ -431,11 +467,15 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
     }
     {  // step 4: B = Q^T A (l x n) in FP64
       if (!oz.empty() && oz_product(kQtA) != RSVD_OK) return RSVD_ERR_LAUNCH;
+      RSVD_TRY(gemm_XtY());  // factored: B = (X^T Q)^T Y
       GemmBatch<T, double> g;
       g.count = (int)rsd.size();
       for (int i = 0; i < g.count; ++i) {
         Prob& p = *rsd[i];
-        g.job[i] = GemmJob<T, double>{p.l, p.n, p.m, p.l, p.lda, p.n, (const T*)p.Y0, (const T*)p.A, p.Bm, nullptr, nullptr, 0};
+        if (p.r)
+          g.job[i] = GemmJob<T, double>{p.l, p.n, p.r, p.l, p.ldyf, p.n, (const T*)p.Wf, (const T*)p.Yf, p.Bm, nullptr, nullptr, 0};
+        else
+          g.job[i] = GemmJob<T, double>{p.l, p.n, p.m, p.l, p.lda, p.n, (const T*)p.Y0, (const T*)p.A, p.Bm, nullptr, nullptr, 0};
         if (!p.want_u) g.job[i].m_eff = p.flag + 2;
       }
       RSVD_TRY((launch_gemm<T, double, true, false>(g, s)));
@@ -614,11 +654,12 @@ int run_batched(std::vector<Prob>& probs, const rsvd_params* p, char* work, size
   const size_t ts = tsize_of(p->prec);
   const int tcb = tc_bytes_of(p->prec);
   size_t need = 0;
-  for (auto& pr : probs) need += layout(nullptr, pr.m, pr.n, pr.k, pr.l, ts, nullptr, tcb, use_oz(pr.m, pr.n, pr.l, pr.exact, p));
+  for (auto& pr : probs)
+    need += layout(nullptr, pr.m, pr.n, pr.k, pr.l, ts, nullptr, tcb, pr.r ? 0 : use_oz(pr.m, pr.n, pr.l, pr.exact, p), pr.r);
   if (need > work_bytes) return RSVD_ERR_WORKSPACE;
   size_t off = 0;
   for (auto& pr : probs) {
-    off += layout(&pr, pr.m, pr.n, pr.k, pr.l, ts, work + off, tcb, use_oz(pr.m, pr.n, pr.l, pr.exact, p));
+    off += layout(&pr, pr.m, pr.n, pr.k, pr.l, ts, work + off, tcb, pr.r ? 0 : use_oz(pr.m, pr.n, pr.l, pr.exact, p), pr.r);
   }
   const size_t step = is_tc(p->prec) ? (size_t)kMaxTcJobs : (size_t)kMaxJobs;
   for (size_t c0 = 0; c0 < probs.size(); c0 += step) {
@@ -748,6 +789,43 @@ int rsvd_truncate(int m, int n, const void* A, int lda, const rsvd_params* p, do
   void* Va[1] = {Vt};
   return rsvd_truncate_batched(1, &m, &n, Aa, &lda, &p->k, p, Sa, Ua, &ldu, Va, &ldvt, 0, nullptr, work, work_bytes,
                                info, cuda_stream);
+}
+
+int rsvd_factored_workspace_size(int m, int r, int n, const rsvd_params* p, size_t* bytes) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!bytes) return RSVD_ERR_NULL_POINTER;
+  if (p->prec != RSVD_F64 && p->prec != RSVD_F32) return RSVD_ERR_PRECISION;
+  if (m < 1 || n < 1 || r < 1 || p->k < 1 || p->k > std::min(m, n)) return RSVD_ERR_INVALID_SIZE;
+  const int l = sample_width(m, n, p->k, p->p);
+  if (l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+  *bytes = layout(nullptr, m, n, p->k, l, tsize_of(p->prec), nullptr, 0, 0, r);
+  return RSVD_OK;
+}
+
+int rsvd_truncate_factored(int m, int r, int n, const void* X, int ldx, const void* Y, int ldy, const rsvd_params* p,
+                           double* S, void* U, int ldu, void* Vt, int ldvt, void* work, size_t work_bytes,
+                           rsvd_info* info, void* cuda_stream) {
+  size_t need = 0;
+  int rc = rsvd_factored_workspace_size(m, r, n, p, &need);
+  if (rc) return rc;
+  if (!X || !Y || !S || !U || !Vt || !work || !info) return RSVD_ERR_NULL_POINTER;
+  if (ldx < r || ldy < n || ldu < p->k || ldvt < n) return RSVD_ERR_INVALID_SIZE;
+  if (((uintptr_t)work) % kAlign) return RSVD_ERR_WORKSPACE;
+  if (need > work_bytes) return RSVD_ERR_WORKSPACE;
+  std::vector<Prob> probs(1);
+  Prob& pr = probs[0];
+  std::memset(&pr, 0, sizeof(Prob));
+  pr.m = m; pr.n = n; pr.k = p->k;
+  pr.l = sample_width(m, n, p->k, p->p);
+  pr.exact = 0;  // A is never formed
+  pr.want_u = 1;
+  pr.r = r; pr.Xf = X; pr.ldxf = ldx; pr.Yf = Y; pr.ldyf = ldy;
+  pr.S = S; pr.U = U; pr.ldu = ldu; pr.Vt = Vt; pr.ldvt = ldvt;
+  pr.seed = p->seed; pr.stream = p->stream;
+  pr.info = info;
+  pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+  return run_batched(probs, p, (char*)work, work_bytes, (cudaStream_t)cuda_stream);
 }
 
 // ---------------------------------------------------------------- TEBD
@@ -894,6 +972,154 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
   }
   RSVD_TRY(launch_tebd_finish(fb, s));
   RSVD_TRY((launch_gemm<double, double, false, true>(g3, s)));
+  return RSVD_OK;
+}
+
+namespace {
+struct TebdProdLayout {
+  size_t xb, x, y, g1, g2, S, nrm, fro2, rsvd;
+};
+size_t tebd_prod_bytes(int m, int n, int k, int l, int r, TebdProdLayout* o) {
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t x = off;
+    off += align_up(b);
+    return x;
+  };
+  TebdProdLayout L;
+  L.xb = take((size_t)m * r * 8);
+  L.x = take((size_t)m * r * 8);
+  L.y = take((size_t)r * n * 8);
+  L.g1 = take((size_t)r * r * 8);
+  L.g2 = take((size_t)r * r * 8);
+  L.S = take((size_t)k * 8);
+  L.nrm = take(8);
+  L.fro2 = take(64 * 8);
+  L.rsvd = off;
+  off += layout(nullptr, m, n, k, l, 8, nullptr, 0, 0, r);
+  if (o) *o = L;
+  return off;
+}
+
+// per-bond workspace of the product update over all bonds of the chain (0: invalid sizes)
+size_t tebd_prod_per_bond(int L, int d, const int* D, int K, int pp) {
+  size_t mx = 0;
+  for (int i = 0; i + 1 < L; ++i) {
+    const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
+    if (k < 1 || k > std::min(m, n)) return 0;
+    const int l = sample_width(m, n, k, pp);
+    if (l > kMaxSample) return 0;
+    mx = std::max(mx, tebd_prod_bytes(m, n, k, l, K * k, nullptr));
+  }
+  return mx;
+}
+}  // namespace
+
+int tebd_product_workspace_size(int L, int d, const int* D, int nb, int K, const rsvd_params* p, size_t* bytes) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!D || !bytes) return RSVD_ERR_NULL_POINTER;
+  if (L < 2 || d < 1 || nb < 1 || K < 1) return RSVD_ERR_INVALID_SIZE;
+  const size_t per = tebd_prod_per_bond(L, d, D, K, p->p);
+  if (per == 0) return RSVD_ERR_INVALID_SIZE;
+  *bytes = per * (size_t)nb;
+  return RSVD_OK;
+}
+
+int tebd_product_update(int L, int d, const int* D, int nb, const int* bond, double* B, size_t tensor_stride,
+                        double* lam, size_t lam_stride, int K, const double* uL, const double* uR,
+                        const rsvd_params* p, double* trunc_err, void* work, size_t work_bytes, rsvd_info* info,
+                        void* cuda_stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->prec != RSVD_F64) return RSVD_ERR_PRECISION;
+  if (!D || !bond || !B || !lam || !uL || !uR || !trunc_err || !work || !info) return RSVD_ERR_NULL_POINTER;
+  if (L < 2 || d < 1 || nb < 1 || nb > kMaxJobs || K < 1) return RSVD_ERR_INVALID_SIZE;
+  if (D[0] != 1 || D[L] != 1) return RSVD_ERR_INVALID_SIZE;
+  if (((uintptr_t)work) % kAlign) return RSVD_ERR_WORKSPACE;
+  for (int b = 0; b < nb; ++b) {
+    const int i = bond[b];
+    if (i < 0 || i + 1 >= L) return RSVD_ERR_INVALID_SIZE;
+    for (int c = 0; c < b; ++c)
+      if (std::abs(bond[c] - i) < 2) return RSVD_ERR_INVALID_SIZE;
+    if ((size_t)D[i] * d * D[i + 1] > tensor_stride || (size_t)D[i + 1] * d * D[i + 2] > tensor_stride) return RSVD_ERR_INVALID_SIZE;
+    if ((size_t)D[i + 1] > lam_stride) return RSVD_ERR_INVALID_SIZE;
+  }
+  const size_t per = tebd_prod_per_bond(L, d, D, K, p->p);
+  if (per == 0) return RSVD_ERR_INVALID_SIZE;
+  if (per * (size_t)nb > work_bytes) return RSVD_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  char* base = (char*)work;
+  std::vector<TebdProdLayout> lay(nb);
+  std::vector<Prob> probs(nb);
+  TebdProdBatch tp;
+  tp.count = nb;
+  GemmBatch<double, double> g1, g2;
+  g1.count = g2.count = nb;
+  TebdGramDotBatch gd;
+  gd.count = nb;
+  for (int b = 0; b < nb; ++b) {
+    const int i = bond[b];
+    const int Dl = D[i], Dm = D[i + 1], Dr = D[i + 2];
+    const int m = Dl * d, n = d * Dr, k = Dm, r = K * Dm;
+    const int l = sample_width(m, n, k, p->p);
+    char* wb = base + per * b;
+    tebd_prod_bytes(m, n, k, l, r, &lay[b]);
+    double* XB = (double*)(wb + lay[b].xb);
+    double* X = (double*)(wb + lay[b].x);
+    double* Y = (double*)(wb + lay[b].y);
+    double* G1 = (double*)(wb + lay[b].g1);
+    double* G2 = (double*)(wb + lay[b].g2);
+    tp.job[b] = TebdProdJob{Dl, Dm, Dr, d, K, B + tensor_stride * i, B + tensor_stride * (i + 1),
+                            uL + (size_t)b * K * d * d, uR + (size_t)b * K * d * d, lam + lam_stride * i, XB, X, Y};
+    // ||theta||_F^2 = trace((X^T X)(Y Y^T)), theta = X Y never formed
+    g1.job[b] = GemmJob<double, double>{r, r, m, r, r, r, X, X, G1, nullptr, nullptr, 0};
+    g2.job[b] = GemmJob<double, double>{r, r, n, n, n, r, Y, Y, G2, nullptr, nullptr, 0};
+    gd.job[b] = TebdGramDotJob{r, G1, G2, (double*)(wb + lay[b].fro2)};
+    Prob& pr = probs[b];
+    std::memset(&pr, 0, sizeof(Prob));
+    pr.m = m; pr.n = n; pr.k = k; pr.l = l;
+    pr.exact = 0;
+    pr.want_u = 0;
+    pr.r = r; pr.Xf = X; pr.ldxf = r; pr.Yf = Y; pr.ldyf = n;
+    pr.S = (double*)(wb + lay[b].S);
+    pr.U = nullptr; pr.ldu = k;
+    pr.Vt = B + tensor_stride * (i + 1); pr.ldvt = n;  // V^T is the new B_{i+1}
+    pr.seed = p->seed; pr.stream = p->stream + (uint64_t)i;
+    pr.info = info + b;
+    pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    layout(&pr, m, n, k, l, 8, wb + lay[b].rsvd, 0, 0, r);
+  }
+  RSVD_TRY(launch_tebd_product(tp, s));
+  RSVD_TRY((launch_gemm<double, double, true, false>(g1, s)));
+  RSVD_TRY((launch_gemm<double, double, false, true>(g2, s)));
+  RSVD_TRY(launch_tebd_gram_dot(gd, s));
+  rc = run_chunk<double>(probs, p->q, s);
+  if (rc) return rc;
+  TebdFinBatch fb;
+  fb.count = nb;
+  GemmBatch<double, double> g3, g4;
+  g3.count = g4.count = nb;
+  for (int b = 0; b < nb; ++b) {
+    const int i = bond[b];
+    char* wb = base + per * b;
+    const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1], r = K * k;
+    double* nrm = (double*)(wb + lay[b].nrm);
+    fb.job[b] = TebdFinJob{k, (double*)(wb + lay[b].S), lam + lam_stride * (i + 1), nrm,
+                           (double*)(wb + lay[b].fro2), trunc_err + b};
+    // B_i <- theta_B V / ||S|| = XB (Y V) / ||S||, V^T now in B_{i+1}; W = Y V (r x k) reuses
+    // the factored products' r x l buffer
+    double* Wv = (double*)probs[b].Wf;
+    g3.job[b] = GemmJob<double, double>{r, k, n, n, n, k, (double*)(wb + lay[b].y), B + tensor_stride * (i + 1), Wv,
+                                        nullptr, nullptr, 0};
+    g3.job[b].n_eff = probs[b].flag + 2;
+    g4.job[b] = GemmJob<double, double>{m, k, r, r, k, k, (double*)(wb + lay[b].xb), Wv, B + tensor_stride * i, nrm,
+                                        nullptr, 0};
+    g4.job[b].n_eff = probs[b].flag + 2;
+  }
+  RSVD_TRY(launch_tebd_finish(fb, s));
+  RSVD_TRY((launch_gemm<double, double, false, true>(g3, s)));
+  RSVD_TRY((launch_gemm<double, double, false, false>(g4, s)));
   return RSVD_OK;
 }
 

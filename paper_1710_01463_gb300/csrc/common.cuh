@@ -176,6 +176,34 @@ struct TebdBatch {
   int count;
   TebdJob job[kMaxJobs];
 };
+// product update: XB[(a,s1),(k,b)] = sum_t uL[k][s1,t] Bi[a,t,b], X = lam[a] XB,
+// Y[(k,b),(s2,c)] = sum_t uR[k][s2,t] Bj[b,t,c]
+struct TebdProdJob {
+  int Dl, Dm, Dr, d, K;
+  const double* Bi;     // Dl x d x Dm
+  const double* Bj;     // Dm x d x Dr
+  const double* uL;     // K x d x d
+  const double* uR;     // K x d x d
+  const double* lam;    // Dl
+  double* XB;           // (Dl d) x (K Dm)
+  double* X;            // (Dl d) x (K Dm)
+  double* Y;            // (K Dm) x (d Dr)
+};
+struct TebdProdBatch {
+  int count;
+  TebdProdJob job[kMaxJobs];
+};
+// fro2 partial sums of sum_ij G1[i,j] G2[i,j] (= ||X Y||_F^2 for G1 = X^T X, G2 = Y Y^T)
+struct TebdGramDotJob {
+  int r;
+  const double* G1;
+  const double* G2;
+  double* fro2;
+};
+struct TebdGramDotBatch {
+  int count;
+  TebdGramDotJob job[kMaxJobs];
+};
 struct TebdFinJob {
   int k;
   const double* S;
@@ -349,6 +377,8 @@ struct TebdRankBatch {
 };
 cudaError_t launch_tebd_rank(const TebdRankBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s);
+cudaError_t launch_tebd_product(const TebdProdBatch& b, cudaStream_t s);
+cudaError_t launch_tebd_gram_dot(const TebdGramDotBatch& b, cudaStream_t s);
 template <typename TIn>
 cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s, int skip_loads = 0);
 template <typename T>

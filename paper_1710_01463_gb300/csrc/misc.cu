@@ -152,7 +152,88 @@ __global__ void __launch_bounds__(256) tebd_finish_kernel(const __grid_constant_
   for (int r = threadIdx.x; r < J.k; r += blockDim.x) J.lam[r] = nrm > 0.0 ? J.S[r] / nrm : 0.0;
 }
 
+// product update (Sec. III.A "product update (P)"): the K single-site operators
+// of each side widen the bond to K Dm; consecutive threads take consecutive
+// columns, so the reads of B_i (over b) and B_{i+1} (over c) are coalesced
+__global__ void __launch_bounds__(256) tebd_product_kernel(const __grid_constant__ TebdProdBatch b) {
+  const TebdProdJob& J = b.job[blockIdx.y];
+  const int d = J.d, Dm = J.Dm, Dr = J.Dr;
+  const int r = J.K * Dm, n = d * Dr;
+  const long long nx = (long long)J.Dl * d * r, ny = (long long)r * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nx + ny; e += (long long)gridDim.x * blockDim.x) {
+    if (e < nx) {
+      const int row = (int)(e / r), col = (int)(e % r);
+      const int a = row / d, s1 = row % d, k = col / Dm, c = col % Dm;
+      const double* u = J.uL + ((size_t)k * d + s1) * d;
+      const double* bi = J.Bi + (size_t)a * d * Dm + c;
+      double v = 0.0;
+      for (int t = 0; t < d; ++t) v = fma(u[t], bi[(size_t)t * Dm], v);
+      J.XB[e] = v;
+      J.X[e] = J.lam[a] * v;
+    } else {
+      const long long f = e - nx;
+      const int row = (int)(f / n), col = (int)(f % n);
+      const int k = row / Dm, bb = row % Dm, s2 = col / Dr, c = col % Dr;
+      const double* u = J.uR + ((size_t)k * d + s2) * d;
+      const double* bj = J.Bj + (size_t)bb * d * Dr + c;
+      double v = 0.0;
+      for (int t = 0; t < d; ++t) v = fma(u[t], bj[(size_t)t * Dr], v);
+      J.Y[f] = v;
+    }
+  }
+}
+
+// ||X Y||_F^2 = trace((X^T X)(Y Y^T)) = sum_ij G1[i,j] G2[i,j] (G2 symmetric), as
+// kTebdBlocks partial sums in the layout tebd_finish_kernel reads
+__global__ void __launch_bounds__(256) tebd_gram_dot_kernel(const __grid_constant__ TebdGramDotBatch b) {
+  const TebdGramDotJob& J = b.job[blockIdx.y];
+  const long long tot = (long long)J.r * J.r;
+  double acc0 = 0.0, acc1 = 0.0;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long st = (long long)gridDim.x * blockDim.x;
+  for (; e + st < tot; e += 2 * st) {
+    acc0 = fma(J.G1[e], J.G2[e], acc0);
+    acc1 = fma(J.G1[e + st], J.G2[e + st], acc1);
+  }
+  if (e < tot) acc0 = fma(J.G1[e], J.G2[e], acc0);
+  double acc = acc0 + acc1;
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    J.fro2[blockIdx.x] = s;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_tebd_product(const TebdProdBatch& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  long long mx = 1;
+  for (int i = 0; i < b.count; ++i) {
+    const TebdProdJob& J = b.job[i];
+    const long long r = (long long)J.K * J.Dm;
+    mx = max(mx, (long long)J.Dl * J.d * r + r * J.d * J.Dr);
+  }
+  const long long want = (mx + 255) / 256, cap = 2048LL / b.count + 1;  // about 2048 blocks in all
+  const int gx = (int)(want < cap ? want : cap);
+  prof_begin(KC_TEBD, s);
+  tebd_product_kernel<<<dim3(gx, b.count), 256, 0, s>>>(b);
+  prof_end(KC_TEBD, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tebd_gram_dot(const TebdGramDotBatch& b, cudaStream_t s) {
+  if (b.count <= 0) return cudaSuccess;
+  prof_begin(KC_TEBD, s);
+  tebd_gram_dot_kernel<<<dim3(kTebdBlocks, b.count), 256, 0, s>>>(b);
+  prof_end(KC_TEBD, s);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_sign(const SignBatch<T>& b, cudaStream_t s) {

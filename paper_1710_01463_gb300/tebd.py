@@ -66,6 +66,38 @@ def ring_bond_hamiltonian(i, L, h, W):
     return inter + fl * np.kron(onsite, one) + fr * np.kron(one, onsite)
 
 
+def ring_product_gates(i, L, h, W, tau):
+    """Bond (i, i+1) of the W-wide cylinder as W gates of K = 2 Kronecker terms (the
+    product update, Sec. III.A P): exp(-tau A/2) prod_j exp(-tau C_j) exp(-tau A/2), where
+    C_j = -Z_{i,j} Z_{i+1,j} are the bond's commuting couplings, exp(-tau C_j) =
+    cosh(tau) 1 (x) 1 + sinh(tau) Z_j (x) Z_j, and A is the bond's share of the two rings'
+    own terms (exp(-tau A/2) = gL (x) gR, folded into the first and last coupling).
+    Returns W arrays (2, 2, d, d): [uL, uR] of K = 2 operators each, in the order applied."""
+    def on(op, j):
+        out = np.ones((1, 1))
+        for t in range(W):
+            out = np.kron(out, op if t == j else _I)
+        return out
+    Z = [on(_Z, j) for j in range(W)]
+    X = [on(_X, j) for j in range(W)]
+    onsite = -sum(Z[j] @ Z[(j + 1) % W] for j in range(W)) - h * sum(X)
+    fl = 1.0 if i == 0 else 0.5
+    fr = 1.0 if i + 1 == L - 1 else 0.5
+    gL = bond_gate(fl * onsite, tau / 2)
+    gR = bond_gate(fr * onsite, tau / 2)
+    one = np.eye(2 ** W)
+    out = []
+    for j in range(W):
+        uL = [np.cosh(tau) * one, np.sinh(tau) * Z[j]]
+        uR = [one, Z[j]]
+        if j == 0:
+            uL, uR = [u @ gL for u in uL], [u @ gR for u in uR]
+        if j == W - 1:
+            uL, uR = [gL @ u for u in uL], [gR @ u for u in uR]
+        out.append(np.array([uL, uR]))
+    return out
+
+
 def bond_gate(hb, tau):
     """exp(-tau h_b) through the eigenbasis of the symmetric h_b."""
     w, V = np.linalg.eigh(hb)
@@ -75,11 +107,17 @@ def bond_gate(hb, tau):
 class TebdChain:
     """MPS of an L-site chain with right-canonical tensors B[i] and Schmidt values lam[j]."""
 
-    def __init__(self, L, chi, h=1.0, p=10, q=2, seed=0, device="cuda", max_sweeps=0, simt=False, S=0.5, W=None):
+    def __init__(self, L, chi, h=1.0, p=10, q=2, seed=0, device="cuda", max_sweeps=0, simt=False, S=0.5, W=None,
+                 update="block"):
         """S: spin of the chain (d = 2S + 1); W: circumference of the 2D cylinder (d = 2^W;
-        overrides S)."""
+        overrides S).  update: "block" (one d^2 x d^2 gate per bond, tebd_bond_update) or,
+        for the cylinder, "product" (each bond as W gates of K = 2 Kronecker terms,
+        tebd_product_update: W compressions of a rank <= 2 chi product per bond)."""
         if L < 2:
             raise ValueError("L >= 2 required")
+        if update not in ("block", "product") or (update == "product" and not W):
+            raise ValueError("update is 'block', or 'product' for the cylinder")
+        self.update = update
         self.S, self.W = S, W
         d = 2 ** W if W else int(round(2 * S)) + 1
         self.L, self.d, self.chi, self.h = L, d, chi, h
@@ -97,11 +135,16 @@ class TebdChain:
         lib = _lib.load()
         par = _params(1, p, q, _lib.RSVD_F64, seed, 0, 0, simt)
         sz = ctypes.c_size_t(0)
-        _lib.check(lib.tebd_workspace_size(L, d, self.D_arr, nb, ctypes.byref(par), ctypes.byref(sz)),
-                   "tebd_workspace_size")
+        if update == "product":
+            _lib.check(lib.tebd_product_workspace_size(L, d, self.D_arr, nb, 2, ctypes.byref(par), ctypes.byref(sz)),
+                       "tebd_product_workspace_size")
+        else:
+            _lib.check(lib.tebd_workspace_size(L, d, self.D_arr, nb, ctypes.byref(par), ctypes.byref(sz)),
+                       "tebd_workspace_size")
         self.work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=self.device)
-        self.trunc_err = torch.zeros((3, nb), dtype=torch.float64, device=self.device)
-        self.info = torch.zeros((3, nb, _lib.INFO_INTS), dtype=torch.int32, device=self.device)
+        nsub = W if update == "product" else 1  # compressions per bond and layer
+        self.trunc_err = torch.zeros((3, nsub, nb), dtype=torch.float64, device=self.device)
+        self.info = torch.zeros((3, nsub, nb, _lib.INFO_INTS), dtype=torch.int32, device=self.device)
         self.bond_arr = [_lib.int_array(b) for b in self.layers]
         self.dt = None
 
@@ -109,6 +152,18 @@ class TebdChain:
         """Form the gates of the three layers of one Trotter step."""
         self.dt = float(dt)
         gates = []
+        if self.update == "product":
+            # gates[t][j]: (nb, 2, 2, d, d) -> uL = [:, 0], uR = [:, 1], each (nb, K, d, d)
+            for layer, tau in ((0, dt / 2), (1, dt), (0, dt / 2)):
+                per = [ring_product_gates(i, self.L, self.h, self.W, tau) for i in self.layers[layer]]
+                gl = []
+                for j in range(self.W):
+                    g = np.stack([pb[j] for pb in per]) if per else np.zeros((0, 2, 2, self.d, self.d))
+                    gl.append((torch.tensor(np.ascontiguousarray(g[:, 0]), dtype=torch.float64, device=self.device),
+                               torch.tensor(np.ascontiguousarray(g[:, 1]), dtype=torch.float64, device=self.device)))
+                gates.append(gl)
+            self.gates = gates
+            return
         for layer, tau in ((0, dt / 2), (1, dt), (0, dt / 2)):
             g = [bond_gate(self.bond_term(i), tau).ravel() for i in self.layers[layer]]
             gates.append(torch.tensor(np.stack(g), dtype=torch.float64, device=self.device))
@@ -139,6 +194,9 @@ class TebdChain:
         """One second-order Trotter step (three layers), asynchronous."""
         lib = _lib.load()
         sh = _stream_handle(stream)
+        if self.update == "product":
+            self._step_product(step_index, lib, sh)
+            return
         for j, layer in enumerate((0, 1, 0)):
             bonds = self.layers[layer]
             if not bonds:
@@ -149,10 +207,31 @@ class TebdChain:
                                       ctypes.c_void_p(self.B.data_ptr()), self.tensor_stride,
                                       ctypes.c_void_p(self.lam.data_ptr()), self.lam_stride,
                                       ctypes.c_void_p(self.gates[j].data_ptr()), ctypes.byref(par),
-                                      ctypes.c_void_p(self.trunc_err[j].data_ptr()),
-                                      ctypes.c_void_p(self.work.data_ptr()), self.work.numel(),
-                                      ctypes.c_void_p(self.info[j].data_ptr()), sh)
+                                      ctypes.c_void_p(self.trunc_err[j, 0].data_ptr()),
+                                      ctypes.c_void_p(self.work.data_ptr()), ctypes.c_size_t(self.work.numel()),
+                                      ctypes.c_void_p(self.info[j, 0].data_ptr()), sh)
             _lib.check(rc, "tebd_bond_update")
+
+    def _step_product(self, step_index, lib, sh):
+        """Product-update Trotter step: per layer, the W coupling gates one after another,
+        each ONE call of tebd_product_update over the layer's bonds.  Philox stream of gate j
+        of bond i in layer t: ((3 step + t) W + j) L + i."""
+        for t, layer in enumerate((0, 1, 0)):
+            bonds = self.layers[layer]
+            if not bonds:
+                continue
+            for j in range(self.W):
+                uL, uR = self.gates[t][j]
+                par = _params(1, self.p, self.q, _lib.RSVD_F64, self.seed, ((3 * step_index + t) * self.W + j) * self.L,
+                              self.max_sweeps, self.simt)
+                rc = lib.tebd_product_update(self.L, self.d, self.D_arr, len(bonds), self.bond_arr[layer],
+                                             ctypes.c_void_p(self.B.data_ptr()), ctypes.c_size_t(self.tensor_stride),
+                                             ctypes.c_void_p(self.lam.data_ptr()), ctypes.c_size_t(self.lam_stride), 2,
+                                             ctypes.c_void_p(uL.data_ptr()), ctypes.c_void_p(uR.data_ptr()),
+                                             ctypes.byref(par), ctypes.c_void_p(self.trunc_err[t, j].data_ptr()),
+                                             ctypes.c_void_p(self.work.data_ptr()), ctypes.c_size_t(self.work.numel()),
+                                             ctypes.c_void_p(self.info[t, j].data_ptr()), sh)
+                _lib.check(rc, "tebd_product_update")
 
     def tensors(self):
         """Host copies of the B tensors, shaped (D[i], d, D[i+1])."""

@@ -147,3 +147,51 @@ def test_spin1_chain_reaches_ed_ground_energy(mods):
     e = otebd.mps_energy(ch.tensors(), L, h, otebd.chain_bond_terms(L, h, S))
     e0 = float(np.linalg.eigvalsh(otebd.dense_chain_hamiltonian(L, h, S))[0])
     assert abs(e - e0) <= 1e-7 * abs(e0)
+
+
+@pytest.mark.parametrize("W,L,chi,steps", [(2, 6, 16, 4), (1, 8, 8, 4), (3, 4, 24, 2)])
+def test_product_update_matches_oracle(mods, W, L, chi, steps):
+    # the cylinder with product updates (Sec. III.A P): each bond as W gates of K = 2
+    # Kronecker terms, one factored compression per gate
+    h, dt, p, q, seed = 3.0, 0.05, 6, 2, 9
+    d = 2 ** W
+    ch = mods.TebdChain(L, chi, h=h, p=p, q=q, seed=seed, W=W, update="product")
+    vec = inputs.product_state_vectors(L, d, 78)
+    ch.set_product_state(vec)
+    ch.set_dt(dt)
+    B, lam = otebd.product_state(vec, otebd.bond_dims(L, d, chi))
+    comp = otebd.make_compressor("rsvd", p=p, q=q, seed=seed)
+    for s in range(steps):
+        ch.step(s)
+        otebd.trotter_step_product(B, lam, L, h, W, dt, comp, s)
+    torch.cuda.synchronize()
+    assert int((ch.info[..., 0] != 0).sum()) == 0
+    lam_g = ch.schmidt_values()
+    for j in range(1, L):
+        np.testing.assert_allclose(lam_g[j], lam[j], atol=1e-10 * np.max(lam[j]) + 1e-14)
+    terms = otebd.cylinder_bond_terms(L, h, W)
+    assert otebd.mps_energy(ch.tensors(), L, h, terms) == pytest.approx(otebd.mps_energy(B, L, h, terms), rel=1e-10)
+    te = ch.trunc_err.cpu().numpy()
+    assert np.all(te >= 0) and np.all(te < 1e-2)
+
+
+def test_product_and_block_updates_reach_the_same_ground_state(mods):
+    # the two Trotter forms differ by O(dt^2) in the state; both approach the ED ground
+    # energy of a small cylinder
+    L, W, h = 4, 2, 3.0
+    e0 = float(np.linalg.eigvalsh(otebd.dense_cylinder_hamiltonian(L, h, W))[0])
+    terms = otebd.cylinder_bond_terms(L, h, W)
+    out = {}
+    for update in ("block", "product"):
+        ch = mods.TebdChain(L, 16, h=h, p=10, q=2, seed=2, W=W, update=update)
+        ch.set_product_state(np.ones((L, 4)) + 0.1 * np.arange(L * 4).reshape(L, 4))
+        step = 0
+        for dt, n in ((0.2, 40), (0.02, 200)):
+            ch.set_dt(dt)
+            for _ in range(n):
+                ch.step(step)
+                step += 1
+        torch.cuda.synchronize()
+        out[update] = otebd.mps_energy(ch.tensors(), L, h, terms)
+    for e in out.values():
+        assert 0 <= e - e0 < 1e-6 * abs(e0)
