@@ -27,6 +27,7 @@ METRIC = "RSVD truncations/s & TFLOP/s vs full-SVD-truncate, 1 GB300, at stated 
 UNIT = "truncations/s"
 L_SITES, CHI, D_LOC, H_FIELD, DT, P_OVER, Q_POW, SEED = 64, 128, 2, 1.0, 0.01, 10, 2, 5
 SPIN, WIDTH = 0.5, 0  # model: spin-S chain (d = 2S + 1), or the 2D cylinder of circumference WIDTH (d = 2^WIDTH)
+UPDATE, K_TERMS = "block", 2  # TEBD update form; "product": each cylinder bond as WIDTH gates of K_TERMS = 2 terms
 PREP_STEPS, PREP_DT = 20, 0.1
 WORKLOAD = "tebd_tfim_L64_chi128_d2_dt0.01_p10_q2_fp64"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
@@ -50,7 +51,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 
 
 def base_config():
     return {"workload": WORKLOAD, "model": model_name(), "L": L_SITES, "chi": CHI, "d": D_LOC, "h": H_FIELD, "dt": DT,
-            "p": P_OVER, "q": Q_POW, "bond_matrix": f"{CHI * D_LOC}x{CHI * D_LOC}",
+            "p": P_OVER, "q": Q_POW, "update": UPDATE,
+            "bond_matrix": (f"{CHI * D_LOC}x{CHI * D_LOC}" if UPDATE == "block" else
+                            f"X Y, X {CHI * D_LOC}x{K_TERMS * CHI}, Y {K_TERMS * CHI}x{CHI * D_LOC} (never formed)"),
             "fp64_products_with_A": "tcgen05 tensor cores, exact 9-slice BF16 split, FP64-class error",
             "truncations_per_step": truncations_per_step(), "l2": "flushed (512 MB write) before every timed step"}
 
@@ -67,9 +70,10 @@ def bond_term_oracle(otebd, i):
 
 
 def truncations_per_step():
+    """Bond compressions per Trotter step (product updates: one per coupling gate)."""
     a = len(range(0, L_SITES - 1, 2))
     b = len(range(1, L_SITES - 1, 2))
-    return 2 * a + b
+    return (2 * a + b) * (WIDTH if UPDATE == "product" else 1)
 
 
 def job_ms(local_ms):
@@ -181,6 +185,8 @@ def step_flops(info):
     costs 6n (the TEBD update does not accumulate the rotations of U).
     """
     flops = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "ozgemm": 0.0}
+    if UPDATE == "product":
+        return product_step_flops(info, flops)
     for j, lay in enumerate(bond_shapes()):
         for b, (m, n, k, l) in enumerate(lay):
             rec = info[j][0][b]  # (layer, compression, bond) records
@@ -192,8 +198,8 @@ def step_flops(info):
             r = min(l, qr_cols) if qr_cols > 0 else l
             flops["gemm"] += 2.0 * m * n * min(k, r) + 2.0 * m * n * min(k, r)
             if not (m <= l and m <= 16):
-                # products with A: on the tensor cores by exact slicing when m, n, l <= 256
-                oz = m <= 256 and n <= 256 and l <= 256
+                # products with A: on the tensor cores by exact slicing when m, n <= 1024 and l <= 256
+                oz = m <= 1024 and n <= 1024 and l <= 256
                 flops["ozgemm" if oz else "gemm"] += 2.0 * m * n * l + (2 * Q_POW + 1) * 2.0 * m * n * r
                 for it in range(2 * Q_POW + 1):
                     rows = m if it % 2 == 0 else n
@@ -206,6 +212,36 @@ def step_flops(info):
                         flops["gemm"] += 2 * rows * l * l
             flops["jacobi"] += (sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * 6.0 * n
                                 + (sweeps + 1) * 2.0 * n * l)
+    return flops
+
+
+def product_step_flops(info, flops):
+    """step_flops of the product update: per compression of theta = X Y (X m x r, Y r x n,
+    r = K k, never formed) every product with A is two GEMMs through r columns: the sketch
+    2 (n + m) r l, then (2q + 1) more of 2 (m + n) r r_eff (r_eff = the effective rank, as in
+    step_flops) and B = (X^T Q)^T Y; the Grams X^T X, Y Y^T (2 m r^2 + 2 n r^2) for
+    ||theta||_F; W = Y V (2 r n k) and B_i = X_B W (2 m r k); orthonormalisations and
+    Jacobi as in step_flops."""
+    for j, lay in enumerate(bond_shapes()):
+        for w in range(WIDTH):
+            for b, (m, n, k, l) in enumerate(lay):
+                rec = info[j][w][b]
+                sweeps, rots, qr_cols = int(rec[3]), int(rec[5]), int(rec[6])
+                rr = min(l, qr_cols) if qr_cols > 0 else l
+                r = K_TERMS * k
+                flops["gemm"] += 2.0 * (m + n) * r * l + (2 * Q_POW + 1) * 2.0 * (m + n) * r * rr
+                flops["gemm"] += 2.0 * m * r * r + 2.0 * n * r * r + 2.0 * r * n * min(k, rr) + 2.0 * m * r * min(k, rr)
+                for it in range(2 * Q_POW + 1):
+                    rows = m if it % 2 == 0 else n
+                    lw = l if it == 0 else rr
+                    if 3 * l > rows:
+                        flops["householder"] += hh_flops(rows, lw, rr)
+                    else:
+                        flops["gram"] += 2 * rows * l * l
+                        flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
+                        flops["gemm"] += 2 * rows * l * l
+                flops["jacobi"] += (sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * 6.0 * n
+                                    + (sweeps + 1) * 2.0 * n * l)
     return flops
 
 
@@ -225,7 +261,8 @@ def run_ours(args):
     from paper_1710_01463_gb300.tebd import TebdChain
 
     lib = _lib.load()
-    ch = TebdChain(L_SITES, CHI, h=H_FIELD, p=P_OVER, q=Q_POW, seed=SEED + 1000 * rank, S=SPIN, W=WIDTH or None)
+    ch = TebdChain(L_SITES, CHI, h=H_FIELD, p=P_OVER, q=Q_POW, seed=SEED + 1000 * rank, S=SPIN, W=WIDTH or None,
+                   update=UPDATE)
     ch.set_product_state(inputs.product_state_vectors(L_SITES, D_LOC, 102 + rank))
     ch.set_dt(PREP_DT)
     for s in range(PREP_STEPS):
@@ -383,9 +420,13 @@ def error_leg(ch):
 
 
 def comparator_leg():
-    """Full SVD + truncate with torch.linalg.svd (cuSOLVER) FP64 on 32 bond-sized matrices."""
+    """Full SVD + truncate with torch.linalg.svd (cuSOLVER) FP64 on 32 bond-sized matrices
+    (product update: the paper's TSVD of the P form, QR of X then the SVD of the
+    (K chi) x (chi d) matrix R Y)."""
     import torch
     from paper_1710_01463_gb300 import inputs
+    if UPDATE == "product":
+        return product_comparator_leg()
     A = torch.stack([torch.from_numpy(inputs.dense_case(CHI * D_LOC, CHI * D_LOC, seed=300 + j)) for j in range(32)]).cuda()
     torch.linalg.svd(A[:2], full_matrices=False)
     torch.cuda.synchronize()
@@ -397,6 +438,28 @@ def comparator_leg():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     return {"kind": f"torch.linalg.svd (cuSOLVER) FP64 + slice to chi, batch of 32 {CHI * D_LOC}x{CHI * D_LOC} matrices",
+            "truncations_per_s": round(32 / (ms / 1e3), 3), "ms_per_truncation": round(ms / 32, 4)}
+
+
+def product_comparator_leg():
+    import torch
+    from paper_1710_01463_gb300 import inputs
+    m = n = CHI * D_LOC
+    r = K_TERMS * CHI
+    X = torch.stack([torch.from_numpy(inputs.random_dense(m, r, 400 + j)) for j in range(32)]).cuda()
+    Y = torch.stack([torch.from_numpy(inputs.random_dense(r, n, 500 + j)) for j in range(32)]).cuda()
+    torch.linalg.svd(torch.linalg.qr(X[:2])[1] @ Y[:2], full_matrices=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    Qx, R = torch.linalg.qr(X)
+    U, S, Vh = torch.linalg.svd(R @ Y, full_matrices=False)
+    Uk, Sk, Vk = (Qx @ U[..., :CHI]).contiguous(), S[..., :CHI].contiguous(), Vh[..., :CHI, :].contiguous()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"kind": f"torch.linalg.qr of X ({m}x{r}) + torch.linalg.svd (cuSOLVER) of R Y ({r}x{n}) FP64 + slice "
+                    f"to chi, batch of 32",
             "truncations_per_s": round(32 / (ms / 1e3), 3), "ms_per_truncation": round(ms / 32, 4)}
 
 
@@ -414,14 +477,20 @@ def cpu_leg(ch):
     n = 0
     while True:
         for i in bonds:
-            G = otebd.gate(bond_term_oracle(otebd, i), DT / 2)
-            otebd.bond_update(B, lam, i, G, comp, 7 * L_SITES + i)
-            n += 1
+            if UPDATE == "product":
+                for j, (uL, uR) in enumerate(otebd.cylinder_product_gates(i, L_SITES, H_FIELD, WIDTH, DT / 2)):
+                    otebd.product_update(B, lam, i, uL, uR, comp, (7 * WIDTH + j) * L_SITES + i)
+                    n += 1
+            else:
+                G = otebd.gate(bond_term_oracle(otebd, i), DT / 2)
+                otebd.bond_update(B, lam, i, G, comp, 7 * L_SITES + i)
+                n += 1
         if time.time() - t0 > 10.0:
             break
     el = time.time() - t0
     return {"value": round(n / el, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} central {CHI * D_LOC}x{CHI * D_LOC} bond updates (RSVD k={CHI}, p={P_OVER}, q={Q_POW}) "
+            "sample": f"{n} central {CHI * D_LOC}x{CHI * D_LOC} bond compressions ({UPDATE} update; RSVD k={CHI}, "
+                      f"p={P_OVER}, q={Q_POW}) "
                       f"of the L={L_SITES} {model_name()} chain, numpy FP64, "
                       f"BLAS threads = all host cores, Philox in pure Python"}
 
@@ -457,7 +526,7 @@ def rsvd_flops(m, n, k, l, q, sweeps, rots, prec, qr_cols=0, want_u=True):
     of B runs on the l x l factor of an orthonormalisation of B^T."""
     f = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "tcgemm": 0.0, "ozgemm": 0.0}
     exact = m <= l and m <= 16
-    oz = prec == "f64" and m <= 256 and n <= 256 and l <= 256  # FP64 products with A on the tensor cores
+    oz = prec == "f64" and m <= 1024 and n <= 1024 and l <= 256  # FP64 products with A on the tensor cores
 
     def orth(rows):
         if 3 * l > rows:
@@ -791,10 +860,16 @@ def run_reference(args):
     # a step of the reference arm: 4 central bond updates (a bounded sample of one Trotter step)
     bonds = [i for i in range(0, L_SITES - 1, 2)][14:18]
 
+    per = WIDTH if UPDATE == "product" else 1  # compressions per bond update
+
     def one(step):
         for i in bonds:
-            G = otebd.gate(bond_term_oracle(otebd, i), DT / 2)
-            otebd.bond_update(B, lam, i, G, comp, (3 * step) * L_SITES + i)
+            if UPDATE == "product":
+                for j, (uL, uR) in enumerate(otebd.cylinder_product_gates(i, L_SITES, H_FIELD, WIDTH, DT / 2)):
+                    otebd.product_update(B, lam, i, uL, uR, comp, (3 * step * WIDTH + j) * L_SITES + i)
+            else:
+                G = otebd.gate(bond_term_oracle(otebd, i), DT / 2)
+                otebd.bond_update(B, lam, i, G, comp, (3 * step) * L_SITES + i)
 
     for s in range(args.warmup):
         one(s)
@@ -802,9 +877,9 @@ def run_reference(args):
     for s in range(args.steps):
         one(args.warmup + s)
     el = time.time() - t0
-    value = len(bonds) * args.steps / el
-    sample = (f"{len(bonds)} central 256x256 bond updates per step (RSVD k=128, p=10, q=2), numpy FP64 oracle, "
-              f"bond matrices from a product state")
+    value = len(bonds) * per * args.steps / el
+    sample = (f"{len(bonds) * per} central {CHI * D_LOC}x{CHI * D_LOC} bond compressions per step ({UPDATE} update; "
+              f"RSVD k={CHI}, p={P_OVER}, q={Q_POW}), numpy FP64 oracle, bond matrices from a product state")
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -832,16 +907,23 @@ def main():
     ap.add_argument("--spin", type=float, default=0.5, help="TEBD: spin S of the chain (d = 2S + 1; Sec. III.B)")
     ap.add_argument("--cylinder-width", type=int, default=0,
                     help="TEBD: circumference W of the 2D cylinder mapped onto a chain of rings (d = 2^W)")
+    ap.add_argument("--update", default="block", choices=["block", "product"],
+                    help="TEBD: block update (one d^2 x d^2 gate per bond) or, for the cylinder, product update "
+                         "(each bond as W gates of K = 2 Kronecker terms; Sec. III.A)")
     ap.add_argument("--field", type=float, default=None,
                     help="TEBD: field h (default 1 for S = 1/2, 1.5 for S > 1/2, 3.044 for the cylinder)")
     args = ap.parse_args()
-    global L_SITES, WORKLOAD, SPIN, WIDTH, D_LOC, H_FIELD
+    global L_SITES, WORKLOAD, SPIN, WIDTH, D_LOC, H_FIELD, UPDATE
     if args.chain_length != L_SITES:
         L_SITES = args.chain_length
     SPIN, WIDTH = args.spin, args.cylinder_width
+    if args.update == "product" and not WIDTH:
+        ap.error("--update product needs --cylinder-width")
+    UPDATE = args.update
     D_LOC = 2 ** WIDTH if WIDTH else int(round(2 * SPIN)) + 1
     H_FIELD = args.field if args.field is not None else (3.044 if WIDTH else (1.0 if SPIN == 0.5 else 1.5))
-    WORKLOAD = (f"tebd_{model_name()}_L{L_SITES}_chi{CHI}_d{D_LOC}_dt{DT:g}_p{P_OVER}_q{Q_POW}_fp64"
+    WORKLOAD = (f"tebd_{model_name()}{'_product' if UPDATE == 'product' else ''}_L{L_SITES}_chi{CHI}_d{D_LOC}"
+                f"_dt{DT:g}_p{P_OVER}_q{Q_POW}_fp64"
                 + (f"_h{H_FIELD:g}" if args.field is not None else ""))
     if args.warmup < 3:
         args.warmup = 3

@@ -261,12 +261,14 @@ int rsvd_truncate_factored(int m, int r, int n, const void* X, int ldx, const vo
 /*
  * rsvd_gemm_f64_tc - the FP64 tensor-core product of the FP64 path (exposed so
  * that it can be verified on its own): C = A B^T with A (M x K, lda), B (N x K,
- * ldb) and C (M x N, ldc) row-major FP64 device matrices, N <= 256, K <= 256.
+ * ldb) and C (M x N, ldc) row-major FP64 device matrices, N <= 256, K <= 1024.
  * Every row of A and of B is split exactly into nine BF16 slices of 6-bit
  * integers relative to the row's power-of-two exponent (only bits below
  * 2^-54 of the row's largest magnitude are dropped); the slice products are
- * summed exactly by tcgen05.mma in FP32 tensor memory, level by level, and
- * the levels in FP64.  Error: at most about 2.3 K 2^-53 max|A_r| max|B_c| per
+ * summed exactly by tcgen05.mma in FP32 tensor memory, level by level over
+ * chunks of at most 256 values of K, and the levels of all chunks in FP64.
+ * The FP64 path of rsvd_truncate / tebd_bond_update takes this product for
+ * the products with A when m, n <= 1024 and l <= 256.  Error: at most about 2.3 K 2^-53 max|A_r| max|B_c| per
  * entry (the normwise class of an FP64 GEMM).  A row holding Inf or NaN gives
  * NaN.
  * work: device workspace of rsvd_gemm_f64_tc_workspace_size(M, N, K) bytes

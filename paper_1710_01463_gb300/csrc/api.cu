@@ -149,10 +149,12 @@ inline int sample_width(int m, int n, int k, int p) { return std::min(k + p, std
 constexpr int kExactMaxRows = 16;
 inline int use_exact_path(int m, int l) { return (m <= l && m <= kExactMaxRows) ? 1 : 0; }
 
-// FP64 products with A on the tensor cores: exact level sums need K <= 256
-// (K = n for A Z, m for A^T Y) and the thin operand fits one CTA row (l <= 256)
+// FP64 products with A on the tensor cores: K <= 1024 (K = n for A Z, m for
+// A^T Y; exact level sums per chunk of 256) and the thin operand fits one CTA
+// row (l <= 256)
 inline int use_oz(int m, int n, int l, int exact, const rsvd_params* p) {
-  return (p->prec == RSVD_F64 && !(p->flags & RSVD_FLAG_F64_SIMT) && !exact && m <= kOzMaxK && n <= kOzMaxK && l <= 256)
+  return (p->prec == RSVD_F64 && !(p->flags & RSVD_FLAG_F64_SIMT) && !exact && m <= kOzMaxKTotal &&
+          n <= kOzMaxKTotal && l <= 256)
              ? 1
              : 0;
 }

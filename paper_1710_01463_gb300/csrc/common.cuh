@@ -302,10 +302,11 @@ bool make_tmap(CUtensorMap* map, const void* base, int rows, int cols, int ld, i
 // value x of a row r is 2^e_r * sum_{i=1..9} p_i 2^-6i + (truncation below
 // 2^(e_r - 54)) with integer p_i in [-63, 63] held exactly in BF16; the slice
 // products of one level L = i + j <= 11 are summed exactly in an FP32
-// accumulator (|sum| <= 9 * 256 * 63^2 < 2^24 for K <= 256) and the levels in
-// FP64.
+// accumulator over a K chunk of at most 256 (|sum| <= 9 * 256 * 63^2 < 2^24)
+// and the levels of all chunks in FP64.
 constexpr int kOzSlices = 9;
-constexpr int kOzMaxK = 256;
+constexpr int kOzMaxK = 256;       // K per exactly accumulated chunk
+constexpr int kOzMaxKTotal = 1024; // K of one product (chunks of kOzMaxK)
 constexpr int kMaxOzJobs = 32;
 struct OzJob {
   CUtensorMap tp;    // slices of P: kOzSlices blocks of M rows, row length Kp, box 128 rows x 64

@@ -1,6 +1,6 @@
 // FP64 products C = P S on the tcgen05 tensor cores, for the products with A
 // of Alg. RSVD (Sec. II.B) - the sketch A Omega, the power-iteration products
-// A^T Q and A Z, and the projection (as B^T = A^T Q) - when K <= 256.
+// A^T Q and A Z, and the projection (as B^T = A^T Q) - when K <= 1024.
 //
 // Exact slicing (an error-free splitting of each FP64 row into small
 // integers, in the spirit of Ozaki's scheme): a row r of P with largest
@@ -13,9 +13,10 @@
 //
 //   C[r][c] = 2^(e_r + f_c) sum_L 2^-6L T_L[r][c],   T_L = sum_{i+j=L} P_i S_j^T
 //
-// Every product p_i q_j is an integer below 2^12 and |T_L| <= 9 * 256 * 63^2
-// < 2^24, so the tcgen05 BF16 MMA accumulates each level exactly in FP32 in
-// tensor memory (K <= 256).  Levels L = 2 .. 11 are kept (53 slice products).
+// Every product p_i q_j is an integer below 2^12; over a chunk of at most 256
+// values of K, |T_L| <= 9 * 256 * 63^2 < 2^24, so the tcgen05 BF16 MMA
+// accumulates each level of a chunk exactly in FP32 in tensor memory, and the
+// chunks are added in FP64.  Levels L = 2 .. 11 are kept (53 slice products).
 // Error per entry, with 2^e_r <= 2 max|P_r| and 2^f_c <= 2 max|S_c|: the bits
 // cut off by the slicing add at most 2 K 2^-53 max|P_r| max|S_c|, the dropped
 // levels L >= 12 at most 0.25 K 2^-53 max|P_r| max|S_c| - the normwise class
@@ -28,9 +29,13 @@
 // to the TMEM accumulator of its level (ten levels x ntile <= 480 columns).
 // Level L receives its last product with i = L - 1 (L <= 10) or i = 9, so the
 // epilogue warps read level L back and add it in FP64 while the MMAs of later
-// slices run.  Warp 0 issues the TMA loads, warp 1 (one elected thread) the
-// MMAs, warps 2-5 the epilogue.  Every mbarrier wait is bounded; on a timeout
-// the kernel records an error and finishes without further work.
+// slices run.  A longer K runs chunk after chunk of 256 through the same
+// accumulators: the first product of level L in the next chunk waits until
+// the epilogue has read level L of this one (levels 2 .. 9 are read while the
+// chunk still runs, so only levels 10 and 11 hold the next chunk up).  Warp 0
+// issues the TMA loads, warp 1 (one elected thread) the MMAs, warps 2-5 the
+// epilogue.  Every mbarrier wait is bounded; on a timeout the kernel records
+// an error and finishes without further work.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -45,7 +50,8 @@ constexpr int kOzM = 128;
 constexpr int kOzBK = 64;     // BF16 elements of K per stage (128 bytes)
 constexpr int kOzMmaK = 16;   // K per MMA
 constexpr int kOzMaxNt = 48;  // columns per CTA (ten level accumulators fit 512 TMEM columns)
-constexpr int kOzMaxKt = kOzMaxK / 64;    // K tiles of one P slice
+constexpr int kOzMaxKt = kOzMaxK / 64;    // K tiles of one P slice chunk
+constexpr int kOzLevels = kOzSlices + 1;  // levels L = 2 .. 11
 
 // ---------------------------------------------------------------- slicing
 // One warp per row of the slice block: the row's exponent from the largest
@@ -109,9 +115,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
     }
     return;
   }
-  const int nk = (J.K + kOzBK - 1) / kOzBK;  // K tiles (<= kOzMaxKt)
-  constexpr uint32_t kTileA = kOzM * 128;    // one K tile of a P slice: 128 rows x 128 bytes
-  const uint32_t p_bytes = (uint32_t)nk * kTileA;
+  const int nkt = (J.K + kOzBK - 1) / kOzBK;  // K tiles in all
+  const int nc = (nkt + kOzMaxKt - 1) / kOzMaxKt;  // chunks of at most kOzMaxKt tiles
+  constexpr uint32_t kTileA = kOzM * 128;     // one K tile of a P slice: 128 rows x 128 bytes
   const uint32_t s_bytes = (uint32_t)NT * 128;
   const uint32_t s_stage = (s_bytes + 1023) / 1024 * 1024;
 
@@ -124,7 +130,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   uint64_t* sfull = pempty + 2;
   uint64_t* sempty = sfull + stages;
   uint64_t* ifull = sempty + stages;  // [kOzSlices]: the products of slice i are complete
-  uint32_t* tmem_slot = (uint32_t*)(ifull + kOzSlices);
+  uint64_t* lempty = ifull + kOzSlices;  // [kOzLevels]: the epilogue has read level L
+  uint32_t* tmem_slot = (uint32_t*)(lempty + kOzLevels);
   __shared__ int err;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -141,6 +148,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
       mbar_init(&sempty[s], 1);
     }
     for (int i = 0; i < kOzSlices; ++i) mbar_init(&ifull[i], 1);
+    for (int L = 0; L < kOzLevels; ++L) mbar_init(&lempty[L], 4);  // one arrival per epilogue warp
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -160,32 +168,38 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   if (warp == 0 && lane == 0) {
     // producer: slice i of P (all K tiles), then the S tiles of every j it pairs with
     int step = 0;
-    for (int i = 1; i <= kOzSlices && !*errv; ++i) {
-      const int pb = (i - 1) & 1, use = (i - 1) >> 1;
-      if (use > 0 && !mbar_wait(&pempty[pb], (use - 1) & 1)) {
-        atomicExch(&err, 1);
-        break;
-      }
-      mbar_expect_tx(&pfull[pb], p_bytes);
-      for (int kt = 0; kt < nk; ++kt)
-        tma_load_2d(pbuf + ((size_t)pb * kOzMaxKt + kt) * kTileA, &J.tp, &pfull[pb], kt * kOzBK, (i - 1) * J.M + m0);
-      for (int j = 1; j <= jmax(i) && !*errv; ++j)
-        for (int kt = 0; kt < nk; ++kt, ++step) {
-          const int s = step % stages;
-          if (step >= stages && !mbar_wait(&sempty[s], ((step / stages) & 1) ^ 1)) {
-            atomicExch(&err, 1);
-            break;
-          }
-          mbar_expect_tx(&sfull[s], s_bytes);
-          tma_load_2d(sbuf + (size_t)s * s_stage, &J.ts, &sfull[s], kt * kOzBK, (j - 1) * J.Npad + n0);
+    for (int c = 0; c < nc && !*errv; ++c) {
+      const int kt0 = c * kOzMaxKt, nk = min(kOzMaxKt, nkt - kt0);
+      for (int i = 1; i <= kOzSlices && !*errv; ++i) {
+        const int t = c * kOzSlices + i - 1, pb = t & 1, use = t >> 1;
+        if (use > 0 && !mbar_wait(&pempty[pb], (use - 1) & 1)) {
+          atomicExch(&err, 1);
+          break;
         }
+        mbar_expect_tx(&pfull[pb], (uint32_t)nk * kTileA);
+        for (int kt = 0; kt < nk; ++kt)
+          tma_load_2d(pbuf + ((size_t)pb * kOzMaxKt + kt) * kTileA, &J.tp, &pfull[pb], (kt0 + kt) * kOzBK,
+                      (i - 1) * J.M + m0);
+        for (int j = 1; j <= jmax(i) && !*errv; ++j)
+          for (int kt = 0; kt < nk; ++kt, ++step) {
+            const int s = step % stages;
+            if (step >= stages && !mbar_wait(&sempty[s], ((step / stages) & 1) ^ 1)) {
+              atomicExch(&err, 1);
+              break;
+            }
+            mbar_expect_tx(&sfull[s], s_bytes);
+            tma_load_2d(sbuf + (size_t)s * s_stage, &J.ts, &sfull[s], (kt0 + kt) * kOzBK, (j - 1) * J.Npad + n0);
+          }
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: product (i, j) accumulates into the TMEM columns of level i + j
     const uint32_t id = idesc<__nv_bfloat16>(kOzM, NT);
     int step = 0;
-    for (int i = 1; i <= kOzSlices && !*errv; ++i) {
-      const int pb = (i - 1) & 1, use = (i - 1) >> 1;
+    for (int c = 0; c < nc && !*errv; ++c) {
+     const int nk = min(kOzMaxKt, nkt - c * kOzMaxKt);
+     for (int i = 1; i <= kOzSlices && !*errv; ++i) {
+      const int t = c * kOzSlices + i - 1, pb = t & 1, use = t >> 1;
       if (!mbar_wait(&pfull[pb], use & 1)) {
         atomicExch(&err, 1);
         break;
@@ -196,6 +210,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
         const int L = i + j;
         const uint32_t td = tmem + (uint32_t)((L - 2) * NT);
         const bool first_of_level = i == max(1, L - kOzSlices);
+        if (c > 0 && first_of_level) {  // the epilogue has read this level of the previous chunk
+          if (!mbar_wait(&lempty[L - 2], (c - 1) & 1)) {
+            atomicExch(&err, 1);
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
         for (int kt = 0; kt < nk; ++kt, ++step) {
           const int s = step % stages;
           if (!mbar_wait(&sfull[s], (step / stages) & 1)) {
@@ -216,6 +237,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
       }
       mma_commit(&pempty[pb]);
       mma_commit(&ifull[i - 1]);
+     }
     }
   } else if (warp >= 2) {
     // epilogue: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31.
@@ -226,26 +248,32 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
     for (int c = 0; c < kOzMaxNt; ++c) acc[c] = 0.0;
     bool ok = true;
-    for (int i = 1; i <= kOzSlices && ok; ++i) {
-      if (!mbar_wait(&ifull[i - 1], 0)) {
-        ok = false;
-        atomicExch(&err, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int L = i + 1; L <= (i == kOzSlices ? kOzSlices + 2 : i + 1); ++L) {
-        const double w = __longlong_as_double((long long)(1023 - 6 * L) << 52);  // 2^-6L
-        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * NT);
+    for (int c = 0; c < nc && ok; ++c)
+      for (int i = 1; i <= kOzSlices && ok; ++i) {
+        // warp-uniform: the level reads and the arrivals below are warp-collective
+        if (!__all_sync(0xffffffffu, mbar_wait(&ifull[i - 1], c & 1) ? 1 : 0)) {
+          ok = false;
+          atomicExch(&err, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int L = i + 1; L <= (i == kOzSlices ? kOzSlices + 2 : i + 1); ++L) {
+          const double w = __longlong_as_double((long long)(1023 - 6 * L) << 52);  // 2^-6L
+          const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * NT);
 #pragma unroll
-        for (int c0 = 0; c0 < kOzMaxNt; c0 += 16)
-          if (c0 < NT) {
-            float t[16];
-            ld16(tl + (uint32_t)c0, t);
+          for (int c0 = 0; c0 < kOzMaxNt; c0 += 16)
+            if (c0 < NT) {
+              float t[16];
+              ld16(tl + (uint32_t)c0, t);
 #pragma unroll
-            for (int u = 0; u < 16; ++u) acc[c0 + u] = fma((double)t[u], w, acc[c0 + u]);
-          }
+              for (int u = 0; u < 16; ++u) acc[c0 + u] = fma((double)t[u], w, acc[c0 + u]);
+            }
+          // level L may now be overwritten by the next chunk
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&lempty[L - 2]);
+        }
       }
-    }
     if (ok && !*errv && row < J.M) {
       const int er = J.ep[row];
 #pragma unroll
@@ -269,7 +297,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
 
 size_t oz_smem_bytes(int ntile, int stages) {
   const size_t s_stage = ((size_t)ntile * 128 + 1023) / 1024 * 1024;
-  return 1024 + 2 * (size_t)kOzMaxKt * kOzM * 128 + s_stage * stages + (4 + 2 * (size_t)stages + kOzSlices) * 8 + 16;
+  return 1024 + 2 * (size_t)kOzMaxKt * kOzM * 128 + s_stage * stages +
+         (4 + 2 * (size_t)stages + kOzSlices + kOzLevels) * 8 + 16;
 }
 
 }  // namespace
@@ -323,7 +352,8 @@ extern "C" size_t rsvd_gemm_f64_tc_workspace_size(int M, int N, int K) {
 extern "C" int rsvd_gemm_f64_tc(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
                                 int ldc, void* work, size_t work_bytes, int* err, void* cuda_stream) {
   using namespace rsvd;
-  if (M < 1 || N < 1 || N > 256 || K < 1 || K > kOzMaxK || lda < K || ldb < K || ldc < N) return RSVD_ERR_INVALID_SIZE;
+  if (M < 1 || N < 1 || N > 256 || K < 1 || K > kOzMaxKTotal || lda < K || ldb < K || ldc < N)
+    return RSVD_ERR_INVALID_SIZE;
   if (!A || !B || !C || !work) return RSVD_ERR_NULL_POINTER;
   if (work_bytes < rsvd_gemm_f64_tc_workspace_size(M, N, K)) return RSVD_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)cuda_stream;

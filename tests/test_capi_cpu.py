@@ -56,9 +56,9 @@ def lib_global():
 
 
 def test_workspace_size_grows_with_size(lib):
-    # within one product path (FP64 FMAs, or tensor-core slices for m, n <= 256)
-    assert 0 < wsize(256, 256, flags=1) < wsize(1024, 1024) < wsize(2048, 2048)
-    assert 0 < wsize(128, 128) < wsize(256, 256)
+    # within one product path (FP64 FMAs, or tensor-core slices for m, n <= 1024)
+    assert 0 < wsize(256, 256, flags=1) < wsize(1024, 1024, flags=1) < wsize(2048, 2048)
+    assert 0 < wsize(128, 128) < wsize(256, 256) < wsize(1024, 1024)
     assert wsize(256, 256) % 256 == 0
 
 
@@ -67,6 +67,10 @@ def test_workspace_holds_the_fp64_slices(lib):
     extra = wsize(256, 256) - wsize(256, 256, flags=1)
     assert extra >= 9 * 2 * (256 * 256 + 256 * 256 + 48 * 256)
     assert extra < 4 * 1024 * 1024
+    # up to m, n = 1024 (K in chunks of 256); beyond, the FP64 FMA path holds no slices
+    extra = wsize(1024, 1024) - wsize(1024, 1024, flags=1)
+    assert extra >= 9 * 2 * (1024 * 1024 + 1024 * 1024 + 48 * 1024)
+    assert wsize(1025, 1024) == wsize(1025, 1024, flags=1)
 
 
 def test_unknown_flags_rejected(lib):

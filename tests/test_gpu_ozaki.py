@@ -2,8 +2,9 @@
 
 Compared with an extended-precision product (numpy longdouble) of the same
 FP64 inputs: the error of every entry is within 4 * 2^-53 * K * max|A_r| *
-max|B_c| (the normwise class of an FP64 GEMM); integer inputs give exact
-results; a row holding NaN gives NaN in its row of C only.
+max|B_c| (the normwise class of an FP64 GEMM), for K in one chunk (<= 256) and
+over several chunks (up to 1024); integer inputs give exact results; a row
+holding NaN gives NaN in its row of C only.
 """
 import ctypes
 
@@ -48,7 +49,8 @@ def bound(A, B):
 
 
 @pytest.mark.parametrize("M,N,K", [(256, 144, 256), (300, 138, 256), (128, 256, 256), (37, 5, 1), (200, 64, 250),
-                                   (1, 1, 7), (513, 200, 129)])
+                                   (1, 1, 7), (513, 200, 129), (512, 138, 512), (384, 144, 384), (130, 48, 1024),
+                                   (257, 100, 257), (64, 17, 700)])
 def test_sliced_product_within_fp64_bound(lib, M, N, K):
     rng = np.random.default_rng(M * 1000 + N + K)
     # rows of widely different scales, entries spanning several binades within a row
@@ -82,10 +84,20 @@ def test_nan_row_propagates(lib):
     assert np.all(np.isfinite(C[:129]))
 
 
+def test_integer_inputs_exact_over_chunks(lib):
+    # K = 768: three chunks of 256, each level sum exact, chunks added in FP64 (integers
+    # below 2^53 stay exact)
+    rng = np.random.default_rng(5)
+    A = rng.integers(-1000, 1000, size=(130, 768)).astype(np.float64)
+    B = rng.integers(-1000, 1000, size=(40, 768)).astype(np.float64)
+    C = run(lib, A, B)
+    np.testing.assert_array_equal(C, (A.astype(np.int64) @ B.astype(np.int64).T).astype(np.float64))
+
+
 def test_rejects_long_k(lib):
-    A = torch.zeros((4, 300), dtype=torch.float64, device="cuda")
+    A = torch.zeros((4, 1100), dtype=torch.float64, device="cuda")
     C = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
     work = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
-    rc = lib.rsvd_gemm_f64_tc(4, 4, 300, ctypes.c_void_p(A.data_ptr()), 300, ctypes.c_void_p(A.data_ptr()), 300,
+    rc = lib.rsvd_gemm_f64_tc(4, 4, 1100, ctypes.c_void_p(A.data_ptr()), 1100, ctypes.c_void_p(A.data_ptr()), 1100,
                               ctypes.c_void_p(C.data_ptr()), 4, ctypes.c_void_p(work.data_ptr()), work.numel(), None, None)
-    assert rc == -1  # RSVD_ERR_INVALID_SIZE: exact level sums need K <= 256
+    assert rc == -1  # RSVD_ERR_INVALID_SIZE: K <= 1024
