@@ -210,9 +210,25 @@ def step_flops(info):
                         flops["gram"] += 2 * rows * l * l
                         flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
                         flops["gemm"] += 2 * rows * l * l
-            flops["jacobi"] += (sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * 6.0 * n
-                                + (sweeps + 1) * 2.0 * n * l)
+            svd_b_flops(flops, n, k, l, sweeps, rots)
     return flops
+
+
+def svd_b_flops(flops, n, k, l, sweeps, rots):
+    """The SVD of B (l x n): Jacobi on B, or for wide B (n >= 3l) the orthonormalisation of
+    B^T (n x l), M = B Q_b (2 l n l), Jacobi on M (l x l) and V^T = W Q_b^T (2 k l n).
+    Jacobi per sweep: row norms (2 n l) and all l (l - 1) / 2 pair products (2 n each); per
+    applied rotation 6 n."""
+    if 10 * n >= 30 * l:
+        if 3 * l > n:
+            flops["householder"] += hh_flops(n, l, l)
+        else:
+            flops["gram"] += 2 * n * l * l
+            flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
+            flops["gemm"] += 2 * n * l * l
+        flops["gemm"] += 2.0 * l * n * l + 2.0 * k * l * n
+        n = l
+    flops["jacobi"] += sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * 6.0 * n + (sweeps + 1) * 2.0 * n * l
 
 
 def product_step_flops(info, flops):
@@ -240,8 +256,7 @@ def product_step_flops(info, flops):
                         flops["gram"] += 2 * rows * l * l
                         flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
                         flops["gemm"] += 2 * rows * l * l
-                flops["jacobi"] += (sweeps * (l * (l - 1) / 2.0) * 2.0 * n + rots * 6.0 * n
-                                    + (sweeps + 1) * 2.0 * n * l)
+                svd_b_flops(flops, n, k, l, sweeps, rots)
     return flops
 
 
@@ -522,7 +537,7 @@ def profile_classes(lib):
 
 def rsvd_flops(m, n, k, l, q, sweeps, rots, prec, qr_cols=0, want_u=True):
     """Algorithmic flops of one RSVD by kernel class (see step_flops), plus the
-    tensor-core products of the BF16 / TF32 forms.  Wide B (n >= 4l): the SVD
+    tensor-core products of the BF16 / TF32 forms.  Wide B (n >= 3l): the SVD
     of B runs on the l x l factor of an orthonormalisation of B^T."""
     f = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "tcgemm": 0.0, "ozgemm": 0.0}
     exact = m <= l and m <= 16
@@ -543,7 +558,7 @@ def rsvd_flops(m, n, k, l, q, sweeps, rots, prec, qr_cols=0, want_u=True):
     if want_u:
         f["gemm"] += 2.0 * m * l * k  # lift
     jn = n
-    if n >= 4 * l:  # B^T = Q_b R, M = B Q_b, V^T = W Q_b^T
+    if 10 * n >= 30 * l:  # B^T = Q_b R, M = B Q_b, V^T = W Q_b^T
         orth(n)
         f["gemm"] += 2.0 * l * n * l + 2.0 * k * l * n
         jn = l

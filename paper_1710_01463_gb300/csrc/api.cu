@@ -48,7 +48,7 @@ struct Prob {
   // tensor-core path: A^T, Omega^T / Z^T, Q^T in the operand precision
   void *At, *WT, *QT;
   int ldAt, ldWT, ldQT;
-  // wide B (n >= 4 l): B^T = Q_b R first, Jacobi on M = B Q_b (l x l)
+  // wide B (n >= 3 l): B^T = Q_b R first, Jacobi on M = B Q_b (l x l)
   int wide;
   double *Bt, *Bt2, *Mb, *RinvD;
   void *Wb, *Qbt;
@@ -68,13 +68,18 @@ struct Prob {
 
 inline int pad8(int x) { return (x + 7) / 8 * 8; }
 
+// B (l x n) is "wide" when n >= kWide10 / 10 * l (3 l: measured on TEBD bonds with n / l
+// = 1.9, 2.8 and 3.7, only the last gains): its SVD then runs on the l x l
+// factor M = B Q_b of an orthonormalisation B^T = Q_b R
+constexpr int kWide10 = 30;
+
 // Workspace of one matrix (bytes), with the buffer offsets when `p` is given.
 // tc_bytes > 0 (the operand size of the tensor-core precisions) adds A^T
 // (n x m), Omega^T / Z^T (l x n) and Q^T (l x m) with 8-element-aligned rows.
 size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int tc_bytes = 0, int oz = 0, int r = 0) {
   const int mx = std::max(m, n);
   const int nchunk = ceil_div(mx, kGramChunk);
-  const int wide = n >= 4 * l ? 1 : 0;
+  const int wide = 10 * n >= kWide10 * l ? 1 : 0;
   const int jn = wide ? l : n;  // columns of the matrix the Jacobi SVD works on
   const int cs = jacobi_cluster_size(l, jn);
   const int glob = jacobi_fits_smem(l, jn, cs) ? 0 : 1;
@@ -202,7 +207,7 @@ OrthBatch<T> orth_batch(const std::vector<Prob*>& ps, bool onY) {
 }
 
 // Rank-k SVD of B (l x n, FP64, in Bm) for every matrix: one-sided Jacobi on
-// B itself, or - for wide B (n >= 4 l) - on the l x l matrix M = B Q_b where
+// B itself, or - for wide B (n >= 3 l) - on the l x l matrix M = B Q_b where
 // B^T = Q_b R is an FP64 orthonormalisation of B^T (same CholeskyQR2 /
 // Householder machinery as the samples); then B = M Q_b^T and the rows of V^T
 // are the Jacobi's normalised rows times Q_b^T.  Writes S, V^T and the sorted
