@@ -94,7 +94,8 @@ typedef struct {
 typedef struct {
   int status;          /* RSVD_OK, RSVD_WARN_NOCONV or RSVD_ERR_NONFINITE */
   int path;            /* RSVD_PATH_* bits */
-  int chol_fallbacks;  /* orthonormalisations that fell back to Householder QR */
+  int chol_fallbacks;  /* orthonormalisations that fell back to Householder QR (CholeskyQR2 broke
+                          down, or the sample was known to be rank deficient) */
   int jacobi_sweeps;   /* sweeps of the one-sided Jacobi SVD of B */
   int l;               /* sample width used */
   int rotations;       /* plane rotations applied by the Jacobi SVD (all sweeps) */

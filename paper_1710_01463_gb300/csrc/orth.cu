@@ -65,6 +65,15 @@ __device__ __forceinline__ void tilepair(int idx, int T, int& ti, int& tj) {
   tj = ti + idx;
 }
 
+// A sample whose Q is kept to its effective columns (trunc_q) after an earlier
+// Householder QR of the same matrix ended early has exact zero columns beyond
+// them: its Gram matrix is singular and CholeskyQR2 would break down, so it
+// goes to Householder QR directly
+template <typename T>
+__device__ __forceinline__ bool known_deficient(const OrthJob<T>& J) {
+  return J.trunc_q && J.rank_eff && *J.rank_eff < J.l;
+}
+
 // partial G over one chunk of rows for one kGramTile x kGramTile tile (ti <= tj),
 // one output per thread.  16-wide tiles: the FMA loop is FP64-bound at any
 // tile size, so the small tile loses nothing and pads less (l = 80 computes
@@ -73,7 +82,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ OrthBatch<T> b, int gated, int src1) {
   static_assert(kGramTile == 16, "one output per thread of a 16 x 16 tile");
   const OrthJob<T>& J = b.job[blockIdx.z];
-  if (J.hh_first || (gated && *J.flag != 0)) return;
+  if (J.hh_first || (gated && *J.flag != 0) || known_deficient(J)) return;
   const int l = J.l;
   const int nt = (l + kGramTile - 1) / kGramTile;
   if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ OrthB
 template <typename T>
 __global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant__ OrthBatch<T> b, int gated) {
   const OrthJob<T>& J = b.job[blockIdx.y];
-  if (J.hh_first || (gated && *J.flag != 0)) return;
+  if (J.hh_first || (gated && *J.flag != 0) || known_deficient(J)) return;
   const int l = J.l;
   const int nchunk = (J.rows + kGramChunk - 1) / kGramChunk;
   const long long tot = (long long)l * l;
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant_
 template <typename T>
 __global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ OrthBatch<T> b, int pass, int use_smem) {
   const OrthJob<T>& J = b.job[blockIdx.x];
-  if (pass == 0 && J.hh_first) {
+  if (pass == 0 && (J.hh_first || known_deficient(J))) {
     if (threadIdx.x == 0) *J.flag = 1;
     return;
   }
