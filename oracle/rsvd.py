@@ -92,3 +92,38 @@ def truncation_error_frobenius(s_full, k):
     """Eckart-Young-Mirsky (Sec. II.A): minimal Frobenius error of a rank-k factorization."""
     s_full = np.asarray(s_full, dtype=np.float64)
     return float(np.sqrt(np.sum(s_full[k:] ** 2)))
+
+
+def rsvd_fixed_error(A, eps, k0, k_max, p, q, seed, stream=0):
+    """Fixed-error Alg. RSVD (the fixed-error form the paper proposes in Sec. V, after
+    Halko-Martinsson-Tropp and Gu): the smallest rank k <= k_max whose factorization has
+    ||A - U diag(s) V^T||_F <= eps ||A||_F.
+
+    The error of the rank-k result Q B_k (B = Q^T A, B_k its rank-k TSVD) is known from
+    the sample alone: Q Q^T is an orthogonal projector, so
+        ||A - Q B_k||_F^2 = ||A - Q B||_F^2 + sum_{i > k} s_i(B)^2.
+    Trial ranks k0, 2 k0, 4 k0, ... (capped at k_max and min(m, n)), each a full Alg.
+    RSVD with l = min(k + p, m, n); the test matrix of a larger trial extends the
+    previous one (its columns nest).  k >= 1.  Returns (U, s, Vt, err) with
+    err = ||A - U diag(s) Vt||_F / ||A||_F (0 for A = 0); when no k <= k_max reaches
+    eps, k is the last trial rank and err > eps."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    fro2 = float(np.sum(A * A))
+    cap = min(k_max, m, n)
+    kt = max(1, min(k0, cap))
+    while True:
+        l = sample_width(m, n, kt, p)
+        Q = rsvd_basis(A, l, q, seed, stream)
+        B = Q.T @ A
+        Ub, s, Vt = np.linalg.svd(B, full_matrices=False)
+        r2 = float(np.sum((A - Q @ B) ** 2))
+        # err2[k] = r2 + sum_{i >= k} s_i^2 (0-based i), k = 0 .. len(s); summed smallest first
+        err2 = np.append(r2 + np.cumsum((s ** 2)[::-1])[::-1], r2)
+        ok = [k for k in range(1, kt + 1) if err2[k] <= eps * eps * fro2]
+        if ok or kt >= cap:
+            k = ok[0] if ok else kt
+            U, s_k, Vt_k = canonical_signs(Q @ Ub[:, :k], s[:k], Vt[:k, :])
+            err = float(np.sqrt(err2[k] / fro2)) if fro2 > 0 else 0.0
+            return U, s_k, Vt_k, err
+        kt = min(2 * kt, cap)

@@ -20,6 +20,7 @@ import numpy as np
 import pytest
 
 from oracle import philox
+from oracle import rsvd as orsvd
 from oracle.rsvd import canonical_signs, qr_pos, rsvd, rsvd_basis, tsvd
 from paper_1710_01463_gb300 import inputs
 
@@ -170,3 +171,67 @@ def test_power_iterations_improve_accuracy():
         err[q] = np.linalg.norm(A - (U * s) @ Vt, 2)
     assert err[2] < 0.8 * err[0]
     assert err[2] >= s_true[20] * (1 - 1e-12)
+
+
+# ---------------------------------------------------------------- fixed-error RSVD
+def minimal_rank(s_full, eps):
+    """Smallest k >= 1 with sqrt(sum_{i>k} s_i^2) <= eps ||s|| (Eckart-Young)."""
+    tot = np.sum(s_full ** 2)
+    for k in range(1, len(s_full) + 1):
+        if np.sum(s_full[k:] ** 2) <= eps * eps * tot:
+            return k
+    return len(s_full)
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-3, 3e-6, 1e-9])
+def test_fixed_error_rank_matches_eckart_young_when_exact(eps):
+    # rank-40 A: once l >= 40 the sample spans the range, s(B) = s(A), and the chosen rank
+    # is the TSVD's minimal rank (eps kept away from the boundaries of the exp spectrum)
+    rng = np.random.default_rng(21)
+    s = np.exp(-np.arange(1, 41) / 3.0)
+    U = np.linalg.qr(rng.standard_normal((120, 40)))[0]
+    V = np.linalg.qr(rng.standard_normal((90, 40)))[0]
+    A = (U * s) @ V.T
+    Ur, sr, Vtr, err = orsvd.rsvd_fixed_error(A, eps, 8, 60, 40, 1, 3)
+    k = minimal_rank(s, eps)
+    assert len(sr) == k
+    np.testing.assert_allclose(sr, s[:k], rtol=1e-10)
+    assert err <= eps
+
+
+@pytest.mark.parametrize("k0,kmax,eps", [(4, 200, 1e-6), (16, 200, 1e-3), (4, 12, 1e-8), (64, 64, 1e-2)])
+def test_fixed_error_reports_its_true_error_and_is_minimal(k0, kmax, eps):
+    # the reported error is ||A - U S V^T|| / ||A|| computed directly (pins the
+    # Pythagoras identity: a dropped residual term or an off-by-one in the tail sum fails),
+    # and rank k - 1 of the same factorization misses eps
+    A = inputs.spectral_matrix(200, 150, inputs.exp_spectrum(150, 6.0), 8)
+    U, s, Vt, err = orsvd.rsvd_fixed_error(A, eps, k0, kmax, 8, 1, 5)
+    fro = np.linalg.norm(A)
+    direct = np.linalg.norm(A - (U * s) @ Vt) / fro
+    assert err == pytest.approx(direct, rel=1e-6, abs=1e-15)
+    k = len(s)
+    if err <= eps:
+        assert k == 1 or np.linalg.norm(A - (U[:, :k - 1] * s[:k - 1]) @ Vt[:k - 1]) / fro > eps
+    else:
+        assert k == min(kmax, 150)  # the cap was reached
+
+
+def test_fixed_error_grows_from_a_small_trial_rank():
+    A = inputs.spectral_matrix(160, 160, inputs.harmonic_spectrum(160), 9)
+    U, s, Vt, err = orsvd.rsvd_fixed_error(A, 0.05, 2, 160, 8, 2, 1)
+    assert err <= 0.05 and len(s) > 2
+    # the same result as one fixed-rank RSVD at the final trial rank (nested Omega: the
+    # trials differ only in their width)
+    kt = 2
+    while kt < len(s):
+        kt *= 2
+    U2, s2, Vt2 = orsvd.rsvd(A, kt, 8, 2, 1)
+    np.testing.assert_allclose(s, s2[:len(s)], rtol=1e-12)
+
+
+def test_fixed_error_of_zero_and_exact_rank():
+    U, s, Vt, err = orsvd.rsvd_fixed_error(np.zeros((30, 20)), 1e-6, 4, 20, 4, 1, 0)
+    assert len(s) == 1 and s[0] == 0.0 and err == 0.0
+    A = np.outer(np.arange(1.0, 31.0), np.arange(1.0, 21.0))
+    U, s, Vt, err = orsvd.rsvd_fixed_error(A, 1e-12, 4, 20, 4, 1, 0)
+    assert len(s) == 1 and err <= 1e-12
