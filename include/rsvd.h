@@ -260,6 +260,36 @@ int rsvd_truncate_factored(int m, int r, int n, const void* X, int ldx, const vo
                            rsvd_info* info, void* cuda_stream);
 
 /*
+ * rsvd_tol_workspace_size - workspace bytes of rsvd_truncate_tol.
+ */
+int rsvd_tol_workspace_size(int m, int n, int k_max, const rsvd_params* p, size_t* bytes);
+
+/*
+ * rsvd_truncate_tol - fixed-error Alg. RSVD (the fixed-error form proposed in
+ * Sec. V): the smallest rank k <= min(k_max, m, n) with
+ * ||A - U diag(S) V^T||_F <= eps ||A||_F, FP64 (p->prec = RSVD_F64).
+ * The error of the rank-k result Q B_k (B = Q^T A) is exact from the sample:
+ * Q Q^T is an orthogonal projector, so ||A - Q B_k||_F^2 = ||A - Q B||_F^2 +
+ * sum_{i>k} s_i(B)^2; the residual A - Q B is formed on the device.  Trial
+ * ranks p->k, 2 p->k, 4 p->k, ... (capped), each a full Alg. RSVD with
+ * l = min(k + p->p, m, n) and the same Philox stream, so the test matrix of a
+ * larger trial extends the previous one.  Each trial ends with one
+ * device-to-host read of the decision and a synchronisation of the stream.
+ *   A   device, m x n row-major (lda);  S (k_max), U (m x k_max, ldu >=
+ *       min(k_max, m, n)), Vt (k_max x n, ldvt): device outputs, of which the
+ *       first *k_out singular values / columns of U / rows of V^T are the result.
+ *   k_out, err_out  HOST: the rank and ||A - U S V^T||_F / ||A||_F (0 for
+ *       A = 0).  When no k up to the cap reaches eps, k_out is the cap and
+ *       err_out > eps (the return code is still RSVD_OK).
+ *   info  device record of the last trial.
+ * Errors: RSVD_ERR_INVALID_SIZE (also eps < 0 or NaN), RSVD_ERR_NULL_POINTER,
+ * RSVD_ERR_PRECISION, RSVD_ERR_WORKSPACE, RSVD_ERR_LAUNCH.
+ */
+int rsvd_truncate_tol(int m, int n, const double* A, int lda, double eps, int k_max, const rsvd_params* p, double* S,
+                      double* U, int ldu, double* Vt, int ldvt, int* k_out, double* err_out, void* work,
+                      size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
  * rsvd_gemm_f64_tc - the FP64 tensor-core product of the FP64 path (exposed so
  * that it can be verified on its own): C = A B^T with A (M x K, lda), B (N x K,
  * ldb) and C (M x N, ldc) row-major FP64 device matrices, N <= 256, K <= 1024.

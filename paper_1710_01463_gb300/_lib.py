@@ -42,6 +42,8 @@ EXPORTED = (
     "tebd_product_update",
     "rsvd_factored_workspace_size",
     "rsvd_truncate_factored",
+    "rsvd_tol_workspace_size",
+    "rsvd_truncate_tol",
     "rsvd_status_string",
     "rsvd_profile_enable",
     "rsvd_profile_collect",

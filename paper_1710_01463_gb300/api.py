@@ -129,6 +129,38 @@ def rsvd_truncate_factored(X, Y, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, wo
     return U, S, Vt, info
 
 
+def rsvd_truncate_tol(A, eps, k0, k_max, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None):
+    """Fixed-error RSVD (rsvd_truncate_tol): the smallest rank k <= k_max with
+    ||A - U diag(S) Vt||_F <= eps ||A||_F, trial ranks k0, 2 k0, ...; A a float64 CUDA
+    tensor.  Returns (U, S, Vt, err, info) cut to the chosen rank."""
+    lib = _lib.load()
+    _require_cuda(A)
+    if A.dim() != 2 or A.stride(1) != 1 or A.dtype != torch.float64:
+        raise ValueError("A must be a row-major float64 2-D tensor")
+    m, n = A.shape
+    cap = min(int(k_max), m, n)
+    par = _params(k0, p, q, _lib.RSVD_F64, seed, stream, max_sweeps)
+    sz = ctypes.c_size_t(0)
+    _lib.check(lib.rsvd_tol_workspace_size(m, n, int(k_max), ctypes.byref(par), ctypes.byref(sz)),
+               "rsvd_tol_workspace_size")
+    if work is None or work.numel() < sz.value:
+        work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=A.device)
+    U = torch.empty((m, cap), dtype=torch.float64, device=A.device)
+    S = torch.empty((cap,), dtype=torch.float64, device=A.device)
+    Vt = torch.empty((cap, n), dtype=torch.float64, device=A.device)
+    info = torch.zeros((1, _lib.INFO_INTS), dtype=torch.int32, device=A.device)
+    k = ctypes.c_int(0)
+    err = ctypes.c_double(0.0)
+    rc = lib.rsvd_truncate_tol(m, n, ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_double(eps), int(k_max),
+                               ctypes.byref(par), ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                               U.stride(0), ctypes.c_void_p(Vt.data_ptr()), Vt.stride(0), ctypes.byref(k),
+                               ctypes.byref(err), ctypes.c_void_p(work.data_ptr()), ctypes.c_size_t(work.numel()),
+                               ctypes.c_void_p(info.data_ptr()), _stream_handle())
+    _lib.check(rc, "rsvd_truncate_tol")
+    kk = k.value
+    return U[:, :kk], S[:kk], Vt[:kk], err.value, info
+
+
 class BatchedPlan:
     """Preallocated outputs and workspace of rsvd_truncate_batched for fixed shapes."""
 

@@ -835,6 +835,100 @@ int rsvd_truncate_factored(int m, int r, int n, const void* X, int ldx, const vo
   return run_batched(probs, p, (char*)work, work_bytes, (cudaStream_t)cuda_stream);
 }
 
+// ---------------------------------------------------------------- fixed-error RSVD
+namespace {
+struct TolLayout {
+  size_t rsvd, E, r2, fro2, res, total;
+};
+TolLayout tol_layout(int m, int n, int kcap, const rsvd_params* p) {
+  TolLayout L;
+  const int l = sample_width(m, n, kcap, p->p);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t x = off;
+    off += align_up(b);
+    return x;
+  };
+  L.rsvd = take(layout(nullptr, m, n, kcap, l, 8, nullptr, 0, use_oz(m, n, l, use_exact_path(m, l), p)));
+  L.E = take((size_t)m * n * 8);
+  L.r2 = take(kSqParts * 8);
+  L.fro2 = take(kSqParts * 8);
+  L.res = take(sizeof(TolResult));
+  L.total = off;
+  return L;
+}
+}  // namespace
+
+int rsvd_tol_workspace_size(int m, int n, int k_max, const rsvd_params* p, size_t* bytes) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!bytes) return RSVD_ERR_NULL_POINTER;
+  if (p->prec != RSVD_F64) return RSVD_ERR_PRECISION;
+  if (m < 1 || n < 1 || k_max < 1 || p->k < 1) return RSVD_ERR_INVALID_SIZE;
+  const int kcap = std::min(k_max, std::min(m, n));
+  if (sample_width(m, n, kcap, p->p) > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+  *bytes = tol_layout(m, n, kcap, p).total;
+  return RSVD_OK;
+}
+
+int rsvd_truncate_tol(int m, int n, const double* A, int lda, double eps, int k_max, const rsvd_params* p, double* S,
+                      double* U, int ldu, double* Vt, int ldvt, int* k_out, double* err_out, void* work,
+                      size_t work_bytes, rsvd_info* info, void* cuda_stream) {
+  size_t need = 0;
+  int rc = rsvd_tol_workspace_size(m, n, k_max, p, &need);
+  if (rc) return rc;
+  if (!A || !S || !U || !Vt || !k_out || !err_out || !work || !info) return RSVD_ERR_NULL_POINTER;
+  const int kcap = std::min(k_max, std::min(m, n));
+  if (!(eps >= 0.0) || lda < n || ldu < kcap || ldvt < n) return RSVD_ERR_INVALID_SIZE;
+  if (((uintptr_t)work) % kAlign) return RSVD_ERR_WORKSPACE;
+  if (need > work_bytes) return RSVD_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  char* base = (char*)work;
+  const TolLayout L = tol_layout(m, n, kcap, p);
+  double* E = (double*)(base + L.E);
+  double* r2p = (double*)(base + L.r2);
+  double* fro2p = (double*)(base + L.fro2);
+  TolResult* res = (TolResult*)(base + L.res);
+  RSVD_TRY(launch_sq_sum(A, m, n, lda, fro2p, s));
+  int kt = std::max(1, std::min(p->k, kcap));
+  TolResult host{};
+  for (;;) {
+    rsvd_params pk = *p;
+    pk.k = kt;
+    std::vector<Prob> probs(1);
+    Prob& pr = probs[0];
+    std::memset(&pr, 0, sizeof(Prob));
+    pr.m = m; pr.n = n; pr.k = kt;
+    pr.l = sample_width(m, n, kt, p->p);
+    pr.exact = use_exact_path(m, pr.l);
+    pr.want_u = 1;
+    pr.A = A; pr.lda = lda;
+    pr.S = S; pr.U = U; pr.ldu = ldu; pr.Vt = Vt; pr.ldvt = ldvt;
+    pr.seed = p->seed; pr.stream = p->stream;  // the same Philox stream: Omega's columns nest
+    pr.info = info;
+    pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    rc = run_batched(probs, &pk, base + L.rsvd, L.E - L.rsvd, s);
+    if (rc) return rc;
+    // E = A - Q B: the residual of the projection, ||E||_F^2 = ||(I - Q Q^T) A||_F^2
+    RSVD_TRY(cudaMemcpy2DAsync(E, (size_t)n * 8, A, (size_t)lda * 8, (size_t)n * 8, m, cudaMemcpyDeviceToDevice, s));
+    GemmBatch<double, double> g;
+    g.count = 1;
+    g.job[0] = GemmJob<double, double>{m, n, pr.l, pr.l, n, n, (const double*)pr.Y0, pr.Bm, E, nullptr, nullptr, 0};
+    g.job[0].alpha = -1.0;
+    g.job[0].accumulate = 1;
+    RSVD_TRY((launch_gemm<double, double, false, false>(g, s)));
+    RSVD_TRY(launch_sq_sum(E, m, n, n, r2p, s));
+    RSVD_TRY(launch_tol_rank(pr.sig, pr.l, kt, r2p, fro2p, eps, res, s));
+    RSVD_TRY(cudaMemcpyAsync(&host, res, sizeof(TolResult), cudaMemcpyDeviceToHost, s));
+    RSVD_TRY(cudaStreamSynchronize(s));
+    if (!host.grow || kt >= kcap) break;
+    kt = std::min(2 * kt, kcap);
+  }
+  *k_out = host.k;
+  *err_out = host.err;
+  return RSVD_OK;
+}
+
 // ---------------------------------------------------------------- TEBD
 namespace {
 struct TebdLayout {

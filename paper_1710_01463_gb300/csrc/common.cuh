@@ -379,6 +379,17 @@ struct TebdRankBatch {
 cudaError_t launch_tebd_rank(const TebdRankBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_product(const TebdProdBatch& b, cudaStream_t s);
+// fixed-error RSVD: partial sums of squares of a rows x cols FP64 matrix (ld), and
+// the rank decision from the sample (see misc.cu)
+constexpr int kSqParts = 64;
+cudaError_t launch_sq_sum(const double* X, int rows, int cols, int ld, double* part, cudaStream_t s);
+struct TolResult {
+  int k;       // chosen rank
+  int grow;    // 1: no k <= k_trial reaches eps
+  double err;  // ||A - Q B_k||_F / ||A||_F
+};
+cudaError_t launch_tol_rank(const double* sig, int l, int k_trial, const double* r2_part, const double* fro2_part,
+                            double eps, TolResult* out, cudaStream_t s);
 cudaError_t launch_tebd_gram_dot(const TebdGramDotBatch& b, cudaStream_t s);
 template <typename TIn>
 cudaError_t launch_tc_gemm(const TcBatch& b, cudaStream_t s, int skip_loads = 0);

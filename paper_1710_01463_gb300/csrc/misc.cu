@@ -209,7 +209,123 @@ __global__ void __launch_bounds__(256) tebd_gram_dot_kernel(const __grid_constan
   }
 }
 
+// ---------------------------------------------------------------- fixed-error RSVD
+// kSqParts partial sums of x^2 over a rows x cols matrix (ld), two chains per thread
+__global__ void __launch_bounds__(256) sq_sum_kernel(const double* X, int rows, int cols, int ld, double* part) {
+  const long long tot = (long long)rows * cols;
+  const long long st = (long long)gridDim.x * blockDim.x;
+  double a0 = 0.0, a1 = 0.0;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + st < tot; e += 2 * st) {
+    const double x0 = X[(e / cols) * ld + e % cols], x1 = X[((e + st) / cols) * ld + (e + st) % cols];
+    a0 = fma(x0, x0, a0);
+    a1 = fma(x1, x1, a1);
+  }
+  if (e < tot) {
+    const double x0 = X[(e / cols) * ld + e % cols];
+    a0 = fma(x0, x0, a0);
+  }
+  double acc = a0 + a1;
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// One warp.  err2(k) = r2 + sum_{i >= k} sig_i^2 (0-based, sig sorted descending) is the
+// squared error of the rank-k result; the smallest k in [1, k_trial] with
+// err2(k) <= eps^2 fro2 is chosen, else k_trial with grow = 1.  Lane j sums a contiguous
+// chunk of sig from its small end; the chunk totals of the lanes above j give its
+// starting suffix, and walking its chunk downwards it meets err2(i + 1) before adding
+// sig_i^2, so every k = 1 .. l is seen by exactly one lane.
+__global__ void tol_rank_kernel(const double* sig, int l, int k_trial, const double* r2_part, const double* fro2_part,
+                                double eps, TolResult* out) {
+  const int lane = threadIdx.x;
+  double r2 = 0.0, fro2 = 0.0;
+  for (int i = lane; i < kSqParts; i += 32) {
+    r2 += r2_part[i];
+    fro2 += fro2_part[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    fro2 += __shfl_xor_sync(0xffffffffu, fro2, o);
+  }
+  const int c = (l + 31) / 32;
+  const int i0 = min(l, lane * c), i1 = min(l, i0 + c);
+  double own = 0.0;
+  for (int i = i1 - 1; i >= i0; --i) own = fma(sig[i], sig[i], own);
+  // sum of the chunk totals of the lanes above this one: an inclusive suffix scan, read
+  // from the next lane (no subtraction, so the large head values do not round the tail)
+  double suf = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double v = __shfl_down_sync(0xffffffffu, suf, o);
+    if (lane + o < 32) suf += v;
+  }
+  double above = __shfl_down_sync(0xffffffffu, suf, 1);
+  if (lane == 31) above = 0.0;
+  const double thr = eps * eps * fro2;
+  double run = r2 + above;
+  int best = 0x7fffffff;
+  double best_err2 = 0.0;
+  for (int i = i1 - 1; i >= i0; --i) {
+    const int k = i + 1;  // run == err2(k) here
+    if (k <= k_trial && run <= thr) {
+      best = k;
+      best_err2 = run;
+    }
+    run = fma(sig[i], sig[i], run);
+  }
+  // smallest qualifying k over the warp (err2 is non-increasing in k)
+  int kmin = best;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+  const int owner = __ffs(__ballot_sync(0xffffffffu, best == kmin)) - 1;
+  const double e2 = __shfl_sync(0xffffffffu, best_err2, owner);
+  // err2(k_trial) for the case that no k qualifies: from the lane whose walk met it
+  double et = 0.0;
+  {
+    double r = r2 + above;
+    for (int i = i1 - 1; i >= i0; --i) {
+      if (i + 1 == k_trial) et = r;
+      r = fma(sig[i], sig[i], r);
+    }
+  }
+  const bool has_t = k_trial >= i0 + 1 && k_trial <= i1;
+  const int tl = __ffs(__ballot_sync(0xffffffffu, has_t)) - 1;
+  et = __shfl_sync(0xffffffffu, et, tl < 0 ? 0 : tl);
+  if (lane == 0) {
+    const bool found = kmin != 0x7fffffff;
+    out->k = found ? kmin : k_trial;
+    out->grow = found ? 0 : 1;
+    const double ee = found ? e2 : et;
+    out->err = fro2 > 0.0 ? sqrt(ee / fro2) : 0.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sq_sum(const double* X, int rows, int cols, int ld, double* part, cudaStream_t s) {
+  prof_begin(KC_TEBD, s);
+  sq_sum_kernel<<<kSqParts, 256, 0, s>>>(X, rows, cols, ld, part);
+  prof_end(KC_TEBD, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tol_rank(const double* sig, int l, int k_trial, const double* r2_part, const double* fro2_part,
+                            double eps, TolResult* out, cudaStream_t s) {
+  prof_begin(KC_SELECT, s);
+  tol_rank_kernel<<<1, 32, 0, s>>>(sig, l, k_trial, r2_part, fro2_part, eps, out);
+  prof_end(KC_SELECT, s);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tebd_product(const TebdProdBatch& b, cudaStream_t s) {
   if (b.count <= 0) return cudaSuccess;
