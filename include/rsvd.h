@@ -260,6 +260,37 @@ int rsvd_truncate_factored(int m, int r, int n, const void* X, int ldx, const vo
                            rsvd_info* info, void* cuda_stream);
 
 /*
+ * rsvd_sectors_adaptive_workspace_size - workspace bytes of
+ * rsvd_truncate_sectors_adaptive (ranks up to min(chi, m_b, n_b)).
+ */
+int rsvd_sectors_adaptive_workspace_size(int batch, const int* m, const int* n, int chi, const rsvd_params* p,
+                                         size_t* bytes);
+
+/*
+ * rsvd_truncate_sectors_adaptive - block-wise Alg. RSVD of a block-diagonal
+ * matrix with the global post-selection of the chi largest singular values
+ * (Sec. III.A), with per-block trial ranks found adaptively instead of guessed
+ * (the alternative route to the sector sizes that Sec. V proposes): after each
+ * selection, a block all of whose k'_b values were kept while
+ * k'_b < min(chi, m_b, n_b) may hold more values above the cut, so its trial
+ * rank is doubled (capped there) and only that block is compressed again (same
+ * Philox stream p->stream + b: its larger test matrix extends the previous
+ * one); until no block is saturated.  Each round ends with one device-to-host
+ * read of the kept counts and a synchronisation of the stream.
+ *   batch <= 64 blocks; A[b] (m_b x n_b, lda[b]) of p->prec (RSVD_F64 or
+ *   RSVD_F32);  k_trial  HOST in/out: first guesses, on return the final trial
+ *   ranks (an estimate for the next call);  S[b] (min(chi, m_b, n_b)), U[b]
+ *   (ldu[b] >= that), Vt[b] as for rsvd_truncate_batched;  k_out  DEVICE
+ *   int[batch], the kept counts;  rounds  HOST, the number of rounds.
+ * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_PRECISION,
+ * RSVD_ERR_WORKSPACE, RSVD_ERR_LAUNCH.
+ */
+int rsvd_truncate_sectors_adaptive(int batch, const int* m, const int* n, const void* const* A, const int* lda,
+                                   int* k_trial, const rsvd_params* p, int chi, double* const* S, void* const* U,
+                                   const int* ldu, void* const* Vt, const int* ldvt, int* k_out, int* rounds,
+                                   void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
  * rsvd_tol_workspace_size - workspace bytes of rsvd_truncate_tol.
  */
 int rsvd_tol_workspace_size(int m, int n, int k_max, const rsvd_params* p, size_t* bytes);

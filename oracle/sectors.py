@@ -69,3 +69,27 @@ def block_rsvd_global(blocks, chi, p, q, seed, ranks=None, policy="maximal", c=0
     res = [rsvd(A, kb, p, q, seed, stream=b) for b, (A, kb) in enumerate(zip(blocks, ranks))]
     kept = global_select([r[1] for r in res], chi)
     return [(U[:, :kb], s[:kb], Vt[:kb]) for (U, s, Vt), kb in zip(res, kept)], kept, ranks
+
+
+def block_rsvd_adaptive(blocks, chi, p, q, seed, ranks0):
+    """Adaptive per-block trial ranks (the fixed-error route to the sector sizes that
+    Sec. V proposes, here for the global top-chi cut): start from any trial ranks, select
+    the chi largest over all blocks; a block all of whose k'_b values were kept while
+    k'_b < min(chi, m_b, n_b) may hold more values above the cut, so its trial rank is
+    doubled (capped there) and the block compressed again (same Philox stream b: the
+    larger test matrix extends the previous one); repeat until no block is saturated.
+    Returns (factors, kept, ranks, rounds)."""
+    caps = [min(chi, *A.shape) for A in blocks]
+    ranks = [max(1, min(k, c)) for k, c in zip(ranks0, caps)]
+    res = [rsvd(A, kb, p, q, seed, stream=b) for b, (A, kb) in enumerate(zip(blocks, ranks))]
+    rounds = 1
+    while True:
+        kept = global_select([r[1] for r in res], chi)
+        grow = [b for b in range(len(blocks)) if kept[b] == ranks[b] and ranks[b] < caps[b]]
+        if not grow:
+            break
+        for b in grow:
+            ranks[b] = min(2 * ranks[b], caps[b])
+            res[b] = rsvd(blocks[b], ranks[b], p, q, seed, stream=b)
+        rounds += 1
+    return [(U[:, :kb], s[:kb], Vt[:kb]) for (U, s, Vt), kb in zip(res, kept)], kept, ranks, rounds

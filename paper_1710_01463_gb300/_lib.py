@@ -43,6 +43,8 @@ EXPORTED = (
     "rsvd_factored_workspace_size",
     "rsvd_truncate_factored",
     "rsvd_tol_workspace_size",
+    "rsvd_sectors_adaptive_workspace_size",
+    "rsvd_truncate_sectors_adaptive",
     "rsvd_truncate_tol",
     "rsvd_status_string",
     "rsvd_profile_enable",

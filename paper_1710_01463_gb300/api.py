@@ -220,6 +220,62 @@ def rsvd_truncate_batched(As, ks, p=8, q=2, seed=0, stream=0, chi_global=0, max_
     return U, S, Vt, plan.k_out, plan.info
 
 
+class AdaptiveSectorsPlan:
+    """Preallocated outputs and workspace of rsvd_truncate_sectors_adaptive for fixed block
+    shapes: block-wise RSVD with the global top-chi cut and per-block trial ranks grown
+    until no block is saturated.  `ranks` carries the last trial ranks into the next run
+    (estimates from the previous iteration)."""
+
+    def __init__(self, shapes, chi, ranks0, p=8, q=2, seed=0, stream=0, dtype=torch.float64, device="cuda",
+                 max_sweeps=0):
+        lib = _lib.load()
+        self.shapes = [(int(m), int(n)) for m, n in shapes]
+        self.chi = int(chi)
+        self.dtype = dtype
+        B = len(self.shapes)
+        caps = [min(self.chi, m, n) for m, n in self.shapes]
+        self.ranks = [max(1, min(int(k), c)) for k, c in zip(ranks0, caps)]
+        self.par = _params(1, p, q, _DTYPE_PREC[dtype], seed, stream, max_sweeps)
+        self.m_arr = _lib.int_array([s[0] for s in self.shapes])
+        self.n_arr = _lib.int_array([s[1] for s in self.shapes])
+        sz = ctypes.c_size_t(0)
+        _lib.check(lib.rsvd_sectors_adaptive_workspace_size(B, self.m_arr, self.n_arr, self.chi, ctypes.byref(self.par),
+                                                            ctypes.byref(sz)), "rsvd_sectors_adaptive_workspace_size")
+        self.work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=device)
+        out = torch.float64 if dtype == torch.float64 else torch.float32
+        self.U = [torch.empty((m, c), dtype=out, device=device) for (m, _), c in zip(self.shapes, caps)]
+        self.S = [torch.empty((c,), dtype=torch.float64, device=device) for c in caps]
+        self.Vt = [torch.empty((c, n), dtype=out, device=device) for (_, n), c in zip(self.shapes, caps)]
+        self.info = torch.zeros((B, _lib.INFO_INTS), dtype=torch.int32, device=device)
+        self.k_out = torch.zeros((B,), dtype=torch.int32, device=device)
+        self.S_ptr = _lib.ptr_array([t.data_ptr() for t in self.S])
+        self.U_ptr = _lib.ptr_array([t.data_ptr() for t in self.U])
+        self.V_ptr = _lib.ptr_array([t.data_ptr() for t in self.Vt])
+        self.ldu = _lib.int_array([t.stride(0) for t in self.U])
+        self.ldv = _lib.int_array([t.stride(0) for t in self.Vt])
+        self.rounds = 0
+
+    def run(self, As, stream=None):
+        lib = _lib.load()
+        for A, (m, n) in zip(As, self.shapes):
+            _require_cuda(A)
+            if tuple(A.shape) != (m, n) or A.dtype != self.dtype or A.stride(1) != 1:
+                raise ValueError("block shape / dtype / layout mismatch")
+        A_ptr = _lib.ptr_array([A.data_ptr() for A in As])
+        lda = _lib.int_array([A.stride(0) for A in As])
+        kt = _lib.int_array(self.ranks)
+        rounds = ctypes.c_int(0)
+        rc = lib.rsvd_truncate_sectors_adaptive(len(As), self.m_arr, self.n_arr, A_ptr, lda, kt, ctypes.byref(self.par),
+                                                self.chi, self.S_ptr, self.U_ptr, self.ldu, self.V_ptr, self.ldv,
+                                                ctypes.c_void_p(self.k_out.data_ptr()), ctypes.byref(rounds),
+                                                ctypes.c_void_p(self.work.data_ptr()), ctypes.c_size_t(self.work.numel()),
+                                                ctypes.c_void_p(self.info.data_ptr()), _stream_handle(stream))
+        _lib.check(rc, "rsvd_truncate_sectors_adaptive")
+        self.ranks = [int(kt[i]) for i in range(len(As))]
+        self.rounds = rounds.value
+        return self.U, self.S, self.Vt, self.k_out
+
+
 def rsvd_truncate_backward_batched(As, Us, Ss, Vts, Ubars=None, Sbars=None, Vtbars=None, max_iter=300, tol=None):
     """Abar for each matrix from its factors and the cotangents (see include/rsvd.h)."""
     lib = _lib.load()

@@ -787,6 +787,87 @@ int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* con
   return RSVD_OK;
 }
 
+int rsvd_sectors_adaptive_workspace_size(int batch, const int* m, const int* n, int chi, const rsvd_params* p,
+                                         size_t* bytes) {
+  if (!m || !n || !p || !bytes) return RSVD_ERR_NULL_POINTER;
+  if (batch < 1 || batch > kMaxJobs || chi < 1) return RSVD_ERR_INVALID_SIZE;
+  std::vector<int> cap(batch);
+  for (int b = 0; b < batch; ++b) cap[b] = std::min(chi, std::min(m[b], n[b]));
+  return rsvd_batched_workspace_size(batch, m, n, cap.data(), p, bytes);
+}
+
+int rsvd_truncate_sectors_adaptive(int batch, const int* m, const int* n, const void* const* A, const int* lda,
+                                   int* k_trial, const rsvd_params* p, int chi, double* const* S, void* const* U,
+                                   const int* ldu, void* const* Vt, const int* ldvt, int* k_out, int* rounds,
+                                   void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream) {
+  size_t need = 0;
+  int rc = rsvd_sectors_adaptive_workspace_size(batch, m, n, chi, p, &need);
+  if (rc) return rc;
+  if (!A || !lda || !k_trial || !S || !U || !ldu || !Vt || !ldvt || !k_out || !rounds || !work || !info)
+    return RSVD_ERR_NULL_POINTER;
+  if (is_tc(p->prec)) return RSVD_ERR_PRECISION;
+  if (((uintptr_t)work) % kAlign) return RSVD_ERR_WORKSPACE;
+  if (need > work_bytes) return RSVD_ERR_WORKSPACE;
+  std::vector<int> cap(batch), k(batch);
+  for (int b = 0; b < batch; ++b) {
+    cap[b] = std::min(chi, std::min(m[b], n[b]));
+    if (lda[b] < n[b] || ldu[b] < cap[b] || ldvt[b] < n[b]) return RSVD_ERR_INVALID_SIZE;
+    if (!A[b] || !S[b] || !U[b] || !Vt[b]) return RSVD_ERR_NULL_POINTER;
+    k[b] = std::max(1, std::min(k_trial[b], cap[b]));
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<int> todo(batch), kept(batch);
+  for (int b = 0; b < batch; ++b) todo[b] = b;
+  int r = 0;
+  for (;;) {
+    ++r;
+    // Alg. RSVD of the blocks whose trial rank changed (all of them in the first round);
+    // block b keeps Philox stream p->stream + b, so a larger trial extends its Omega
+    std::vector<Prob> probs(todo.size());
+    for (size_t t = 0; t < todo.size(); ++t) {
+      const int b = todo[t];
+      Prob& pr = probs[t];
+      std::memset(&pr, 0, sizeof(Prob));
+      pr.m = m[b]; pr.n = n[b]; pr.k = k[b];
+      pr.l = sample_width(m[b], n[b], k[b], p->p);
+      if (pr.l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+      pr.exact = use_exact_path(pr.m, pr.l);
+      pr.want_u = 1;
+      pr.A = A[b]; pr.lda = lda[b];
+      pr.S = S[b]; pr.U = U[b]; pr.ldu = ldu[b]; pr.Vt = Vt[b]; pr.ldvt = ldvt[b];
+      pr.seed = p->seed; pr.stream = p->stream + (uint64_t)b;
+      pr.info = info + b;
+      pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    }
+    rc = run_batched(probs, p, (char*)work, work_bytes, s);
+    if (rc) return rc;
+    // the chi largest over all blocks (Sec. III.A post-selection)
+    SelectBatch sb;
+    sb.count = batch;
+    sb.chi = chi;
+    sb.total = 0;
+    sb.k_out = k_out;
+    for (int b = 0; b < batch; ++b) {
+      sb.job[b] = SelectJob{S[b], k[b]};
+      sb.total += k[b];
+    }
+    RSVD_TRY(launch_select(sb, s));
+    RSVD_TRY(cudaMemcpyAsync(kept.data(), k_out, sizeof(int) * batch, cudaMemcpyDeviceToHost, s));
+    RSVD_TRY(cudaStreamSynchronize(s));
+    // a block all of whose values were kept may hold more above the cut: double its rank
+    todo.clear();
+    for (int b = 0; b < batch; ++b)
+      if (kept[b] == k[b] && k[b] < cap[b]) {
+        k[b] = std::min(2 * k[b], cap[b]);
+        todo.push_back(b);
+      }
+    if (todo.empty()) break;
+  }
+  for (int b = 0; b < batch; ++b) k_trial[b] = k[b];
+  *rounds = r;
+  return RSVD_OK;
+}
+
 int rsvd_truncate(int m, int n, const void* A, int lda, const rsvd_params* p, double* S, void* U, int ldu, void* Vt,
                   int ldvt, void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream) {
   if (!p) return RSVD_ERR_NULL_POINTER;

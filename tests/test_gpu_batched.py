@@ -4,7 +4,7 @@ import pytest
 
 from gpu_util import need_gpu, sigma_tol, torch
 from oracle import rsvd as orsvd
-from oracle.sectors import block_rsvd_global, global_select
+from oracle.sectors import block_rsvd_adaptive, block_rsvd_global, global_select
 from paper_1710_01463_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -71,3 +71,36 @@ def test_global_selection_ties(api):
     got = k_out.cpu().tolist()
     assert sum(got) == 7
     assert got == global_select([s.cpu().numpy() for s in S], 7)
+
+
+@pytest.mark.parametrize("start,dtype", [("ones", torch.float64), ("even", torch.float64), ("ones", torch.float32)])
+def test_adaptive_sector_ranks_match_oracle(api, start, dtype):
+    # per-block trial ranks grown until no block is saturated.  FP64: the same rounds,
+    # final ranks and kept counts as the oracle (integer work, bit-exact) and its values at
+    # the FP64 bar.  FP32: values near the cut lie closer than FP32 rounding (3.7e-5
+    # sigma_1 apart), so the unique parts are checked: the counts are the selection over
+    # the GPU's own values, no block ends saturated below its cap, and every kept value is
+    # within 2e-5 sigma_1 of the oracle's
+    blocks = small_sectors(9, 4)
+    chi = 40
+    r0 = [1] * len(blocks) if start == "ones" else [max(1, chi // len(blocks))] * len(blocks)
+    plan = api.AdaptiveSectorsPlan([b.shape for b in blocks], chi, r0, p=8, q=2, seed=5, dtype=dtype)
+    U, S, Vt, k_out = plan.run([torch.from_numpy(b).to(dtype).cuda() for b in blocks])
+    torch.cuda.synchronize()
+    res, kept, ranks, rounds = block_rsvd_adaptive(blocks, chi, 8, 2, 5, r0)
+    got_kept = k_out.cpu().tolist()
+    smax = max(float(r[1][0]) for r in res if r[1].size)
+    if dtype == torch.float64:
+        assert got_kept == kept
+        assert plan.ranks == ranks and plan.rounds == rounds
+    else:
+        assert global_select([s.cpu().numpy()[:r] for s, r in zip(S, plan.ranks)], chi) == got_kept
+        for kb, r, blk in zip(got_kept, plan.ranks, blocks):
+            assert kb < r or r == min(chi, *blk.shape)
+    for b in range(len(blocks)):
+        kb = min(kept[b], got_kept[b])
+        ref = res[b][1][:kb]
+        got = S[b].cpu().numpy()[:kb]
+        tol = (1e-10 * np.abs(ref) + 1e-14 * smax) if dtype == torch.float64 else 2e-5 * smax
+        assert np.all(np.abs(got - ref) <= tol)
+    assert all(d["status"] == 0 for d in api.info_dicts(plan.info))
