@@ -190,7 +190,7 @@ def step_flops(info):
     for j, lay in enumerate(bond_shapes()):
         for b, (m, n, k, l) in enumerate(lay):
             rec = info[j][0][b]  # (layer, compression, bond) records
-            sweeps, rots, qr_cols = int(rec[3]), int(rec[5]), int(rec[6])
+            sweeps, rots, qr_cols, falls = int(rec[3]), int(rec[5]), int(rec[6]), int(rec[2])
             # the bond update forms no U: after the first orthonormalisation only the leading
             # r columns of Q carry the range (r = reported qr_columns, else l), and the products,
             # the later QRs, the contraction B_i B_{i+1} (over the nonzero Schmidt values,
@@ -210,6 +210,9 @@ def step_flops(info):
                         flops["gram"] += 2 * rows * l * l
                         flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
                         flops["gemm"] += 2 * rows * l * l
+                # orthonormalisations whose CholeskyQR2 broke down ran Householder QR as well
+                # (device count; which ones is not recorded: rows (m + n) / 2, the effective width)
+                flops["householder"] += falls * hh_flops((m + n) // 2, r, r)
             svd_b_flops(flops, n, k, l, sweeps, rots)
     return flops
 
@@ -242,7 +245,7 @@ def product_step_flops(info, flops):
         for w in range(WIDTH):
             for b, (m, n, k, l) in enumerate(lay):
                 rec = info[j][w][b]
-                sweeps, rots, qr_cols = int(rec[3]), int(rec[5]), int(rec[6])
+                sweeps, rots, qr_cols, falls = int(rec[3]), int(rec[5]), int(rec[6]), int(rec[2])
                 rr = min(l, qr_cols) if qr_cols > 0 else l
                 r = K_TERMS * k
                 flops["gemm"] += 2.0 * (m + n) * r * l + (2 * Q_POW + 1) * 2.0 * (m + n) * r * rr
@@ -256,6 +259,7 @@ def product_step_flops(info, flops):
                         flops["gram"] += 2 * rows * l * l
                         flops["cholesky"] += 2 * (2.0 * l ** 3 / 3.0)
                         flops["gemm"] += 2 * rows * l * l
+                flops["householder"] += falls * hh_flops((m + n) // 2, rr, rr)
                 svd_b_flops(flops, n, k, l, sweeps, rots)
     return flops
 
@@ -345,7 +349,10 @@ def run_ours(args):
         launches += cnt * per_group.get(name, 1)
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(dom_ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(dom_ach / FP64_PEAK_TFLOPS, 4),
-                "traffic": traffic_of("tebd", dom)[0], "traffic_source": traffic_of("tebd", dom)[1],
+                # the captured traffic belongs to the default chain (its 256-row samples) only
+                "traffic": traffic_of("tebd" if model_name() == "tfim" and UPDATE == "block" else WORKLOAD, dom)[0],
+                "traffic_source": traffic_of("tebd" if model_name() == "tfim" and UPDATE == "block" else WORKLOAD,
+                                             dom)[1],
                 "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s; "
                                "DFMA microbenchmark on this GB300: 1.20 TFLOP/s)"}
 
@@ -679,8 +686,17 @@ def run_workload(args):
         config["policy"] = "previous step's kept count + 16 (first step: maximal)"
         plan = api.BatchedPlan([tuple(A.shape) for A in As], ks, p, q, 103 + 1000 * rank, 0, dtype, dev,
                                chi_global=512)
+    adaptive = wl == "sectors" and args.policy == "adaptive"
+    if adaptive:
+        # the paper's chi / N (c = 0) as the first guess of every step; saturated blocks grow
+        r0 = [max(1, 512 // len(As))] * len(As)
+        plan = api.AdaptiveSectorsPlan([tuple(A.shape) for A in As], 512, r0, p, q, 103 + 1000 * rank, 0, dtype, dev)
+        config["policy"] = ("adaptive: first guess chi / N = 16 every step, the ranks of saturated blocks doubled "
+                            "until none is (flops counted for the final round only)")
 
     def step():
+        if adaptive:
+            plan.ranks = list(r0)
         plan.run(As)
         if wl == "grad":
             Ub = [2.0 * (W @ (W.T @ U)) for U in plan.U]
@@ -714,6 +730,8 @@ def run_workload(args):
     ms_per_step = tot_ms / args.steps
     units_per_step = 1 if wl == "sectors" else B
     value = ws * units_per_step / (ms_per_step / 1e3)
+    if adaptive:
+        ks = list(plan.ranks)
 
     # algorithmic work
     fl = {"gemm": 0.0, "gram": 0.0, "cholesky": 0.0, "householder": 0.0, "jacobi": 0.0, "tcgemm": 0.0, "ozgemm": 0.0}
@@ -788,6 +806,9 @@ def run_workload(args):
               "device_status": {"max_jacobi_sweeps": int(stat[..., 3].max()),
                                 "mean_jacobi_sweeps": round(float(stat[..., 3].mean()), 3),
                                 "nonzero_status": int((stat[..., 0] != 0).sum())}}
+    if adaptive:
+        result["device_status"]["adaptive_rounds"] = plan.rounds
+        result["device_status"]["final_trial_ranks"] = list(plan.ranks)
     if rank == 0 and not args.no_extras:
         # e2e: inputs from pinned host memory, results back to the host, every step
         hA = [A.cpu().pin_memory() for A in As]
@@ -812,7 +833,8 @@ def run_workload(args):
         sv = np.linalg.svd(A0, compute_uv=False)
         s_gpu = plan.S[0].cpu().numpy()
         big = sv[:k0] > 1e-8 * sv[0]
-        u0, v0 = plan.U[0].double().cpu().numpy(), plan.Vt[0].double().cpu().numpy()
+        s_gpu = s_gpu[:k0]
+        u0, v0 = plan.U[0][:, :k0].double().cpu().numpy(), plan.Vt[0][:k0].double().cpu().numpy()
         err = np.linalg.norm(A0 - (u0 * s_gpu) @ v0)
         dtr = np.sqrt(np.sum(sv[k0:] ** 2))
         _, so, _ = orsvd.rsvd(A0, k0, p, q, 103, 0)
@@ -915,7 +937,7 @@ def main():
     ap.add_argument("--workload", default="tebd", choices=["tebd", "dense", "mixed", "sectors", "grad"],
                     help="tebd (default): the TEBD bond-update workload; the others time the remaining configurations")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32"], help="mixed workload: operand precision")
-    ap.add_argument("--policy", default="estimate", choices=["estimate", "maximal"],
+    ap.add_argument("--policy", default="estimate", choices=["estimate", "maximal", "adaptive"],
                     help="sectors workload: per-block trial ranks")
     ap.add_argument("--chain-length", type=int, default=64,
                     help="L (default 64); a shorter chain keeps the 256 x 256 central bonds (profiling case)")
