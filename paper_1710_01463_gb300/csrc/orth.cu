@@ -424,30 +424,27 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
 
 // ---------------------------------------------------------------- blocked Householder QR
 // Same factorization as householder_kernel, blocked by panels of kNb columns
-// (compact WY form, H_j0 ... H_j1-1 = I - V T V^T): rank 0 of the cluster
-// gathers the panel's rows through distributed shared memory and factors it
-// alone (block-level barriers only), every CTA then applies I - V T^T V^T to
-// its rows of the trailing columns: partial products V^T Y per CTA, each CTA
-// sums and transforms one slice of the columns, and the slices are exchanged.
-// Q is accumulated backwards panel by panel the same way.  Four cluster
-// barriers per panel instead of three per column.
+// (compact WY form, H_j0 ... H_j1-1 = I - V T V^T): the cluster factors the
+// panel together, each CTA on its own rows (two cluster barriers per column:
+// one CTA factoring the panel alone was bound by its SM's FP64 issue, 82% of
+// the kernel's cycles), then every CTA applies I - V T^T V^T to its rows of
+// the trailing columns: partial products V^T Y per CTA, each CTA sums and
+// transforms one slice of the columns, and the slices are exchanged.  Q is
+// accumulated backwards panel by panel the same way.
 constexpr int kNb = 16;
 constexpr int kPanelMaxCluster = 8;  // the blocked kernel runs on portable cluster sizes
 // shared memory of the blocked kernel: up to about 110 KB two CTAs share an SM;
 // above, one CTA per SM, which still beats the column kernel by far
-constexpr size_t kPanelSmemMax = 220 * 1024;  // with the kernel's 4.6 KB of static shared memory, within 227 KB
+constexpr size_t kPanelSmemMax = 218 * 1024;  // with the kernel's 6 KB of static shared memory, within 227 KB
 
 struct PanelLayout {
   size_t ys, vo, wp, ws, alpha, total;  // shared-memory offsets in doubles
 };
 
-constexpr int kPanStride = kNb + 1;  // panel rows in shared memory, padded against bank conflicts
-
 // Shared memory: own rows of Y (then Q) and of V, one V^T Y buffer, T^T W and
-// the reflector scalars.  Rank 0 factors the panel (one row per thread) in the
-// region of the two V^T Y buffers, which are idle at that point; the T
-// matrices of all panels are kept in the matrix's global scratch (hq,
-// L2-resident) for the accumulation of Q.
+// the reflector scalars; the T matrices of all panels are kept in the
+// matrix's global scratch (hq, L2-resident) for the accumulation of Q.  A CTA
+// holds at most 64 rows (two per lane of a column's warp).
 __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) {
   const int rs = (rows + csize - 1) / csize;
   PanelLayout L;
@@ -456,29 +453,10 @@ __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) 
   L.vo = o; o += (size_t)rs * l;
   L.wp = o;
   L.ws = o + (size_t)kNb * l;
-  const size_t wbuf = 2 * (size_t)kNb * l, pan = (size_t)rows * kPanStride;
-  o += wbuf > pan ? wbuf : pan;
+  o += 2 * (size_t)kNb * l;
   L.alpha = o; o += (size_t)l;
   L.total = o;
   return L;
-}
-
-// Sums kNb = 16 per-lane values over a warp by recursive halving (16 shuffles
-// instead of 80): lanes 2i and 2i + 1 return the warp's sum of value i.
-__device__ __forceinline__ double warp_reduce_scatter16(double (&a)[kNb], int lane) {
-  static_assert(kNb == 16, "the halving schedule assumes 16 values");
-#pragma unroll
-  for (int lev = 0; lev < 4; ++lev) {
-    const int off = 16 >> lev, half = 8 >> lev;
-    const bool up = (lane & off) != 0;
-#pragma unroll
-    for (int k = 0; k < half; ++k) {
-      const double send = up ? a[k] : a[k + half];
-      const double keep = up ? a[k + half] : a[k];
-      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
 }
 
 // sum over own rows rr0 .. nr-1 of a[rr * ld] * b[rr * ld] (a column of V
@@ -591,12 +569,14 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   double* alpha = sm + L.alpha;
   double* Tall = J.hq;         // T of every panel, npanel x kNb x kNb (global scratch)
   __shared__ double red[kHhThreads / 32][2];
-  __shared__ double red1[kHhThreads / 32];
-  __shared__ double red16[kHhThreads / 32][kNb];
   __shared__ double fin[kNb];
   __shared__ double Ts[kNb][kNb];  // T of the current panel
   __shared__ double x0s;
   __shared__ double sc[2];
+  __shared__ double npart[kPanelMaxCluster];       // the cluster's partial norms of a panel column
+  __shared__ double spart[kPanelMaxCluster][kNb];  // the cluster's partial products v^T x_c
+  __shared__ double vbuf[64];                      // v on the own rows (rs <= 64)
+  __shared__ double Gv[kNb][kNb];                  // V^T V of the panel (strictly upper part)
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = kHhThreads / 32;
 
   for (int e = tid; e < nr * l; e += kHhThreads) {
@@ -659,116 +639,127 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       npanel_used = p;
       break;  // identical decision in every CTA of the cluster
     }
-    if (rank == 0) {
-      // one panel row per thread (rows <= kHhThreads is a launch condition):
-      // x[c] = Pan[tid][c] = Y[j0 + tid, j0 + c]; columns c < jj are replaced by
-      // the reflectors v_c as they are formed.  FP64 issue is the scarce
-      // resource (a warp instruction holds the SM's FP64 pipe for 16 cycles):
-      // only the warps that hold panel rows compute, and the reflector scalars
-      // and T's column are formed by warp 0 alone.
-      double* x = Wp + (size_t)tid * kPanStride;
-      const int r = j0 + tid;
-      const bool live = tid < R;
-      const int nlw = (R + 31) / 32;  // warps holding panel rows
-      const bool wlive = warp < nlw;
-      if (live) {
-        const int owner = r / rs;
-        const double* src = cluster.map_shared_rank(Ys, owner) + (size_t)(r - owner * rs) * l + j0;
-#pragma unroll
-        for (int c = 0; c < kNb; ++c) x[c] = c < nb ? src[c] : 0.0;
-      }
-      if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = 0.0;
+    {
+      // The panel is factored by the whole cluster: warp c holds panel column c of
+      // this CTA's own rows (lane and lane + 32), so the FP64 work of the reflections
+      // is spread over the cluster's SMs.  Per column jj two cluster barriers: after
+      // the partial norms (and the diagonal entry), and after the partial products
+      // v^T x_c.  Partials are pushed into every CTA's shared memory before the
+      // barrier, so the reads after it are local; every CTA sums them in the same
+      // fixed order and forms the same scalars, T and alpha.  A slot is rewritten
+      // only after a later barrier that every reader of its previous value passed.
+      static_assert(kHhThreads / 32 == kNb, "one warp per panel column");
+      const int c = warp;
+      const int rA = lane, rB = lane + 32;
+      const bool inA = rA < nr, inB = rB < nr;
+      const int gA = r0 + rA, gB = r0 + rB;
+      double xA = (inA && c < nb) ? Ys[rA * l + j0 + c] : 0.0;
+      double xB = (inB && c < nb) ? Ys[rB * l + j0 + c] : 0.0;
       for (int jj = 0; jj < nb; ++jj) {
-        if (wlive) {  // squared norm of column jj over panel rows jj .. R-1
-          const double xj = live ? x[jj] : 0.0;
-          double a = tid >= jj ? xj * xj : 0.0;
+        const int gd = j0 + jj;  // the diagonal row of column jj
+        if (c == jj) {
+          double a = (inA && gA >= gd ? xA * xA : 0.0) + (inB && gB >= gd ? xB * xB : 0.0);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-          if (lane == 0) red1[warp] = a;
-          if (tid == jj) x0s = xj;
-        }
-        __syncthreads();
-        if (warp == 0) {
-          double a = lane < nlw ? red1[lane] : 0.0;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-          if (lane == 0) {
-            // a >= +0: sign tests on the bit patterns (an FP64 compare-and-branch
-            // costs hundreds of cycles on this part), ||x|| = a rsqrt(a)
-            const double x0 = x0s;
-            double al = 0.0, inv = 0.0;
-            if (__double_as_longlong(a) > 0) {
-              const double nx = a * rsqrt(a);
-              al = __double_as_longlong(x0) >= 0 ? -nx : nx;
-              const double w0 = x0 - al;
-              const double vn2 = fma(w0, w0, fma(-x0, x0, a));
-              inv = __double_as_longlong(vn2) > 0 ? rsqrt(vn2) : 0.0;
-            }
-            sc[0] = inv;
-            sc[1] = (x0 - al) * inv;  // v at row jj
-            alpha[j0 + jj] = al;
-            Ts[jj][jj] = 2.0;
+          if (lane < C) *cluster.map_shared_rank(&npart[rank], lane) = a;  // lane q pushes to CTA q
+          if (gd >= r0 && gd < r0 + nr) {  // this CTA holds the diagonal entry
+            const int rd = gd - r0;
+            const double xd = __shfl_sync(0xffffffffu, rd < 32 ? xA : xB, rd & 31);
+            if (lane < C) *cluster.map_shared_rank(&x0s, lane) = xd;
           }
         }
-        __syncthreads();
-        double v = 0.0;
-        if (wlive) {
-          // this row's entry of the unit reflector v (zero above the diagonal),
-          // then one reduction of kNb slots: slot c = sum over rows of x[c] v,
-          // which is v_c^T v (a column of T) for c < jj and v^T Y[:, c] for c > jj
-          v = tid == jj ? sc[1] : (live && tid > jj) ? x[jj] * sc[0] : 0.0;
-          double sl[kNb];
+        cluster.sync();
+        if (tid == 0) {
+          // sum of the partials by a fixed tree; sign tests on the bit patterns (an
+          // FP64 compare-and-branch costs hundreds of cycles on this part), and
+          // ||x|| = a rsqrt(a)
+          double pv[kPanelMaxCluster];
 #pragma unroll
-          for (int c = 0; c < kNb; ++c) sl[c] = (live && c != jj) ? x[c] * v : 0.0;
-          const double part = warp_reduce_scatter16(sl, lane);
-          if ((lane & 1) == 0) red16[warp][lane >> 1] = part;
+          for (int q = 0; q < kPanelMaxCluster; ++q) pv[q] = q < C ? npart[q] : 0.0;
+#pragma unroll
+          for (int w2 = 1; w2 < kPanelMaxCluster; w2 <<= 1)
+#pragma unroll
+            for (int q = 0; q + w2 < kPanelMaxCluster; q += 2 * w2) pv[q] += pv[q + w2];
+          const double a = pv[0], x0 = x0s;
+          double al = 0.0, inv = 0.0;
+          if (__double_as_longlong(a) > 0) {
+            const double nx = a * rsqrt(a);
+            al = __double_as_longlong(x0) >= 0 ? -nx : nx;
+            const double w0 = x0 - al;
+            const double vn2 = fma(w0, w0, fma(-x0, x0, a));
+            inv = __double_as_longlong(vn2) > 0 ? rsqrt(vn2) : 0.0;
+          }
+          sc[0] = inv;
+          sc[1] = (x0 - al) * inv;  // v at the diagonal row
+          alpha[gd] = al;
         }
         __syncthreads();
-        if (warp == 0) {
-          double pw[kHhThreads / 32];  // the warps' partials, summed by a fixed tree
-#pragma unroll
-          for (int q = 0; q < kHhThreads / 32; ++q) pw[q] = (lane < kNb && q < nlw) ? red16[q][lane] : 0.0;
-#pragma unroll
-          for (int w2 = 1; w2 < kHhThreads / 32; w2 <<= 1)
-#pragma unroll
-            for (int q = 0; q + w2 < kHhThreads / 32; q += 2 * w2) pw[q] += pw[q + w2];
-          const double f = pw[0];
-          if (lane < kNb) fin[lane] = lane > jj ? -2.0 * f : f;
-          // T[0:jj, jj] = -2 T[0:jj, 0:jj] (V[:, 0:jj]^T v): lane i sums q = i .. jj-1, two chains
-          double t0 = 0.0, t1 = 0.0;
-          int q = 0;
-          for (; q + 1 < jj; q += 2) {
-            const double fq0 = __shfl_sync(0xffffffffu, f, q), fq1 = __shfl_sync(0xffffffffu, f, q + 1);
-            if (lane <= q) t0 = fma(Ts[lane][q], fq0, t0);
-            if (lane <= q + 1) t1 = fma(Ts[lane][q + 1], fq1, t1);
-          }
-          if (q < jj) {
-            const double fq0 = __shfl_sync(0xffffffffu, f, q);
-            if (lane <= q) t0 = fma(Ts[lane][q], fq0, t0);
-          }
-          if (lane < jj) Ts[lane][jj] = -2.0 * (t0 + t1);
+        if (c == jj) {  // the unit reflector v on the own rows (zero above the diagonal)
+          vbuf[rA] = !inA ? 0.0 : gA == gd ? sc[1] : gA > gd ? xA * sc[0] : 0.0;
+          vbuf[rB] = !inB ? 0.0 : gB == gd ? sc[1] : gB > gd ? xB * sc[0] : 0.0;
         }
         __syncthreads();
-        if (live) {
-          for (int c = jj + 1; c < nb; ++c) x[c] = fma(fin[c], v, x[c]);
-          x[jj] = v;
+        const double vA = vbuf[rA], vB = vbuf[rB];
+        {  // v^T x_c: for c < jj the T column's V_c^T v, for c > jj the reflection's
+          double sp = (c != jj && c < nb) ? fma(xA, vA, xB * vB) : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+          if (lane < C) *cluster.map_shared_rank(&spart[rank][c], lane) = sp;  // lane q pushes to CTA q
+        }
+        cluster.sync();
+        // one warp sums every column's partials (lane c, a fixed tree): an FP64
+        // instruction holds the SM's FP64 pipe for 16 cycles whatever its active
+        // lanes, so sixteen warps each summing one column would cost 16 times more
+        if (warp == 0 && lane < kNb) {
+          double pv[kPanelMaxCluster];
+#pragma unroll
+          for (int q = 0; q < kPanelMaxCluster; ++q) pv[q] = q < C ? spart[q][lane] : 0.0;
+#pragma unroll
+          for (int w2 = 1; w2 < kPanelMaxCluster; w2 <<= 1)
+#pragma unroll
+            for (int q = 0; q + w2 < kPanelMaxCluster; q += 2 * w2) pv[q] += pv[q + w2];
+          fin[lane] = -2.0 * pv[0];
+          if (lane < jj) Gv[lane][jj] = pv[0];  // v_lane^T v_jj, for T
+        }
+        __syncthreads();  // fin complete
+        if (c > jj && c < nb) {
+          xA = fma(fin[c], vA, xA);
+          xB = fma(fin[c], vB, xB);
+        } else if (c == jj) {
+          xA = vA;
+          xB = vB;
         }
       }
-      // V's rows go straight to their owners' V slices; T to the global copy
-      // that the accumulation of Q reads back
-      if (live) {
-        const int owner = r / rs;
-        double* dst = cluster.map_shared_rank(Vo, owner) + (size_t)(r - owner * rs) * l + j0;
-        for (int c = 0; c < nb; ++c) dst[c] = x[c];
+      // T of the panel (H_0 ... H_nb-1 = I - V T V^T, unit reflectors, tau = 2) by the
+      // UT transform: T^-1 = I / 2 + strictly upper (V^T V); lane c solves for
+      // column c by back substitution, T[c][c] = 2, T[i][c] = -2 sum_{j=i+1..c}
+      // (V^T V)[i][j] T[j][c]
+      if (warp == 0 && lane < kNb) {  // column cc of T, in place in Ts
+        const int cc = lane;
+#pragma unroll
+        for (int i = 0; i < kNb; ++i) Ts[i][cc] = (i == cc && cc < nb) ? 2.0 : 0.0;
+        if (cc < nb)
+          for (int i = cc - 1; i >= 0; --i) {
+            double t0 = 0.0, t1 = 0.0;
+            int j = i + 1;
+            for (; j + 1 <= cc; j += 2) {
+              t0 = fma(Gv[i][j], Ts[j][cc], t0);
+              t1 = fma(Gv[i][j + 1], Ts[j + 1][cc], t1);
+            }
+            if (j <= cc) t0 = fma(Gv[i][j], Ts[j][cc], t0);
+            Ts[i][cc] = -2.0 * (t0 + t1);
+          }
+      }
+      // the reflectors into this CTA's rows of V; T to the global copy that the
+      // accumulation of Q reads back
+      if (c < nb) {
+        if (inA) Vo[rA * l + j0 + c] = xA;
+        if (inB) Vo[rB * l + j0 + c] = xB;
       }
       __syncthreads();
-      if (tid < kNb * kNb) Tp[tid] = Ts[tid / kNb][tid % kNb];
+      if (rank == 0 && tid < kNb * kNb) Tp[tid] = Ts[tid / kNb][tid % kNb];
     }
-    cluster.sync();  // panel factored: V in place everywhere, alpha and T readable from rank 0
-    if (rank != 0) {
-      if (tid < nb) alpha[j0 + tid] = cluster.map_shared_rank(alpha, 0)[j0 + tid];
-      if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = cluster.map_shared_rank(&Ts[0][0], 0)[tid];
-    }
+    cluster.sync();  // panel factored: V in place everywhere
     __syncthreads();
     // trailing update of columns j0 + nb .. l-1: Y <- Y - V T^T (V^T Y); V is
     // zero on the rows above j0, which neither contribute nor change
@@ -924,7 +915,8 @@ cudaError_t launch_householder(const OrthBatch<T>& b, cudaStream_t s) {
   for (int i = 0; i < b.count; ++i) {
     const OrthJob<T>& J = b.job[i];
     const bool fits = panel_layout(J.rows, J.l, kPanelMaxCluster).total * sizeof(double) <= kPanelSmemMax;
-    if (J.l >= kNb && J.l <= 256 && J.rows <= kHhThreads && fits) pb.job[pb.count++] = J;
+    // at most 64 rows per CTA (two per lane of a column's warp) on clusters of kPanelMaxCluster
+    if (J.l >= kNb && J.l <= 256 && J.rows <= 64 * kPanelMaxCluster && fits) pb.job[pb.count++] = J;
     else cb.job[cb.count++] = J;
   }
   if (pb.count > 0) {
