@@ -57,7 +57,7 @@ __device__ __forceinline__ void round_pair(int r, int s, int lp, int& i, int& j)
 }
 
 struct JLayout {
-  int nc, np, npairs, lp;
+  int nc, np, npairs, lp, cs;
 };
 
 __host__ __device__ inline JLayout jlayout(int l, int n, int csize) {
@@ -66,13 +66,16 @@ __host__ __device__ inline JLayout jlayout(int l, int n, int csize) {
   L.np = (l + csize - 1) / csize;
   L.lp = l + (l & 1);
   L.npairs = L.lp / 2;
+  L.cs = csize;
   return L;
 }
 
 __host__ __device__ inline size_t jsmem_small(int l, const JLayout& L) {
-  // norms, nrm_part, gpart[2][npairs], order (int, padded to doubles),
-  // rotation cosines and sines [npairs] and flags (int, padded)
-  return sizeof(double) * ((size_t)2 * l + 4 * (size_t)L.npairs + (size_t)(l + 1) / 2 + 1 + (size_t)(L.npairs + 1) / 2 + 1);
+  // norms, nrm_part, gpart[2][cluster size][npairs] (every CTA's partial of every
+  // pair, pushed), order (int, padded to doubles), rotation cosines and sines
+  // [npairs] and flags (int, padded)
+  return sizeof(double) * ((size_t)2 * l + (2 * (size_t)L.cs + 2) * L.npairs + (size_t)(l + 1) / 2 + 1 +
+                           (size_t)(L.npairs + 1) / 2 + 1);
 }
 
 // Sum over the CTAs of the cluster of v[i] in their shared memory: every
@@ -103,9 +106,9 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   extern __shared__ double sm[];
   double* norms = sm;
   double* nrm_part = norms + l;
-  double* gpart = nrm_part + l;                 // [2][npairs]
-  int* order = (int*)(gpart + 2 * L.npairs);
-  double* rcs = gpart + 2 * L.npairs + (l + 1) / 2 + 1;  // per pair of the round: cos, sin, rotate?
+  double* gpart = nrm_part + l;                 // [2][C][npairs]: the CTAs' partials, pushed
+  int* order = (int*)(gpart + 2 * C * L.npairs);
+  double* rcs = gpart + 2 * C * L.npairs + (l + 1) / 2 + 1;  // per pair of the round: cos, sin, rotate?
   double* rsn = rcs + L.npairs;
   int* rfl = (int*)(rsn + L.npairs);
   double* Bs;
@@ -211,7 +214,11 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
     const int lpl = nlive + (nlive & 1);
     const int npl2 = lpl / 2;
     for (int r = 0; r < lpl - 1; ++r) {
-      double* gp = gpart + (r & 1) * L.npairs;
+      // this round's partials: slot [q][s] holds CTA q's partial of pair s, pushed by
+      // that CTA before the barrier, so the sums below read local shared memory.  A
+      // slot of parity r & 1 is rewritten two rounds later, after a barrier that
+      // every CTA reaches only after its sums of this round
+      double* gp = gpart + (r & 1) * C * L.npairs;
       for (int s = team; s < npl2; s += nteam) {
         int a, bq;
         round_pair(r, s, lpl, a, bq);
@@ -222,7 +229,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         }
 #pragma unroll
         for (int o = kTeam / 2; o > 0; o >>= 1) g += __shfl_xor_sync(tmask, g, o, kTeam);
-        if (tl == 0) gp[s] = g;
+        for (int q = tl; q < C; q += kTeam) cluster.map_shared_rank(gp, q)[rank * L.npairs + s] = g;
       }
       cluster.sync();
       // rotation scalars, one lane per pair, in as few warps as possible (a
@@ -237,7 +244,14 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         if (bq < nlive) {
           const int i = live[a], j = live[bq];
           const double al = norms[i], be = norms[j];
-          const double g = cluster_tree_sum(cluster, gp, s, C);
+          double pv[kMaxCluster];  // the CTAs' partials by the same fixed tree in every CTA
+#pragma unroll
+          for (int q = 0; q < kMaxCluster; ++q) pv[q] = q < C ? gp[q * L.npairs + s] : 0.0;
+#pragma unroll
+          for (int w = 1; w < kMaxCluster; w <<= 1)
+#pragma unroll
+            for (int q = 0; q + w < kMaxCluster; q += 2 * w) pv[q] += pv[q + w];
+          const double g = pv[0];
           // al, be > 0 and g^2 > tol^2 al be, compared as bit patterns (all >= +0)
           if (__double_as_longlong(al) > 0 && __double_as_longlong(be) > 0 &&
               __double_as_longlong(g * g) > __double_as_longlong(tol2 * (al * be))) {
