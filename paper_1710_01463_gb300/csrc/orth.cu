@@ -441,10 +441,14 @@ struct PanelLayout {
   size_t ys, vo, wp, ws, alpha, total;  // shared-memory offsets in doubles
 };
 
-// Shared memory: own rows of Y (then Q) and of V, one V^T Y buffer, T^T W and
+constexpr int kProdStride = 33;  // per-lane products of the panel columns, padded against bank conflicts
+
+// Shared memory: own rows of Y (then Q) and of V, one V^T Y buffer (which also
+// holds the panel's per-lane products while the panel is factored), T^T W and
 // the reflector scalars; the T matrices of all panels are kept in the
 // matrix's global scratch (hq, L2-resident) for the accumulation of Q.  A CTA
-// holds at most 64 rows (two per lane of a column's warp).
+// holds at most 64 rows (two per lane of a column's warp).  The static shared
+// memory is kept small: two CTAs of the 256-row TEBD samples share an SM.
 __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) {
   const int rs = (rows + csize - 1) / csize;
   PanelLayout L;
@@ -453,7 +457,8 @@ __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) 
   L.vo = o; o += (size_t)rs * l;
   L.wp = o;
   L.ws = o + (size_t)kNb * l;
-  o += 2 * (size_t)kNb * l;
+  const size_t wbuf = 2 * (size_t)kNb * l, prod = (size_t)kNb * kProdStride;
+  o += wbuf > prod ? wbuf : prod;
   L.alpha = o; o += (size_t)l;
   L.total = o;
   return L;
@@ -685,8 +690,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
           if (__double_as_longlong(a) > 0) {
             const double nx = a * rsqrt(a);
             al = __double_as_longlong(x0) >= 0 ? -nx : nx;
-            const double w0 = x0 - al;
-            const double vn2 = fma(w0, w0, fma(-x0, x0, a));
+            const double vn2 = 2.0 * fma(fabs(x0), nx, a);  // ||x - alpha e||^2 = 2 (a + |x0| ||x||)
             inv = __double_as_longlong(vn2) > 0 ? rsqrt(vn2) : 0.0;
           }
           sc[0] = inv;
@@ -700,11 +704,26 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
         }
         __syncthreads();
         const double vA = vbuf[rA], vB = vbuf[rB];
-        {  // v^T x_c: for c < jj the T column's V_c^T v, for c > jj the reflection's
-          double sp = (c != jj && c < nb) ? fma(xA, vA, xB * vB) : 0.0;
+        // v^T x_c (for c < jj the T column's V_c^T v, for c > jj the reflection's): each
+        // warp leaves its lanes' products, and warp 0 sums all columns (lanes 2i and
+        // 2i + 1 half of column i each) and pushes them, lane-parallel - 17 FP64
+        // instructions in one warp instead of a 5-level shuffle tree in each of 16
+        double (*prod)[kProdStride] = (double (*)[kProdStride])Wp;  // the V^T Y buffer is idle here
+        prod[c][lane] = (c != jj && c < nb) ? fma(xA, vA, xB * vB) : 0.0;
+        __syncthreads();
+        if (warp == 0) {
+          const int cc = lane >> 1, h = (lane & 1) * 16;
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
-          if (lane < C) *cluster.map_shared_rank(&spart[rank][c], lane) = sp;  // lane q pushes to CTA q
+          for (int t = 0; t < 16; t += 4) {
+            s0 += prod[cc][h + t];
+            s1 += prod[cc][h + t + 1];
+            s2 += prod[cc][h + t + 2];
+            s3 += prod[cc][h + t + 3];
+          }
+          double sp = (s0 + s1) + (s2 + s3);
+          sp += __shfl_xor_sync(0xffffffffu, sp, 1);
+          for (int q = lane & 1; q < C; q += 2) *cluster.map_shared_rank(&spart[rank][cc], q) = sp;
         }
         cluster.sync();
         // one warp sums every column's partials (lane c, a fixed tree): an FP64
@@ -734,21 +753,20 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       // UT transform: T^-1 = I / 2 + strictly upper (V^T V); lane c solves for
       // column c by back substitution, T[c][c] = 2, T[i][c] = -2 sum_{j=i+1..c}
       // (V^T V)[i][j] T[j][c]
-      if (warp == 0 && lane < kNb) {  // column cc of T, in place in Ts
+      if (warp == 0 && lane < kNb) {  // column cc of T in registers (fully unrolled, predicated)
         const int cc = lane;
+        double tc[kNb];
 #pragma unroll
-        for (int i = 0; i < kNb; ++i) Ts[i][cc] = (i == cc && cc < nb) ? 2.0 : 0.0;
-        if (cc < nb)
-          for (int i = cc - 1; i >= 0; --i) {
-            double t0 = 0.0, t1 = 0.0;
-            int j = i + 1;
-            for (; j + 1 <= cc; j += 2) {
-              t0 = fma(Gv[i][j], Ts[j][cc], t0);
-              t1 = fma(Gv[i][j + 1], Ts[j + 1][cc], t1);
-            }
-            if (j <= cc) t0 = fma(Gv[i][j], Ts[j][cc], t0);
-            Ts[i][cc] = -2.0 * (t0 + t1);
-          }
+        for (int i = 0; i < kNb; ++i) tc[i] = i == cc ? 2.0 : 0.0;
+#pragma unroll
+        for (int i = kNb - 2; i >= 0; --i) {
+          double t4[4] = {0.0, 0.0, 0.0, 0.0};  // four chains: a dependent FP64 FMA costs about 64 cycles
+#pragma unroll
+          for (int j = i + 1; j < kNb; ++j) t4[(j - i) & 3] = fma(j <= cc ? Gv[i][j] : 0.0, tc[j], t4[(j - i) & 3]);
+          if (i < cc) tc[i] = -2.0 * ((t4[0] + t4[1]) + (t4[2] + t4[3]));
+        }
+#pragma unroll
+        for (int i = 0; i < kNb; ++i) Ts[i][cc] = cc < nb ? tc[i] : 0.0;
       }
       // the reflectors into this CTA's rows of V; T to the global copy that the
       // accumulation of Q reads back
