@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The paper has no derivative; the loss and its gradient are this build's
-differentiable form of the truncated factorization.  Loss of the rank-k
+The paper has no derivative; the loss and its gradient below are a
+differentiable form of the truncated factorization defined here.  Loss of the rank-k
 truncation (U_k, s_k, V_k) of A:
 
     loss(A) = sum_{i<=k} w_i s_i + || W^T U_k ||_F^2,   W in R^{m x r}.

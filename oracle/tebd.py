@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 Models (Sec. III.B): the spin-S chain of Eq. ising_chain and the 2D cylinder of
 Eq. ising_cylinder mapped onto a chain of rings (d = 2^W).  The paper writes the
-couplings in x and the field in z; this build uses the unitarily equivalent form
+couplings in x and the field in z; this module uses the unitarily equivalent form
 with the axes exchanged (rotate x <-> z, then by pi about x to flip the field's
 sign), which has the same spectrum: at S = 1/2, H = -sum Z_j Z_{j+1} - h sum X_j.
 Open boundaries; the spin-1/2 chain is critical at h = 1.

@@ -2,8 +2,8 @@
 accumulation; Gram / Cholesky / SVD of B in FP64) against the FP64 oracle.
 
 The oracle factorises the same matrix as the GPU sees it (A rounded to bfloat16
-for the BF16 form) with its own FP64 test matrix.  The bounds are this build's
-stated errors for the reduced-precision forms (the thin operand is split into
+for the BF16 form) with its own FP64 test matrix.  The bounds are the stated
+errors of the reduced-precision forms (the thin operand is split into
 high and low parts, so only A's own rounding and FP32 accumulation remain):
 singular values within 1e-4 of sigma_1 (BF16 storage of A is exact input) and
 2e-3 relative for TF32 (A truncated to 10 mantissa bits); U and V^T orthonormal
