@@ -443,10 +443,12 @@ struct PanelLayout {
 
 constexpr int kProdStride = 33;  // per-lane products of the panel columns, padded against bank conflicts
 
-// Shared memory: own rows of Y (then Q) and of V, one V^T Y buffer (which also
-// holds the panel's per-lane products while the panel is factored), T^T W and
-// the reflector scalars; the T matrices of all panels are kept in the
-// matrix's global scratch (hq, L2-resident) for the accumulation of Q.  A CTA
+// Shared memory: own rows of Y (then Q), own rows of the current panel's V,
+// one V^T Y buffer (which also holds the panel's per-lane products while the
+// panel is factored), T^T W and the reflector scalars.  The V and T of all
+// panels are kept in the matrix's global scratch (hw and hq, L2-resident) for
+// the accumulation of Q: with only the current panel of V in shared memory,
+// two CTAs of 384-row samples fit an SM.  A CTA
 // holds at most 64 rows (two per lane of a column's warp).  The static shared
 // memory is kept small: two CTAs of the 256-row TEBD samples share an SM.
 __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) {
@@ -454,7 +456,7 @@ __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) 
   PanelLayout L;
   size_t o = 0;
   L.ys = o; o += (size_t)rs * l;
-  L.vo = o; o += (size_t)rs * l;
+  L.vo = o; o += (size_t)rs * kNb;
   L.wp = o;
   L.ws = o + (size_t)kNb * l;
   const size_t wbuf = 2 * (size_t)kNb * l, prod = (size_t)kNb * kProdStride;
@@ -464,19 +466,19 @@ __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) 
   return L;
 }
 
-// sum over own rows rr0 .. nr-1 of a[rr * ld] * b[rr * ld] (a column of V
-// times a column of Y), four independent chains: a dependent FP64 FMA costs
-// about 64 cycles on this part
-__device__ __forceinline__ double dot_rows(const double* a, const double* b, int ld, int rr0, int nr) {
+// sum over own rows rr0 .. nr-1 of a[rr * lda] * b[rr * ldb] (a column of the
+// panel's V times a column of Y), four independent chains: a dependent FP64 FMA
+// costs about 64 cycles on this part
+__device__ __forceinline__ double dot_rows2(const double* a, int lda, const double* b, int ldb, int rr0, int nr) {
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int rr = rr0;
   for (; rr + 3 < nr; rr += 4) {
-    s0 = fma(a[rr * ld], b[rr * ld], s0);
-    s1 = fma(a[(rr + 1) * ld], b[(rr + 1) * ld], s1);
-    s2 = fma(a[(rr + 2) * ld], b[(rr + 2) * ld], s2);
-    s3 = fma(a[(rr + 3) * ld], b[(rr + 3) * ld], s3);
+    s0 = fma(a[rr * lda], b[rr * ldb], s0);
+    s1 = fma(a[(rr + 1) * lda], b[(rr + 1) * ldb], s1);
+    s2 = fma(a[(rr + 2) * lda], b[(rr + 2) * ldb], s2);
+    s3 = fma(a[(rr + 3) * lda], b[(rr + 3) * ldb], s3);
   }
-  for (; rr < nr; ++rr) s0 = fma(a[rr * ld], b[rr * ld], s0);
+  for (; rr < nr; ++rr) s0 = fma(a[rr * lda], b[rr * ldb], s0);
   return (s0 + s1) + (s2 + s3);
 }
 
@@ -568,7 +570,8 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   const PanelLayout L = panel_layout(rows, l, C);
   extern __shared__ double sm[];
   double* Ys = sm + L.ys;      // own rows of Y, later of Q   (rs x l)
-  double* Vo = sm + L.vo;      // own rows of V              (rs x l)
+  double* Vo = sm + L.vo;      // own rows of the current panel's V (rs x kNb)
+  double* Vg = J.hw;           // V of every panel, all rows (rows x l, global scratch)
   double* Wp = sm + L.wp;      // partial V^T Y               (kNb x l)
   double* Ws = sm + L.ws;      // summed V^T Y, then T^T W    (kNb x l)
   double* alpha = sm + L.alpha;
@@ -584,10 +587,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   __shared__ double Gv[kNb][kNb];                  // V^T V of the panel (strictly upper part)
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = kHhThreads / 32;
 
-  for (int e = tid; e < nr * l; e += kHhThreads) {
-    Ys[e] = (double)J.Y[(size_t)r0 * l + e];
-    Vo[e] = 0.0;
-  }
+  for (int e = tid; e < nr * l; e += kHhThreads) Ys[e] = (double)J.Y[(size_t)r0 * l + e];
   // every CTA must apply the same column signs: columns left unfactored by an
   // early end keep alpha = 0 (sign +1) everywhere
   for (int c = tid; c < l; c += kHhThreads) alpha[c] = 0.0;
@@ -771,8 +771,14 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       // the reflectors into this CTA's rows of V; T to the global copy that the
       // accumulation of Q reads back
       if (c < nb) {
-        if (inA) Vo[rA * l + j0 + c] = xA;
-        if (inB) Vo[rB * l + j0 + c] = xB;
+        if (inA) {
+          Vo[rA * kNb + c] = xA;
+          Vg[(size_t)(r0 + rA) * l + j0 + c] = xA;
+        }
+        if (inB) {
+          Vo[rB * kNb + c] = xB;
+          Vg[(size_t)(r0 + rB) * l + j0 + c] = xB;
+        }
       }
       __syncthreads();
       if (rank == 0 && tid < kNb * kNb) Tp[tid] = Ts[tid / kNb][tid % kNb];
@@ -787,7 +793,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     if (wcols > 0) {
       for (int e = tid; e < nb * wcols; e += kHhThreads) {
         const int jj = e / wcols, c = c1 + e % wcols;
-        Wb[jj * l + c] = dot_rows(Vo + j0 + jj, Ys + c, l, rr0, nr);
+        Wb[jj * l + c] = dot_rows2(Vo + jj, kNb, Ys + c, l, rr0, nr);
       }
     }
     cluster.sync();
@@ -795,7 +801,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       cluster_sum_apply_t<false>(cluster, rank, C, Wb, Ws, Ts, nb, l, c1, wcols);
       for (int e = tid; e < (nr - rr0) * wcols; e += kHhThreads) {
         const int rr = rr0 + e / wcols, c = c1 + e % wcols;
-        Ys[rr * l + c] -= dot_panel(Vo + rr * l + j0, Ws + c, l, nb);
+        Ys[rr * l + c] -= dot_panel(Vo + rr * kNb, Ws + c, l, nb);
       }
     }
     __syncthreads();
@@ -818,15 +824,20 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     double* Wb = Wp;
     cluster.sync();  // the previous panel's remote reads of Wp are done
     if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = Tp[tid];
+    for (int e = tid; e < nr * kNb; e += kHhThreads) {  // this panel's V, own rows
+      const int rr = e / kNb, c = e % kNb;
+      Vo[e] = c < nb ? Vg[(size_t)(r0 + rr) * l + j0 + c] : 0.0;
+    }
+    __syncthreads();
     for (int e = tid; e < nb * wcols; e += kHhThreads) {
       const int jj = e / wcols, c = j0 + e % wcols;
-      Wb[jj * l + c] = dot_rows(Vo + j0 + jj, Ys + c, l, rr0, nr);
+      Wb[jj * l + c] = dot_rows2(Vo + jj, kNb, Ys + c, l, rr0, nr);
     }
     cluster.sync();
     cluster_sum_apply_t<true>(cluster, rank, C, Wb, Ws, Ts, nb, l, j0, wcols);
     for (int e = tid; e < (nr - rr0) * wcols; e += kHhThreads) {
       const int rr = rr0 + e / wcols, c = j0 + e % wcols;
-      Ys[rr * l + c] -= dot_panel(Vo + rr * l + j0, Ws + c, l, nb);
+      Ys[rr * l + c] -= dot_panel(Vo + rr * kNb, Ws + c, l, nb);
     }
     __syncthreads();
   }
