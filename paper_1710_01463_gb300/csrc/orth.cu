@@ -444,11 +444,12 @@ struct PanelLayout {
 constexpr int kProdStride = 33;  // per-lane products of the panel columns, padded against bank conflicts
 
 // Shared memory: own rows of Y (then Q), own rows of the current panel's V,
-// one V^T Y buffer (which also holds the panel's per-lane products while the
-// panel is factored), T^T W and the reflector scalars.  The V and T of all
+// one V^T Y buffer (partials, then the sums and T^T W; it also holds the
+// panel's per-lane products while the panel is factored) and the reflector
+// scalars.  The V and T of all
 // panels are kept in the matrix's global scratch (hw and hq, L2-resident) for
-// the accumulation of Q: with only the current panel of V in shared memory,
-// two CTAs of 384-row samples fit an SM.  A CTA
+// the accumulation of Q: with only the current panel of V in shared memory and
+// one V^T Y buffer, two CTAs of 384- and 512-row samples fit an SM.  A CTA
 // holds at most 64 rows (two per lane of a column's warp).  The static shared
 // memory is kept small: two CTAs of the 256-row TEBD samples share an SM.
 __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) {
@@ -457,9 +458,12 @@ __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) 
   size_t o = 0;
   L.ys = o; o += (size_t)rs * l;
   L.vo = o; o += (size_t)rs * kNb;
+  // the summed V^T Y (Ws) shares the partials' buffer (Wb): a CTA writes sums only
+  // into its own column slice, which no other CTA reads as partials, and the gather
+  // of the other slices follows the barrier after which no partial is read
   L.wp = o;
-  L.ws = o + (size_t)kNb * l;
-  const size_t wbuf = 2 * (size_t)kNb * l, prod = (size_t)kNb * kProdStride;
+  L.ws = o;
+  const size_t wbuf = (size_t)kNb * l, prod = (size_t)kNb * kProdStride;
   o += wbuf > prod ? wbuf : prod;
   L.alpha = o; o += (size_t)l;
   L.total = o;
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   double* Vo = sm + L.vo;      // own rows of the current panel's V (rs x kNb)
   double* Vg = J.hw;           // V of every panel, all rows (rows x l, global scratch)
   double* Wp = sm + L.wp;      // partial V^T Y               (kNb x l)
-  double* Ws = sm + L.ws;      // summed V^T Y, then T^T W    (kNb x l)
+  double* Ws = sm + L.ws;      // summed V^T Y, then T^T W (kNb x l; the same buffer as Wp)
   double* alpha = sm + L.alpha;
   double* Tall = J.hq;         // T of every panel, npanel x kNb x kNb (global scratch)
   __shared__ double red[kHhThreads / 32][2];
