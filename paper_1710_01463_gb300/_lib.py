@@ -128,6 +128,17 @@ def load():
     lib.rsvd_truncate_backward_batched.argtypes = [i, ip, ip, ip, i, pp, ip, pp, pp, ip, pp, ip, pp, ip, pp, pp, ip,
                                                    pp, ip, i, ctypes.c_double, vp, sz, vp, vp]
     lib.rsvd_truncate_noalloc.argtypes = [i, i, vp, i, par, vp, vp, i, vp, i, vp, vp]
+    dbl = ctypes.c_double
+    lib.tebd_product_workspace_size.argtypes = [i, i, ip, i, i, par, ctypes.POINTER(sz)]
+    lib.tebd_product_update.argtypes = [i, i, ip, i, ip, vp, sz, vp, sz, i, vp, vp, par, vp, vp, sz, vp, vp]
+    lib.rsvd_factored_workspace_size.argtypes = [i, i, i, par, ctypes.POINTER(sz)]
+    lib.rsvd_truncate_factored.argtypes = [i, i, i, vp, i, vp, i, par, vp, vp, i, vp, i, vp, sz, vp, vp]
+    lib.rsvd_tol_workspace_size.argtypes = [i, i, i, par, ctypes.POINTER(sz)]
+    lib.rsvd_truncate_tol.argtypes = [i, i, vp, i, dbl, i, par, vp, vp, i, vp, i, ip, ctypes.POINTER(dbl), vp, sz, vp,
+                                      vp]
+    lib.rsvd_sectors_adaptive_workspace_size.argtypes = [i, ip, ip, i, par, ctypes.POINTER(sz)]
+    lib.rsvd_truncate_sectors_adaptive.argtypes = [i, ip, ip, pp, ip, ip, par, i, pp, pp, ip, pp, ip, vp, ip, vp, sz,
+                                                   vp, vp]
     lib.rsvd_noalloc_scratch_bytes.argtypes = []
     lib.rsvd_noalloc_scratch_bytes.restype = ctypes.c_size_t
     lib.rsvd_profile_class_name.argtypes = [i]
