@@ -37,7 +37,7 @@ OZ_SLICE_PRODUCTS = 53  # BF16 slice products per FP64 product on the tensor cor
 # ncu capture of that kernel as it stands (summaries under profiles/); a kernel
 # changed since its capture has no entry (traffic null).
 TRAFFIC_PER_LAUNCH = {
-    ("tebd", "householder"): (7.99232e6, "profiles/householder_panel_tebd_L64_chi128.md"),
+    ("tebd", "householder"): (7.989504e6, "profiles/householder_panel_tebd_L64_chi128.md"),
     ("mixed", "gram"): (20.98e6, "profiles/gram_and_tc_gemm_mixed_bf16_16x4096.md"),
     ("mixed", "tcgemm"): (561.69e6 + 16.31e6, "profiles/gram_and_tc_gemm_mixed_bf16_16x4096.md"),
 }
