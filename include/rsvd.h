@@ -58,7 +58,7 @@ extern "C" {
 #define RSVD_WARN_CG            2   /* device (backward): a conjugate-gradient column did not converge (info.status) */
 
 /* rsvd_params.flags.  By default the FP64 products with A (the sketch, the
- * power iteration and the projection) of matrices with m, n <= 256 and
+ * power iteration and the projection) of matrices with m, n <= 1024 and
  * l <= 256 run on the tensor cores by exact slicing (see rsvd_gemm_f64_tc:
  * FP64-class error); RSVD_FLAG_F64_SIMT computes them with FP64 FMAs instead. */
 #define RSVD_FLAG_F64_SIMT      1
@@ -412,10 +412,12 @@ int rsvd_truncate_backward_batched(int batch, const int* m, const int* n, const 
  * minus the workspace.
  *   Scratch: a fixed 16 MiB array inside the library's device image
  *   (rsvd_noalloc_scratch_bytes), present on every GPU that loads the library
- *   until the process exits.  A matrix whose rsvd_workspace_size exceeds it is
- *   rejected with RSVD_ERR_SCRATCH_LIMIT before anything is launched (FP64:
- *   e.g. 256 x 256 at l = 138 needs about 2.3 MiB, 1024 x 1024 at l = 144 about
- *   10 MiB).
+ *   until the process exits.  FP64 products with A on the tensor cores need
+ *   the slices of A and A^T (up to about 480 x 480 at l = 144 within 16 MiB);
+ *   when they do not fit, the call takes the FP64-FMA products
+ *   (RSVD_FLAG_F64_SIMT, the same factorization within the FP64 bar), which
+ *   fit up to about 1280 x 1280 at l = 144.  A matrix that does not fit either
+ *   way is rejected with RSVD_ERR_SCRATCH_LIMIT before anything is launched.
  *   No cudaMalloc, cudaFree or other allocating call is made.  The first call
  *   on a device looks up the array's device address (cudaGetSymbolAddress,
  *   with that device current) and caches it; make that first call before any

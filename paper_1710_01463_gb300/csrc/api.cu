@@ -1359,11 +1359,19 @@ extern "C" int rsvd_truncate_noalloc(int m, int n, const void* A, int lda, const
   size_t need = 0;
   int rc = rsvd_workspace_size(m, n, p, &need);
   if (rc != RSVD_OK) return rc;
+  rsvd_params q = *p;
+  if (need > kStaticScratchBytes && p->prec == RSVD_F64 && !(p->flags & RSVD_FLAG_F64_SIMT)) {
+    // the FP64 products' tensor-core slices of A and A^T do not fit: the products
+    // with FP64 FMAs need none (the same factorization within the FP64 bar)
+    q.flags |= RSVD_FLAG_F64_SIMT;
+    rc = rsvd_workspace_size(m, n, &q, &need);
+    if (rc != RSVD_OK) return rc;
+  }
   if (need > kStaticScratchBytes) return RSVD_ERR_SCRATCH_LIMIT;
   void* scratch = nullptr;
   rc = static_scratch(&scratch);
   if (rc != RSVD_OK) return rc;
-  return rsvd_truncate(m, n, A, lda, p, S, U, ldu, Vt, ldvt, scratch, kStaticScratchBytes, info, cuda_stream);
+  return rsvd_truncate(m, n, A, lda, &q, S, U, ldu, Vt, ldvt, scratch, kStaticScratchBytes, info, cuda_stream);
 }
 
 extern "C" size_t rsvd_noalloc_scratch_bytes(void) { return kStaticScratchBytes; }

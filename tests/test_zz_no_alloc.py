@@ -75,3 +75,16 @@ def test_size_beyond_the_fixed_scratch_is_rejected(mods):
     A = torch.zeros((4096, 4096), dtype=torch.float64, device="cuda")
     rc, *_ = call_noalloc(_lib, A, 64, 16, 2, 0, 0)
     assert rc == _lib.RSVD_ERR_SCRATCH_LIMIT
+
+
+def test_tensor_core_slices_that_do_not_fit_fall_back_to_fma_products(mods):
+    # 768 x 768 at l = 138: the FP64 tensor-core path's slices of A and A^T need about 32 MiB,
+    # the FP64-FMA products about 10 MiB: the call runs, with the factorization of the
+    # workspace path within the FP64 bar
+    _lib, api = mods
+    A = torch.from_numpy(inputs.spectral_matrix(768, 768, inputs.exp_spectrum(768, 10.0), 21)).cuda()
+    res = call_noalloc(_lib, A, 128, 10, 2, 5, 1)
+    torch.cuda.synchronize()
+    assert res[0] == 0
+    compare(api, res, A, 128, 10, 2, 5, 1)
+
