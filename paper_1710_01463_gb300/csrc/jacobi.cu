@@ -92,6 +92,44 @@ __device__ __forceinline__ double cluster_tree_sum(cg::cluster_group& cluster, c
   return pv[0];
 }
 
+// Point-to-point signals between the CTAs of a cluster: a value stored into
+// another CTA's shared memory completes 8 bytes of that CTA's mbarrier, and the
+// receiver waits on its own mbarrier (cluster-scope acquire).
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void push_f64(double* slot, uint64_t* bar, int rank, double v) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(cluster_addr(slot, rank)),
+               "d"(v), "r"(cluster_addr(bar, rank))
+               : "memory");
+}
+__device__ __forceinline__ void mb_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+__device__ __forceinline__ void mb_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// gives up after about 2^28 cycles (0.13 s) and returns false
+__device__ __forceinline__ bool mb_wait_cluster(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 28)) return false;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_constant__ JacobiBatch<T> b) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -140,7 +178,16 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
       const int i = e / L.np, c = e % L.np;
       Ps[e] = (c < npl && i == p0 + c) ? 1.0 : 0.0;
     }
-  if (tid == 0) nonfinite = 0;
+  __shared__ uint64_t mbR[2];  // round exchanges of even / odd global round number
+  __shared__ int rerr;         // a round exchange timed out
+  if (tid == 0) {
+    nonfinite = 0;
+    rerr = 0;
+    mb_init(&mbR[0]);
+    mb_init(&mbR[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  uint32_t gr = 0;  // rounds done over all sweeps: the exchange buffer and mbarrier phase
   __syncthreads();
 
   const double tol = (double)max(n, 1) * 0x1.0p-53;
@@ -213,12 +260,16 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
 
     const int lpl = nlive + (nlive & 1);
     const int npl2 = lpl / 2;
-    for (int r = 0; r < lpl - 1; ++r) {
-      // this round's partials: slot [q][s] holds CTA q's partial of pair s, pushed by
-      // that CTA before the barrier, so the sums below read local shared memory.  A
-      // slot of parity r & 1 is rewritten two rounds later, after a barrier that
-      // every CTA reaches only after its sums of this round
-      double* gp = gpart + (r & 1) * C * L.npairs;
+    for (int r = 0; r < lpl - 1; ++r, ++gr) {
+      // this round's partials: slot [q][s] holds CTA q's partial of pair s, stored by
+      // that CTA with st.async completing bytes on this CTA's mbarrier of the round's
+      // parity; only the rotation lanes wait for them, and every CTA sums them in the
+      // same order.  A slot (and the mbarrier) of parity gr & 1 is reused two rounds
+      // later: a CTA stores round gr + 2 only after receiving everyone's round gr + 1,
+      // which each CTA sends after it has read its round gr partials
+      double* gp = gpart + (gr & 1) * C * L.npairs;
+      uint64_t* mb = &mbR[gr & 1];
+      if (tid == 0) mb_expect(mb, (uint32_t)C * npl2 * 8);
       for (int s = team; s < npl2; s += nteam) {
         int a, bq;
         round_pair(r, s, lpl, a, bq);
@@ -229,9 +280,9 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         }
 #pragma unroll
         for (int o = kTeam / 2; o > 0; o >>= 1) g += __shfl_xor_sync(tmask, g, o, kTeam);
-        for (int q = tl; q < C; q += kTeam) cluster.map_shared_rank(gp, q)[rank * L.npairs + s] = g;
+        for (int q = tl; q < C; q += kTeam) push_f64(&gp[rank * L.npairs + s], mb, q, g);
       }
-      cluster.sync();
+      if (tid < npl2 && !mb_wait_cluster(mb, (gr >> 1) & 1)) atomicExch(&rerr, 1);
       // rotation scalars, one lane per pair, in as few warps as possible (a
       // warp's FP64 instruction holds the SM's FP64 pipe for 16 cycles whatever
       // the number of active lanes); every CTA sums the partials in rank order,
@@ -351,7 +402,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
     if (tid == 0) {
       J.info->jacobi_sweeps = sweeps;
       J.info->rotations = (int)min(total_rot, (long long)0x7fffffff);
-      if (J.pipe_err && *J.pipe_err)
+      if ((J.pipe_err && *J.pipe_err) || rerr)
         J.info->status = RSVD_ERR_TIMEOUT;
       else if (nonfinite)
         J.info->status = RSVD_ERR_NONFINITE;
