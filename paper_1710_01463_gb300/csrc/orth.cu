@@ -446,12 +446,12 @@ constexpr int kProdStride = 33;  // per-lane products of the panel columns, padd
 // Shared memory: own rows of Y (then Q), own rows of the current panel's V,
 // one V^T Y buffer (partials, then the sums and T^T W; it also holds the
 // panel's per-lane products while the panel is factored) and the reflector
-// scalars.  The V and T of all
-// panels are kept in the matrix's global scratch (hw and hq, L2-resident) for
-// the accumulation of Q: with only the current panel of V in shared memory and
-// one V^T Y buffer, two CTAs of 384- and 512-row samples fit an SM.  A CTA
-// holds at most 64 rows (two per lane of a column's warp).  The static shared
-// memory is kept small: two CTAs of the 256-row TEBD samples share an SM.
+// scalars.  The V and T of all panels are kept in the matrix's global scratch
+// (hw and hq, L2-resident) for the accumulation of Q: with only the current
+// panel of V in shared memory and one V^T Y buffer, two CTAs of 384- and
+// 512-row samples fit an SM.  A CTA holds at most 64 rows (two per lane of a
+// column's warp).  The static shared memory is kept small: two CTAs of the
+// 256-row TEBD samples share an SM.
 __host__ __device__ inline PanelLayout panel_layout(int rows, int l, int csize) {
   const int rs = (rows + csize - 1) / csize;
   PanelLayout L;
