@@ -113,3 +113,94 @@ def test_tebd_rejects_overlapping_bonds(lib):
     bonds = _lib.int_array([0, 2])
     rc = lib.tebd_bond_update(L, 2, D, 2, bonds, fake, 64, fake, 8, fake, ctypes.byref(par32), fake, fake, 1 << 30, fake, None)
     assert rc == -3
+
+
+def test_product_update_host_checks(lib):
+    from paper_1710_01463_gb300 import _lib
+    L = 6
+    D = _lib.int_array([1, 4, 16, 64, 16, 4, 1])  # d = 4
+    par = params(1, 10, 2)
+    s2, s3 = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert lib.tebd_product_workspace_size(L, 4, D, 2, 2, ctypes.byref(par), ctypes.byref(s2)) == 0
+    assert lib.tebd_product_workspace_size(L, 4, D, 2, 3, ctypes.byref(par), ctypes.byref(s3)) == 0
+    assert 0 < s2.value < s3.value  # X, Y and the Grams grow with K
+    assert lib.tebd_product_workspace_size(L, 4, D, 2, 0, ctypes.byref(par), ctypes.byref(s2)) == -1
+    fake = ctypes.c_void_p(4096)
+    big = ctypes.c_size_t(1 << 40)
+    adjacent = _lib.int_array([1, 2])
+    assert lib.tebd_product_update(L, 4, D, 2, adjacent, fake, 4096, fake, 64, 2, fake, fake, ctypes.byref(par), fake,
+                                   fake, big, fake, None) == -1
+    ok_bonds = _lib.int_array([0, 2])
+    assert lib.tebd_product_update(L, 4, D, 2, ok_bonds, fake, 4096, fake, 64, 0, fake, fake, ctypes.byref(par), fake,
+                                   fake, big, fake, None) == -1
+    assert lib.tebd_product_update(L, 4, D, 2, ok_bonds, fake, 4096, fake, 64, 2, fake, fake,
+                                   ctypes.byref(params(1, 10, 2, 1)), fake, fake, big, fake, None) == -3
+    # a tensor stride too small for the bond's tensors
+    assert lib.tebd_product_update(L, 4, D, 2, ok_bonds, fake, 16, fake, 64, 2, fake, fake, ctypes.byref(par), fake,
+                                   fake, big, fake, None) == -1
+
+
+def test_factored_host_checks(lib):
+    s32, s64 = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    par = params(20, 8, 2)
+    assert lib.rsvd_factored_workspace_size(300, 32, 200, ctypes.byref(par), ctypes.byref(s32)) == 0
+    assert lib.rsvd_factored_workspace_size(300, 64, 200, ctypes.byref(par), ctypes.byref(s64)) == 0
+    assert s32.value < s64.value  # the r x l buffer between the two products
+    assert lib.rsvd_factored_workspace_size(300, 32, 200, ctypes.byref(params(20, 8, 2, 3)), ctypes.byref(s32)) == -3
+    assert lib.rsvd_factored_workspace_size(10, 32, 200, ctypes.byref(params(20, 8, 2)), ctypes.byref(s32)) == -1
+    fake = ctypes.c_void_p(4096)
+    big = ctypes.c_size_t(1 << 40)
+    # ldx < r
+    assert lib.rsvd_truncate_factored(300, 32, 200, fake, 31, fake, 200, ctypes.byref(par), fake, fake, 20, fake, 200,
+                                      fake, big, fake, None) == -1
+    # misaligned workspace
+    assert lib.rsvd_truncate_factored(300, 32, 200, fake, 32, fake, 200, ctypes.byref(par), fake, fake, 20, fake, 200,
+                                      ctypes.c_void_p(4100), big, fake, None) == -4
+
+
+def test_fixed_error_host_checks(lib):
+    sz = ctypes.c_size_t(0)
+    par = params(8, 10, 2)
+    assert lib.rsvd_tol_workspace_size(256, 256, 200, ctypes.byref(par), ctypes.byref(sz)) == 0 and sz.value > 0
+    assert lib.rsvd_tol_workspace_size(256, 256, 200, ctypes.byref(params(8, 10, 2, 1)), ctypes.byref(sz)) == -3
+    assert lib.rsvd_tol_workspace_size(256, 256, 0, ctypes.byref(par), ctypes.byref(sz)) == -1
+    fake = ctypes.c_void_p(4096)
+    k = ctypes.c_int(0)
+    err = ctypes.c_double(0.0)
+    big = ctypes.c_size_t(1 << 40)
+    for eps in (-1.0, float("nan")):
+        assert lib.rsvd_truncate_tol(256, 256, fake, 256, eps, 200, ctypes.byref(par), fake, fake, 200, fake, 256,
+                                     ctypes.byref(k), ctypes.byref(err), fake, big, fake, None) == -1
+    # ldu below min(k_max, m, n)
+    assert lib.rsvd_truncate_tol(256, 256, fake, 256, 1e-6, 200, ctypes.byref(par), fake, fake, 100, fake, 256,
+                                 ctypes.byref(k), ctypes.byref(err), fake, big, fake, None) == -1
+
+
+def test_adaptive_sectors_host_checks(lib):
+    from paper_1710_01463_gb300 import _lib
+    m = _lib.int_array([512, 300, 64])
+    n = _lib.int_array([512, 200, 100])
+    par = params(1, 8, 2)
+    sz, ref = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert lib.rsvd_sectors_adaptive_workspace_size(3, m, n, 64, ctypes.byref(par), ctypes.byref(sz)) == 0
+    caps = _lib.int_array([64, 64, 64])
+    assert lib.rsvd_batched_workspace_size(3, m, n, caps, ctypes.byref(par), ctypes.byref(ref)) == 0
+    assert sz.value == ref.value  # sized for the largest trial rank, min(chi, m_b, n_b)
+    assert lib.rsvd_sectors_adaptive_workspace_size(3, m, n, 0, ctypes.byref(par), ctypes.byref(sz)) == -1
+    m65 = _lib.int_array([64] * 65)
+    assert lib.rsvd_sectors_adaptive_workspace_size(65, m65, m65, 8, ctypes.byref(par), ctypes.byref(sz)) == -1
+    fake = ctypes.c_void_p(4096)
+    ptrs = _lib.ptr_array([4096] * 3)
+    lds = _lib.int_array([512, 200, 100])
+    kt = _lib.int_array([4, 4, 4])
+    rounds = ctypes.c_int(0)
+    big = ctypes.c_size_t(1 << 40)
+    bf16 = params(1, 8, 2, 3)
+    m2 = _lib.int_array([512, 512, 512])
+    assert lib.rsvd_truncate_sectors_adaptive(3, m2, m2, ptrs, _lib.int_array([512] * 3), kt, ctypes.byref(bf16), 64,
+                                              ptrs, ptrs, _lib.int_array([64] * 3), ptrs, _lib.int_array([512] * 3),
+                                              fake, ctypes.byref(rounds), fake, big, fake, None) == -3
+    # ldu below the block's cap
+    assert lib.rsvd_truncate_sectors_adaptive(3, m, n, ptrs, lds, kt, ctypes.byref(par), 64, ptrs, ptrs,
+                                              _lib.int_array([8, 64, 64]), ptrs, lds, fake, ctypes.byref(rounds), fake,
+                                              big, fake, None) == -1
