@@ -72,7 +72,7 @@ def rsvd_workspace_size(m, n, k, p=8, q=2, dtype=torch.float64):
 def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf32=False, simt=False):
     """Rank-k RSVD of one matrix: returns (U, S, Vt, info) as CUDA tensors.
 
-    A float64 -> FP64 products (tensor cores by exact slicing where m, n, l <= 256,
+    A float64 -> FP64 products (tensor cores by exact slicing where m, n <= 1024, l <= 256,
     unless simt=True); float32 -> FP32 (tf32=True: TF32 tensor cores); bfloat16 -> BF16
     tensor cores.  U and Vt are float64 for float64 A, else float32.
     """
