@@ -127,3 +127,57 @@ def rsvd_fixed_error(A, eps, k0, k_max, p, q, seed, stream=0):
             err = float(np.sqrt(err2[k] / fro2)) if fro2 > 0 else 0.0
             return U, s_k, Vt_k, err
         kt = min(2 * kt, cap)
+
+
+# ---------------------------------------------------------------- complex A
+# Sec. II.A states the problem for "real- or complex-valued" A.  Readings for the
+# complex form (the paper is silent): the test matrix Omega is the same real Philox
+# matrix (so a real A in complex storage gives the real algorithm exactly); every
+# transpose is the conjugate transpose; QR takes R_ii real and positive; the sign
+# rule becomes a phase rule - the entry of largest modulus of u_i (lowest index on
+# ties) is made real and positive, v_i taking the conjugate phase so that
+# u_i s_i v_i^H is unchanged.
+
+def qr_pos_complex(Y):
+    """Thin QR with real non-negative diagonal of R (Alg. RSVD step 3, complex)."""
+    Q, R = np.linalg.qr(Y, mode="reduced")
+    d = np.diag(R)
+    ph = np.where(np.abs(d) > 0, d / np.where(np.abs(d) > 0, np.abs(d), 1.0), 1.0)
+    return Q * ph[None, :]
+
+
+def canonical_phases(U, s, Vh):
+    """Make the largest-modulus entry of each u_i real positive (v_i^H follows)."""
+    U = U.copy()
+    Vh = Vh.copy()
+    for i in range(U.shape[1]):
+        j = int(np.argmax(np.abs(U[:, i])))
+        a = U[j, i]
+        if abs(a) > 0:
+            ph = a / abs(a)
+            U[:, i] = U[:, i] / ph
+            Vh[i, :] = Vh[i, :] * ph
+    return U, s, Vh
+
+
+def tsvd_complex(A, k):
+    """Alg. TSVD for complex A: (U_k, s_k, V_k^H) with the phase rule."""
+    U, s, Vh = np.linalg.svd(np.asarray(A, dtype=np.complex128), full_matrices=False)
+    return canonical_phases(U[:, :k], s[:k], Vh[:k, :])
+
+
+def rsvd_complex(A, k, p, q, seed, stream=0):
+    """Alg. RSVD (Sec. II.B) for complex A: Q0 = qr(A Omega); q times Z = qr(A^H Q),
+    Q = qr(A Z); B = Q^H A; rank-k TSVD of B lifted by Q.  Returns (U, s, V^H)."""
+    A = np.asarray(A, dtype=np.complex128)
+    m, n = A.shape
+    l = sample_width(m, n, k, p)
+    omega = gaussian_test_matrix(n, l, seed, stream)
+    Q = qr_pos_complex(A @ omega)
+    for _ in range(q):
+        Z = qr_pos_complex(A.conj().T @ Q)
+        Q = qr_pos_complex(A @ Z)
+    B = Q.conj().T @ A
+    Ub, s, Vh = np.linalg.svd(B, full_matrices=False)
+    return canonical_phases(Q @ Ub[:, :k], s[:k], Vh[:k, :])
+

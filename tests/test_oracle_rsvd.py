@@ -235,3 +235,72 @@ def test_fixed_error_of_zero_and_exact_rank():
     A = np.outer(np.arange(1.0, 31.0), np.arange(1.0, 21.0))
     U, s, Vt, err = orsvd.rsvd_fixed_error(A, 1e-12, 4, 20, 4, 1, 0)
     assert len(s) == 1 and err <= 1e-12
+
+
+# ---------------------------------------------------------------- complex A (NEXT row: oracle only)
+def haar_unitary(n, rng):
+    z = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
+
+
+def test_complex_rsvd_of_real_data_is_the_real_algorithm():
+    A = inputs.spectral_matrix(120, 90, inputs.exp_spectrum(90, 8.0), 3)
+    Uc, sc, Vhc = orsvd.rsvd_complex(A.astype(np.complex128), 20, 8, 2, 11, 2)
+    Ur, sr, Vtr = orsvd.rsvd(A, 20, 8, 2, 11, 2)
+    np.testing.assert_allclose(sc, sr, rtol=1e-12)
+    np.testing.assert_allclose(Uc, Ur, atol=1e-10)
+    np.testing.assert_allclose(Vhc, Vtr, atol=1e-10)
+
+
+def test_complex_rsvd_recovers_a_complex_spectrum_exactly():
+    # A = U diag(s) V^H of rank 30 with Haar unitary factors: with l >= 30 the sample spans the
+    # range and the singular values come back exactly; a transpose in place of a conjugate
+    # transpose anywhere in the power iteration or the projection breaks this
+    rng = np.random.default_rng(8)
+    s = np.exp(-np.arange(1, 31) / 4.0)
+    U = haar_unitary(80, rng)[:, :30]
+    V = haar_unitary(70, rng)[:, :30]
+    A = (U * s) @ V.conj().T
+    Ur, sr, Vhr = orsvd.rsvd_complex(A, 30, 10, 2, 5, 0)
+    np.testing.assert_allclose(sr, s, rtol=1e-11)
+    np.testing.assert_allclose(Ur.conj().T @ Ur, np.eye(30), atol=1e-12)
+    np.testing.assert_allclose(Vhr @ Vhr.conj().T, np.eye(30), atol=1e-12)
+    np.testing.assert_allclose((Ur * sr) @ Vhr, A, atol=1e-12)
+    # the phase rule: the largest-modulus entry of every u_i is real and positive
+    idx = np.argmax(np.abs(Ur), axis=0)
+    top = Ur[idx, np.arange(30)]
+    assert np.all(top.real > 0) and np.all(np.abs(top.imag) < 1e-14)
+    # and the factors agree with the complex TSVD
+    Ut, st, Vht = orsvd.tsvd_complex(A, 30)
+    np.testing.assert_allclose(Ur, Ut, atol=1e-9)
+
+
+def test_complex_rsvd_is_covariant_under_a_global_phase():
+    # e^{i phi} A has the same singular values; the phase rule moves the phase into V^H
+    rng = np.random.default_rng(9)
+    A = (rng.standard_normal((60, 40)) + 1j * rng.standard_normal((60, 40))) @ np.diag(np.exp(-np.arange(40) / 5.0))
+    U1, s1, V1 = orsvd.rsvd_complex(A, 10, 8, 2, 3)
+    U2, s2, V2 = orsvd.rsvd_complex(np.exp(0.7j) * A, 10, 8, 2, 3)
+    np.testing.assert_allclose(s2, s1, rtol=1e-12)
+    np.testing.assert_allclose(U2, U1, atol=1e-9)
+    np.testing.assert_allclose(V2, np.exp(0.7j) * V1, atol=1e-9)
+
+
+def test_complex_power_iteration_is_the_literal_power():
+    # full rank, slow decay and l < rank, so the power iteration decides the result: the
+    # literal Y = (A A^H)^q A Omega spans the same space, hence the same B singular values (a
+    # transpose without conjugation inside the iteration changes them)
+    rng = np.random.default_rng(10)
+    m, n, k, p, q = 60, 50, 8, 4, 2
+    s = 1.0 / np.arange(1, n + 1)
+    A = (haar_unitary(m, rng)[:, :n] * s) @ haar_unitary(n, rng).conj().T
+    _, s_r, _ = orsvd.rsvd_complex(A, k, p, q, 21, 1)
+    omega = philox.gaussian_test_matrix(n, k + p, 21, 1)
+    Y = A @ omega
+    for _ in range(q):
+        Y = A @ (A.conj().T @ Y)
+    Qlit, _ = np.linalg.qr(Y)
+    s_lit = np.linalg.svd(Qlit.conj().T @ A, compute_uv=False)[:k]
+    np.testing.assert_allclose(s_r, s_lit, rtol=1e-9)
+    assert np.all(s_r <= s[:k] * (1 + 1e-12))  # interlacing: the sampled values never exceed the true ones
