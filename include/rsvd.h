@@ -62,6 +62,26 @@ extern "C" {
  * l <= 256 run on the tensor cores by exact slicing (see rsvd_gemm_f64_tc:
  * FP64-class error); RSVD_FLAG_F64_SIMT computes them with FP64 FMAs instead. */
 #define RSVD_FLAG_F64_SIMT      1
+/* Alg. TSVD (Sec. II.A) on the same engine, the comparator that the paper's speedup
+ * tau = T_TSVD / T_RSVD is defined against (Sec. IV): no sampling - B = A (all m rows,
+ * m <= 1024), the one-sided Jacobi SVD of A itself (for n >= 3m on the m x m factor of
+ * an orthonormalisation of A^T), then truncation to k; p and q are ignored.  Honoured
+ * by rsvd_truncate, rsvd_truncate_batched (RSVD_F64 / RSVD_F32; RSVD_ERR_PRECISION for
+ * the tensor-core precisions) and tebd_bond_update; the other entry points return
+ * RSVD_ERR_INVALID_SIZE. */
+#define RSVD_FLAG_FULL_SVD      2
+/* Measurement aid: the independent groups of work of a call (Householder-first and
+ * CholeskyQR2 orthonormalisations, Jacobi SVDs of different cluster sizes) run one after
+ * another on the caller's stream instead of concurrently on side streams, so that the
+ * kernels' durations add up to the call's time.  Same results bit for bit. */
+#define RSVD_FLAG_SERIAL        4
+/* Test of a failure path, not for production use: the CTAs of the Jacobi SVD's
+ * thread-block clusters send none of their round partials, so every exchange wait
+ * runs out (after about 0.13 s), the cluster leaves the iteration together and
+ * info.status reports RSVD_ERR_TIMEOUT (the results are invalid; nothing faults or
+ * hangs, and the context stays usable).  Honoured by rsvd_truncate and
+ * rsvd_truncate_batched. */
+#define RSVD_FLAG_TEST_NO_EXCHANGE (1 << 30)
 
 /* Paths recorded in rsvd_info.path (bit set). */
 #define RSVD_PATH_EXACT         1   /* m <= l and m <= 16: Q = I, B = A (the sample covers the range) */
@@ -87,7 +107,8 @@ typedef struct {
   uint64_t seed;    /* Philox key word 0 */
   uint64_t stream;  /* Philox key word 1 of the first matrix; matrix b uses stream + b */
   int max_sweeps;   /* Jacobi sweep cap (0 = default 40) */
-  int flags;        /* 0, or RSVD_FLAG_F64_SIMT */
+  int flags;        /* 0, or RSVD_FLAG_F64_SIMT / RSVD_FLAG_FULL_SVD / RSVD_FLAG_SERIAL
+                       (RSVD_FLAG_TEST_NO_EXCHANGE: tests only) */
 } rsvd_params;
 
 /* Device-written record, one per matrix. */
@@ -102,6 +123,14 @@ typedef struct {
   int qr_columns;      /* columns the last Householder QR factored before its trailing block
                           fell to rounding level (l when it ran to the end; 0 if none ran):
                           a numerical-rank estimate of the sample, rounded up to 16 */
+  int qr_kflop;        /* algorithmic work of all Householder QRs of this matrix, in units of
+                          1000 flops: per QR of a rows x c sample stopped after r reflectors,
+                          with Q formed on qc columns, f(c) + f(qc), f(x) = 4 rows x r -
+                          2 (rows + x) r^2 + 4 r^3 / 3 (the standard factorization and
+                          explicit-Q counts) */
+  int jacobi_pairs;    /* row pairs whose inner product the Jacobi SVD formed (all sweeps) */
+  int cg_iterations;   /* rsvd_truncate_backward_batched: conjugate-gradient iterations in which
+                          a column was still active (both sides); 0 elsewhere */
 } rsvd_info;
 
 /*
@@ -420,8 +449,12 @@ int rsvd_truncate_backward_batched(int batch, const int* m, const int* n, const 
  *   way is rejected with RSVD_ERR_SCRATCH_LIMIT before anything is launched.
  *   No cudaMalloc, cudaFree or other allocating call is made.  The first call
  *   on a device looks up the array's device address (cudaGetSymbolAddress,
- *   with that device current) and caches it; make that first call before any
- *   stream capture.
+ *   with that device current) and caches it (looked up again after the
+ *   device's context was replaced, e.g. by cudaDeviceReset); the first call
+ *   from each host thread on a device also creates that thread's side streams
+ *   and events for the call's independent groups of work (cudaStreamCreate,
+ *   cudaEventCreate: no device memory).  Make the first call from every
+ *   thread before any stream capture.
  *   All calls share the one array and it keeps the previous call's contents
  *   (every word a call reads it has written itself first): calls whose work
  *   overlaps on the GPU - different streams, or host threads issuing at once -

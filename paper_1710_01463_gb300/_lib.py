@@ -29,6 +29,9 @@ RSVD_F32 = 1
 RSVD_TF32 = 2
 RSVD_BF16 = 3
 RSVD_FLAG_F64_SIMT = 1
+RSVD_FLAG_FULL_SVD = 2
+RSVD_FLAG_SERIAL = 4
+RSVD_FLAG_TEST_NO_EXCHANGE = 1 << 30
 
 EXPORTED = (
     "rsvd_gaussian",
@@ -82,6 +85,9 @@ class RsvdInfo(ctypes.Structure):
         ("l", ctypes.c_int),
         ("rotations", ctypes.c_int),
         ("qr_columns", ctypes.c_int),
+        ("qr_kflop", ctypes.c_int),
+        ("jacobi_pairs", ctypes.c_int),
+        ("cg_iterations", ctypes.c_int),
     ]
 
 
@@ -95,6 +101,11 @@ class RsvdError(RuntimeError):
         self.code = code
         msg = load().rsvd_status_string(code).decode() if _lib is not None else str(code)
         super().__init__(f"{where}: status {code} ({msg})")
+
+
+def status_string(code):
+    """rsvd_status_string of a status code."""
+    return load().rsvd_status_string(int(code)).decode()
 
 
 def load():

@@ -30,11 +30,12 @@ def _stream_handle(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _params(k, p, q, prec, seed, stream, max_sweeps=0, simt=False):
+def _params(k, p, q, prec, seed, stream, max_sweeps=0, simt=False, flags=0):
     """rsvd_params; simt=True sets RSVD_FLAG_F64_SIMT (FP64 products with A on FP64 FMAs
-    instead of the tensor cores by exact slicing)."""
+    instead of the tensor cores by exact slicing); flags adds further RSVD_FLAG_* bits."""
     return _lib.RsvdParams(int(k), int(p), int(q), int(prec), int(seed) & ((1 << 64) - 1),
-                           int(stream) & ((1 << 64) - 1), int(max_sweeps), _lib.RSVD_FLAG_F64_SIMT if simt else 0)
+                           int(stream) & ((1 << 64) - 1), int(max_sweeps),
+                           (_lib.RSVD_FLAG_F64_SIMT if simt else 0) | int(flags))
 
 
 def _require_cuda(*ts):
@@ -46,7 +47,8 @@ def _require_cuda(*ts):
 def info_dicts(info):
     """Decode a (batch, INFO_INTS) int32 info tensor into a list of dicts."""
     rows = info.view(-1, _lib.INFO_INTS).cpu().tolist()
-    keys = ("status", "path", "chol_fallbacks", "jacobi_sweeps", "l", "rotations", "qr_columns")
+    keys = ("status", "path", "chol_fallbacks", "jacobi_sweeps", "l", "rotations", "qr_columns", "qr_kflop",
+            "jacobi_pairs", "cg_iterations")
     return [dict(zip(keys, r)) for r in rows]
 
 
@@ -69,7 +71,7 @@ def rsvd_workspace_size(m, n, k, p=8, q=2, dtype=torch.float64):
     return sz.value
 
 
-def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf32=False, simt=False):
+def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf32=False, simt=False, flags=0):
     """Rank-k RSVD of one matrix: returns (U, S, Vt, info) as CUDA tensors.
 
     A float64 -> FP64 products (tensor cores by exact slicing where m, n <= 1024, l <= 256,
@@ -82,7 +84,7 @@ def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf3
         raise ValueError("A must be a row-major 2-D tensor")
     prec = _prec_of(A, tf32)
     m, n = A.shape
-    par = _params(k, p, q, prec, seed, stream, max_sweeps, simt)
+    par = _params(k, p, q, prec, seed, stream, max_sweeps, simt, flags)
     sz = ctypes.c_size_t(0)
     _lib.check(lib.rsvd_workspace_size(m, n, ctypes.byref(par), ctypes.byref(sz)), "rsvd_workspace_size")
     if work is None or work.numel() < sz.value:
@@ -314,15 +316,32 @@ def rsvd_truncate_backward_batched(As, Us, Ss, Vts, Ubars=None, Sbars=None, Vtba
     return Abars, info
 
 
+def check_info(info, what):
+    """Read the device status records of a call (synchronises the stream): raise on an
+    error status (negative: non-finite input, a timed-out device wait), warn on a warning
+    (the Jacobi sweep cap, an unconverged conjugate-gradient column)."""
+    import warnings
+    for d in info_dicts(info):
+        st = d["status"]
+        if st < 0:
+            raise RuntimeError(f"{what}: device status {st} ({_lib.status_string(st)})")
+        if st > 0:
+            warnings.warn(f"{what}: device status {st} ({_lib.status_string(st)})", RuntimeWarning, stacklevel=3)
+
+
 class RSVDTrunc(torch.autograd.Function):
     """(U, S, Vt) = rank-k RSVD of A (forward: rsvd_truncate), with the
     derivative of the truncated factorization (backward: the library's
-    rsvd_truncate_backward_batched)."""
+    rsvd_truncate_backward_batched).  Both passes read their device status
+    records: an error status raises, a warning (Jacobi sweep cap, unconverged
+    conjugate gradients; max_iter caps the latter) is issued as a RuntimeWarning."""
 
     @staticmethod
-    def forward(ctx, A, k, p=8, q=2, seed=0, stream=0):
+    def forward(ctx, A, k, p=8, q=2, seed=0, stream=0, max_iter=300):
         U, S, Vt, info = rsvd_truncate(A.contiguous(), k, p, q, seed, stream)
+        check_info(info, "rsvd_truncate")
         ctx.save_for_backward(A.contiguous(), U, S, Vt)
+        ctx.max_iter = int(max_iter)
         return U, S, Vt
 
     @staticmethod
@@ -331,5 +350,6 @@ class RSVDTrunc(torch.autograd.Function):
         Ub = None if gU is None else [gU.contiguous().to(A.dtype)]
         Sb = None if gS is None else [gS.contiguous().to(torch.float64)]
         Vb = None if gVt is None else [gVt.contiguous().to(A.dtype)]
-        Abar, _ = rsvd_truncate_backward_batched([A], [U], [S], [Vt], Ub, Sb, Vb)
-        return Abar[0], None, None, None, None, None
+        Abar, info = rsvd_truncate_backward_batched([A], [U], [S], [Vt], Ub, Sb, Vb, max_iter=ctx.max_iter)
+        check_info(info, "rsvd_truncate_backward_batched")
+        return Abar[0], None, None, None, None, None, None

@@ -40,6 +40,8 @@ struct Prob {
   unsigned long long seed, stream;
   rsvd_info* info;
   int max_sweeps;
+  int no_exchange;  // RSVD_FLAG_TEST_NO_EXCHANGE
+  int serial;       // RSVD_FLAG_SERIAL: independent groups one after another on the caller's stream
   // workspace
   void *Y0, *Y1, *Z0, *Z1, *Rinv, *Ps;
   double *G, *part, *hw, *hq, *Bm, *Bg, *Pg, *sig;
@@ -144,6 +146,10 @@ size_t layout(Prob* p, int m, int n, int k, int l, size_t tsize, char* base, int
 }
 
 inline int sample_width(int m, int n, int k, int p) { return std::min(k + p, std::min(m, n)); }
+// rows of B: the sample width, or all m rows for Alg. TSVD (RSVD_FLAG_FULL_SVD: B = A)
+inline int b_rows(int m, int n, int k, const rsvd_params* p) {
+  return (p->flags & RSVD_FLAG_FULL_SVD) ? m : sample_width(m, n, k, p->p);
+}
 
 // When the sample spans the whole column space (m <= l), a small matrix skips
 // the sampling: Q = I, B = A.  Larger ones keep the sampled path with l = m:
@@ -153,6 +159,9 @@ inline int sample_width(int m, int n, int k, int p) { return std::min(k + p, std
 // many sweeps over all rows of A.
 constexpr int kExactMaxRows = 16;
 inline int use_exact_path(int m, int l) { return (m <= l && m <= kExactMaxRows) ? 1 : 0; }
+inline int exact_of(int m, int l, const rsvd_params* p) {
+  return (p->flags & RSVD_FLAG_FULL_SVD) ? 1 : use_exact_path(m, l);
+}
 
 // FP64 products with A on the tensor cores: K <= 1024 (K = n for A Z, m for
 // A^T Y; exact level sums per chunk of 256) and the thin operand fits one CTA
@@ -180,6 +189,7 @@ OrthBatch<T> orth_batch(const std::vector<Prob*>& ps, bool onY) {
   b.count = (int)ps.size();
   b.max_chunks = 0;
   b.max_tilepairs = 0;
+  b.serial = ps.empty() ? 0 : ps[0]->serial;
   for (size_t i = 0; i < ps.size(); ++i) {
     Prob& p = *ps[i];
     OrthJob<T>& J = b.job[i];
@@ -234,6 +244,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       ob.count = wc;
       ob.max_chunks = 0;
       ob.max_tilepairs = 0;
+      ob.serial = wide[0]->serial;
       for (int i = 0; i < wc; ++i) {
         Prob& p = *wide[i];
         OrthJob<double>& J = ob.job[i];
@@ -288,18 +299,20 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       J.want_vt = 1;
       J.want_p = p.want_u;
       J.pipe_err = tc_err ? p.flag + 1 : nullptr;
+      J.no_exchange = p.no_exchange;
     }
   }
   {
     const int ng = (int)groups.size();
-    const int nside = std::min(ng - 1, kSideStreams);
+    const int nside = (cnt > 0 && probs[0].serial) ? 0 : std::min(ng - 1, kSideStreams);
     SideStreams* ss = nullptr;
     if (nside > 0) {
       ss = side_streams();
       if (!ss) return RSVD_ERR_LAUNCH;
       RSVD_TRY(fork_side(ss, nside, s));
     }
-    for (int g = 0; g < ng; ++g) RSVD_TRY(launch_jacobi<T>(groups[g], g == 0 ? s : ss->stream[(g - 1) % kSideStreams]));
+    for (int g = 0; g < ng; ++g)
+      RSVD_TRY(launch_jacobi<T>(groups[g], (g == 0 || !ss) ? s : ss->stream[(g - 1) % kSideStreams]));
     if (ss) RSVD_TRY(join_side(ss, nside, s));
   }
   if (!wide.empty()) {  // V^T = W Q_b^T
@@ -646,7 +659,7 @@ int run_chunk_tc(std::vector<Prob>& probs, int q, cudaStream_t s) {
 
 int check_params(const rsvd_params* p) {
   if (!p) return RSVD_ERR_NULL_POINTER;
-  if (p->p < 0 || p->q < 0 || p->q > 64 || p->max_sweeps < 0 || (p->flags & ~RSVD_FLAG_F64_SIMT) != 0)
+  if (p->p < 0 || p->q < 0 || p->q > 64 || p->max_sweeps < 0 || (p->flags & ~(RSVD_FLAG_F64_SIMT | RSVD_FLAG_FULL_SVD | RSVD_FLAG_SERIAL | RSVD_FLAG_TEST_NO_EXCHANGE)) != 0)
     return RSVD_ERR_INVALID_SIZE;
   if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_TF32 && p->prec != RSVD_BF16)
     return RSVD_ERR_PRECISION;
@@ -720,11 +733,11 @@ int rsvd_batched_workspace_size(int batch, const int* m, const int* n, const int
   size_t tot = 0;
   for (int b = 0; b < batch; ++b) {
     if (m[b] < 1 || n[b] < 1 || k[b] < 1 || k[b] > std::min(m[b], n[b])) return RSVD_ERR_INVALID_SIZE;
-    const int l = sample_width(m[b], n[b], k[b], p->p);
+    const int l = b_rows(m[b], n[b], k[b], p);
     if (l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
     if (is_tc(p->prec) && (l > 256 || m[b] <= l)) return RSVD_ERR_INVALID_SIZE;
     tot += layout(nullptr, m[b], n[b], k[b], l, tsize_of(p->prec), nullptr, tc_bytes_of(p->prec),
-                  use_oz(m[b], n[b], l, use_exact_path(m[b], l), p));
+                  use_oz(m[b], n[b], l, exact_of(m[b], l, p), p));
   }
   *bytes = tot;
   return RSVD_OK;
@@ -741,6 +754,7 @@ int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* con
                           void* cuda_stream) {
   int rc = check_params(p);
   if (rc) return rc;
+  if ((p->flags & RSVD_FLAG_FULL_SVD) && is_tc(p->prec)) return RSVD_ERR_PRECISION;
   if (batch < 1 || chi_global < 0) return RSVD_ERR_INVALID_SIZE;
   if (!m || !n || !A || !lda || !k || !S || !U || !ldu || !Vt || !ldvt || !work || !info) return RSVD_ERR_NULL_POINTER;
   if (chi_global > 0 && !k_out) return RSVD_ERR_NULL_POINTER;
@@ -755,7 +769,7 @@ int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* con
     Prob& pr = probs[b];
     std::memset(&pr, 0, sizeof(Prob));
     pr.m = m[b]; pr.n = n[b]; pr.k = k[b];
-    pr.l = sample_width(m[b], n[b], k[b], p->p);
+    pr.l = b_rows(m[b], n[b], k[b], p);
     if (pr.l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
     if (is_tc(p->prec)) {
       // tensor-core operands: l <= 256, a sample narrower than A, TMA-describable rows
@@ -763,13 +777,15 @@ int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* con
       if (pr.l > 256 || m[b] <= pr.l) return RSVD_ERR_INVALID_SIZE;
       if (((uintptr_t)A[b]) % 16 || ((size_t)lda[b] * eb) % 16) return RSVD_ERR_INVALID_SIZE;
     }
-    pr.exact = use_exact_path(pr.m, pr.l);
+    pr.exact = exact_of(pr.m, pr.l, p);
     pr.want_u = 1;
     pr.A = A[b]; pr.lda = lda[b];
     pr.S = S[b]; pr.U = U[b]; pr.ldu = ldu[b]; pr.Vt = Vt[b]; pr.ldvt = ldvt[b];
     pr.seed = p->seed; pr.stream = p->stream + (uint64_t)b;
     pr.info = info + b;
     pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
+    pr.no_exchange = (p->flags & RSVD_FLAG_TEST_NO_EXCHANGE) ? 1 : 0;
     total_k += k[b];
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -790,6 +806,7 @@ int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* con
 int rsvd_sectors_adaptive_workspace_size(int batch, const int* m, const int* n, int chi, const rsvd_params* p,
                                          size_t* bytes) {
   if (!m || !n || !p || !bytes) return RSVD_ERR_NULL_POINTER;
+  if (p->flags & RSVD_FLAG_FULL_SVD) return RSVD_ERR_INVALID_SIZE;
   if (batch < 1 || batch > kMaxJobs || chi < 1) return RSVD_ERR_INVALID_SIZE;
   std::vector<int> cap(batch);
   for (int b = 0; b < batch; ++b) cap[b] = std::min(chi, std::min(m[b], n[b]));
@@ -838,6 +855,7 @@ int rsvd_truncate_sectors_adaptive(int batch, const int* m, const int* n, const 
       pr.seed = p->seed; pr.stream = p->stream + (uint64_t)b;
       pr.info = info + b;
       pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
     }
     rc = run_batched(probs, p, (char*)work, work_bytes, s);
     if (rc) return rc;
@@ -882,6 +900,7 @@ int rsvd_truncate(int m, int n, const void* A, int lda, const rsvd_params* p, do
 int rsvd_factored_workspace_size(int m, int r, int n, const rsvd_params* p, size_t* bytes) {
   int rc = check_params(p);
   if (rc) return rc;
+  if (p->flags & RSVD_FLAG_FULL_SVD) return RSVD_ERR_INVALID_SIZE;
   if (!bytes) return RSVD_ERR_NULL_POINTER;
   if (p->prec != RSVD_F64 && p->prec != RSVD_F32) return RSVD_ERR_PRECISION;
   if (m < 1 || n < 1 || r < 1 || p->k < 1 || p->k > std::min(m, n)) return RSVD_ERR_INVALID_SIZE;
@@ -913,6 +932,7 @@ int rsvd_truncate_factored(int m, int r, int n, const void* X, int ldx, const vo
   pr.seed = p->seed; pr.stream = p->stream;
   pr.info = info;
   pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
   return run_batched(probs, p, (char*)work, work_bytes, (cudaStream_t)cuda_stream);
 }
 
@@ -943,6 +963,7 @@ TolLayout tol_layout(int m, int n, int kcap, const rsvd_params* p) {
 int rsvd_tol_workspace_size(int m, int n, int k_max, const rsvd_params* p, size_t* bytes) {
   int rc = check_params(p);
   if (rc) return rc;
+  if (p->flags & RSVD_FLAG_FULL_SVD) return RSVD_ERR_INVALID_SIZE;
   if (!bytes) return RSVD_ERR_NULL_POINTER;
   if (p->prec != RSVD_F64) return RSVD_ERR_PRECISION;
   if (m < 1 || n < 1 || k_max < 1 || p->k < 1) return RSVD_ERR_INVALID_SIZE;
@@ -988,6 +1009,7 @@ int rsvd_truncate_tol(int m, int n, const double* A, int lda, double eps, int k_
     pr.seed = p->seed; pr.stream = p->stream;  // the same Philox stream: Omega's columns nest
     pr.info = info;
     pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
     rc = run_batched(probs, &pk, base + L.rsvd, L.E - L.rsvd, s);
     if (rc) return rc;
     // E = A - Q B: the residual of the projection, ||E||_F^2 = ||(I - Q Q^T) A||_F^2
@@ -1046,9 +1068,9 @@ int tebd_workspace_size(int L, int d, const int* D, int nb, const rsvd_params* p
   for (int i = 0; i + 1 < L; ++i) {
     const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
     if (k < 1 || k > std::min(m, n)) return RSVD_ERR_INVALID_SIZE;
-    if (sample_width(m, n, k, p->p) > kMaxSample) return RSVD_ERR_INVALID_SIZE;
-    const int l = sample_width(m, n, k, p->p);
-    mx = std::max(mx, tebd_bond_bytes(m, n, k, l, use_oz(m, n, l, use_exact_path(m, l), p), nullptr));
+    const int l = b_rows(m, n, k, p);
+    if (l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+    mx = std::max(mx, tebd_bond_bytes(m, n, k, l, use_oz(m, n, l, exact_of(m, l, p), p), nullptr));
   }
   *bytes = mx * (size_t)nb;
   return RSVD_OK;
@@ -1071,15 +1093,15 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
       if (std::abs(bond[c] - i) < 2) return RSVD_ERR_INVALID_SIZE;
     const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
     if (k < 1 || k > std::min(m, n)) return RSVD_ERR_INVALID_SIZE;
-    if (sample_width(m, n, k, p->p) > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+    if (b_rows(m, n, k, p) > kMaxSample) return RSVD_ERR_INVALID_SIZE;
     if ((size_t)D[i] * d * D[i + 1] > tensor_stride || (size_t)D[i + 1] * d * D[i + 2] > tensor_stride) return RSVD_ERR_INVALID_SIZE;
     if ((size_t)D[i + 1] > lam_stride) return RSVD_ERR_INVALID_SIZE;
   }
   size_t per = 0;
   for (int i = 0; i + 1 < L; ++i) {
     const int m = D[i] * d, n = d * D[i + 2], k = D[i + 1];
-    const int l = sample_width(m, n, k, p->p);
-    per = std::max(per, tebd_bond_bytes(m, n, k, l, use_oz(m, n, l, use_exact_path(m, l), p), nullptr));
+    const int l = b_rows(m, n, k, p);
+    per = std::max(per, tebd_bond_bytes(m, n, k, l, use_oz(m, n, l, exact_of(m, l, p), p), nullptr));
   }
   if (per * (size_t)nb > work_bytes) return RSVD_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -1096,9 +1118,9 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     const int i = bond[b];
     const int Dl = D[i], Dm = D[i + 1], Dr = D[i + 2];
     const int m = Dl * d, n = d * Dr, k = Dm;
-    const int l = sample_width(m, n, k, p->p);
+    const int l = b_rows(m, n, k, p);
     char* wb = base + per * b;
-    const int oz = use_oz(m, n, l, use_exact_path(m, l), p);
+    const int oz = use_oz(m, n, l, exact_of(m, l, p), p);
     tebd_bond_bytes(m, n, k, l, oz, &lay[b]);
     double* T2 = (double*)(wb + lay[b].t2);
     double* thB = (double*)(wb + lay[b].thetaB);
@@ -1117,7 +1139,7 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     Prob& pr = probs[b];
     std::memset(&pr, 0, sizeof(Prob));
     pr.m = m; pr.n = n; pr.k = k; pr.l = l;
-    pr.exact = use_exact_path(m, l);
+    pr.exact = exact_of(m, l, p);
     pr.want_u = 0;
     pr.A = th; pr.lda = n;
     pr.S = (double*)(wb + lay[b].S);
@@ -1126,6 +1148,7 @@ int tebd_bond_update(int L, int d, const int* D, int nb, const int* bond, double
     pr.seed = p->seed; pr.stream = p->stream + (uint64_t)i;
     pr.info = info + b;
     pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
     layout(&pr, m, n, k, l, 8, wb + lay[b].rsvd, 0, oz);
   }
   RSVD_TRY(launch_tebd_rank(rb, s));
@@ -1200,6 +1223,7 @@ size_t tebd_prod_per_bond(int L, int d, const int* D, int K, int pp) {
 int tebd_product_workspace_size(int L, int d, const int* D, int nb, int K, const rsvd_params* p, size_t* bytes) {
   int rc = check_params(p);
   if (rc) return rc;
+  if (p->flags & RSVD_FLAG_FULL_SVD) return RSVD_ERR_INVALID_SIZE;
   if (!D || !bytes) return RSVD_ERR_NULL_POINTER;
   if (L < 2 || d < 1 || nb < 1 || K < 1) return RSVD_ERR_INVALID_SIZE;
   const size_t per = tebd_prod_per_bond(L, d, D, K, p->p);
@@ -1214,6 +1238,7 @@ int tebd_product_update(int L, int d, const int* D, int nb, const int* bond, dou
                         void* cuda_stream) {
   int rc = check_params(p);
   if (rc) return rc;
+  if (p->flags & RSVD_FLAG_FULL_SVD) return RSVD_ERR_INVALID_SIZE;
   if (p->prec != RSVD_F64) return RSVD_ERR_PRECISION;
   if (!D || !bond || !B || !lam || !uL || !uR || !trunc_err || !work || !info) return RSVD_ERR_NULL_POINTER;
   if (L < 2 || d < 1 || nb < 1 || nb > kMaxJobs || K < 1) return RSVD_ERR_INVALID_SIZE;
@@ -1270,6 +1295,7 @@ int tebd_product_update(int L, int d, const int* D, int nb, const int* bond, dou
     pr.seed = p->seed; pr.stream = p->stream + (uint64_t)i;
     pr.info = info + b;
     pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
     layout(&pr, m, n, k, l, 8, wb + lay[b].rsvd, 0, 0, r);
   }
   RSVD_TRY(launch_tebd_product(tp, s));
@@ -1323,12 +1349,21 @@ constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB, held by eve
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxScratchDevices = 64;
-void* g_scratch_dev_ptr[kMaxScratchDevices] = {};
+struct ScratchAddr {
+  void* ctx;  // the context the address belongs to
+  void* ptr;
+};
+ScratchAddr g_scratch_dev_ptr[kMaxScratchDevices] = {};
 std::mutex g_scratch_mutex;
 
 // Device address of g_static_scratch on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up with
-// cudaGetSymbolAddress once per device (with that device current) and cached.
+// cudaGetSymbolAddress once per device (with that device current) and cached;
+// it is looked up again when the device's context was replaced (after a
+// cudaDeviceReset the module, and the array, are loaded anew).  The same set-up
+// creates this host thread's side streams and events for the call's independent
+// groups of work, so that a first call made before any stream capture leaves
+// nothing to create later on this thread.
 int static_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1337,17 +1372,24 @@ int static_scratch(void** out) {
     return RSVD_ERR_LAUNCH;
   }
   if (dev < 0 || dev >= kMaxScratchDevices) return RSVD_ERR_INVALID_SIZE;
+  if (!side_streams()) {
+    last_cuda_error() = cudaGetLastError();
+    return RSVD_ERR_LAUNCH;
+  }
+  void* ctx = current_context();
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_dev_ptr[dev]) {
+  ScratchAddr& a = g_scratch_dev_ptr[dev];
+  if (!a.ptr || a.ctx != ctx) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_static_scratch);
     if (e != cudaSuccess || ptr == nullptr) {
       last_cuda_error() = e;
       return RSVD_ERR_LAUNCH;
     }
-    g_scratch_dev_ptr[dev] = ptr;
+    a.ptr = ptr;
+    a.ctx = ctx;
   }
-  *out = g_scratch_dev_ptr[dev];
+  *out = a.ptr;
   return RSVD_OK;
 }
 

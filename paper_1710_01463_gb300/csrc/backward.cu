@@ -87,10 +87,17 @@ __global__ void __launch_bounds__(256) cg_update_zr_kernel(const __grid_constant
 }
 
 // per column: convergence / breakdown bookkeeping, beta = rho_new / rho
+// (flags[0]: a column broke down; flags[1]: iterations in which a column was still active)
 template <typename T>
 __global__ void cg_scalar_kernel(const __grid_constant__ BwBatch<T> b, int init) {
   const BwJob<T>& J = b.job[blockIdx.x];
-  if (init && threadIdx.x == 0) *J.flags = 0;
+  if (init && threadIdx.x == 0) {
+    J.flags[0] = 0;
+    J.flags[1] = 0;
+  }
+  int had = 0;
+  for (int c = threadIdx.x; c < J.k && !init; c += blockDim.x) had |= J.active[c];
+  if (__syncthreads_or(had) && threadIdx.x == 0) J.flags[1] += 1;
   for (int c = threadIdx.x; c < J.k; c += blockDim.x) {
     if (init) {
       J.rho[c] = J.rho0[c];
@@ -317,7 +324,9 @@ __global__ void bw_info_kernel(const __grid_constant__ BwBatch<T> b, const __gri
       info->jacobi_sweeps = 0;
       info->l = J.k;
       info->rotations = 0;
+      info->cg_iterations = 0;
     }
+    info->cg_iterations += J.flags[1];
     if ((any || (*J.flags & 1)) && info->status == RSVD_OK) info->status = RSVD_WARN_CG;
   }
 }
@@ -540,6 +549,10 @@ __global__ void bw_info_init_kernel(const __grid_constant__ InfoPtrs<T> ip, int 
     info->jacobi_sweeps = 0;
     info->l = 0;
     info->rotations = 0;
+    info->qr_columns = 0;
+    info->qr_kflop = 0;
+    info->jacobi_pairs = 0;
+    info->cg_iterations = 0;
   }
 }
 

@@ -89,6 +89,7 @@ struct OrthBatch {
   int count;
   int max_chunks;
   int max_tilepairs;
+  int serial = 0;  // run the Householder-first and CholeskyQR2 groups one after another on the caller's stream
   OrthJob<T> job[kMaxJobs];
 };
 
@@ -109,6 +110,7 @@ struct JacobiJob {
   int want_vt;
   int want_p = 1;                 // accumulate the rotations P (needed only for U~ = P^T)
   const int* pipe_err = nullptr;  // optional: nonzero when an earlier tensor-core pipeline wait timed out
+  int no_exchange = 0;            // test of the failure path: no CTA sends its round partials
 };
 template <typename T>
 struct JacobiBatch {
@@ -409,11 +411,13 @@ cudaError_t& last_cuda_error();
 constexpr int kSideStreams = 4;
 struct SideStreams {
   bool ready = false;
+  void* ctx = nullptr;  // the CUDA context they were created in
   cudaStream_t stream[kSideStreams] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kSideStreams] = {};
 };
 SideStreams* side_streams();                               // this thread's, for the current device; null on failure
+void* current_context();  // the calling thread's current CUDA context (driver handle), null if none
 cudaError_t fork_side(SideStreams* ss, int n, cudaStream_t s);  // side streams 0..n-1 wait for s's work so far
 cudaError_t join_side(SideStreams* ss, int n, cudaStream_t s);  // s waits for side streams 0..n-1
 

@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   const int max_sweeps = J.max_sweeps;
   int sweeps = 0;
   long long total_rot = 0;
+  long long total_pairs = 0;  // inner products formed: nlive (nlive - 1) / 2 per sweep
   bool converged = false;
   for (;;) {
     // exact row norms of this sweep (four independent partial sums: a dependent
@@ -211,7 +212,10 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         s3 = fma(row[c + 3], row[c + 3], s3);
       }
       for (; c < ncl; ++c) s0 = fma(row[c], row[c], s0);
-      nrm_part[i] = (s0 + s1) + (s2 + s3);
+      // a CTA whose round exchange timed out contributes +Inf to row 0: every CTA then
+      // sees a non-finite norm after the same sum and leaves the iteration at the same
+      // point (no CTA keeps sweeping, or pushing into the shared memory of one that left)
+      nrm_part[i] = (i == 0 && rerr) ? __longlong_as_double(0x7ff0000000000000LL) : (s0 + s1) + (s2 + s3);
     }
     cluster.sync();
     for (int i = tid; i < l; i += kJacobiThreads) norms[i] = cluster_tree_sum(cluster, nrm_part, i, C);
@@ -260,7 +264,12 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
 
     const int lpl = nlive + (nlive & 1);
     const int npl2 = lpl / 2;
+    total_pairs += (long long)nlive * (nlive - 1) / 2;
     for (int r = 0; r < lpl - 1; ++r, ++gr) {
+      // after a timed-out exchange (rerr is uniform in the CTA after the round's last
+      // __syncthreads) this CTA sends and waits no more; the sweep head then ends the
+      // iteration in every CTA (see the row norms), so a CTA waits out at most one limit
+      if (rerr) break;
       // this round's partials: slot [q][s] holds CTA q's partial of pair s, stored by
       // that CTA with st.async completing bytes on this CTA's mbarrier of the round's
       // parity; only the rotation lanes wait for them, and every CTA sums them in the
@@ -280,7 +289,8 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         }
 #pragma unroll
         for (int o = kTeam / 2; o > 0; o >>= 1) g += __shfl_xor_sync(tmask, g, o, kTeam);
-        for (int q = tl; q < C; q += kTeam) push_f64(&gp[rank * L.npairs + s], mb, q, g);
+        if (!J.no_exchange)
+          for (int q = tl; q < C; q += kTeam) push_f64(&gp[rank * L.npairs + s], mb, q, g);
       }
       if (tid < npl2 && !mb_wait_cluster(mb, (gr >> 1) & 1)) atomicExch(&rerr, 1);
       // rotation scalars, one lane per pair, in as few warps as possible (a
@@ -400,9 +410,14 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
       if (r < k) J.S[r] = v;
     }
     if (tid == 0) {
+      // a timed-out exchange in any CTA of the cluster (each CTA's flag is final: no
+      // round runs after the cluster barrier above, and every CTA stays until the last one)
+      int any_err = 0;
+      for (int q = 0; q < C; ++q) any_err |= *cluster.map_shared_rank(&rerr, q);
       J.info->jacobi_sweeps = sweeps;
       J.info->rotations = (int)min(total_rot, (long long)0x7fffffff);
-      if ((J.pipe_err && *J.pipe_err) || rerr)
+      J.info->jacobi_pairs = (int)min(total_pairs, (long long)0x7fffffff);
+      if ((J.pipe_err && *J.pipe_err) || any_err)
         J.info->status = RSVD_ERR_TIMEOUT;
       else if (nonfinite)
         J.info->status = RSVD_ERR_NONFINITE;

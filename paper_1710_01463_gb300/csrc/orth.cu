@@ -34,6 +34,10 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepB
     J.info->jacobi_sweeps = 0;
     J.info->l = J.l;
     J.info->rotations = 0;
+    J.info->qr_columns = 0;
+    J.info->qr_kflop = 0;
+    J.info->jacobi_pairs = 0;
+    J.info->cg_iterations = 0;
     J.flag[0] = 0;
     J.flag[1] = 0;
     J.flag[2] = J.l;  // columns of Q that carry the sampled range
@@ -248,6 +252,16 @@ inline int chol_threads(int l) { return l <= 64 ? 128 : (l <= 128 ? 256 : 512); 
 constexpr int kHhThreads = 512;
 constexpr int kHhTeam = 8;  // lanes per column in the partial products and their exchange
 
+// Algorithmic work of a Householder QR of a rows x c sample stopped after r
+// reflectors, with the explicit Q formed on qc columns (kflop, rounded): the
+// standard counts sum_{j<r} 4 (rows - j)(x - j) for x = c and x = qc
+__device__ __forceinline__ int hh_kflop(int rows, int c, int qc, int r) {
+  auto f = [&](double x) {
+    return 4.0 * rows * x * r - 2.0 * ((double)rows + x) * r * (double)r + 4.0 / 3.0 * r * (double)r * r;
+  };
+  return (int)((f(c) + f(qc)) * 1e-3 + 0.5);
+}
+
 struct HLayout {
   int rs;  // rows per CTA
 };
@@ -417,6 +431,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
     if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
     atomicOr(&J.info->path, RSVD_PATH_HOUSEHOLDER);
     J.info->qr_columns = l;
+    atomicAdd(&J.info->qr_kflop, hh_kflop(rows, l, l, l));
     if (J.trunc_q && J.rank_eff) *J.rank_eff = l;
   }
   cluster.sync();  // no CTA leaves while others may read its shared memory
@@ -854,6 +869,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
     atomicOr(&J.info->path, RSVD_PATH_HOUSEHOLDER);
     J.info->qr_columns = min(l, npanel_used * kNb);
+    atomicAdd(&J.info->qr_kflop, hh_kflop(rows, lc, qc, min(lc, npanel_used * kNb)));
     if (J.trunc_q && J.rank_eff) *J.rank_eff = qc;
   }
   cluster.sync();  // no CTA leaves while others may read its shared memory
@@ -1042,7 +1058,7 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s) {
   }
   cudaError_t e = cudaSuccess;
   SideStreams* fk = nullptr;
-  if (hb.count > 0 && cq.count > 0) {
+  if (hb.count > 0 && cq.count > 0 && !b.serial) {
     fk = side_streams();
     if (!fk) return cudaErrorUnknown;
     e = fork_side(fk, 1, s);

@@ -131,14 +131,18 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   uint64_t* sempty = sfull + stages;
   uint64_t* ifull = sempty + stages;  // [kOzSlices]: the products of slice i are complete
   uint64_t* lempty = ifull + kOzSlices;  // [kOzLevels]: the epilogue has read level L
-  uint32_t* tmem_slot = (uint32_t*)(lempty + kOzLevels);
+  uint64_t* mdone = lempty + kOzLevels;  // every MMA issued has completed
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
   __shared__ int err;
+  __shared__ int keep_tmem;  // an in-flight copy or MMA could not be drained: leave TMEM allocated
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   constexpr uint32_t ncols = 512;
 
   if (threadIdx.x == 0) {
     err = 0;
+    keep_tmem = 0;
+    mbar_init(mdone, 1);
     for (int t = 0; t < 2; ++t) {
       mbar_init(&pfull[t], 1);
       mbar_init(&pempty[t], 1);
@@ -168,6 +172,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   if (warp == 0 && lane == 0) {
     // producer: slice i of P (all K tiles), then the S tiles of every j it pairs with
     int step = 0;
+    int p_last[2] = {-1, -1};  // last use issued of each P buffer
     for (int c = 0; c < nc && !*errv; ++c) {
       const int kt0 = c * kOzMaxKt, nk = min(kOzMaxKt, nkt - kt0);
       for (int i = 1; i <= kOzSlices && !*errv; ++i) {
@@ -177,6 +182,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
           break;
         }
         mbar_expect_tx(&pfull[pb], (uint32_t)nk * kTileA);
+        p_last[pb] = use;
         for (int kt = 0; kt < nk; ++kt)
           tma_load_2d(pbuf + ((size_t)pb * kOzMaxKt + kt) * kTileA, &J.tp, &pfull[pb], (kt0 + kt) * kOzBK,
                       (i - 1) * J.M + m0);
@@ -191,6 +197,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
             tma_load_2d(sbuf + (size_t)s * s_stage, &J.ts, &sfull[s], (kt0 + kt) * kOzBK, (j - 1) * J.Npad + n0);
           }
       }
+    }
+    // no load may still be writing shared memory when the CTA leaves: wait (bounded) for
+    // the last load of every buffer and stage (already complete on the normal path)
+    bool drained = true;
+    for (int pb = 0; pb < 2; ++pb)
+      if (p_last[pb] >= 0) drained = mbar_wait(&pfull[pb], p_last[pb] & 1) && drained;
+    for (int st = max(0, step - stages); st < step; ++st)
+      drained = mbar_wait(&sfull[st % stages], (st / stages) & 1) && drained;
+    if (!drained) {
+      atomicExch(&err, 1);
+      keep_tmem = 1;
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: product (i, j) accumulates into the TMEM columns of level i + j
@@ -238,6 +255,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
       mma_commit(&pempty[pb]);
       mma_commit(&ifull[i - 1]);
      }
+    }
+    // every MMA issued has completed before TMEM is released (bounded wait)
+    mma_commit(mdone);
+    if (!mbar_wait(mdone, 0)) {
+      atomicExch(&err, 1);
+      keep_tmem = 1;
     }
   } else if (warp >= 2) {
     // epilogue: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31.
@@ -288,7 +311,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 1) {
+  if (warp == 1 && !keep_tmem) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
   }
@@ -298,7 +321,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
 size_t oz_smem_bytes(int ntile, int stages) {
   const size_t s_stage = ((size_t)ntile * 128 + 1023) / 1024 * 1024;
   return 1024 + 2 * (size_t)kOzMaxKt * kOzM * 128 + s_stage * stages +
-         (4 + 2 * (size_t)stages + kOzSlices + kOzLevels) * 8 + 16;
+         (4 + 2 * (size_t)stages + kOzSlices + kOzLevels + 1) * 8 + 16;
 }
 
 }  // namespace

@@ -6,15 +6,35 @@
 
 namespace rsvd {
 
+void* current_context() {
+  // cuCtxGetCurrent through the runtime's driver entry point (the library links the
+  // runtime only)
+  using Fn = int (*)(void**);
+  static Fn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = (Fn)p;
+  }
+  void* ctx = nullptr;
+  return fn(&ctx) == 0 ? ctx : nullptr;
+}
+
 SideStreams* side_streams() {
   constexpr int kMaxDevices = 64;
   thread_local SideStreams ss[kMaxDevices];  // per host thread: concurrent callers never share events
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
   SideStreams& x = ss[dev];
-  if (!x.ready) {
+  // created once per host thread and device, and again when the device's context was
+  // replaced (cudaDeviceReset): handles of a destroyed context are not reused
+  if (!x.ready || x.ctx != current_context()) {
     SideStreams y;
     if (cudaEventCreateWithFlags(&y.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    y.ctx = current_context();  // current now: the runtime made the device's context current
     for (int i = 0; i < kSideStreams; ++i)
       if (cudaStreamCreateWithFlags(&y.stream[i], cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&y.join[i], cudaEventDisableTiming) != cudaSuccess)

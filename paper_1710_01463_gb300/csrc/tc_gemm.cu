@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
   uint64_t* done = empty + stages;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   __shared__ int err;
+  __shared__ int keep_tmem;  // an in-flight copy or MMA could not be drained: leave TMEM allocated
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   uint32_t ncols = 32;
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 
   if (threadIdx.x == 0) {
     err = 0;
+    keep_tmem = 0;
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
 
   if (warp == 0 && lane == 0 && !skip_loads) {
     // producer
+    int issued = 0;
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % stages;
       if (kt >= stages && !mbar_wait(&empty[s], ((kt / stages) & 1) ^ 1)) {
@@ -88,7 +91,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       mbar_expect_tx(&full[s], a_bytes + b_bytes);
       tma_load_2d(sa, &J.ta, &full[s], kt * BK, m0);
       tma_load_2d(sa + a_bytes, &J.tb, &full[s], kt * BK, 0);
+      issued = kt + 1;
     }
+    // no load may still be writing shared memory when the CTA leaves: wait (bounded) for
+    // the last load of every stage (already complete on the normal path)
+    for (int kt = max(0, issued - stages); kt < issued; ++kt)
+      if (!mbar_wait(&full[kt % stages], (kt / stages) & 1)) {
+        atomicExch(&err, 1);
+        keep_tmem = 1;
+      }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     const uint32_t id = idesc<TIn>(kTcM, N);
@@ -109,6 +120,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
       mma_commit(&empty[s]);
     }
     mma_commit(done);
+    // every MMA issued has completed before TMEM is released (bounded wait)
+    if (!mbar_wait(done, 0)) {
+      atomicExch(&err, 1);
+      keep_tmem = 1;
+    }
   } else if (warp >= 2) {
     // epilogue: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31
     const int q = warp % 4;
@@ -137,7 +153,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const __grid_con
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 1) {
+  if (warp == 1 && !keep_tmem) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
   }

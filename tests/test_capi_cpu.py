@@ -75,7 +75,28 @@ def test_workspace_holds_the_fp64_slices(lib):
 
 def test_unknown_flags_rejected(lib):
     sz = ctypes.c_size_t(0)
-    assert lib.rsvd_workspace_size(64, 64, ctypes.byref(params(flags=2)), ctypes.byref(sz)) == -1
+    assert lib.rsvd_workspace_size(64, 64, ctypes.byref(params(flags=8)), ctypes.byref(sz)) == -1
+    assert lib.rsvd_workspace_size(64, 64, ctypes.byref(params(flags=1 << 29)), ctypes.byref(sz)) == -1
+
+
+def test_full_svd_flag_workspace_and_rejections(lib):
+    # Alg. TSVD on the same engine: B = A holds all m rows (m <= 1024), so the workspace
+    # grows beyond the sampled path's; entry points without a TSVD form reject the flag
+    from paper_1710_01463_gb300 import _lib
+    full = _lib.RSVD_FLAG_FULL_SVD
+    assert wsize(256, 256, flags=full) > wsize(256, 256)
+    sz = ctypes.c_size_t(0)
+    assert lib.rsvd_workspace_size(1025, 64, ctypes.byref(params(flags=full)), ctypes.byref(sz)) == -1
+    assert lib.rsvd_factored_workspace_size(64, 16, 64, ctypes.byref(params(k=8, flags=full)), ctypes.byref(sz)) == -1
+    assert lib.rsvd_tol_workspace_size(64, 64, 16, ctypes.byref(params(k=8, flags=full)), ctypes.byref(sz)) == -1
+    m = _lib.int_array([64, 80])
+    n = _lib.int_array([70, 90])
+    assert lib.rsvd_sectors_adaptive_workspace_size(2, m, n, 16, ctypes.byref(params(k=8, flags=full)),
+                                                    ctypes.byref(sz)) == -1
+    D = _lib.int_array([1, 2, 4, 2, 1])
+    assert lib.tebd_workspace_size(4, 2, D, 2, ctypes.byref(params(k=1, flags=full)), ctypes.byref(sz)) == 0
+    assert lib.tebd_product_workspace_size(4, 2, D, 2, 2, ctypes.byref(params(k=1, flags=full)),
+                                           ctypes.byref(sz)) == -1
 
 
 @pytest.mark.parametrize("m,n,k,p,q,prec,code", [

@@ -104,3 +104,20 @@ def test_cg_cap_is_reported(api):
                                                     [c(Ub)], None, None, max_iter=1, tol=1e-14)
     torch.cuda.synchronize()
     assert api.info_dicts(info)[0]["status"] == 2
+
+
+def test_autograd_warns_on_cg_cap(api):
+    # RSVDTrunc reads the backward's status: a conjugate-gradient cap that is too small
+    # reaches the caller as a RuntimeWarning, not as a silently unconverged gradient
+    A = inputs.spectral_matrix(90, 70, 1.0 / (1.0 + 0.3 * np.arange(1, 71)), 5)
+    At = torch.from_numpy(A).cuda().requires_grad_(True)
+    U, S, Vt = api.RSVDTrunc.apply(At, 6, 10, 2, 3, 0, 1)
+    with pytest.warns(RuntimeWarning, match="status 2"):
+        ((U[:, :3] ** 2).sum() * 0.0 + (U ** 3).sum() + S.sum()).backward()
+
+
+def test_autograd_raises_on_nonfinite_input(api):
+    A = inputs.spectral_matrix(40, 30, 1.0 / np.arange(1, 31), 6)
+    A[3, 4] = np.nan
+    with pytest.raises(RuntimeError, match="status -6"):
+        api.RSVDTrunc.apply(torch.from_numpy(A).cuda(), 4, 6, 1, 3, 0)

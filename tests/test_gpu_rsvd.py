@@ -118,6 +118,23 @@ def test_nonfinite_input_reported(api):
     assert api.info_dicts(info)[0]["status"] == -6
 
 
+def test_jacobi_exchange_timeout_reported(api):
+    # the failure path of the Jacobi SVD's cluster exchange: with the test flag no CTA
+    # sends its partials, every CTA's first wait runs out (about 0.13 s), the cluster
+    # leaves the iteration together and the status says so; the context stays usable
+    from paper_1710_01463_gb300 import _lib
+    A = inputs.dense_case(96, 80, seed=101)
+    Ad = torch.from_numpy(A).cuda()
+    U, S, Vt, info = api.rsvd_truncate(Ad, 12, 6, 2, 201, flags=_lib.RSVD_FLAG_TEST_NO_EXCHANGE)
+    torch.cuda.synchronize()
+    assert api.info_dicts(info)[0]["status"] == _lib.RSVD_ERR_TIMEOUT
+    U, S, Vt, info = api.rsvd_truncate(Ad, 12, 6, 2, 201)
+    torch.cuda.synchronize()
+    assert api.info_dicts(info)[0]["status"] == 0
+    _, So, _ = orsvd.rsvd(A, 12, 6, 2, 201)
+    assert np.all(np.abs(S.cpu().numpy() - So) <= sigma_tol(So))
+
+
 def test_sweep_cap_reported(api):
     A = inputs.dense_case()
     U, S, Vt, info = api.rsvd_truncate(torch.from_numpy(A).cuda(), 32, 8, 2, 201, max_sweeps=1)

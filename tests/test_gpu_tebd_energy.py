@@ -1,10 +1,21 @@
-"""TEBD on the GPU reaches the ground energy of the open critical transverse-field
-Ising chain (L = 64, chi = 128): the free-fermion closed form
-E0 = 1 - 1/sin(pi / (2 (2L + 1))) = -81.12598012314353 (stored in
-tests/golden/tfim_critical_e0.json), within 1e-6 relative - the bound set by
-the second-order Trotter error at the final dt (energy error ~ dt^4) and the
-bond-dimension truncation.  Imaginary-time schedule dt = 0.1, 0.05, 0.02 as in
-the paper's protocol of reducing dt (Sec. III.C)."""
+"""TEBD on the GPU at the full size of the benchmark: the open critical transverse-field
+Ising chain, L = 64, chi = 128, 256 x 256 bond matrices, FP64, p = 10, q = 2.
+
+* Ground energy: after the imaginary-time schedule dt = 0.1, 0.05, 0.02 (the paper's
+  protocol of reducing dt, Sec. III.C) the MPS energy is within 1e-6 relative of the
+  free-fermion closed form E0 = 1 - 1/sin(pi / (2 (2L + 1))) = -81.12598012314353
+  (tests/golden/tfim_critical_e0.json) - the bound set by the Trotter error at the
+  final dt (energy error ~ dt^4) and the truncation.
+* Stepwise parity (Sec. III.A block update): from the benchmark's own states - the
+  converged ground state and the early state after 20 coarse steps - two Trotter steps
+  at dt = 0.01 on the GPU and in the oracle (same Philox streams, the GPU state copied
+  to the oracle) give every Schmidt value within 1e-10 max(lambda_j) + 1e-14 and the
+  same MPS energy within 1e-10 relative.  The run takes the default production path:
+  FP64 products with A on the tensor cores by exact slicing, and the Householder QR
+  stopping at the sample's numerical rank with the later products over that rank only
+  (rsvd_info.qr_columns < l asserted on every 256 x 256 bond of the early state, whose
+  samples are numerically rank deficient, and on some bonds of the ground state).
+"""
 import json
 import os
 
@@ -18,26 +29,75 @@ from paper_1710_01463_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+L, CHI, H, P, Q, SEED = 64, 128, 1.0, 10, 2, 5
 
 
-def test_tebd_l64_reaches_free_fermion_energy():
+def make_chain(schedule):
     need_gpu()
     from paper_1710_01463_gb300 import tebd
-    e0 = json.load(open(os.path.join(HERE, "golden", "tfim_critical_e0.json")))["energies"]["64"]["closed_form"]
-    L = 64
-    ch = tebd.TebdChain(L, 128, h=1.0, p=10, q=2, seed=11)
+    ch = tebd.TebdChain(L, CHI, h=H, p=P, q=Q, seed=SEED)
     ch.set_product_state(inputs.product_state_vectors(L, 2, 102))
-    step = 0
-    for dt, n in ((0.1, 700), (0.05, 500), (0.02, 250)):
-        ch.set_dt(dt)
-        for _ in range(n):
-            ch.step(step)
-            step += 1
+    nxt = ch.evolve(schedule)
     torch.cuda.synchronize()
+    return ch, nxt
+
+
+@pytest.fixture(scope="module")
+def ground():
+    from paper_1710_01463_gb300 import tebd
+    return make_chain(tebd.SCHEDULE_GROUND)
+
+
+def test_tebd_l64_reaches_free_fermion_energy(ground):
+    ch, _ = ground
+    e0 = json.load(open(os.path.join(HERE, "golden", "tfim_critical_e0.json")))["energies"]["64"]["closed_form"]
     assert int((ch.info[..., 0] < 0).sum()) == 0
-    e = otebd.mps_energy(ch.tensors(), L, 1.0)
+    e = otebd.mps_energy(ch.tensors(), L, H)
     rel = (e - e0) / abs(e0)
     assert 0.0 <= rel < 1e-6, rel
     lam = ch.schmidt_values()
     for j in range(1, L):
         assert abs(np.sum(lam[j] ** 2) - 1.0) < 1e-12
+
+
+def stepwise_parity(ch, first, all_early, steps=2, dt=0.01):
+    B = ch.tensors()
+    lam = ch.schmidt_values()
+    comp = otebd.make_compressor("rsvd", p=P, q=Q, seed=SEED)
+    terms = otebd.chain_bond_terms(L, H)
+    ch.set_dt(dt)
+    qr_cols = []
+    for s in range(first, first + steps):
+        ch.step(s)
+        otebd.trotter_step(B, lam, L, H, dt, comp, s, terms)
+        torch.cuda.synchronize()
+        info = ch.info.cpu().numpy()  # (layer, compression, bond, fields)
+        assert np.all(info[..., 0] == 0), info[..., 0]
+        # the 256 x 256 bonds (l = 138): the Householder QR stopped at the numerical rank
+        for layer, bonds in enumerate((ch.layers[0], ch.layers[1], ch.layers[0])):
+            for b, i in enumerate(bonds):
+                if ch.D[i] * 2 == 256 and ch.D[i + 2] * 2 == 256:
+                    qr_cols.append(int(info[layer, 0, b, 6]))
+                    assert int(info[layer, 0, b, 4]) == 138
+    # the early state's samples are numerically rank deficient on every 256 x 256 bond;
+    # at the ground state most are not, and the early stop runs on some bonds only
+    assert qr_cols and (max(qr_cols) if all_early else min(qr_cols)) < 138, qr_cols
+    lam_g = ch.schmidt_values()
+    for j in range(1, L):
+        a, b = lam_g[j], lam[j]
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-10 * np.max(b) + 1e-14)
+    e_g = otebd.mps_energy(ch.tensors(), L, H)
+    e_o = otebd.mps_energy(B, L, H)
+    assert e_g == pytest.approx(e_o, rel=1e-10)
+    return qr_cols
+
+
+def test_tebd_l64_steps_match_oracle_at_ground_state(ground):
+    ch, nxt = ground
+    stepwise_parity(ch, nxt, all_early=False)
+
+
+def test_tebd_l64_steps_match_oracle_early_state():
+    from paper_1710_01463_gb300 import tebd
+    ch, nxt = make_chain(tebd.SCHEDULE_EARLY)
+    stepwise_parity(ch, nxt, all_early=True)

@@ -28,7 +28,7 @@ def mods():
     return _lib, api
 
 
-def call_noalloc(_lib, A, k, p, q, seed, stream):
+def call_noalloc(_lib, A, k, p, q, seed, stream, cuda_stream=None):
     lib = _lib.load()
     m, n = A.shape
     U = torch.empty((m, k), dtype=A.dtype, device=A.device)
@@ -40,7 +40,7 @@ def call_noalloc(_lib, A, k, p, q, seed, stream):
     rc = lib.rsvd_truncate_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.byref(par),
                                    ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(U.data_ptr()), U.stride(0),
                                    ctypes.c_void_p(Vt.data_ptr()), Vt.stride(0), ctypes.c_void_p(info.data_ptr()),
-                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+                                   ctypes.c_void_p((cuda_stream or torch.cuda.current_stream()).cuda_stream))
     return rc, U, S, Vt, info
 
 
@@ -65,6 +65,24 @@ def test_two_calls_in_a_row_match_workspace_path(mods):
     torch.cuda.synchronize()
     compare(api, first, A1, 32, 8, 2, 201, 0)
     compare(api, second, A2, 20, 6, 2, 7, 3)
+
+
+def test_back_to_back_on_one_stream_same_shape(mods):
+    # two calls queued on one non-default stream with no synchronisation between them,
+    # same shape and different data: the second call's kernels (and the side streams
+    # each call forks from and joins back to that stream) start only after the first
+    # call's work on the shared array is done, so both results are right
+    _lib, api = mods
+    A1 = torch.from_numpy(inputs.dense_case(256, 256, seed=101)).cuda()
+    A2 = torch.from_numpy(inputs.spectral_matrix(256, 256, inputs.exp_spectrum(256, 9.0), 33)).cuda()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        first = call_noalloc(_lib, A1, 32, 8, 2, 201, 0, side)
+        second = call_noalloc(_lib, A2, 32, 8, 2, 11, 2, side)
+    torch.cuda.synchronize()
+    compare(api, first, A1, 32, 8, 2, 201, 0)
+    compare(api, second, A2, 32, 8, 2, 11, 2)
 
 
 def test_size_beyond_the_fixed_scratch_is_rejected(mods):
