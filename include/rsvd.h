@@ -320,6 +320,35 @@ int rsvd_truncate_sectors_adaptive(int batch, const int* m, const int* n, const 
                                    void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
 
 /*
+ * rsvd_complex_workspace_size - workspace bytes of rsvd_truncate_complex.
+ */
+int rsvd_complex_workspace_size(int m, int n, const rsvd_params* p, size_t* bytes);
+
+/*
+ * rsvd_truncate_complex - Alg. RSVD (Sec. II.B) of a complex m-by-n matrix (the paper
+ * runs its simulations in complex double, Sec. IV): A ~ U diag(S) V^H with a real
+ * Gaussian test matrix Omega (n x l, the one of rsvd_gaussian with key (seed, stream)),
+ * every transpose a conjugate transpose, and the phase rule in place of the sign rule:
+ * the entry of largest modulus of u_i (lowest row index on ties) is real and positive,
+ * row i of V^H taking the conjugate phase so that u_i s_i v_i^H is unchanged.
+ *   A   [in]  device, m x n complex, interleaved (re, im) pairs, row-major, lda >= n
+ *             (complex elements); double (RSVD_F64) or float (RSVD_F32)
+ *   S   [out] device, k doubles, descending
+ *   U   [out] device, m x k complex (ldu >= k), orthonormal columns
+ *   Vh  [out] device, k x n complex (ldvh >= n): V^H, orthonormal rows
+ * Computed through the real embedding R(A) = [Re A, -Im A; Im A, Re A] (2m x 2n; the
+ * same products, orthonormalisations and Jacobi SVD as rsvd_truncate, with the test
+ * matrix diag(Omega, Omega)): its singular values are those of A twice, and its sampled
+ * subspaces are the realifications of the complex algorithm's, so the results agree with
+ * the complex algorithm in exact arithmetic.  Flags as rsvd_truncate
+ * (RSVD_FLAG_FULL_SVD: Alg. TSVD of A on the same engine, m <= 512).
+ * Errors: RSVD_ERR_INVALID_SIZE, RSVD_ERR_NULL_POINTER, RSVD_ERR_PRECISION (tensor-core
+ * precisions), RSVD_ERR_WORKSPACE, RSVD_ERR_LAUNCH.
+ */
+int rsvd_truncate_complex(int m, int n, const void* A, int lda, const rsvd_params* p, double* S, void* U, int ldu,
+                          void* Vh, int ldvh, void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
  * rsvd_tol_workspace_size - workspace bytes of rsvd_truncate_tol.
  */
 int rsvd_tol_workspace_size(int m, int n, int k_max, const rsvd_params* p, size_t* bytes);

@@ -58,6 +58,8 @@ EXPORTED = (
     "rsvd_gemm_f64_tc",
     "rsvd_backward_workspace_size",
     "rsvd_truncate_backward_batched",
+    "rsvd_complex_workspace_size",
+    "rsvd_truncate_complex",
     "rsvd_truncate_noalloc",
     "rsvd_noalloc_scratch_bytes",
 )
@@ -139,6 +141,8 @@ def load():
     lib.rsvd_truncate_backward_batched.argtypes = [i, ip, ip, ip, i, pp, ip, pp, pp, ip, pp, ip, pp, ip, pp, pp, ip,
                                                    pp, ip, i, ctypes.c_double, vp, sz, vp, vp]
     lib.rsvd_truncate_noalloc.argtypes = [i, i, vp, i, par, vp, vp, i, vp, i, vp, vp]
+    lib.rsvd_complex_workspace_size.argtypes = [i, i, par, ctypes.POINTER(sz)]
+    lib.rsvd_truncate_complex.argtypes = [i, i, vp, i, par, vp, vp, i, vp, i, vp, sz, vp, vp]
     dbl = ctypes.c_double
     lib.tebd_product_workspace_size.argtypes = [i, i, ip, i, i, par, ctypes.POINTER(sz)]
     lib.tebd_product_update.argtypes = [i, i, ip, i, ip, vp, sz, vp, sz, i, vp, vp, par, vp, vp, sz, vp, vp]

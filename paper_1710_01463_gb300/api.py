@@ -101,6 +101,34 @@ def rsvd_truncate(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, tf3
     return U, S, Vt, info
 
 
+def rsvd_truncate_complex(A, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None, flags=0):
+    """Rank-k RSVD of a complex matrix (rsvd_truncate_complex): A a complex128 (FP64) or
+    complex64 (FP32) CUDA tensor, row-major.  Returns (U, S, Vh, info): U m x k and Vh
+    k x n complex (Vh = V^H), S float64."""
+    lib = _lib.load()
+    _require_cuda(A)
+    if A.dim() != 2 or A.stride(1) != 1 or A.dtype not in (torch.complex128, torch.complex64):
+        raise ValueError("A must be a row-major complex128 or complex64 2-D tensor")
+    prec = _lib.RSVD_F64 if A.dtype == torch.complex128 else _lib.RSVD_F32
+    m, n = A.shape
+    par = _params(k, p, q, prec, seed, stream, max_sweeps, False, flags)
+    sz = ctypes.c_size_t(0)
+    _lib.check(lib.rsvd_complex_workspace_size(m, n, ctypes.byref(par), ctypes.byref(sz)),
+               "rsvd_complex_workspace_size")
+    if work is None or work.numel() < sz.value:
+        work = torch.empty(max(sz.value, 1), dtype=torch.uint8, device=A.device)
+    U = torch.empty((m, k), dtype=A.dtype, device=A.device)
+    S = torch.empty((k,), dtype=torch.float64, device=A.device)
+    Vh = torch.empty((k, n), dtype=A.dtype, device=A.device)
+    info = torch.zeros((1, _lib.INFO_INTS), dtype=torch.int32, device=A.device)
+    rc = lib.rsvd_truncate_complex(m, n, ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.byref(par),
+                                   ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(U.data_ptr()), U.stride(0),
+                                   ctypes.c_void_p(Vh.data_ptr()), Vh.stride(0), ctypes.c_void_p(work.data_ptr()),
+                                   ctypes.c_size_t(work.numel()), ctypes.c_void_p(info.data_ptr()), _stream_handle())
+    _lib.check(rc, "rsvd_truncate_complex")
+    return U, S, Vh, info
+
+
 def rsvd_truncate_factored(X, Y, k, p=8, q=2, seed=0, stream=0, max_sweeps=0, work=None):
     """Rank-k RSVD of A = X Y without forming A (rsvd_truncate_factored): X (m x r) and Y
     (r x n) float64 or float32 CUDA tensors.  Returns (U, S, Vt, info)."""

@@ -42,6 +42,7 @@ struct Prob {
   int max_sweeps;
   int no_exchange;  // RSVD_FLAG_TEST_NO_EXCHANGE
   int serial;       // RSVD_FLAG_SERIAL: independent groups one after another on the caller's stream
+  int cplx;         // the real embedding of a complex matrix: Omega enters as diag(Omega, Omega)
   // workspace
   void *Y0, *Y1, *Z0, *Z1, *Rinv, *Ps;
   double *G, *part, *hw, *hq, *Bm, *Bg, *Pg, *sig;
@@ -347,12 +348,24 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
   }
   if (!rs.empty()) {
     const int rc = (int)rs.size();
-    {  // step 1: Omega (n x l) into Z0
+    {  // step 1: Omega (n x l) into Z0; for the real embedding of a complex matrix the
+       // (n/2 x l/2) test matrix twice on the diagonal, zeros elsewhere
       OmegaBatch<T> b;
-      b.count = rc;
+      b.count = 0;
       for (int i = 0; i < rc; ++i) {
         Prob& p = *rs[i];
-        b.job[i] = OmegaJob<T>{p.n, p.l, p.l, (T*)p.Z0, p.seed, p.stream};
+        if (!p.cplx) {
+          b.job[b.count++] = OmegaJob<T>{p.n, p.l, p.l, (T*)p.Z0, p.seed, p.stream};
+          continue;
+        }
+        RSVD_TRY(cudaMemsetAsync(p.Z0, 0, (size_t)p.n * p.l * sizeof(T), s));
+        const int nc = p.n / 2, lc = p.l / 2;
+        b.job[b.count++] = OmegaJob<T>{nc, lc, p.l, (T*)p.Z0, p.seed, p.stream};
+        b.job[b.count++] = OmegaJob<T>{nc, lc, p.l, (T*)p.Z0 + (size_t)nc * p.l + lc, p.seed, p.stream};
+        if (b.count + 2 > kMaxJobs) {
+          RSVD_TRY(launch_omega<T>(b, s));
+          b.count = 0;
+        }
       }
       RSVD_TRY(launch_omega<T>(b, s));
     }
@@ -711,6 +724,7 @@ const char* rsvd_status_string(int status) {
     case RSVD_ERR_LAUNCH: return cudaGetErrorString(last_cuda_error());
     case RSVD_ERR_NONFINITE: return "non-finite value in the input";
     case RSVD_WARN_NOCONV: return "Jacobi SVD reached its sweep cap";
+    case RSVD_WARN_CG: return "a conjugate-gradient column did not converge or met non-positive curvature";
     case RSVD_ERR_TIMEOUT: return "a device pipeline wait timed out (results invalid)";
     case RSVD_ERR_SCRATCH_LIMIT: return "matrix needs more scratch than the fixed no-allocation array holds";
     default: return "unknown status";
@@ -1332,6 +1346,101 @@ int tebd_product_update(int L, int d, const int* D, int nb, const int* bond, dou
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- complex matrices
+namespace rsvd {
+namespace {
+struct CplxLayout {
+  size_t R, Ur, Vtr, Sr, rsvd, total;
+};
+// workspace of the complex call: R(A) (2m x 2n), the real factors (2m x 2k, 2k x 2n, 2k
+// values) and the real call's workspace for R(A) at rank 2k, oversampling 2p
+int cplx_layout(int m, int n, const rsvd_params* p, CplxLayout* L) {
+  const size_t ts = tsize_of(p->prec);
+  rsvd_params q = *p;
+  q.k = 2 * p->k;
+  q.p = 2 * p->p;
+  size_t real = 0;
+  const int m2 = 2 * m, n2 = 2 * n;
+  int rc = rsvd_workspace_size(m2, n2, &q, &real);
+  if (rc) return rc;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t x = off;
+    off += align_up(b);
+    return x;
+  };
+  L->R = take((size_t)m2 * n2 * ts);
+  L->Ur = take((size_t)m2 * q.k * ts);
+  L->Vtr = take((size_t)q.k * n2 * ts);
+  L->Sr = take((size_t)q.k * 8);
+  L->rsvd = take(real);
+  L->total = off;
+  return RSVD_OK;
+}
+}  // namespace
+}  // namespace rsvd
+
+extern "C" int rsvd_complex_workspace_size(int m, int n, const rsvd_params* p, size_t* bytes) {
+  using namespace rsvd;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!bytes) return RSVD_ERR_NULL_POINTER;
+  if (p->prec != RSVD_F64 && p->prec != RSVD_F32) return RSVD_ERR_PRECISION;
+  if (m < 1 || n < 1 || p->k < 1 || p->k > std::min(m, n)) return RSVD_ERR_INVALID_SIZE;
+  CplxLayout L;
+  rc = cplx_layout(m, n, p, &L);
+  if (rc) return rc;
+  *bytes = L.total;
+  return RSVD_OK;
+}
+
+extern "C" int rsvd_truncate_complex(int m, int n, const void* A, int lda, const rsvd_params* p, double* S, void* U,
+                                     int ldu, void* Vh, int ldvh, void* work, size_t work_bytes, rsvd_info* info,
+                                     void* cuda_stream) {
+  using namespace rsvd;
+  size_t need = 0;
+  int rc = rsvd_complex_workspace_size(m, n, p, &need);
+  if (rc) return rc;
+  if (!A || !S || !U || !Vh || !work || !info) return RSVD_ERR_NULL_POINTER;
+  if (lda < n || ldu < p->k || ldvh < n) return RSVD_ERR_INVALID_SIZE;
+  if (((uintptr_t)work) % kAlign) return RSVD_ERR_WORKSPACE;
+  if (need > work_bytes) return RSVD_ERR_WORKSPACE;
+  CplxLayout L;
+  cplx_layout(m, n, p, &L);
+  char* base = (char*)work;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const bool f64 = p->prec == RSVD_F64;
+  RSVD_TRY(f64 ? launch_realify<double>(m, n, (const double*)A, lda, (double*)(base + L.R), s)
+               : launch_realify<float>(m, n, (const float*)A, lda, (float*)(base + L.R), s));
+  rsvd_params q = *p;
+  q.k = 2 * p->k;
+  q.p = 2 * p->p;
+  std::vector<Prob> probs(1);
+  Prob& pr = probs[0];
+  std::memset(&pr, 0, sizeof(Prob));
+  pr.m = 2 * m; pr.n = 2 * n; pr.k = q.k;
+  pr.l = b_rows(pr.m, pr.n, pr.k, &q);  // 2 min(k + p, m, n), or 2m for Alg. TSVD
+  pr.exact = exact_of(pr.m, pr.l, &q);
+  pr.want_u = 1;
+  pr.A = base + L.R; pr.lda = 2 * n;
+  pr.S = (double*)(base + L.Sr);
+  pr.U = base + L.Ur; pr.ldu = q.k;
+  pr.Vt = base + L.Vtr; pr.ldvt = 2 * n;
+  pr.seed = p->seed; pr.stream = p->stream;
+  pr.info = info;
+  pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+  pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
+  pr.no_exchange = (p->flags & RSVD_FLAG_TEST_NO_EXCHANGE) ? 1 : 0;
+  pr.cplx = 1;
+  rc = run_batched(probs, &q, base + L.rsvd, L.total - L.rsvd, s);
+  if (rc) return rc;
+  RSVD_TRY(f64 ? launch_complex_extract<double>(m, n, p->k, pr.S, (const double*)pr.U, q.k, (const double*)pr.Vt,
+                                                2 * n, S, (double*)U, ldu, (double*)Vh, ldvh, s)
+               : launch_complex_extract<float>(m, n, p->k, pr.S, (const float*)pr.U, q.k, (const float*)pr.Vt,
+                                               2 * n, S, (float*)U, ldu, (float*)Vh, ldvh, s));
+  return RSVD_OK;
+}
 
 // ---------------------------------------------------------------- no-allocation entry point
 // Some callers cannot hand the library a workspace: code that runs where

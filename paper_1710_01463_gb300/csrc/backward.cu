@@ -29,6 +29,7 @@ constexpr int kColRows = 8;  // warps per CTA in the column reductions
 template <typename T>
 __global__ void __launch_bounds__(256) coldot_kernel(const __grid_constant__ BwBatch<T> b, int which) {
   const BwJob<T>& J = b.job[blockIdx.y];
+  if (which != 2 && !J.flags[2]) return;  // the solve of this matrix has ended
   const int rows = J.rows, k = J.k;
   const int c = blockIdx.x * kColTile + (threadIdx.x % 32);
   const int w = threadIdx.x / 32;
@@ -55,6 +56,7 @@ __global__ void __launch_bounds__(256) coldot_kernel(const __grid_constant__ BwB
 template <typename T>
 __global__ void __launch_bounds__(256) cg_apply_kernel(const __grid_constant__ BwBatch<T> b, int init) {
   const BwJob<T>& J = b.job[blockIdx.y];
+  if (!init && !J.flags[2]) return;
   const size_t tot = (size_t)J.rows * J.k;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(e % J.k);
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(256) cg_apply_kernel(const __grid_constant__ B
 template <typename T>
 __global__ void __launch_bounds__(256) cg_update_zr_kernel(const __grid_constant__ BwBatch<T> b) {
   const BwJob<T>& J = b.job[blockIdx.y];
+  if (!J.flags[2]) return;
   const size_t tot = (size_t)J.rows * J.k;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(e % J.k);
@@ -98,6 +101,7 @@ __global__ void cg_scalar_kernel(const __grid_constant__ BwBatch<T> b, int init)
   int had = 0;
   for (int c = threadIdx.x; c < J.k && !init; c += blockDim.x) had |= J.active[c];
   if (__syncthreads_or(had) && threadIdx.x == 0) J.flags[1] += 1;
+  int still = 0;
   for (int c = threadIdx.x; c < J.k; c += blockDim.x) {
     if (init) {
       J.rho[c] = J.rho0[c];
@@ -124,12 +128,18 @@ __global__ void cg_scalar_kernel(const __grid_constant__ BwBatch<T> b, int init)
     }
     J.rho[c] = rn;
   }
+  for (int c = threadIdx.x; c < J.k; c += blockDim.x) still |= J.active[c];
+  // every launch of the next iteration reads this flag (stream order) and skips the
+  // matrix once no column is left: the work ends with the slowest column
+  const int any = __syncthreads_or(still);
+  if (threadIdx.x == 0) J.flags[2] = any ? 1 : 0;
 }
 
 // p = r + beta p (active columns)
 template <typename T>
 __global__ void __launch_bounds__(256) cg_update_p_kernel(const __grid_constant__ BwBatch<T> b) {
   const BwJob<T>& J = b.job[blockIdx.y];
+  if (!J.flags[2]) return;
   const size_t tot = (size_t)J.rows * J.k;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(e % J.k);
@@ -164,6 +174,7 @@ __global__ void __launch_bounds__(256) bw_core_kernel(const __grid_constant__ Bw
 template <typename T>
 __global__ void __launch_bounds__(256) colscale_kernel(const __grid_constant__ BwScaleBatch<T> b) {
   const BwScaleJob<T>& J = b.job[blockIdx.y];
+  if (J.gate && !*J.gate) return;
   const size_t tot = (size_t)J.rows * J.k;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / J.k), c = (int)(e % J.k);
@@ -425,18 +436,18 @@ int bw_chunk(std::vector<BwProb>& P, int max_iter, double tol, cudaStream_t s) {
     // projection X -> X - U (U^T X) (side 0) or X - V (V^T X) (side 1), in place on `dst`
     auto project = [&](auto src_of) -> int {
       BW_TRY(forsel([&](BwProb& q, GemmBatch<T, T>& g) {
-        if (side == 0) g.job[g.count++] = G{q.k, q.k, q.m, q.ldu, q.k, q.k, (const T*)q.U, src_of(q), (T*)q.G1, nullptr, nullptr, 0};
-        else g.job[g.count++] = G{q.k, q.k, q.n, q.ldvt, q.k, q.k, (const T*)q.Vt, src_of(q), (T*)q.G1, nullptr, nullptr, 0};
+        if (side == 0) g.job[g.count++] = G{q.k, q.k, q.m, q.ldu, q.k, q.k, (const T*)q.U, src_of(q), (T*)q.G1, nullptr, q.flags + 2, 1};
+        else g.job[g.count++] = G{q.k, q.k, q.n, q.ldvt, q.k, q.k, (const T*)q.Vt, src_of(q), (T*)q.G1, nullptr, q.flags + 2, 1};
       }, [&](const GemmBatch<T, T>& g) { return side == 0 ? TN(g) : NN(g); }));
       if (side == 0) {
         BW_TRY(forsel([&](BwProb& q, GemmBatch<T, T>& g) {
-          G j{q.m, q.k, q.k, q.ldu, q.k, q.k, (const T*)q.U, (const T*)q.G1, (T*)src_of(q), nullptr, nullptr, 0};
+          G j{q.m, q.k, q.k, q.ldu, q.k, q.k, (const T*)q.U, (const T*)q.G1, (T*)src_of(q), nullptr, q.flags + 2, 1};
           j.alpha = -1.0; j.accumulate = 1;
           g.job[g.count++] = j;
         }, NN));
       } else {
         BW_TRY(forsel([&](BwProb& q, GemmBatch<T, T>& g) {
-          G j{q.n, q.k, q.k, q.ldvt, q.k, q.k, (const T*)q.Vt, (const T*)q.G1, (T*)src_of(q), nullptr, nullptr, 0};
+          G j{q.n, q.k, q.k, q.ldvt, q.k, q.k, (const T*)q.Vt, (const T*)q.G1, (T*)src_of(q), nullptr, q.flags + 2, 1};
           j.alpha = -1.0; j.accumulate = 1;
           g.job[g.count++] = j;
         }, TN));
@@ -451,6 +462,7 @@ int bw_chunk(std::vector<BwProb>& P, int max_iter, double tol, cudaStream_t s) {
           BwProb& q = P[sel[j]];
           const int rows = side == 0 ? q.m : q.n;
           sc.job[j] = BwScaleJob<T>{rows, q.k, (const T*)q.p, q.k, nullptr, 0, (T*)q.t};
+          sc.job[j].gate = q.flags + 2;
         }
         BW_TRY(launch_bw_colscale<T>(sc, s));
       }
@@ -458,17 +470,17 @@ int bw_chunk(std::vector<BwProb>& P, int max_iter, double tol, cudaStream_t s) {
       if (rc) return rc;
       if (side == 0) {  // t1 = A^T t (n x k), t = A t1 (m x k)
         BW_TRY(forsel([&](BwProb& q, GemmBatch<T, T>& g) {
-          g.job[g.count++] = G{q.n, q.k, q.m, q.lda, q.k, q.k, (const T*)q.A, (const T*)q.t, (T*)q.t1, nullptr, nullptr, 0};
+          g.job[g.count++] = G{q.n, q.k, q.m, q.lda, q.k, q.k, (const T*)q.A, (const T*)q.t, (T*)q.t1, nullptr, q.flags + 2, 1};
         }, TN));
         BW_TRY(forsel([&](BwProb& q, GemmBatch<T, T>& g) {
-          g.job[g.count++] = G{q.m, q.k, q.n, q.lda, q.k, q.k, (const T*)q.A, (const T*)q.t1, (T*)q.t, nullptr, nullptr, 0};
+          g.job[g.count++] = G{q.m, q.k, q.n, q.lda, q.k, q.k, (const T*)q.A, (const T*)q.t1, (T*)q.t, nullptr, q.flags + 2, 1};
         }, NN));
       } else {  // t1 = A t (m x k), t = A^T t1 (n x k)
         BW_TRY(forsel([&](BwProb& q, GemmBatch<T, T>& g) {
-          g.job[g.count++] = G{q.m, q.k, q.n, q.lda, q.k, q.k, (const T*)q.A, (const T*)q.t, (T*)q.t1, nullptr, nullptr, 0};
+          g.job[g.count++] = G{q.m, q.k, q.n, q.lda, q.k, q.k, (const T*)q.A, (const T*)q.t, (T*)q.t1, nullptr, q.flags + 2, 1};
         }, NN));
         BW_TRY(forsel([&](BwProb& q, GemmBatch<T, T>& g) {
-          g.job[g.count++] = G{q.n, q.k, q.m, q.lda, q.k, q.k, (const T*)q.A, (const T*)q.t1, (T*)q.t, nullptr, nullptr, 0};
+          g.job[g.count++] = G{q.n, q.k, q.m, q.lda, q.k, q.k, (const T*)q.A, (const T*)q.t1, (T*)q.t, nullptr, q.flags + 2, 1};
         }, TN));
       }
       rc = project([](BwProb& q) { return (const T*)q.t; });

@@ -228,7 +228,8 @@ struct BwJob {
   const double* s;          // k singular values
   double *pw, *rho, *rho_new, *rho0, *beta;  // k each
   int* active;              // k
-  int* flags;               // bit 0: a column met a non-positive curvature
+  int* flags;               // [0] bit 0: a column met a non-positive curvature; [1] iterations run;
+                            // [2] some column is still active (the loop's launches skip when 0)
   double tol2;
 };
 template <typename T>
@@ -258,6 +259,7 @@ struct BwScaleJob {
   const double* s;          // nullptr: plain copy
   int transpose;            // 1: out[r, c] = in[c * ldin + r]
   T* out;
+  const int* gate = nullptr;  // optional: run only if *gate != 0
 };
 template <typename T>
 struct BwScaleBatch {
@@ -403,6 +405,14 @@ template <typename T>
 cudaError_t launch_bw_core(const BwCoreBatch<T>& b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bw_colscale(const BwScaleBatch<T>& b, cudaStream_t s);
+
+// complex matrices through their real embedding (complex.cu): R(A) = [X -Y; Y X] from the
+// interleaved complex A, and the complex factors from the real ones (phase rule applied)
+template <typename T>
+cudaError_t launch_realify(int m, int n, const T* A, int lda, T* R, cudaStream_t s);
+template <typename T>
+cudaError_t launch_complex_extract(int m, int n, int k, const double* Sr, const T* Ur, int ldur, const T* Vtr,
+                                   int ldvr, double* S, T* U, int ldu, T* Vh, int ldvh, cudaStream_t s);
 
 // last CUDA error seen by a launch of this library (per host thread)
 cudaError_t& last_cuda_error();

@@ -20,6 +20,8 @@ Recipe (all FP64 on the host, numpy PCG64 streams):
   W ~ N(0, 1) of shape m x 8.
 * TEBD: a random product state (Sec. III.C: "product state with randomized
   tensors of bond dimension one").
+* Complex case: A = U diag(s) V^H with U, V the Q factors (R_ii > 0) of seeded
+  complex Gaussian matrices (the paper runs in complex double, Sec. IV).
 """
 import numpy as np
 
@@ -45,6 +47,24 @@ def spectral_matrix(m, n, s, seed):
     U = haar_like_orthogonal(m, 2 * seed)[:, :r]
     V = haar_like_orthogonal(n, 2 * seed + 1)[:, :r]
     return (U * s[None, :]) @ V.T
+
+
+def haar_like_unitary(n, seed):
+    """Q factor (R_ii > 0) of the QR factorization of a seeded complex N(0,1) n x n matrix."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Q, R = np.linalg.qr(G)
+    d = np.diag(R)
+    return Q * np.where(np.abs(d) > 0, d / np.where(np.abs(d) > 0, np.abs(d), 1.0), 1.0)[None, :]
+
+
+def complex_spectral_matrix(m, n, s, seed):
+    """Complex A = U[:, :r] diag(s) V[:, :r]^H with seeded Haar-like unitary factors."""
+    s = np.asarray(s, dtype=np.float64)
+    r = s.size
+    U = haar_like_unitary(m, 2 * seed)[:, :r]
+    V = haar_like_unitary(n, 2 * seed + 1)[:, :r]
+    return (U * s[None, :]) @ V.conj().T
 
 
 def permuted_spectral_matrix(m, n, s, base_seed, j):

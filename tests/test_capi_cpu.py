@@ -35,8 +35,9 @@ def test_exports_every_declared_function(lib):
 
 
 def test_status_strings(lib):
-    for code in (0, -1, -2, -3, -4, -6, 1):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, 1, 2):
         assert len(lib.rsvd_status_string(code)) > 0
+        assert lib.rsvd_status_string(code) != b"unknown status"
 
 
 def params(k=32, p=8, q=2, prec=0, flags=0):

@@ -304,3 +304,26 @@ def test_complex_power_iteration_is_the_literal_power():
     s_lit = np.linalg.svd(Qlit.conj().T @ A, compute_uv=False)[:k]
     np.testing.assert_allclose(s_r, s_lit, rtol=1e-9)
     assert np.all(s_r <= s[:k] * (1 + 1e-12))  # interlacing: the sampled values never exceed the true ones
+
+
+def test_complex_rsvd_equals_real_algorithm_on_the_real_embedding():
+    # The reading the GPU path takes for complex A: Alg. RSVD of the real embedding
+    # R(A) = [Re A, -Im A; Im A, Re A] with the test matrix diag(Omega, Omega) and
+    # rank 2k, oversampling 2p has the complex algorithm's singular values, each twice
+    # (R(A^H) = R(A)^T and every sampled subspace is a realification)
+    from oracle.philox import gaussian_test_matrix
+    m, n, k, p, q = 96, 80, 12, 6, 2
+    A = inputs.complex_spectral_matrix(m, n, inputs.exp_spectrum(80, 10.0), 40 + m)
+    R = np.block([[A.real, -A.imag], [A.imag, A.real]])
+    l = min(k + p, m, n)
+    om = gaussian_test_matrix(n, l, 201, 3)
+    omr = np.zeros((2 * n, 2 * l))
+    omr[:n, :l] = om
+    omr[n:, l:] = om
+    _, sr, _ = orsvd.rsvd(R, 2 * k, 2 * p, q, 201, 3, omega=omr)
+    _, so, _ = orsvd.rsvd_complex(A, k, p, q, 201, 3)
+    np.testing.assert_allclose(sr[0::2], so, rtol=1e-12)
+    np.testing.assert_allclose(sr[1::2], so, rtol=1e-12)
+    # a plain (non-block-diagonal) real test matrix of the same width samples other spaces
+    _, sx, _ = orsvd.rsvd(R, 2 * k, 2 * p, q, 201, 3)
+    assert np.max(np.abs(sx[0::2] - so) / so) > 1e-12
