@@ -511,6 +511,26 @@ int rsvd_profile_enable(int max_launches);
 int rsvd_profile_collect(double* ms, int* launches, int nclass);
 const char* rsvd_profile_class_name(int cls);
 
+/*
+ * Tile autotuner of the batched SIMT products (FP64 and FP32 GEMMs of every entry
+ * point; a measurement-driven choice, not part of the method).  The library keeps a
+ * host cache of tile choices keyed by the launch's shape class (types, transposes,
+ * batch size, largest M, N, K rounded up to 16).  rsvd_autotune_enable(1): from now
+ * on a launch whose class is not cached yet times every candidate tile (CUDA events,
+ * synchronising the host; never while its stream is being captured, and not for
+ * products that accumulate into their output) and caches the fastest; (0) stops
+ * tuning.  Cached choices are always used, inside graph captures too.  The choice
+ * changes no result: every tile sums each output over K in the same order.
+ * rsvd_autotune_entries: cached classes; rsvd_autotune_clear: empties the cache;
+ * rsvd_autotune_save / _load: the cache as a text file (load returns the entries read,
+ * or RSVD_ERR_INVALID_SIZE if the file cannot be opened).  Thread-safe.
+ */
+int rsvd_autotune_enable(int on);
+int rsvd_autotune_entries(void);
+int rsvd_autotune_clear(void);
+int rsvd_autotune_save(const char* path);
+int rsvd_autotune_load(const char* path);
+
 /* rsvd_status_string - static description of a status code (never NULL). */
 const char* rsvd_status_string(int status);
 

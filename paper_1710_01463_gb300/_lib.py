@@ -60,6 +60,11 @@ EXPORTED = (
     "rsvd_truncate_backward_batched",
     "rsvd_complex_workspace_size",
     "rsvd_truncate_complex",
+    "rsvd_autotune_enable",
+    "rsvd_autotune_entries",
+    "rsvd_autotune_clear",
+    "rsvd_autotune_save",
+    "rsvd_autotune_load",
     "rsvd_truncate_noalloc",
     "rsvd_noalloc_scratch_bytes",
 )
@@ -141,6 +146,11 @@ def load():
     lib.rsvd_truncate_backward_batched.argtypes = [i, ip, ip, ip, i, pp, ip, pp, pp, ip, pp, ip, pp, ip, pp, pp, ip,
                                                    pp, ip, i, ctypes.c_double, vp, sz, vp, vp]
     lib.rsvd_truncate_noalloc.argtypes = [i, i, vp, i, par, vp, vp, i, vp, i, vp, vp]
+    lib.rsvd_autotune_enable.argtypes = [i]
+    lib.rsvd_autotune_entries.argtypes = []
+    lib.rsvd_autotune_clear.argtypes = []
+    lib.rsvd_autotune_save.argtypes = [ctypes.c_char_p]
+    lib.rsvd_autotune_load.argtypes = [ctypes.c_char_p]
     lib.rsvd_complex_workspace_size.argtypes = [i, i, par, ctypes.POINTER(sz)]
     lib.rsvd_truncate_complex.argtypes = [i, i, vp, i, par, vp, vp, i, vp, i, vp, sz, vp, vp]
     dbl = ctypes.c_double

@@ -8,6 +8,10 @@
 // shared reads and 16-wide coalesced stores through a stride-16 register-tile
 // layout; register double-buffering of the next K slice overlaps the global
 // loads with the FMAs.
+#include <cstdio>
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace rsvd {
@@ -203,6 +207,49 @@ int sm_count() {
   return n;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Host cache of measured tile choices, keyed by the launch's shape class: operand and
+// output types, transposes, batch size and the largest M, N, K of the batch (rounded up
+// to multiples of 16).  With tuning enabled (rsvd_autotune_enable), a launch whose class
+// is not cached yet - on a stream that is not being captured, with no job accumulating
+// into or overwriting an operand - runs every candidate tile twice under CUDA events
+// (synchronising the host), caches the fastest and then runs it; cached choices are used
+// whether tuning is enabled or not (also inside a graph capture).  The cache is the
+// library's only host state besides the side streams; it can be written to and read
+// from a text file.
+struct TuneKey {
+  int tin, tout, ta, tx, count, M, N, K;
+  bool operator<(const TuneKey& o) const {
+    const int a[8] = {tin, tout, ta, tx, count, M, N, K}, b[8] = {o.tin, o.tout, o.ta, o.tx, o.count, o.M, o.N, o.K};
+    for (int i = 0; i < 8; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+  }
+};
+struct Tuner {
+  std::mutex mu;
+  std::map<TuneKey, int> best;
+  bool on = false;
+  long long tuned = 0;  // launches timed so far
+};
+Tuner& tuner() {
+  static Tuner t;
+  return t;
+}
+
+template <typename Tin, typename Tout, bool TA, bool TX>
+cudaError_t launch_choice(const GemmBatch<Tin, Tout>& b, int c, cudaStream_t s) {
+  switch (c) {
+    case 1: return launch_tile<Tin, Tout, TA, TX, 64, 48>(b, s);
+    case 2: return launch_tile<Tin, Tout, TA, TX, 48, 64>(b, s);
+    case 3: if constexpr (sizeof(Tin) == 8) return launch_tile<Tin, Tout, TA, TX, 48, 32>(b, s); break;
+    case 4: if constexpr (sizeof(Tin) == 8) return launch_tile<Tin, Tout, TA, TX, 32, 48>(b, s); break;
+    case 5: if constexpr (sizeof(Tin) == 8) return launch_tile<Tin, Tout, TA, TX, 32, 32>(b, s); break;
+    default: break;
+  }
+  return launch_tile<Tin, Tout, TA, TX, 64, 64>(b, s);
+}
+
 // Tile shape per launch.  The FMA loop of every shape keeps the SM's FP64 pipe
 // busy, so an FP64 launch takes about as long as its most loaded SM:
 // ceil(tiles / SMs) x tile area.  Small batches of narrow products (the sample
@@ -230,15 +277,57 @@ cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
   int best = 0;
   for (int t = 1; t < ns; ++t)
     if (cost[t] < cost[best]) best = t;
-  switch (best) {
-    case 1: return launch_tile<Tin, Tout, TA, TX, 64, 48>(b, s);
-    case 2: return launch_tile<Tin, Tout, TA, TX, 48, 64>(b, s);
-    case 3: if constexpr (f64) return launch_tile<Tin, Tout, TA, TX, 48, 32>(b, s); break;
-    case 4: if constexpr (f64) return launch_tile<Tin, Tout, TA, TX, 32, 48>(b, s); break;
-    case 5: if constexpr (f64) return launch_tile<Tin, Tout, TA, TX, 32, 32>(b, s); break;
-    default: break;
+  // measured choice of this shape class, when cached (or tuned now)
+  TuneKey key{(int)sizeof(Tin), (int)sizeof(Tout), TA ? 1 : 0, TX ? 1 : 0, b.count, 0, 0, 0};
+  bool safe = true;
+  for (int i = 0; i < b.count; ++i) {
+    key.M = max(key.M, (b.job[i].M + 15) / 16 * 16);
+    key.N = max(key.N, (b.job[i].N + 15) / 16 * 16);
+    key.K = max(key.K, (b.job[i].K + 15) / 16 * 16);
+    const void* C = b.job[i].C;
+    if (b.job[i].accumulate || C == (const void*)b.job[i].A || C == (const void*)b.job[i].X) safe = false;
   }
-  return launch_tile<Tin, Tout, TA, TX, 64, 64>(b, s);
+  Tuner& T = tuner();
+  bool tune = false;
+  {
+    std::lock_guard<std::mutex> lock(T.mu);
+    auto it = T.best.find(key);
+    if (it != T.best.end()) return launch_choice<Tin, Tout, TA, TX>(b, it->second, s);
+    tune = T.on && safe;
+  }
+  if (tune) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) tune = false;
+  }
+  if (tune) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+      float tbest = 1e30f;
+      int cbest = best;
+      bool ok = true;
+      for (int t = 0; t < ns && ok; ++t) {
+        float tt = 0.f;
+        for (int rep = 0; rep < 2 && ok; ++rep) {  // the first run warms the caches
+          ok = cudaEventRecord(e0, s) == cudaSuccess && launch_choice<Tin, Tout, TA, TX>(b, t, s) == cudaSuccess &&
+               cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+               cudaEventElapsedTime(&tt, e0, e1) == cudaSuccess;
+        }
+        if (ok && tt < tbest) {
+          tbest = tt;
+          cbest = t;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ok) {
+        std::lock_guard<std::mutex> lock(T.mu);
+        T.best[key] = cbest;
+        T.tuned += 1;
+        best = cbest;
+      }
+    }
+  }
+  return launch_choice<Tin, Tout, TA, TX>(b, best, s);
 }
 
 #define INST(Tin, Tout)                                                                           \
@@ -251,3 +340,62 @@ INST(float, double)
 #undef INST
 
 }  // namespace rsvd
+
+// ---------------------------------------------------------------- autotuner entry points
+extern "C" int rsvd_autotune_enable(int on) {
+  rsvd::Tuner& T = rsvd::tuner();
+  std::lock_guard<std::mutex> lock(T.mu);
+  T.on = on != 0;
+  return RSVD_OK;
+}
+
+extern "C" int rsvd_autotune_entries(void) {
+  rsvd::Tuner& T = rsvd::tuner();
+  std::lock_guard<std::mutex> lock(T.mu);
+  return (int)T.best.size();
+}
+
+extern "C" int rsvd_autotune_clear(void) {
+  rsvd::Tuner& T = rsvd::tuner();
+  std::lock_guard<std::mutex> lock(T.mu);
+  T.best.clear();
+  return RSVD_OK;
+}
+
+extern "C" int rsvd_autotune_save(const char* path) {
+  if (!path) return RSVD_ERR_NULL_POINTER;
+  rsvd::Tuner& T = rsvd::tuner();
+  std::lock_guard<std::mutex> lock(T.mu);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return RSVD_ERR_INVALID_SIZE;
+  std::fprintf(f, "# librsvd gemm tiles: tin tout ta tx count M N K choice\n");
+  for (const auto& kv : T.best) {
+    const rsvd::TuneKey& k = kv.first;
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", k.tin, k.tout, k.ta, k.tx, k.count, k.M, k.N, k.K, kv.second);
+  }
+  std::fclose(f);
+  return RSVD_OK;
+}
+
+extern "C" int rsvd_autotune_load(const char* path) {
+  if (!path) return RSVD_ERR_NULL_POINTER;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return RSVD_ERR_INVALID_SIZE;
+  rsvd::Tuner& T = rsvd::tuner();
+  std::lock_guard<std::mutex> lock(T.mu);
+  char line[256];
+  int n = 0;
+  while (std::fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    rsvd::TuneKey k;
+    int c = 0;
+    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &k.tin, &k.tout, &k.ta, &k.tx, &k.count, &k.M, &k.N, &k.K,
+                    &c) == 9 &&
+        c >= 0 && c < 6 && (c < 3 || k.tin == 8)) {
+      T.best[k] = c;
+      ++n;
+    }
+  }
+  std::fclose(f);
+  return n;
+}

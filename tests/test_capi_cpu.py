@@ -226,3 +226,22 @@ def test_adaptive_sectors_host_checks(lib):
     assert lib.rsvd_truncate_sectors_adaptive(3, m, n, ptrs, lds, kt, ctypes.byref(par), 64, ptrs, ptrs,
                                               _lib.int_array([8, 64, 64]), ptrs, lds, fake, ctypes.byref(rounds), fake,
                                               big, fake, None) == -1
+
+
+def test_autotune_cache_round_trip(lib, tmp_path):
+    # the host cache of measured tile choices: enable / clear / entries, and the text file
+    # written and read back (no GPU needed: nothing is timed here)
+    assert lib.rsvd_autotune_clear() == 0
+    assert lib.rsvd_autotune_entries() == 0
+    path = tmp_path / "tiles.txt"
+    path.write_text("# tin tout ta tx count M N K choice\n8 8 0 0 3 256 144 256 5\n4 4 1 0 16 1024 144 1024 2\n"
+                    "4 4 0 0 1 64 64 64 4\n")  # the last choice does not exist for FP32: skipped
+    assert lib.rsvd_autotune_load(str(path).encode()) == 2
+    assert lib.rsvd_autotune_entries() == 2
+    out = tmp_path / "out.txt"
+    assert lib.rsvd_autotune_save(str(out).encode()) == 0
+    rows = [r for r in out.read_text().splitlines() if not r.startswith("#")]
+    assert sorted(rows) == sorted(["8 8 0 0 3 256 144 256 5", "4 4 1 0 16 1024 144 1024 2"])
+    assert lib.rsvd_autotune_load(str(tmp_path / "missing.txt").encode()) == -1
+    assert lib.rsvd_autotune_enable(1) == 0 and lib.rsvd_autotune_enable(0) == 0
+    assert lib.rsvd_autotune_clear() == 0 and lib.rsvd_autotune_entries() == 0

@@ -62,3 +62,42 @@ def test_tebd_step_replays_bit_identically(mods):
     assert torch.equal(ch.B, B1) and torch.equal(ch.lam, lam1)
     assert int((ch.info[..., 0] != 0).sum()) == 0
     assert np.isfinite(ch.trunc_err.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("policy", ["maximal", "estimate"])
+def test_sector_bond_step_replays_bit_identically(mods, policy):
+    # the batching form of the sector workload: the 32 uneven blocks (64..2048) of one
+    # block-diagonal bond, FP32 products, with the global top-chi selection, as ONE graph
+    # replay (no host synchronisation inside the step); trial ranks maximal or from a
+    # previous step's kept counts + 16
+    api, _ = mods
+    blocks = [b.astype(np.float32) for b in inputs.sector_blocks(N=32, lo=64, hi=2048, seed=104)]
+    As = [torch.from_numpy(b).cuda() for b in blocks]
+    ks = [min(512, *b.shape) for b in blocks]
+    plan = api.BatchedPlan([b.shape for b in blocks], ks, 16, 2, 103, 0, torch.float32, "cuda", chi_global=512)
+    plan.run(As)
+    torch.cuda.synchronize()
+    if policy == "estimate":
+        kept = plan.k_out.cpu().tolist()
+        ks = [min(min(b.shape), kk + 16) for b, kk in zip(blocks, kept)]
+        plan = api.BatchedPlan([b.shape for b in blocks], ks, 16, 2, 103, 0, torch.float32, "cuda", chi_global=512)
+        plan.run(As)  # eager reference
+        torch.cuda.synchronize()
+    ref = ([s.clone() for s in plan.S], [u.clone() for u in plan.U], [v.clone() for v in plan.Vt],
+           plan.k_out.clone())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.run(As)
+    for s in plan.S:
+        s.zero_()
+    plan.k_out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(plan.k_out, ref[3]) and int(plan.k_out.sum()) == 512
+    for a, b in zip(plan.S, ref[0]):
+        assert torch.equal(a, b)
+    for a, b in zip(plan.U, ref[1]):
+        assert torch.equal(a, b)
+    for a, b in zip(plan.Vt, ref[2]):
+        assert torch.equal(a, b)
+    assert all(d["status"] == 0 for d in api.info_dicts(plan.info))
