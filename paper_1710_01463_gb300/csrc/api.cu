@@ -284,9 +284,10 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
     b.count = 0;
     b.csize = probs[i0].csize;
     b.use_global = probs[i0].use_global;
+    const int csize0 = b.csize;
     for (int i = i0; i < cnt; ++i) {
       Prob& p = probs[i];
-      if (done[i] || p.csize != b.csize || p.use_global != b.use_global) continue;
+      if (done[i] || p.csize != csize0 || p.use_global != b.use_global) continue;
       done[i] = 1;
       JacobiJob<T>& J = b.job[b.count++];
       J.l = p.l; J.n = p.wide ? p.l : p.n; J.k = p.k;
@@ -301,6 +302,19 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       J.want_p = p.want_u;
       J.pipe_err = tc_err ? p.flag + 1 : nullptr;
       J.no_exchange = p.no_exchange;
+    }
+    // spread the group over the SMs: a cluster size between the smallest whose slices fit
+    // shared memory and one of at least 16 columns per CTA (at most 16 CTAs)
+    if (!b.use_global && b.csize > 1) {
+      int cmin = 16, cmax = 16;
+      for (int i = 0; i < b.count; ++i) {
+        const int l = b.job[i].l, n = b.job[i].n;
+        int c = 1;
+        while (c < 16 && !jacobi_fits_smem(l, n, c)) ++c;
+        cmin = i == 0 ? c : std::max(cmin, c);
+        cmax = std::min(cmax, std::max(1, n / 16));
+      }
+      if (cmin <= cmax) b.csize = spread_cluster(b.count, cmin, cmax);
     }
   }
   {

@@ -431,6 +431,28 @@ void* current_context();  // the calling thread's current CUDA context (driver h
 cudaError_t fork_side(SideStreams* ss, int n, cudaStream_t s);  // side streams 0..n-1 wait for s's work so far
 cudaError_t join_side(SideStreams* ss, int n, cudaStream_t s);  // s waits for side streams 0..n-1
 
+// number of SMs of the current device
+int sm_count();
+// Cluster size for a launch of `count` independent matrices, each split over c CTAs
+// (cmin <= c <= cmax): the busiest SM of a launch with count * c CTAs placed one per SM
+// before any SM takes a second carries ceil(count c / SMs) CTAs of 1/c of a matrix each;
+// the smallest c that minimises that load is taken (fewer CTAs per cluster, cheaper
+// barriers).  The choice depends on the batch, so a matrix's rounding (the order of its
+// cluster sums) can differ between batches of different sizes.
+inline int spread_cluster(int count, int cmin, int cmax) {
+  const long long sms = sm_count();
+  int best = cmax;
+  double bl = 1e300;
+  for (int c = cmin; c <= cmax; ++c) {
+    const double load = (double)((count * (long long)c + sms - 1) / sms) / c;
+    if (load < bl * (1.0 - 1e-12)) {
+      bl = load;
+      best = c;
+    }
+  }
+  return best;
+}
+
 // shared-memory budget of the Jacobi kernel for given sizes (bytes), and the
 // cluster size chosen for them
 int jacobi_cluster_size(int l, int n);

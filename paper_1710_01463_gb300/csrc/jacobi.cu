@@ -72,10 +72,11 @@ __host__ __device__ inline JLayout jlayout(int l, int n, int csize) {
 
 __host__ __device__ inline size_t jsmem_small(int l, const JLayout& L) {
   // norms, nrm_part, gpart[2][cluster size][npairs] (every CTA's partial of every
-  // pair, pushed), order (int, padded to doubles), rotation cosines and sines
-  // [npairs] and flags (int, padded)
+  // pair, pushed), order (int, padded to doubles), the rotations' two update
+  // coefficients [npairs] and flags (int, padded), the rows' scale factors and their
+  // inverses [l each]
   return sizeof(double) * ((size_t)2 * l + (2 * (size_t)L.cs + 2) * L.npairs + (size_t)(l + 1) / 2 + 1 +
-                           (size_t)(L.npairs + 1) / 2 + 1);
+                           (size_t)(L.npairs + 1) / 2 + 1 + (size_t)2 * l);
 }
 
 // Sum over the CTAs of the cluster of v[i] in their shared memory: every
@@ -146,9 +147,15 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   double* nrm_part = norms + l;
   double* gpart = nrm_part + l;                 // [2][C][npairs]: the CTAs' partials, pushed
   int* order = (int*)(gpart + 2 * C * L.npairs);
-  double* rcs = gpart + 2 * C * L.npairs + (l + 1) / 2 + 1;  // per pair of the round: cos, sin, rotate?
-  double* rsn = rcs + L.npairs;
+  double* rcs = gpart + 2 * C * L.npairs + (l + 1) / 2 + 1;  // per pair of the round: the update
+  double* rsn = rcs + L.npairs;                                // coefficients, rotate?
   int* rfl = (int*)(rsn + L.npairs);
+  // Rows are stored scaled (fast Givens form): row i of the matrix is dsc[i] times the
+  // stored row, so a rotation updates each element pair with two FMAs instead of four
+  // multiplications and additions; isc = 1 / dsc.  The scales shrink by cos(theta) >= 1/sqrt(2)
+  // per rotation and are folded back into the rows at every sweep head and every 64 rounds.
+  double* dsc = rsn + L.npairs + (L.npairs + 1) / 2 + 1;
+  double* isc = dsc + l;
   double* Bs;
   double* Ps;
   if (b.use_global) {
@@ -178,6 +185,23 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
       const int i = e / L.np, c = e % L.np;
       Ps[e] = (c < npl && i == p0 + c) ? 1.0 : 0.0;
     }
+  for (int i = tid; i < l; i += kJacobiThreads) {
+    dsc[i] = 1.0;
+    isc[i] = 1.0;
+  }
+  // fold the scale factors into the stored rows (every CTA at the same points: the
+  // factors are identical across the cluster, as are all rotation decisions)
+  auto rescale = [&]() {
+    for (int e = tid; e < l * L.nc; e += kJacobiThreads) Bs[e] *= dsc[e / L.nc];
+    if (want_p)
+      for (int e = tid; e < l * L.np; e += kJacobiThreads) Ps[e] *= dsc[e / L.np];
+    __syncthreads();
+    for (int i = tid; i < l; i += kJacobiThreads) {
+      dsc[i] = 1.0;
+      isc[i] = 1.0;
+    }
+    __syncthreads();
+  };
   __shared__ uint64_t mbR[2];  // round exchanges of even / odd global round number
   __shared__ int rerr;         // a round exchange timed out
   if (tid == 0) {
@@ -199,6 +223,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   long long total_pairs = 0;  // inner products formed: nlive (nlive - 1) / 2 per sweep
   bool converged = false;
   for (;;) {
+    if (sweeps > 0) rescale();
     // exact row norms of this sweep (four independent partial sums: a dependent
     // FP64 operation costs about 64 cycles on this part)
     for (int i = tid; i < l; i += kJacobiThreads) {
@@ -312,7 +337,8 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
           for (int w = 1; w < kMaxCluster; w <<= 1)
 #pragma unroll
             for (int q = 0; q + w < kMaxCluster; q += 2 * w) pv[q] += pv[q + w];
-          const double g = pv[0];
+          const double di = dsc[i], dj = dsc[j];
+          const double g = pv[0] * (di * dj);  // the inner product of the (unscaled) rows
           // al, be > 0 and g^2 > tol^2 al be, compared as bit patterns (all >= +0)
           if (__double_as_longlong(al) > 0 && __double_as_longlong(be) > 0 &&
               __double_as_longlong(g * g) > __double_as_longlong(tol2 * (al * be))) {
@@ -335,8 +361,16 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
             const float tf = fabsf(zf) < 1e18f ? copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)))
                                                : 0.5f / zf;
             const double t = (double)tf;
-            cs = rsqrt(fma(t, t, 1.0));
-            sn = cs * t;
+            const double t2 = fma(t, t, 1.0);
+            const double c = rsqrt(t2);
+            // (c, c t) rotation in scaled form: x_i <- x_i - t (d_j / d_i) x_j,
+            // x_j <- x_j + t (d_i / d_j) x_i, d_i, d_j <- c d_i, c d_j
+            cs = t * dj * isc[i];
+            sn = t * di * isc[j];
+            dsc[i] = c * di;
+            dsc[j] = c * dj;
+            isc[i] *= t2 * c;
+            isc[j] *= t2 * c;
             norms[i] = al - t * g;
             norms[j] = be + t * g;
             atomicAdd(&rot_count, 1);
@@ -353,19 +387,20 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         int a, bq;
         round_pair(r, s, lpl, a, bq);
         const int i = live[a], j = live[bq];
-        const double cs = rcs[s], sn = rsn[s];
+        const double ca = rcs[s], cb = rsn[s];
         for (int c = tl; c < ncl; c += kTeam) {
           const double x = Bs[i * L.nc + c], y = Bs[j * L.nc + c];
-          Bs[i * L.nc + c] = cs * x - sn * y;
-          Bs[j * L.nc + c] = sn * x + cs * y;
+          Bs[i * L.nc + c] = fma(-ca, y, x);
+          Bs[j * L.nc + c] = fma(cb, x, y);
         }
         for (int c = tl; want_p && c < npl; c += kTeam) {
           const double x = Ps[i * L.np + c], y = Ps[j * L.np + c];
-          Ps[i * L.np + c] = cs * x - sn * y;
-          Ps[j * L.np + c] = sn * x + cs * y;
+          Ps[i * L.np + c] = fma(-ca, y, x);
+          Ps[j * L.np + c] = fma(cb, x, y);
         }
       }
       __syncthreads();
+      if ((r & 63) == 63) rescale();  // the scales stay above 2^-32 between foldings
     }
     ++sweeps;
     total_rot += rot_count;

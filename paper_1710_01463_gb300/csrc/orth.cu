@@ -969,7 +969,16 @@ cudaError_t launch_householder(const OrthBatch<T>& b, cudaStream_t s) {
     else cb.job[cb.count++] = J;
   }
   if (pb.count > 0) {
-    const int pcs = kPanelMaxCluster;  // fixed: no matrix's rounding depends on the rest of its batch
+    // spread over the SMs (at most 64 rows per CTA, at most kPanelMaxCluster CTAs, and
+    // the shared-memory slices within budget)
+    int cmin = 1;
+    for (int i = 0; i < pb.count; ++i) {
+      int c = max(1, ceil_div(pb.job[i].rows, 64));
+      while (c < kPanelMaxCluster && panel_layout(pb.job[i].rows, pb.job[i].l, c).total * sizeof(double) > kPanelSmemMax)
+        ++c;
+      cmin = max(cmin, c);
+    }
+    const int pcs = spread_cluster(pb.count, min(cmin, kPanelMaxCluster), kPanelMaxCluster);
     size_t psmem = 0;
     for (int i = 0; i < pb.count; ++i)
       psmem = max(psmem, panel_layout(pb.job[i].rows, pb.job[i].l, pcs).total * sizeof(double));
