@@ -330,13 +330,17 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         if (bq < nlive) {
           const int i = live[a], j = live[bq];
           const double al = norms[i], be = norms[j];
-          double pv[kMaxCluster];  // the CTAs' partials by the same fixed tree in every CTA
+          // the CTAs' partials by the same fixed tree in every CTA, over the cluster's
+          // size only (an FP64 instruction costs its warp a full pipe slot even with one
+          // active lane, so no additions of padding zeros)
+          double pv[kMaxCluster];
 #pragma unroll
           for (int q = 0; q < kMaxCluster; ++q) pv[q] = q < C ? gp[q * L.npairs + s] : 0.0;
 #pragma unroll
           for (int w = 1; w < kMaxCluster; w <<= 1)
 #pragma unroll
-            for (int q = 0; q + w < kMaxCluster; q += 2 * w) pv[q] += pv[q + w];
+            for (int q = 0; q + w < kMaxCluster; q += 2 * w)
+              if (q + w < C) pv[q] += pv[q + w];
           const double di = dsc[i], dj = dsc[j];
           const double g = pv[0] * (di * dj);  // the inner product of the (unscaled) rows
           // al, be > 0 and g^2 > tol^2 al be, compared as bit patterns (all >= +0)

@@ -598,10 +598,9 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   __shared__ double red[kHhThreads / 32][2];
   __shared__ double fin[kNb];
   __shared__ double Ts[kNb][kNb];  // T of the current panel
-  __shared__ double x0s;
   __shared__ double sc[2];
-  __shared__ double npart[kPanelMaxCluster];       // the cluster's partial norms of a panel column
-  __shared__ double spart[kPanelMaxCluster][kNb];  // the cluster's partial products v^T x_c
+  __shared__ double spart[2][kPanelMaxCluster][kNb];  // the cluster's partial products x_jj^T x_c
+  __shared__ double xrowp[2][kNb];                     // the diagonal row's entries of the panel columns
   __shared__ double vbuf[64];                      // v on the own rows (rs <= 64)
   __shared__ double Gv[kNb][kNb];                  // V^T V of the panel (strictly upper part)
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = kHhThreads / 32;
@@ -666,12 +665,16 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     {
       // The panel is factored by the whole cluster: warp c holds panel column c of
       // this CTA's own rows (lane and lane + 32), so the FP64 work of the reflections
-      // is spread over the cluster's SMs.  Per column jj two cluster barriers: after
-      // the partial norms (and the diagonal entry), and after the partial products
-      // v^T x_c.  Partials are pushed into every CTA's shared memory before the
-      // barrier, so the reads after it are local; every CTA sums them in the same
-      // fixed order and forms the same scalars, T and alpha.  A slot is rewritten
-      // only after a later barrier that every reader of its previous value passed.
+      // is spread over the cluster's SMs.  Per column jj ONE cluster barrier: every CTA
+      // forms the partial products x_jj^T x_c of the column with all panel columns over
+      // its rows at and below the diagonal (c = jj gives ||x_jj||^2) and the CTA holding
+      // the diagonal row sends that row's entries; after the barrier every CTA sums the
+      // partials in the same fixed order and forms alpha, the reflector's scale and
+      // v^T x_c = (x_jj^T x_c - alpha x_c[d]) / ||x_jj - alpha e_d|| (d the diagonal
+      // row) - the same quantities as the reflector applied first, without a second
+      // exchange.  For c < jj (columns holding earlier reflectors) this is v_c^T v_jj,
+      // for T.  The exchange slots alternate between two buffers: a slot is rewritten
+      // two columns later, after a barrier that every reader of its value has passed.
       static_assert(kHhThreads / 32 == kNb, "one warp per panel column");
       const int c = warp;
       const int rA = lane, rB = lane + 32;
@@ -681,54 +684,23 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       double xB = (inB && c < nb) ? Ys[rB * l + j0 + c] : 0.0;
       for (int jj = 0; jj < nb; ++jj) {
         const int gd = j0 + jj;  // the diagonal row of column jj
-        if (c == jj) {
-          double a = (inA && gA >= gd ? xA * xA : 0.0) + (inB && gB >= gd ? xB * xB : 0.0);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-          if (lane < C) *cluster.map_shared_rank(&npart[rank], lane) = a;  // lane q pushes to CTA q
-          if (gd >= r0 && gd < r0 + nr) {  // this CTA holds the diagonal entry
-            const int rd = gd - r0;
-            const double xd = __shfl_sync(0xffffffffu, rd < 32 ? xA : xB, rd & 31);
-            if (lane < C) *cluster.map_shared_rank(&x0s, lane) = xd;
-          }
+        const int buf = jj & 1;
+        if (c == jj) {  // column jj at and below the diagonal, for every warp's products
+          vbuf[rA] = (inA && gA >= gd) ? xA : 0.0;
+          vbuf[rB] = (inB && gB >= gd) ? xB : 0.0;
         }
-        cluster.sync();
-        if (tid == 0) {
-          // sum of the partials by a fixed tree; sign tests on the bit patterns (an
-          // FP64 compare-and-branch costs hundreds of cycles on this part), and
-          // ||x|| = a rsqrt(a)
-          double pv[kPanelMaxCluster];
-#pragma unroll
-          for (int q = 0; q < kPanelMaxCluster; ++q) pv[q] = q < C ? npart[q] : 0.0;
-#pragma unroll
-          for (int w2 = 1; w2 < kPanelMaxCluster; w2 <<= 1)
-#pragma unroll
-            for (int q = 0; q + w2 < kPanelMaxCluster; q += 2 * w2) pv[q] += pv[q + w2];
-          const double a = pv[0], x0 = x0s;
-          double al = 0.0, inv = 0.0;
-          if (__double_as_longlong(a) > 0) {
-            const double nx = a * rsqrt(a);
-            al = __double_as_longlong(x0) >= 0 ? -nx : nx;
-            const double vn2 = 2.0 * fma(fabs(x0), nx, a);  // ||x - alpha e||^2 = 2 (a + |x0| ||x||)
-            inv = __double_as_longlong(vn2) > 0 ? rsqrt(vn2) : 0.0;
-          }
-          sc[0] = inv;
-          sc[1] = (x0 - al) * inv;  // v at the diagonal row
-          alpha[gd] = al;
+        if (gd >= r0 && gd < r0 + nr && c < nb) {  // this CTA holds the diagonal row
+          const int rd = gd - r0;
+          const double xd = __shfl_sync(0xffffffffu, rd < 32 ? xA : xB, rd & 31);
+          if (lane < C) *cluster.map_shared_rank(&xrowp[buf][c], lane) = xd;  // lane q pushes to CTA q
         }
         __syncthreads();
-        if (c == jj) {  // the unit reflector v on the own rows (zero above the diagonal)
-          vbuf[rA] = !inA ? 0.0 : gA == gd ? sc[1] : gA > gd ? xA * sc[0] : 0.0;
-          vbuf[rB] = !inB ? 0.0 : gB == gd ? sc[1] : gB > gd ? xB * sc[0] : 0.0;
-        }
-        __syncthreads();
-        const double vA = vbuf[rA], vB = vbuf[rB];
-        // v^T x_c (for c < jj the T column's V_c^T v, for c > jj the reflection's): each
-        // warp leaves its lanes' products, and warp 0 sums all columns (lanes 2i and
+        const double wA = vbuf[rA], wB = vbuf[rB];
+        // each warp leaves its lanes' products, and warp 0 sums all columns (lanes 2i and
         // 2i + 1 half of column i each) and pushes them, lane-parallel - 17 FP64
         // instructions in one warp instead of a 5-level shuffle tree in each of 16
         double (*prod)[kProdStride] = (double (*)[kProdStride])Wp;  // the V^T Y buffer is idle here
-        prod[c][lane] = (c != jj && c < nb) ? fma(xA, vA, xB * vB) : 0.0;
+        prod[c][lane] = c < nb ? fma(xA, wA, xB * wB) : 0.0;
         __syncthreads();
         if (warp == 0) {
           const int cc = lane >> 1, h = (lane & 1) * 16;
@@ -742,24 +714,46 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
           }
           double sp = (s0 + s1) + (s2 + s3);
           sp += __shfl_xor_sync(0xffffffffu, sp, 1);
-          for (int q = lane & 1; q < C; q += 2) *cluster.map_shared_rank(&spart[rank][cc], q) = sp;
+          for (int q = lane & 1; q < C; q += 2) *cluster.map_shared_rank(&spart[buf][rank][cc], q) = sp;
         }
         cluster.sync();
-        // one warp sums every column's partials (lane c, a fixed tree): an FP64
-        // instruction holds the SM's FP64 pipe for 16 cycles whatever its active
-        // lanes, so sixteen warps each summing one column would cost 16 times more
+        // one warp, lane c: the sum of column c's partials (a fixed tree over the
+        // cluster), the reflector's scalars (redundantly in every lane: an FP64 warp
+        // instruction costs the same with one active lane or sixteen), v^T x_c.  Sign
+        // tests on the bit patterns (an FP64 compare-and-branch costs hundreds of
+        // cycles on this part), and ||x|| = a rsqrt(a)
         if (warp == 0 && lane < kNb) {
           double pv[kPanelMaxCluster];
 #pragma unroll
-          for (int q = 0; q < kPanelMaxCluster; ++q) pv[q] = q < C ? spart[q][lane] : 0.0;
+          for (int q = 0; q < kPanelMaxCluster; ++q) pv[q] = q < C ? spart[buf][q][lane] : 0.0;
 #pragma unroll
           for (int w2 = 1; w2 < kPanelMaxCluster; w2 <<= 1)
 #pragma unroll
-            for (int q = 0; q + w2 < kPanelMaxCluster; q += 2 * w2) pv[q] += pv[q + w2];
-          fin[lane] = -2.0 * pv[0];
-          if (lane < jj) Gv[lane][jj] = pv[0];  // v_lane^T v_jj, for T
+            for (int q = 0; q + w2 < kPanelMaxCluster; q += 2 * w2)
+              if (q + w2 < C) pv[q] += pv[q + w2];
+          const double dc = pv[0];
+          const double a = __shfl_sync(0x0000ffffu, dc, jj);  // ||x_jj||^2 below the diagonal
+          const double x0 = xrowp[buf][jj];
+          double al = 0.0, inv = 0.0;
+          if (__double_as_longlong(a) > 0) {
+            const double nx = a * rsqrt(a);
+            al = __double_as_longlong(x0) >= 0 ? -nx : nx;
+            const double vn2 = 2.0 * fma(fabs(x0), nx, a);  // ||x - alpha e||^2 = 2 (a + |x0| ||x||)
+            inv = __double_as_longlong(vn2) > 0 ? rsqrt(vn2) : 0.0;
+          }
+          const double vtx = fma(-al, xrowp[buf][lane], dc) * inv;  // v^T x_lane
+          fin[lane] = -2.0 * vtx;
+          if (lane < jj) Gv[lane][jj] = vtx;  // v_lane^T v_jj, for T
+          if (lane == jj) {
+            sc[0] = inv;
+            sc[1] = (x0 - al) * inv;  // v at the diagonal row
+            alpha[gd] = al;
+          }
         }
-        __syncthreads();  // fin complete
+        __syncthreads();  // fin and the scalars complete
+        // the unit reflector v on the own rows (zero above the diagonal)
+        const double vA = !inA ? 0.0 : gA == gd ? sc[1] : gA > gd ? wA * sc[0] : 0.0;
+        const double vB = !inB ? 0.0 : gB == gd ? sc[1] : gB > gd ? wB * sc[0] : 0.0;
         if (c > jj && c < nb) {
           xA = fma(fin[c], vA, xA);
           xB = fma(fin[c], vB, xB);
