@@ -103,7 +103,14 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const __grid_constant__ O
 }
 
 // ---------------------------------------------------------------- product
-__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_constant__ OzBatch b, int stages) {
+// Per K tile of 64 (128 bytes of every slice row): all nine slice tiles of S (ntile
+// rows each) are loaded once and stay in shared memory (two buffers, alternating
+// between K tiles), while the nine slice tiles of P (128 rows) stream through a ring;
+// P tile i meets S tiles j = 1 .. 11 - i (at most 9), four MMAs of K = 16 each, into the
+// TMEM accumulator of level i + j.  Every tile is loaded once per CTA.
+constexpr int kOzPStages = 4;  // P tiles in flight
+
+__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_constant__ OzBatch b) {
   const OzJob& J = b.job[blockIdx.z];
   const int NT = b.ntile;
   const int m0 = blockIdx.x * kOzM, n0 = blockIdx.y * NT;
@@ -115,23 +122,23 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
     }
     return;
   }
-  const int nkt = (J.K + kOzBK - 1) / kOzBK;  // K tiles in all
-  const int nc = (nkt + kOzMaxKt - 1) / kOzMaxKt;  // chunks of at most kOzMaxKt tiles
-  constexpr uint32_t kTileA = kOzM * 128;     // one K tile of a P slice: 128 rows x 128 bytes
+  const int nkt = (J.K + kOzBK - 1) / kOzBK;        // K tiles in all
+  const int nc = (nkt + kOzMaxKt - 1) / kOzMaxKt;   // chunks of at most kOzMaxKt tiles (exact level sums)
+  constexpr uint32_t kTileA = kOzM * 128;           // one K tile of a P slice: 128 rows x 128 bytes
   const uint32_t s_bytes = (uint32_t)NT * 128;
-  const uint32_t s_stage = (s_bytes + 1023) / 1024 * 1024;
+  const uint32_t s_tile = (s_bytes + 1023) / 1024 * 1024;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) / 1024 * 1024);
-  uint8_t* pbuf = smem;                                   // [2][kOzMaxKt] P tiles
-  uint8_t* sbuf = smem + 2 * (size_t)kOzMaxKt * kTileA;  // [stages] S tiles
-  uint64_t* pfull = (uint64_t*)(sbuf + (size_t)stages * s_stage);
-  uint64_t* pempty = pfull + 2;
-  uint64_t* sfull = pempty + 2;
-  uint64_t* sempty = sfull + stages;
-  uint64_t* ifull = sempty + stages;  // [kOzSlices]: the products of slice i are complete
-  uint64_t* lempty = ifull + kOzSlices;  // [kOzLevels]: the epilogue has read level L
-  uint64_t* mdone = lempty + kOzLevels;  // every MMA issued has completed
+  uint8_t* pbuf = smem;                                          // [kOzPStages] P tiles
+  uint8_t* sbuf = smem + (size_t)kOzPStages * kTileA;            // [2][kOzSlices] S tiles
+  uint64_t* pfull = (uint64_t*)(sbuf + (size_t)2 * kOzSlices * s_tile);
+  uint64_t* pempty = pfull + kOzPStages;
+  uint64_t* sfull = pempty + kOzPStages;  // [2]
+  uint64_t* sempty = sfull + 2;           // [2]
+  uint64_t* cdone = sempty + 2;           // the chunk's MMAs are complete
+  uint64_t* lread = cdone + 1;            // the epilogue has read the chunk's levels
+  uint64_t* mdone = lread + 1;            // every MMA issued has completed
   uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
   __shared__ int err;
   __shared__ int keep_tmem;  // an in-flight copy or MMA could not be drained: leave TMEM allocated
@@ -142,17 +149,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   if (threadIdx.x == 0) {
     err = 0;
     keep_tmem = 0;
-    mbar_init(mdone, 1);
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < kOzPStages; ++t) {
       mbar_init(&pfull[t], 1);
       mbar_init(&pempty[t], 1);
     }
-    for (int s = 0; s < stages; ++s) {
-      mbar_init(&sfull[s], 1);
-      mbar_init(&sempty[s], 1);
+    for (int t = 0; t < 2; ++t) {
+      mbar_init(&sfull[t], 1);
+      mbar_init(&sempty[t], 1);
     }
-    for (int i = 0; i < kOzSlices; ++i) mbar_init(&ifull[i], 1);
-    for (int L = 0; L < kOzLevels; ++L) mbar_init(&lempty[L], 4);  // one arrival per epilogue warp
+    mbar_init(cdone, 1);
+    mbar_init(lread, 4);  // one arrival per epilogue warp
+    mbar_init(mdone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -170,91 +177,89 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   auto jmax = [](int i) { return min(kOzSlices, kOzSlices + 2 - i); };
 
   if (warp == 0 && lane == 0) {
-    // producer: slice i of P (all K tiles), then the S tiles of every j it pairs with
-    int step = 0;
-    int p_last[2] = {-1, -1};  // last use issued of each P buffer
-    for (int c = 0; c < nc && !*errv; ++c) {
-      const int kt0 = c * kOzMaxKt, nk = min(kOzMaxKt, nkt - kt0);
-      for (int i = 1; i <= kOzSlices && !*errv; ++i) {
-        const int t = c * kOzSlices + i - 1, pb = t & 1, use = t >> 1;
-        if (use > 0 && !mbar_wait(&pempty[pb], (use - 1) & 1)) {
+    // producer: per K tile the nine S tiles (into the buffer of the tile's parity), then
+    // the nine P tiles through the ring
+    int pstep = 0;
+    int last_s[2] = {-1, -1};  // last use issued of each S buffer
+    for (int kt = 0; kt < nkt && !*errv; ++kt) {
+      const int sb = kt & 1, su = kt >> 1;
+      if (su > 0 && !mbar_wait(&sempty[sb], (su - 1) & 1)) {
+        atomicExch(&err, 1);
+        break;
+      }
+      mbar_expect_tx(&sfull[sb], (uint32_t)kOzSlices * s_bytes);
+      last_s[sb] = su;
+      for (int j = 1; j <= kOzSlices; ++j)
+        tma_load_2d(sbuf + ((size_t)sb * kOzSlices + j - 1) * s_tile, &J.ts, &sfull[sb], kt * kOzBK,
+                    (j - 1) * J.Npad + n0);
+      for (int i = 1; i <= kOzSlices && !*errv; ++i, ++pstep) {
+        const int ps = pstep % kOzPStages;
+        if (pstep >= kOzPStages && !mbar_wait(&pempty[ps], ((pstep / kOzPStages) & 1) ^ 1)) {
           atomicExch(&err, 1);
           break;
         }
-        mbar_expect_tx(&pfull[pb], (uint32_t)nk * kTileA);
-        p_last[pb] = use;
-        for (int kt = 0; kt < nk; ++kt)
-          tma_load_2d(pbuf + ((size_t)pb * kOzMaxKt + kt) * kTileA, &J.tp, &pfull[pb], (kt0 + kt) * kOzBK,
-                      (i - 1) * J.M + m0);
-        for (int j = 1; j <= jmax(i) && !*errv; ++j)
-          for (int kt = 0; kt < nk; ++kt, ++step) {
-            const int s = step % stages;
-            if (step >= stages && !mbar_wait(&sempty[s], ((step / stages) & 1) ^ 1)) {
-              atomicExch(&err, 1);
-              break;
-            }
-            mbar_expect_tx(&sfull[s], s_bytes);
-            tma_load_2d(sbuf + (size_t)s * s_stage, &J.ts, &sfull[s], (kt0 + kt) * kOzBK, (j - 1) * J.Npad + n0);
-          }
+        mbar_expect_tx(&pfull[ps], kTileA);
+        tma_load_2d(pbuf + (size_t)ps * kTileA, &J.tp, &pfull[ps], kt * kOzBK, (i - 1) * J.M + m0);
       }
     }
     // no load may still be writing shared memory when the CTA leaves: wait (bounded) for
     // the last load of every buffer and stage (already complete on the normal path)
     bool drained = true;
-    for (int pb = 0; pb < 2; ++pb)
-      if (p_last[pb] >= 0) drained = mbar_wait(&pfull[pb], p_last[pb] & 1) && drained;
-    for (int st = max(0, step - stages); st < step; ++st)
-      drained = mbar_wait(&sfull[st % stages], (st / stages) & 1) && drained;
+    for (int sb = 0; sb < 2; ++sb)
+      if (last_s[sb] >= 0) drained = mbar_wait(&sfull[sb], last_s[sb] & 1) && drained;
+    for (int st = max(0, pstep - kOzPStages); st < pstep; ++st)
+      drained = mbar_wait(&pfull[st % kOzPStages], (st / kOzPStages) & 1) && drained;
     if (!drained) {
       atomicExch(&err, 1);
       keep_tmem = 1;
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: product (i, j) accumulates into the TMEM columns of level i + j
+    // MMA issuer: product (i, j) accumulates into the TMEM columns of level i + j; the
+    // first product of a level in a chunk (i = max(1, L - 9), first K tile, first MMA)
+    // overwrites it
     const uint32_t id = idesc<__nv_bfloat16>(kOzM, NT);
-    int step = 0;
+    int pstep = 0;
     for (int c = 0; c < nc && !*errv; ++c) {
-     const int nk = min(kOzMaxKt, nkt - c * kOzMaxKt);
-     for (int i = 1; i <= kOzSlices && !*errv; ++i) {
-      const int t = c * kOzSlices + i - 1, pb = t & 1, use = t >> 1;
-      if (!mbar_wait(&pfull[pb], use & 1)) {
-        atomicExch(&err, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t pa = smem_u32(pbuf + (size_t)pb * kOzMaxKt * kTileA);
-      for (int j = 1; j <= jmax(i) && !*errv; ++j) {
-        const int L = i + j;
-        const uint32_t td = tmem + (uint32_t)((L - 2) * NT);
-        const bool first_of_level = i == max(1, L - kOzSlices);
-        if (c > 0 && first_of_level) {  // the epilogue has read this level of the previous chunk
-          if (!mbar_wait(&lempty[L - 2], (c - 1) & 1)) {
-            atomicExch(&err, 1);
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (c > 0) {  // the epilogue has read the previous chunk's levels
+        if (!mbar_wait(lread, (c - 1) & 1)) {
+          atomicExch(&err, 1);
+          break;
         }
-        for (int kt = 0; kt < nk; ++kt, ++step) {
-          const int s = step % stages;
-          if (!mbar_wait(&sfull[s], (step / stages) & 1)) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+      const int kt0 = c * kOzMaxKt, nk = min(kOzMaxKt, nkt - kt0);
+      for (int t = 0; t < nk && !*errv; ++t) {
+        const int kt = kt0 + t, sb = kt & 1;
+        if (!mbar_wait(&sfull[sb], (kt >> 1) & 1)) {
+          atomicExch(&err, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t s0 = smem_u32(sbuf + (size_t)sb * kOzSlices * s_tile);
+        for (int i = 1; i <= kOzSlices; ++i, ++pstep) {
+          const int ps = pstep % kOzPStages;
+          if (!mbar_wait(&pfull[ps], (pstep / kOzPStages) & 1)) {
             atomicExch(&err, 1);
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sa = pa + (uint32_t)kt * kTileA;
-          const uint32_t sb = smem_u32(sbuf + (size_t)s * s_stage);
+          const uint32_t pa = smem_u32(pbuf + (size_t)ps * kTileA);
+          for (int j = 1; j <= jmax(i); ++j) {
+            const int L = i + j;
+            const uint32_t td = tmem + (uint32_t)((L - 2) * NT);
+            const bool first = t == 0 && i == max(1, L - kOzSlices);
+            const uint32_t sa = s0 + (uint32_t)(j - 1) * s_tile;
 #pragma unroll
-          for (int kk = 0; kk < kOzBK / kOzMmaK; ++kk) {
-            const uint32_t off = kk * kOzMmaK * 2;  // 32 bytes per MMA step
-            mma<__nv_bfloat16>(td, smem_desc(sa + off), smem_desc(sb + off), id,
-                               (first_of_level && kt == 0 && kk == 0) ? 0u : 1u);
+            for (int kk = 0; kk < kOzBK / kOzMmaK; ++kk) {
+              const uint32_t off = kk * kOzMmaK * 2;  // 32 bytes per MMA step
+              mma<__nv_bfloat16>(td, smem_desc(pa + off), smem_desc(sa + off), id, (first && kk == 0) ? 0u : 1u);
+            }
           }
-          mma_commit(&sempty[s]);
+          mma_commit(&pempty[ps]);
         }
+        mma_commit(&sempty[sb]);
       }
-      mma_commit(&pempty[pb]);
-      mma_commit(&ifull[i - 1]);
-     }
+      mma_commit(cdone);
     }
     // every MMA issued has completed before TMEM is released (bounded wait)
     mma_commit(mdone);
@@ -263,47 +268,46 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
       keep_tmem = 1;
     }
   } else if (warp >= 2) {
-    // epilogue: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31.
-    // Level L is complete once slice i = min(L - 1, kOzSlices) is done.
+    // epilogue: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31; after each
+    // chunk the ten levels are read and added in FP64 with their weights 2^-6L
     const int q = warp % 4;
     const int row = m0 + q * 32 + lane;
     double acc[kOzMaxNt];
 #pragma unroll
-    for (int c = 0; c < kOzMaxNt; ++c) acc[c] = 0.0;
+    for (int cc = 0; cc < kOzMaxNt; ++cc) acc[cc] = 0.0;
     bool ok = true;
-    for (int c = 0; c < nc && ok; ++c)
-      for (int i = 1; i <= kOzSlices && ok; ++i) {
-        // warp-uniform: the level reads and the arrivals below are warp-collective
-        if (!__all_sync(0xffffffffu, mbar_wait(&ifull[i - 1], c & 1) ? 1 : 0)) {
-          ok = false;
-          atomicExch(&err, 1);
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int L = i + 1; L <= (i == kOzSlices ? kOzSlices + 2 : i + 1); ++L) {
-          const double w = __longlong_as_double((long long)(1023 - 6 * L) << 52);  // 2^-6L
-          const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * NT);
-#pragma unroll
-          for (int c0 = 0; c0 < kOzMaxNt; c0 += 16)
-            if (c0 < NT) {
-              float t[16];
-              ld16(tl + (uint32_t)c0, t);
-#pragma unroll
-              for (int u = 0; u < 16; ++u) acc[c0 + u] = fma((double)t[u], w, acc[c0 + u]);
-            }
-          // level L may now be overwritten by the next chunk
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&lempty[L - 2]);
-        }
+    for (int c = 0; c < nc && ok; ++c) {
+      // warp-uniform: the level reads and the arrival below are warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait(cdone, c & 1) ? 1 : 0)) {
+        ok = false;
+        atomicExch(&err, 1);
+        break;
       }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int L = 2; L <= kOzSlices + 2; ++L) {
+        const double w = __longlong_as_double((long long)(1023 - 6 * L) << 52);  // 2^-6L
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * NT);
+#pragma unroll
+        for (int c0 = 0; c0 < kOzMaxNt; c0 += 16)
+          if (c0 < NT) {
+            float t[16];
+            ld16(tl + (uint32_t)c0, t);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[c0 + u] = fma((double)t[u], w, acc[c0 + u]);
+          }
+      }
+      // the levels may now be overwritten by the next chunk
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(lread);
+    }
     if (ok && !*errv && row < J.M) {
       const int er = J.ep[row];
 #pragma unroll
-      for (int c = 0; c < kOzMaxNt; ++c) {
-        const int col = n0 + c;
-        if (c < NT && col < J.N) {
-          const double x = ldexp(acc[c], er + J.es[col]);
+      for (int cc = 0; cc < kOzMaxNt; ++cc) {
+        const int col = n0 + cc;
+        if (cc < NT && col < J.N) {
+          const double x = ldexp(acc[cc], er + J.es[col]);
           J.C[J.trans_c ? (size_t)col * J.ldc + row : (size_t)row * J.ldc + col] = x;
         }
       }
@@ -318,10 +322,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
   if (threadIdx.x == 0 && err && J.err) atomicExch(J.err, 1);
 }
 
-size_t oz_smem_bytes(int ntile, int stages) {
-  const size_t s_stage = ((size_t)ntile * 128 + 1023) / 1024 * 1024;
-  return 1024 + 2 * (size_t)kOzMaxKt * kOzM * 128 + s_stage * stages +
-         (4 + 2 * (size_t)stages + kOzSlices + kOzLevels + 1) * 8 + 16;
+size_t oz_smem_bytes(int ntile) {
+  const size_t s_tile = ((size_t)ntile * 128 + 1023) / 1024 * 1024;
+  return 1024 + (size_t)kOzPStages * kOzM * 128 + 2 * (size_t)kOzSlices * s_tile +
+         (2 * (size_t)kOzPStages + 4 + 3) * 8 + 16;
 }
 
 }  // namespace
@@ -349,13 +353,11 @@ cudaError_t launch_oz_gemm(const OzBatch& b, cudaStream_t s) {
     maxM = max(maxM, b.job[i].M);
     maxN = max(maxN, b.job[i].N);
   }
-  int stages = 8;
-  while (stages > 2 && oz_smem_bytes(b.ntile, stages) > 210 * 1024) --stages;
-  const size_t smem = oz_smem_bytes(b.ntile, stages);
+  const size_t smem = oz_smem_bytes(b.ntile);
   cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   prof_begin(KC_OZGEMM, s);
-  oz_gemm_kernel<<<dim3(ceil_div(maxM, kOzM), ceil_div(maxN, b.ntile), b.count), kOzThreads, smem, s>>>(b, stages);
+  oz_gemm_kernel<<<dim3(ceil_div(maxM, kOzM), ceil_div(maxN, b.ntile), b.count), kOzThreads, smem, s>>>(b);
   prof_end(KC_OZGEMM, s);
   return cudaGetLastError();
 }
