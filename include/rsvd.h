@@ -304,7 +304,8 @@ int rsvd_sectors_adaptive_workspace_size(int batch, const int* m, const int* n, 
  * k'_b < min(chi, m_b, n_b) may hold more values above the cut, so its trial
  * rank is doubled (capped there) and only that block is compressed again (same
  * Philox stream p->stream + b: its larger test matrix extends the previous
- * one); until no block is saturated.  Each round ends with one device-to-host
+ * one); until no block of the last round is saturated (a block left out of a
+ * round is not looked at again).  Each round ends with one device-to-host
  * read of the kept counts and a synchronisation of the stream.
  *   batch <= 64 blocks; A[b] (m_b x n_b, lda[b]) of p->prec (RSVD_F64 or
  *   RSVD_F32);  k_trial  HOST in/out: first guesses, on return the final trial
@@ -347,6 +348,30 @@ int rsvd_complex_workspace_size(int m, int n, const rsvd_params* p, size_t* byte
  */
 int rsvd_truncate_complex(int m, int n, const void* A, int lda, const rsvd_params* p, double* S, void* U, int ldu,
                           void* Vh, int ldvh, void* work, size_t work_bytes, rsvd_info* info, void* cuda_stream);
+
+/*
+ * rsvd_truncate_sectors_adaptive_device - rsvd_truncate_sectors_adaptive with the rounds
+ * decided on the device: no host synchronisation, so the whole call can be captured in a
+ * CUDA graph (the batching form of a symmetry-sector bond).  Round r compresses, at the
+ * scheduled rank min(k_first[b] 2^r, cap_b), every block that is still active; a block is
+ * active in round 0 and stays active while all of its values were kept by the round's
+ * global selection and its rank is below cap_b = min(chi, m_b, n_b).  Every launch of a
+ * round is enqueued up front and each block's work is gated by its device flag (an
+ * inactive block's launches return at once), so the results are those of
+ * rsvd_truncate_sectors_adaptive up to the summation order (the cluster sizes follow the
+ * number of blocks enqueued per round).
+ *   k_first  HOST: first guesses;  k_out, k_final, rounds  DEVICE: the kept counts, the
+ *   final trial ranks, the number of rounds in which a block was compressed.  S[b], U[b]
+ *   and Vt[b] hold k_final[b] values and vectors (entries past it are not written).
+ *   Workspace: rsvd_sectors_adaptive_workspace_size.  Other arguments as
+ *   rsvd_truncate_sectors_adaptive.
+ * Errors as rsvd_truncate_sectors_adaptive.
+ */
+int rsvd_truncate_sectors_adaptive_device(int batch, const int* m, const int* n, const void* const* A, const int* lda,
+                                          const int* k_first, const rsvd_params* p, int chi, double* const* S,
+                                          void* const* U, const int* ldu, void* const* Vt, const int* ldvt, int* k_out,
+                                          int* k_final, int* rounds, void* work, size_t work_bytes, rsvd_info* info,
+                                          void* cuda_stream);
 
 /*
  * rsvd_tol_workspace_size - workspace bytes of rsvd_truncate_tol.

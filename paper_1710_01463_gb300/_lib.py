@@ -60,6 +60,7 @@ EXPORTED = (
     "rsvd_truncate_backward_batched",
     "rsvd_complex_workspace_size",
     "rsvd_truncate_complex",
+    "rsvd_truncate_sectors_adaptive_device",
     "rsvd_autotune_enable",
     "rsvd_autotune_entries",
     "rsvd_autotune_clear",
@@ -164,6 +165,8 @@ def load():
     lib.rsvd_sectors_adaptive_workspace_size.argtypes = [i, ip, ip, i, par, ctypes.POINTER(sz)]
     lib.rsvd_truncate_sectors_adaptive.argtypes = [i, ip, ip, pp, ip, ip, par, i, pp, pp, ip, pp, ip, vp, ip, vp, sz,
                                                    vp, vp]
+    lib.rsvd_truncate_sectors_adaptive_device.argtypes = [i, ip, ip, pp, ip, ip, par, i, pp, pp, ip, pp, ip, vp, vp,
+                                                          vp, vp, sz, vp, vp]
     lib.rsvd_noalloc_scratch_bytes.argtypes = []
     lib.rsvd_noalloc_scratch_bytes.restype = ctypes.c_size_t
     lib.rsvd_profile_class_name.argtypes = [i]

@@ -257,8 +257,14 @@ class AdaptiveSectorsPlan:
     (estimates from the previous iteration)."""
 
     def __init__(self, shapes, chi, ranks0, p=8, q=2, seed=0, stream=0, dtype=torch.float64, device="cuda",
-                 max_sweeps=0):
+                 max_sweeps=0, device_rounds=False):
+        """device_rounds=True: rsvd_truncate_sectors_adaptive_device - the rounds are decided on
+        the device (no host synchronisation: the run can be captured in a CUDA graph), every
+        run starts from ranks0, and the final ranks and the rounds stay on the device
+        (k_final, rounds_dev)."""
         lib = _lib.load()
+        self.device_rounds = bool(device_rounds)
+        self.ranks0 = [int(k) for k in ranks0]
         self.shapes = [(int(m), int(n)) for m, n in shapes]
         self.chi = int(chi)
         self.dtype = dtype
@@ -284,6 +290,8 @@ class AdaptiveSectorsPlan:
         self.ldu = _lib.int_array([t.stride(0) for t in self.U])
         self.ldv = _lib.int_array([t.stride(0) for t in self.Vt])
         self.rounds = 0
+        self.k_final = torch.zeros((B,), dtype=torch.int32, device=device)
+        self.rounds_dev = torch.zeros((1,), dtype=torch.int32, device=device)
 
     def run(self, As, stream=None):
         lib = _lib.load()
@@ -293,6 +301,17 @@ class AdaptiveSectorsPlan:
                 raise ValueError("block shape / dtype / layout mismatch")
         A_ptr = _lib.ptr_array([A.data_ptr() for A in As])
         lda = _lib.int_array([A.stride(0) for A in As])
+        if self.device_rounds:
+            caps = [min(self.chi, m, n) for m, n in self.shapes]
+            k0 = _lib.int_array([max(1, min(k, c)) for k, c in zip(self.ranks0, caps)])
+            rc = lib.rsvd_truncate_sectors_adaptive_device(
+                len(As), self.m_arr, self.n_arr, A_ptr, lda, k0, ctypes.byref(self.par), self.chi, self.S_ptr,
+                self.U_ptr, self.ldu, self.V_ptr, self.ldv, ctypes.c_void_p(self.k_out.data_ptr()),
+                ctypes.c_void_p(self.k_final.data_ptr()), ctypes.c_void_p(self.rounds_dev.data_ptr()),
+                ctypes.c_void_p(self.work.data_ptr()), ctypes.c_size_t(self.work.numel()),
+                ctypes.c_void_p(self.info.data_ptr()), _stream_handle(stream))
+            _lib.check(rc, "rsvd_truncate_sectors_adaptive_device")
+            return self.U, self.S, self.Vt, self.k_out
         kt = _lib.int_array(self.ranks)
         rounds = ctypes.c_int(0)
         rc = lib.rsvd_truncate_sectors_adaptive(len(As), self.m_arr, self.n_arr, A_ptr, lda, kt, ctypes.byref(self.par),

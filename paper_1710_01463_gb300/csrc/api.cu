@@ -43,6 +43,7 @@ struct Prob {
   int no_exchange;  // RSVD_FLAG_TEST_NO_EXCHANGE
   int serial;       // RSVD_FLAG_SERIAL: independent groups one after another on the caller's stream
   int cplx;         // the real embedding of a complex matrix: Omega enters as diag(Omega, Omega)
+  const int* active;  // device flag (null: always): every launch of this matrix runs only while it is set
   // workspace
   void *Y0, *Y1, *Z0, *Z1, *Rinv, *Ps;
   double *G, *part, *hw, *hq, *Bm, *Bg, *Pg, *sig;
@@ -213,6 +214,7 @@ OrthBatch<T> orth_batch(const std::vector<Prob*>& ps, bool onY) {
     // the rest (their operands are zero there)
     J.rank_eff = p.flag + 2;
     J.trunc_q = p.want_u ? 0 : 1;
+    J.active = p.active;
   }
   return b;
 }
@@ -237,6 +239,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       for (int i = 0; i < wc; ++i) {
         Prob& p = *wide[i];
         x.job[i] = XposeJob{p.l, p.n, p.n, p.l, p.Bm, p.Bt};
+        x.job[i].active = p.active;
       }
       RSVD_TRY((launch_transpose<double, double>(x, s)));
     }
@@ -251,6 +254,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
         OrthJob<double>& J = ob.job[i];
         J.rows = p.n; J.l = p.l; J.Y = p.Bt; J.Y1 = p.Bt2; J.part = p.part; J.G = p.G; J.Rinv = p.RinvD;
         J.hw = p.hw; J.hq = p.hq; J.flag = p.flag; J.info = p.info; J.hh_first = 3 * p.l > p.n ? 1 : 0;
+        J.active = p.active;
       }
       RSVD_TRY(launch_orth<double>(ob, s));
     }
@@ -260,6 +264,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       for (int i = 0; i < wc; ++i) {
         Prob& p = *wide[i];
         g.job[i] = GemmJob<double, double>{p.l, p.l, p.n, p.n, p.l, p.l, p.Bm, p.Bt, p.Mb, nullptr, nullptr, 0};
+        g.job[i].active = p.active;
       }
       RSVD_TRY((launch_gemm<double, double, false, false>(g, s)));
     }
@@ -269,6 +274,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       for (int i = 0; i < wc; ++i) {
         Prob& p = *wide[i];
         x.job[i] = XposeJob{p.n, p.l, p.l, p.n, p.Bt, p.Qbt};
+        x.job[i].active = p.active;
       }
       RSVD_TRY((launch_transpose<double, T>(x, s)));
     }
@@ -302,6 +308,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       J.want_p = p.want_u;
       J.pipe_err = tc_err ? p.flag + 1 : nullptr;
       J.no_exchange = p.no_exchange;
+      J.active = p.active;
     }
     // spread the group over the SMs: a cluster size between the smallest whose slices fit
     // shared memory and one of at least 16 columns per CTA (at most 16 CTAs)
@@ -337,6 +344,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       Prob& p = *pp;
       g.job[g.count++] = GemmJob<T, T>{p.k, p.n, p.l, p.l, p.n, p.ldvt, (const T*)p.Wb, (const T*)p.Qbt, (T*)p.Vt,
                                        nullptr, nullptr, 0};
+      g.job[g.count - 1].active = p.active;
     }
     RSVD_TRY((launch_gemm<T, T, false, false>(g, s)));
   }
@@ -357,6 +365,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
     for (int i = 0; i < cnt; ++i) {
       Prob& p = probs[i];
       b.job[i] = PrepJob<T>{p.m, p.n, p.l, p.exact, (const T*)p.A, p.lda, (T*)p.Y0, p.Bm, p.flag, p.info};
+      b.job[i].active = p.active;
     }
     RSVD_TRY(launch_prep<T>(b, s));
   }
@@ -370,12 +379,15 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
         Prob& p = *rs[i];
         if (!p.cplx) {
           b.job[b.count++] = OmegaJob<T>{p.n, p.l, p.l, (T*)p.Z0, p.seed, p.stream};
+          b.job[b.count - 1].active = p.active;
           continue;
         }
         RSVD_TRY(cudaMemsetAsync(p.Z0, 0, (size_t)p.n * p.l * sizeof(T), s));
         const int nc = p.n / 2, lc = p.l / 2;
         b.job[b.count++] = OmegaJob<T>{nc, lc, p.l, (T*)p.Z0, p.seed, p.stream};
+        b.job[b.count - 1].active = p.active;
         b.job[b.count++] = OmegaJob<T>{nc, lc, p.l, (T*)p.Z0 + (size_t)nc * p.l + lc, p.seed, p.stream};
+        b.job[b.count - 1].active = p.active;
         if (b.count + 2 > kMaxJobs) {
           RSVD_TRY(launch_omega<T>(b, s));
           b.count = 0;
@@ -406,7 +418,9 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
           sb.count = 0;
         }
         sb.job[sb.count++] = OzSplitJob{(const double*)p.A, p.m, p.n, p.lda, 0, p.m, p.KpA, p.SA, p.eA};
+        sb.job[sb.count - 1].active = p.active;
         sb.job[sb.count++] = OzSplitJob{(const double*)p.A, p.n, p.m, p.lda, 1, p.n, p.KpAt, p.SAt, p.eAt};
+        sb.job[sb.count - 1].active = p.active;
         if (!make_tmap(&maps[i].tpA, p.SA, kOzSlices * p.m, p.n, p.KpA, 2, 128) ||
             !make_tmap(&maps[i].tpAt, p.SAt, kOzSlices * p.n, p.m, p.KpAt, 2, 128) ||
             !make_tmap(&maps[i].tsN, p.SS, kOzSlices * p.Npad, p.n, p.KpS, 2, ntile) ||
@@ -426,6 +440,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
         const bool onA = kind == kAZ;
         sb.job[sb.count++] = OzSplitJob{(const double*)(onA ? p.Z0 : p.Y0), p.l, onA ? p.n : p.m, p.l, 1, p.Npad,
                                         p.KpS, p.SS, p.eS};
+        sb.job[sb.count - 1].active = p.active;
       }
       RSVD_TRY(launch_oz_split(sb, s));
       for (size_t c0 = 0; c0 < oz.size(); c0 += kMaxOzJobs) {
@@ -448,6 +463,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
           J.trans_c = kind == kQtA ? 1 : 0;
           J.n_eff = p.want_u ? nullptr : p.flag + 2;
           J.err = p.flag + 1;  // a timed-out pipeline wait is reported by the Jacobi SVD's status
+          J.active = p.active;
         }
         RSVD_TRY(launch_oz_gemm(b, s));
       }
@@ -461,6 +477,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
         Prob& p = *pp;
         if (!p.r) continue;
         f.job[f.count] = GemmJob<T, T>{p.r, p.l, p.m, p.ldxf, p.l, p.l, (const T*)p.Xf, (const T*)p.Y0, (T*)p.Wf, nullptr, nullptr, 0};
+        f.job[f.count].active = p.active;
         if (!p.want_u) f.job[f.count].n_eff = p.flag + 2;
         ++f.count;
       }
@@ -474,11 +491,14 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
         Prob& p = *pp;
         if (p.r) {
           f.job[f.count] = GemmJob<T, T>{p.r, p.l, p.n, p.ldyf, p.l, p.l, (const T*)p.Yf, (const T*)p.Z0, (T*)p.Wf, nullptr, nullptr, 0};
+          f.job[f.count].active = p.active;
           if (!p.want_u) f.job[f.count].n_eff = p.flag + 2;
           ++f.count;
           g.job[g.count] = GemmJob<T, T>{p.m, p.l, p.r, p.ldxf, p.l, p.l, (const T*)p.Xf, (const T*)p.Wf, (T*)p.Y0, nullptr, nullptr, 0};
+          g.job[g.count].active = p.active;
         } else {
           g.job[g.count] = GemmJob<T, T>{p.m, p.l, p.n, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Z0, (T*)p.Y0, nullptr, nullptr, 0};
+          g.job[g.count].active = p.active;
         }
         if (!p.want_u) g.job[g.count].n_eff = p.flag + 2;
         ++g.count;
@@ -499,6 +519,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
           g.job[i] = GemmJob<T, T>{p.n, p.l, p.r, p.ldyf, p.l, p.l, (const T*)p.Yf, (const T*)p.Wf, (T*)p.Z0, nullptr, nullptr, 0};
         else
           g.job[i] = GemmJob<T, T>{p.n, p.l, p.m, p.lda, p.l, p.l, (const T*)p.A, (const T*)p.Y0, (T*)p.Z0, nullptr, nullptr, 0};
+        g.job[i].active = p.active;
         if (!p.want_u) g.job[i].n_eff = p.flag + 2;
       }
       return launch_gemm<T, T, true, false>(g, s);
@@ -523,6 +544,7 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
           g.job[i] = GemmJob<T, double>{p.l, p.n, p.r, p.l, p.ldyf, p.n, (const T*)p.Wf, (const T*)p.Yf, p.Bm, nullptr, nullptr, 0};
         else
           g.job[i] = GemmJob<T, double>{p.l, p.n, p.m, p.l, p.lda, p.n, (const T*)p.Y0, (const T*)p.A, p.Bm, nullptr, nullptr, 0};
+        g.job[i].active = p.active;
         if (!p.want_u) g.job[i].m_eff = p.flag + 2;
       }
       RSVD_TRY((launch_gemm<T, double, true, false>(g, s)));
@@ -545,7 +567,9 @@ int run_chunk(std::vector<Prob>& probs, int q, cudaStream_t s) {
       Prob& p = probs[i];
       if (!p.want_u) continue;
       g.job[g.count++] = GemmJob<T, T>{p.m, p.k, p.l, p.l, p.l, p.ldu, (const T*)p.Y0, (const T*)p.Ps, (T*)p.U, nullptr, nullptr, 0};
+      g.job[g.count - 1].active = p.active;
       sb.job[sb.count++] = SignJob<T>{p.m, p.n, p.k, (T*)p.U, p.ldu, (T*)p.Vt, p.ldvt};
+      sb.job[sb.count - 1].active = p.active;
     }
     RSVD_TRY((launch_gemm<T, T, false, true>(g, s)));
     RSVD_TRY(launch_sign<T>(sb, s));
@@ -838,7 +862,10 @@ int rsvd_sectors_adaptive_workspace_size(int batch, const int* m, const int* n, 
   if (batch < 1 || batch > kMaxJobs || chi < 1) return RSVD_ERR_INVALID_SIZE;
   std::vector<int> cap(batch);
   for (int b = 0; b < batch; ++b) cap[b] = std::min(chi, std::min(m[b], n[b]));
-  return rsvd_batched_workspace_size(batch, m, n, cap.data(), p, bytes);
+  int rc = rsvd_batched_workspace_size(batch, m, n, cap.data(), p, bytes);
+  if (rc) return rc;
+  *bytes += align_up(sizeof(int) * (2 * (size_t)batch + 1));  // the device rounds' state
+  return RSVD_OK;
 }
 
 int rsvd_truncate_sectors_adaptive(int batch, const int* m, const int* n, const void* const* A, const int* lda,
@@ -883,7 +910,7 @@ int rsvd_truncate_sectors_adaptive(int batch, const int* m, const int* n, const 
       pr.seed = p->seed; pr.stream = p->stream + (uint64_t)b;
       pr.info = info + b;
       pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
-    pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
+      pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
     }
     rc = run_batched(probs, p, (char*)work, work_bytes, s);
     if (rc) return rc;
@@ -900,9 +927,11 @@ int rsvd_truncate_sectors_adaptive(int batch, const int* m, const int* n, const 
     RSVD_TRY(launch_select(sb, s));
     RSVD_TRY(cudaMemcpyAsync(kept.data(), k_out, sizeof(int) * batch, cudaMemcpyDeviceToHost, s));
     RSVD_TRY(cudaStreamSynchronize(s));
-    // a block all of whose values were kept may hold more above the cut: double its rank
-    todo.clear();
-    for (int b = 0; b < batch; ++b)
+    // a block of this round all of whose values were kept may hold more above the cut:
+    // double its rank (a block left out of a round is not looked at again)
+    std::vector<int> ran;
+    ran.swap(todo);
+    for (int b : ran)
       if (kept[b] == k[b] && k[b] < cap[b]) {
         k[b] = std::min(2 * k[b], cap[b]);
         todo.push_back(b);
@@ -911,6 +940,93 @@ int rsvd_truncate_sectors_adaptive(int batch, const int* m, const int* n, const 
   }
   for (int b = 0; b < batch; ++b) k_trial[b] = k[b];
   *rounds = r;
+  return RSVD_OK;
+}
+
+int rsvd_truncate_sectors_adaptive_device(int batch, const int* m, const int* n, const void* const* A, const int* lda,
+                                          const int* k_first, const rsvd_params* p, int chi, double* const* S,
+                                          void* const* U, const int* ldu, void* const* Vt, const int* ldvt, int* k_out,
+                                          int* k_final, int* rounds, void* work, size_t work_bytes, rsvd_info* info,
+                                          void* cuda_stream) {
+  size_t need = 0;
+  int rc = rsvd_sectors_adaptive_workspace_size(batch, m, n, chi, p, &need);
+  if (rc) return rc;
+  if (!A || !lda || !k_first || !S || !U || !ldu || !Vt || !ldvt || !k_out || !k_final || !rounds || !work || !info)
+    return RSVD_ERR_NULL_POINTER;
+  if (is_tc(p->prec)) return RSVD_ERR_PRECISION;
+  if (((uintptr_t)work) % kAlign) return RSVD_ERR_WORKSPACE;
+  if (need > work_bytes) return RSVD_ERR_WORKSPACE;
+  std::vector<int> cap(batch), k0(batch);
+  for (int b = 0; b < batch; ++b) {
+    cap[b] = std::min(chi, std::min(m[b], n[b]));
+    if (lda[b] < n[b] || ldu[b] < cap[b] || ldvt[b] < n[b]) return RSVD_ERR_INVALID_SIZE;
+    if (!A[b] || !S[b] || !U[b] || !Vt[b]) return RSVD_ERR_NULL_POINTER;
+    k0[b] = std::max(1, std::min(k_first[b], cap[b]));
+  }
+  // the device state after the factorizations' workspace: active[batch], then the rounds count
+  const size_t state_off = need - align_up(sizeof(int) * (2 * (size_t)batch + 1));
+  int* active = (int*)((char*)work + state_off);
+  int* dround = active + batch;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  AdaptInitBatch ib;
+  ib.count = batch;
+  ib.active = active;
+  ib.kdev = k_final;
+  ib.rounds = dround;
+  for (int b = 0; b < batch; ++b) ib.k[b] = k0[b];
+  RSVD_TRY(launch_adapt_init(ib, s));
+  // Round r compresses every block whose scheduled rank k0 2^r (capped) still grows, each
+  // gated by its device flag; the selection and the decision of the next round's flags
+  // stay on the device, so the whole sequence is enqueued at once (and capturable)
+  std::vector<int> kr(k0);
+  for (int r = 0;; ++r) {
+    std::vector<Prob> probs;
+    for (int b = 0; b < batch; ++b) {
+      if (r > 0 && kr[b] >= cap[b]) continue;  // reached its cap in the schedule: never active again
+      const int kb = r == 0 ? kr[b] : std::min(2 * kr[b], cap[b]);
+      kr[b] = kb;
+      probs.emplace_back();
+      Prob& pr = probs.back();
+      std::memset(&pr, 0, sizeof(Prob));
+      pr.m = m[b]; pr.n = n[b]; pr.k = kb;
+      pr.l = sample_width(m[b], n[b], kb, p->p);
+      if (pr.l > kMaxSample) return RSVD_ERR_INVALID_SIZE;
+      pr.exact = use_exact_path(pr.m, pr.l);
+      pr.want_u = 1;
+      pr.A = A[b]; pr.lda = lda[b];
+      pr.S = S[b]; pr.U = U[b]; pr.ldu = ldu[b]; pr.Vt = Vt[b]; pr.ldvt = ldvt[b];
+      pr.seed = p->seed; pr.stream = p->stream + (uint64_t)b;
+      pr.info = info + b;
+      pr.max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 40;
+      pr.serial = (p->flags & RSVD_FLAG_SERIAL) ? 1 : 0;
+      pr.active = active + b;
+    }
+    if (probs.empty()) break;
+    rc = run_batched(probs, p, (char*)work, state_off, s);
+    if (rc) return rc;
+    SelectBatch sb;
+    sb.count = batch;
+    sb.chi = chi;
+    sb.total = 0;
+    sb.k_out = k_out;
+    for (int b = 0; b < batch; ++b) {
+      sb.job[b] = SelectJob{S[b], cap[b], k_final + b};
+      sb.total += cap[b];
+    }
+    RSVD_TRY(launch_select(sb, s));
+    AdaptDecideBatch db;
+    db.count = batch;
+    db.active = active;
+    db.kdev = k_final;
+    db.k_out = k_out;
+    db.rounds = dround;
+    for (int b = 0; b < batch; ++b) {
+      db.cap[b] = cap[b];
+      db.next_k[b] = std::min(2 * kr[b], cap[b]);
+    }
+    RSVD_TRY(launch_adapt_decide(db, s));
+  }
+  RSVD_TRY(cudaMemcpyAsync(rounds, dround, sizeof(int), cudaMemcpyDeviceToDevice, s));
   return RSVD_OK;
 }
 

@@ -41,6 +41,7 @@ struct GemmJob {
   // optional device count: the sum over k stops at *k_eff (op(A)'s columns and
   // op(X)'s rows beyond it are zero)
   const int* k_eff = nullptr;
+  const int* active = nullptr;  // optional device flag: the job runs only while *active != 0
 };
 
 template <typename Tin, typename Tout>
@@ -57,6 +58,7 @@ struct OmegaJob {
   T* out;
   unsigned long long seed, stream;
   int transposed = 0;  // 1: write Omega^T (l x n, ld) instead of Omega (n x l, ld)
+  const int* active = nullptr;  // optional device flag: the job runs only while *active != 0
 };
 template <typename T>
 struct OmegaBatch {
@@ -83,6 +85,7 @@ struct OrthJob {
   // is left zero) and records their number here
   int* rank_eff = nullptr;
   int trunc_q = 0;
+  const int* active = nullptr;  // optional device flag: the job runs only while *active != 0
 };
 template <typename T>
 struct OrthBatch {
@@ -111,6 +114,7 @@ struct JacobiJob {
   int want_p = 1;                 // accumulate the rotations P (needed only for U~ = P^T)
   const int* pipe_err = nullptr;  // optional: nonzero when an earlier tensor-core pipeline wait timed out
   int no_exchange = 0;            // test of the failure path: no CTA sends its round partials
+  const int* active = nullptr;    // optional device flag: the job runs only while *active != 0
 };
 template <typename T>
 struct JacobiBatch {
@@ -131,6 +135,7 @@ struct PrepJob {
   double* Bm;
   int* flag;
   rsvd_info* info;
+  const int* active = nullptr;  // optional device flag: the job runs only while *active != 0
 };
 template <typename T>
 struct PrepBatch {
@@ -145,6 +150,7 @@ struct SignJob {
   int ldu;
   T* Vt;
   int ldvt;
+  const int* active = nullptr;  // optional device flag: the job runs only while *active != 0
 };
 template <typename T>
 struct SignBatch {
@@ -154,7 +160,8 @@ struct SignBatch {
 
 struct SelectJob {
   const double* S;
-  int k;
+  int k;                     // values of the matrix (the largest possible count with kdev)
+  const int* kdev = nullptr; // optional device count of the matrix's values (<= k)
 };
 struct SelectBatch {
   int count;
@@ -274,6 +281,7 @@ struct XposeJob {
   const void* in;
   void* out;           // cols x rows
   int fold = 0;        // split transposes: row offset of the low parts
+  const int* active = nullptr;  // optional device flag: the job runs only while *active != 0
 };
 struct XposeBatch {
   int count;
@@ -321,6 +329,7 @@ struct OzJob {
   const int* n_eff;  // optional: columns >= *n_eff are exact zeros
   int* err;          // optional: set to 1 when a pipeline wait timed out
   int M, N, Npad, K, ldc, trans_c;
+  const int* active = nullptr;  // optional device flag: the job runs only while *active != 0
 };
 struct OzBatch {
   int count;
@@ -334,6 +343,7 @@ struct OzSplitJob {
   int rows_blk, Kp;      // slice block: rows_blk rows (rows .. rows_blk-1 zero) of Kp entries (K .. Kp-1 zero)
   __nv_bfloat16* S;      // kOzSlices blocks of rows_blk x Kp
   int* e;                // rows_blk exponents (0 for zero rows)
+  const int* active = nullptr;  // optional device flag: the job runs only while *active != 0
 };
 struct OzSplitBatch {
   int count;
@@ -405,6 +415,23 @@ template <typename T>
 cudaError_t launch_bw_core(const BwCoreBatch<T>& b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bw_colscale(const BwScaleBatch<T>& b, cudaStream_t s);
+
+// device-side rounds of the adaptive sector ranks (misc.cu): the initial flags and ranks,
+// and after each round's selection the next round's flags (a block stays active while all
+// of its values were kept and its rank is below its cap; its rank then grows to next_k)
+struct AdaptInitBatch {
+  int count;
+  int *active, *kdev, *rounds;
+  int k[kMaxJobs];
+};
+struct AdaptDecideBatch {
+  int count;
+  int *active, *kdev, *rounds;
+  const int* k_out;
+  int cap[kMaxJobs], next_k[kMaxJobs];
+};
+cudaError_t launch_adapt_init(const AdaptInitBatch& b, cudaStream_t s);
+cudaError_t launch_adapt_decide(const AdaptDecideBatch& b, cudaStream_t s);
 
 // complex matrices through their real embedding (complex.cu): R(A) = [X -Y; Y X] from the
 // interleaved complex A, and the complex factors from the real ones (phase rule applied)

@@ -29,6 +29,7 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, __nv_bfloat16>(__nv_
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) transpose_kernel(const __grid_constant__ XposeBatch b) {
   const XposeJob& J = b.job[blockIdx.z];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   if (r0 >= J.rows || c0 >= J.cols) return;
   __shared__ Tin tile[32][33];
@@ -60,6 +61,7 @@ __device__ __forceinline__ void split(float x, float& hi, float& lo) {
 template <typename Tout>
 __global__ void __launch_bounds__(256) split_transpose_kernel(const __grid_constant__ XposeBatch b) {
   const XposeJob& J = b.job[blockIdx.z];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   if (r0 >= J.rows || c0 >= J.cols) return;
   __shared__ float tile[32][33];

@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (m0 >= J.M || n0 >= J.N) return;
   if (J.gate && *J.gate != J.gate_val) return;
+  if (J.active && !*J.active) return;
   if ((J.m_eff && m0 >= *J.m_eff) || (J.n_eff && n0 >= *J.n_eff)) {  // a tile of exact zeros
     if (!J.accumulate)
       for (int e = threadIdx.x; e < BM * BN; e += NT) {

@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   const int C = b.csize;
   const int rank = (int)cluster.block_rank();
   const JacobiJob<T>& J = b.job[blockIdx.y];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   const int l = J.l, n = J.n;
   const JLayout L = jlayout(l, n, C);
   const int c0 = rank * L.nc, ncl = max(0, min(n, c0 + L.nc) - c0);

@@ -16,6 +16,7 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(256) sign_kernel(const __grid_constant__ SignBatch<T> b) {
   const SignJob<T>& J = b.job[blockIdx.y];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   const int lane = threadIdx.x % 32;
   const int col = blockIdx.x * 8 + threadIdx.x / 32;
   if (col >= J.k) return;
@@ -79,11 +80,14 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Sel
     ++bb;
   }
   const int i = g - off;
+  // a matrix's count of values may be a device count (<= k): candidates beyond it are none
+  auto kval = [&](int c) { return b.job[c].kdev ? min(*b.job[c].kdev, b.job[c].k) : b.job[c].k; };
+  if (i >= kval(bb)) return;
   const double v = skey(b.job[bb].S[i]);
   int before = 0;
   for (int c = 0; c < b.count; ++c) {
     int gt, ge;
-    count_desc(b.job[c].S, b.job[c].k, v, gt, ge);
+    count_desc(b.job[c].S, kval(c), v, gt, ge);
     before += gt;
     if (c < bb) before += ge - gt;
     else if (c == bb) before += i - gt;  // equal values at lower positions of the same matrix
@@ -409,5 +413,48 @@ cudaError_t launch_tebd_finish(const TebdFinBatch& b, cudaStream_t s) {
 
 template cudaError_t launch_sign<double>(const SignBatch<double>&, cudaStream_t);
 template cudaError_t launch_sign<float>(const SignBatch<float>&, cudaStream_t);
+
+
+// ---------------------------------------------------------------- adaptive rounds on the device
+namespace {
+__global__ void adapt_init_kernel(const __grid_constant__ AdaptInitBatch b) {
+  for (int i = threadIdx.x; i < b.count; i += blockDim.x) {
+    b.active[i] = 1;
+    b.kdev[i] = b.k[i];
+  }
+  if (threadIdx.x == 0) *b.rounds = 0;
+}
+// after a round's selection: a block that ran in it stays active when every one of its
+// values was kept and its rank is below its cap (it may hold more above the cut), and its
+// rank grows for the next round; the round is counted when any block ran in it
+__global__ void adapt_decide_kernel(const __grid_constant__ AdaptDecideBatch b) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < b.count; i += blockDim.x) {
+    if (!b.active[i]) continue;
+    any = 1;
+    const int grow = (b.k_out[i] == b.kdev[i] && b.kdev[i] < b.cap[i]) ? 1 : 0;
+    b.active[i] = grow;
+    if (grow) b.kdev[i] = b.next_k[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && any) *b.rounds += 1;
+}
+}  // namespace
+
+cudaError_t launch_adapt_init(const AdaptInitBatch& b, cudaStream_t s) {
+  prof_begin(KC_SELECT, s);
+  adapt_init_kernel<<<1, 64, 0, s>>>(b);
+  prof_end(KC_SELECT, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_decide(const AdaptDecideBatch& b, cudaStream_t s) {
+  prof_begin(KC_SELECT, s);
+  adapt_decide_kernel<<<1, 64, 0, s>>>(b);
+  prof_end(KC_SELECT, s);
+  return cudaGetLastError();
+}
 
 }  // namespace rsvd

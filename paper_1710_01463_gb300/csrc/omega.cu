@@ -77,6 +77,7 @@ __device__ __forceinline__ void omega_block(const OmegaJob<T>& J, long long blk,
 template <typename T>
 __global__ void __launch_bounds__(256) omega_kernel(const __grid_constant__ OmegaBatch<T> b) {
   const OmegaJob<T>& J = b.job[blockIdx.y];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   const long long total = (long long)J.n * J.l;
   const long long nblk = (total + 3) / 4;
   for (long long blk = (long long)blockIdx.x * blockDim.x + threadIdx.x; blk < nblk;

@@ -27,6 +27,7 @@ constexpr double kPivotTol = 1e-14;
 template <typename T>
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepBatch<T> b) {
   const PrepJob<T>& J = b.job[blockIdx.y];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     J.info->status = RSVD_OK;
     J.info->path = J.exact ? RSVD_PATH_EXACT : 0;
@@ -86,6 +87,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ OrthBatch<T> b, int gated, int src1) {
   static_assert(kGramTile == 16, "one output per thread of a 16 x 16 tile");
   const OrthJob<T>& J = b.job[blockIdx.z];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   if (J.hh_first || (gated && *J.flag != 0) || known_deficient(J)) return;
   const int l = J.l;
   const int nt = (l + kGramTile - 1) / kGramTile;
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ OrthB
 template <typename T>
 __global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant__ OrthBatch<T> b, int gated) {
   const OrthJob<T>& J = b.job[blockIdx.y];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   if (J.hh_first || (gated && *J.flag != 0) || known_deficient(J)) return;
   const int l = J.l;
   const int nchunk = (J.rows + kGramChunk - 1) / kGramChunk;
@@ -150,6 +153,7 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant_
 template <typename T>
 __global__ void __launch_bounds__(512) cholinv_kernel(const __grid_constant__ OrthBatch<T> b, int pass, int use_smem) {
   const OrthJob<T>& J = b.job[blockIdx.x];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   if (pass == 0 && (J.hh_first || known_deficient(J))) {
     if (threadIdx.x == 0) *J.flag = 1;
     return;
@@ -273,6 +277,7 @@ __global__ void __launch_bounds__(kHhThreads) householder_kernel(const __grid_co
                                                                   int use_global) {
   cg::cluster_group cluster = cg::this_cluster();
   const OrthJob<T>& J = b.job[blockIdx.y];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   if (!J.hh_first && *J.flag == 0) return;  // cluster-uniform: one matrix per cluster
   const int C = csize;
   const int rank = (int)cluster.block_rank();
@@ -579,6 +584,7 @@ template <typename T>
 __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const __grid_constant__ OrthBatch<T> b, int csize) {
   cg::cluster_group cluster = cg::this_cluster();
   const OrthJob<T>& J = b.job[blockIdx.y];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   if (!J.hh_first && *J.flag == 0) return;  // cluster-uniform
   const int C = csize;
   const int rank = (int)cluster.block_rank();
@@ -920,6 +926,7 @@ cudaError_t launch_cholqr2(const OrthBatch<T>& b, cudaStream_t s) {
     for (int i = 0; i < b.count; ++i) {
       const OrthJob<T>& J = b.job[i];
       g.job[i] = GemmJob<T, T>{J.rows, J.l, J.l, J.l, J.l, J.l, J.Y, J.Rinv, J.Y1, nullptr, J.flag, 0};
+      g.job[i].active = J.active;
     }
     e = launch_gemm<T, T, false, false>(g, s);
     if (e != cudaSuccess) return e;
@@ -938,6 +945,7 @@ cudaError_t launch_cholqr2(const OrthBatch<T>& b, cudaStream_t s) {
     for (int i = 0; i < b.count; ++i) {
       const OrthJob<T>& J = b.job[i];
       g.job[i] = GemmJob<T, T>{J.rows, J.l, J.l, J.l, J.l, J.l, J.Y1, J.Rinv, J.Y, nullptr, J.flag, 0};
+      g.job[i].active = J.active;
     }
     e = launch_gemm<T, T, false, false>(g, s);
     if (e != cudaSuccess) return e;

@@ -60,6 +60,7 @@ constexpr int kOzLevels = kOzSlices + 1;  // levels L = 2 .. 11
 // row holding Inf or NaN gets NaN slices, so that the product is NaN there.
 __global__ void __launch_bounds__(256) oz_split_kernel(const __grid_constant__ OzSplitBatch b) {
   const OzSplitJob& J = b.job[blockIdx.y];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int r = blockIdx.x * (blockDim.x / 32) + warp;
   if (r >= J.rows_blk) return;
@@ -112,6 +113,7 @@ constexpr int kOzPStages = 4;  // P tiles in flight
 
 __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_constant__ OzBatch b) {
   const OzJob& J = b.job[blockIdx.z];
+  if (J.active && !*J.active) return;  // an inactive job (whole CTA / cluster, before any barrier)
   const int NT = b.ntile;
   const int m0 = blockIdx.x * kOzM, n0 = blockIdx.y * NT;
   if (m0 >= J.M || n0 >= J.N) return;  // whole CTA, before any barrier or TMEM use

@@ -207,7 +207,9 @@ def test_adaptive_sectors_host_checks(lib):
     assert lib.rsvd_sectors_adaptive_workspace_size(3, m, n, 64, ctypes.byref(par), ctypes.byref(sz)) == 0
     caps = _lib.int_array([64, 64, 64])
     assert lib.rsvd_batched_workspace_size(3, m, n, caps, ctypes.byref(par), ctypes.byref(ref)) == 0
-    assert sz.value == ref.value  # sized for the largest trial rank, min(chi, m_b, n_b)
+    # sized for the largest trial rank, min(chi, m_b, n_b), plus the device rounds' state
+    # (2 batch + 1 ints, one 256-byte aligned slot)
+    assert sz.value == ref.value + 256
     assert lib.rsvd_sectors_adaptive_workspace_size(3, m, n, 0, ctypes.byref(par), ctypes.byref(sz)) == -1
     m65 = _lib.int_array([64] * 65)
     assert lib.rsvd_sectors_adaptive_workspace_size(65, m65, m65, 8, ctypes.byref(par), ctypes.byref(sz)) == -1
@@ -226,6 +228,20 @@ def test_adaptive_sectors_host_checks(lib):
     assert lib.rsvd_truncate_sectors_adaptive(3, m, n, ptrs, lds, kt, ctypes.byref(par), 64, ptrs, ptrs,
                                               _lib.int_array([8, 64, 64]), ptrs, lds, fake, ctypes.byref(rounds), fake,
                                               big, fake, None) == -1
+    # the device-rounds form: same checks (nothing is launched when they fail)
+    assert lib.rsvd_truncate_sectors_adaptive_device(3, m2, m2, ptrs, _lib.int_array([512] * 3), kt,
+                                                     ctypes.byref(bf16), 64, ptrs, ptrs, _lib.int_array([64] * 3),
+                                                     ptrs, _lib.int_array([512] * 3), fake, fake, fake, fake, big,
+                                                     fake, None) == -3
+    assert lib.rsvd_truncate_sectors_adaptive_device(3, m, n, ptrs, lds, kt, ctypes.byref(par), 64, ptrs, ptrs,
+                                                     _lib.int_array([8, 64, 64]), ptrs, lds, fake, fake, fake, fake,
+                                                     big, fake, None) == -1
+    assert lib.rsvd_truncate_sectors_adaptive_device(3, m, n, ptrs, lds, kt, ctypes.byref(par), 64, ptrs, ptrs,
+                                                     _lib.int_array([64] * 3), ptrs, lds, fake, None, fake, fake,
+                                                     big, fake, None) == -2
+    assert lib.rsvd_truncate_sectors_adaptive_device(3, m, n, ptrs, lds, kt, ctypes.byref(par), 64, ptrs, ptrs,
+                                                     _lib.int_array([64] * 3), ptrs, lds, fake, fake, fake, fake,
+                                                     ctypes.c_size_t(sz.value - 1), fake, None) == -4
 
 
 def test_autotune_cache_round_trip(lib, tmp_path):

@@ -104,3 +104,72 @@ def test_adaptive_sector_ranks_match_oracle(api, start, dtype):
         tol = (1e-10 * np.abs(ref) + 1e-14 * smax) if dtype == torch.float64 else 2e-5 * smax
         assert np.all(np.abs(got - ref) <= tol)
     assert all(d["status"] == 0 for d in api.info_dicts(plan.info))
+
+
+@pytest.mark.parametrize("start,dtype", [("ones", torch.float64), ("even", torch.float64), ("ones", torch.float32)])
+def test_adaptive_device_rounds_match_host_rounds(api, start, dtype):
+    # the rounds decided on the device (no host synchronisation) against the host-driven
+    # rounds and the oracle: the same kept counts, final ranks and number of rounds
+    # (integer work, bit-exact in FP64), and the values of the two GPU forms at the FP64 bar
+    # (only the cluster sizes of a round, i.e. summation orders, may differ).  FP32: the
+    # counts are the selection over the device form's own values.
+    blocks = small_sectors(9, 4)
+    chi = 40
+    r0 = [1] * len(blocks) if start == "ones" else [max(1, chi // len(blocks))] * len(blocks)
+    As = [torch.from_numpy(b).to(dtype).cuda() for b in blocks]
+    host = api.AdaptiveSectorsPlan([b.shape for b in blocks], chi, r0, p=8, q=2, seed=5, dtype=dtype)
+    host.run(As)
+    dev = api.AdaptiveSectorsPlan([b.shape for b in blocks], chi, r0, p=8, q=2, seed=5, dtype=dtype,
+                                  device_rounds=True)
+    dev.run(As)
+    torch.cuda.synchronize()
+    got_kept = dev.k_out.cpu().tolist()
+    got_ranks = dev.k_final.cpu().tolist()
+    got_rounds = int(dev.rounds_dev.item())
+    if dtype == torch.float64:
+        _, kept, ranks, rounds = block_rsvd_adaptive(blocks, chi, 8, 2, 5, r0)
+        assert got_kept == kept == host.k_out.cpu().tolist()
+        assert got_ranks == ranks == host.ranks
+        assert got_rounds == rounds == host.rounds
+        for b in range(len(blocks)):
+            kb = got_kept[b]
+            s_h, s_d = host.S[b].cpu().numpy()[:kb], dev.S[b].cpu().numpy()[:kb]
+            assert np.all(np.abs(s_h - s_d) <= 1e-12 * max(1.0, float(np.abs(s_h).max(initial=0.0))))
+    else:
+        assert global_select([s.cpu().numpy()[:r] for s, r in zip(dev.S, got_ranks)], chi) == got_kept
+        for kb, r, blk in zip(got_kept, got_ranks, blocks):
+            assert kb < r or r == min(chi, *blk.shape)
+    assert sum(got_kept) == chi
+    assert all(d["status"] == 0 for d in api.info_dicts(dev.info))
+
+
+def test_adaptive_device_rounds_replay_bit_identically(api):
+    # the batching form of an adaptive sector bond: the 32 uneven FP32 blocks (64..2048),
+    # chi = 512, every trial rank starting at 16, the whole adaptive step (all rounds, the
+    # selections and the round decisions) captured as ONE CUDA graph and replayed
+    blocks = [b.astype(np.float32) for b in inputs.sector_blocks(N=32, lo=64, hi=2048, seed=104)]
+    As = [torch.from_numpy(b).cuda() for b in blocks]
+    plan = api.AdaptiveSectorsPlan([b.shape for b in blocks], 512, [16] * len(blocks), p=16, q=2, seed=103,
+                                   dtype=torch.float32, device_rounds=True)
+    plan.run(As)  # eager reference (also warms up)
+    torch.cuda.synchronize()
+    ref = ([s.clone() for s in plan.S], [u.clone() for u in plan.U], plan.k_out.clone(), plan.k_final.clone(),
+           plan.rounds_dev.clone())
+    assert int(ref[2].sum()) == 512 and int(ref[4].item()) >= 2
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.run(As)
+    for s in plan.S:
+        s.zero_()
+    plan.k_out.zero_()
+    plan.k_final.zero_()
+    plan.rounds_dev.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(plan.k_out, ref[2]) and torch.equal(plan.k_final, ref[3])
+    assert torch.equal(plan.rounds_dev, ref[4])
+    for a, b, r in zip(plan.S, ref[0], ref[3].tolist()):  # entries past a block's final rank are unset
+        assert torch.equal(a[:r], b[:r])
+    for a, b, r in zip(plan.U, ref[1], ref[3].tolist()):
+        assert torch.equal(a[:, :r], b[:, :r])
+    assert all(d["status"] == 0 for d in api.info_dicts(plan.info))
