@@ -314,14 +314,20 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
     // shared memory and one of at least 16 columns per CTA (at most 16 CTAs)
     if (!b.use_global && b.csize > 1) {
       int cmin = 16, cmax = 16;
+      double rep = 0.0;
       for (int i = 0; i < b.count; ++i) {
         const int l = b.job[i].l, n = b.job[i].n;
         int c = 1;
         while (c < 16 && !jacobi_fits_smem(l, n, c)) ++c;
         cmin = i == 0 ? c : std::max(cmin, c);
         cmax = std::min(cmax, std::max(1, n / 16));
+        // per round, in FP64 warp instructions: every CTA forms all l/2 pairs' rotation
+        // scalars (about 40 per warp of pairs) and sums the team partials; the inner
+        // products and the rotations (about 1.5 n per pair) are split over the CTAs
+        const double np = (l + 1) / 2;
+        rep = std::max(rep, (std::ceil(np / 32.0) * 40.0 + np / 4.0) / (np * n * 1.5 / 32.0));
       }
-      if (cmin <= cmax) b.csize = spread_cluster(b.count, cmin, cmax);
+      if (cmin <= cmax) b.csize = spread_cluster(b.count, cmin, cmax, rep);
     }
   }
   {

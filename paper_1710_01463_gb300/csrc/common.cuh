@@ -466,13 +466,15 @@ int sm_count();
 // the smallest c that minimises that load is taken (fewer CTAs per cluster: cheaper
 // barriers and fewer partials to exchange; measured faster than two CTAs per SM on the
 // TEBD layers).  The choice depends on the batch, so a matrix's rounding (the order of its
-// cluster sums) can differ between batches of different sizes.
-inline int spread_cluster(int count, int cmin, int cmax) {
+// cluster sums) can differ between batches of different sizes.  `rep` is the work every
+// CTA of a cluster repeats (in units of one whole matrix's divisible work): a CTA then
+// carries rep + 1/c.
+inline int spread_cluster(int count, int cmin, int cmax, double rep = 0.0) {
   const long long sms = sm_count();
   int best = cmax;
   double bl = 1e300;
   for (int c = cmin; c <= cmax; ++c) {
-    const double load = (double)((count * (long long)c + sms - 1) / sms) / c;
+    const double load = (double)((count * (long long)c + sms - 1) / sms) * (rep + 1.0 / c);
     if (load < bl * (1.0 - 1e-12)) {
       bl = load;
       best = c;

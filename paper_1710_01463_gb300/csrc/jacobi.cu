@@ -39,7 +39,11 @@ namespace {
 
 constexpr int kJacobiThreads = 512;
 constexpr int kMaxCluster = 16;  // cluster sizes up to 16 (non-portable above 8)
-constexpr int kTeam = 8;   // lanes per row pair; lane t of a team reads the partials of ranks t, t + 8
+constexpr int kTeam = 8;     // lanes per row pair in the rotation phase
+constexpr int kTeamDot = 4;  // lanes per row pair in the inner-product phase: two levels of shuffle
+                             // additions per pair instead of three (an FP64 warp instruction holds
+                             // the pipe for 16 cycles, so the reduction's additions cost as much
+                             // as the products themselves with 8 lanes)
 constexpr size_t kSmemBudget = 220 * 1024;
 
 __device__ __forceinline__ void round_pair(int r, int s, int lp, int& i, int& j) {
@@ -175,7 +179,8 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
 
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int team = tid / kTeam, tl = tid % kTeam, nteam = kJacobiThreads / kTeam;
-  const unsigned tmask = 0xffu << ((tid % 32) / kTeam * kTeam);  // this team's lanes
+  const int dteam = tid / kTeamDot, dl = tid % kTeamDot, ndteam = kJacobiThreads / kTeamDot;
+  const unsigned dmask = 0xfu << ((tid % 32) / kTeamDot * kTeamDot);  // this inner-product team's lanes
   for (int e = tid; e < l * L.nc; e += kJacobiThreads) {
     const int i = e / L.nc, c = e % L.nc;
     Bs[e] = (c < ncl) ? J.Bm[(size_t)i * n + c0 + c] : 0.0;
@@ -305,18 +310,25 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
       double* gp = gpart + (gr & 1) * C * L.npairs;
       uint64_t* mb = &mbR[gr & 1];
       if (tid == 0) mb_expect(mb, (uint32_t)C * npl2 * 8);
-      for (int s = team; s < npl2; s += nteam) {
+      for (int s = dteam; s < npl2; s += ndteam) {
         int a, bq;
         round_pair(r, s, lpl, a, bq);
-        double g = 0.0;
+        double g0 = 0.0, g1 = 0.0;
         if (bq < nlive) {
-          const int i = live[a], j = live[bq];
-          for (int c = tl; c < ncl; c += kTeam) g = fma(Bs[i * L.nc + c], Bs[j * L.nc + c], g);
+          const double* xi = Bs + live[a] * L.nc;
+          const double* xj = Bs + live[bq] * L.nc;
+          int c = dl;
+          for (; c + kTeamDot < ncl; c += 2 * kTeamDot) {
+            g0 = fma(xi[c], xj[c], g0);
+            g1 = fma(xi[c + kTeamDot], xj[c + kTeamDot], g1);
+          }
+          if (c < ncl) g0 = fma(xi[c], xj[c], g0);
         }
+        double g = g0 + g1;
 #pragma unroll
-        for (int o = kTeam / 2; o > 0; o >>= 1) g += __shfl_xor_sync(tmask, g, o, kTeam);
+        for (int o = kTeamDot / 2; o > 0; o >>= 1) g += __shfl_xor_sync(dmask, g, o, kTeamDot);
         if (!J.no_exchange)
-          for (int q = tl; q < C; q += kTeam) push_f64(&gp[rank * L.npairs + s], mb, q, g);
+          for (int q = dl; q < C; q += kTeamDot) push_f64(&gp[rank * L.npairs + s], mb, q, g);
       }
       if (tid < npl2 && !mb_wait_cluster(mb, (gr >> 1) & 1)) atomicExch(&rerr, 1);
       // rotation scalars, one lane per pair, in as few warps as possible (a
