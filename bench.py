@@ -50,8 +50,13 @@ I_STATUS, I_PATH, I_FALLS, I_SWEEPS, I_L, I_ROTS, I_QRCOLS, I_QRKFLOP, I_PAIRS, 
 # DRAM bytes (read + write) per launch of a workload's dominant kernel, from one
 # ncu capture of that kernel as it stands (summaries under profiles/); a kernel
 # changed since its capture has no entry (traffic null).
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel in the named
+# workload: the evidence that the kernel reads its operands once (for the Jacobi SVD: the
+# central group's launch, 25 bond matrices B of 138 x 256 FP64 = 7.07 MB)
 TRAFFIC_PER_LAUNCH = {
     ("mixed", "tcgemm"): (561.69e6 + 16.31e6, "profiles/gram_and_tc_gemm_mixed_bf16_16x4096.md"),
+    ("tebd_tfim_L64_chi128_d2_dt0.01_p10_q2_fp64", "jacobi"):
+        (7.145e6, "profiles/jacobi_tebd_L64_chi128_ground.md (central group's launch, 25 matrices)"),
 }
 
 
@@ -362,6 +367,7 @@ def timed_steps(ch, first, steps, flush, stream, infos=None):
 
 
 def run_ours(args):
+    import numpy as np
     import torch
 
     from paper_1710_01463_gb300 import _lib, inputs
@@ -376,8 +382,20 @@ def run_ours(args):
     peaks = measured_peaks()
     t_prep = time.time()
     ch = make_chain(rank=rank)
-    ch.set_product_state(inputs.product_state_vectors(L_SITES, D_LOC, 102 + rank))
-    nxt = ch.evolve(tebd_mod.SCHEDULE_GROUND if STATE == "ground" else tebd_mod.SCHEDULE_EARLY)
+    state_file = args.state_file + (f".rank{rank}" if ws > 1 else "") if args.state_file else None
+    if state_file and os.path.exists(state_file):
+        # the prepared state of an earlier run of the same workload (profiling runs)
+        z = np.load(state_file)
+        if str(z["workload"]) != WORKLOAD:
+            raise SystemExit(f"{state_file} holds a state of {z['workload']}, not {WORKLOAD}")
+        ch.state_from_host(z["B"], z["lam"])
+        nxt = int(z["step"])
+    else:
+        ch.set_product_state(inputs.product_state_vectors(L_SITES, D_LOC, 102 + rank))
+        nxt = ch.evolve(tebd_mod.SCHEDULE_GROUND if STATE == "ground" else tebd_mod.SCHEDULE_EARLY)
+        if state_file:
+            B_h, lam_h = ch.state_to_host()
+            np.savez(state_file, B=B_h, lam=lam_h, step=nxt, workload=WORKLOAD)
     ch.set_dt(DT)
     for s in range(args.warmup):
         ch.step(nxt + s)
@@ -411,7 +429,7 @@ def run_ours(args):
     tflops = ws * sum(fl.values()) / (tot_ms / 1e3) / 1e12
     kernels = kernel_table(classes, fl, "f64")
     dom = max(kernels, key=lambda x: kernels[x]["ms_total"])
-    roofline = roofline_of(dom, classes, fl, "f64", "tebd", peaks)
+    roofline = roofline_of(dom, classes, fl, "f64", WORKLOAD, peaks)
     roofline["timing"] = ("sum of the class's launch durations, CUDA events on the launching streams inside the "
                           "timed region (the library's side streams overlap groups of a call)")
 
@@ -465,7 +483,7 @@ def serial_leg(ch, lib, first, flush, stream, peaks, steps=2):
         add_flops(fl, step_flops(inf.cpu().numpy()))
     kt = kernel_table(classes, fl, "f64")
     dom = max(kt, key=lambda x: kt[x]["ms_total"])
-    r = roofline_of(dom, classes, fl, "f64", "tebd", peaks)
+    r = roofline_of(dom, classes, fl, "f64", WORKLOAD, peaks)
     r["ms_per_step"] = round(sum(step_ms) / steps, 4)
     r["kernel_ms_per_step"] = round(sum(v[0] for v in classes.values()) / steps, 4)
     r["shares"] = {k: v["share"] for k, v in kt.items()}
@@ -1112,6 +1130,9 @@ def main():
                     help="tebd (default): the TEBD bond-update workload; the others time the remaining configurations")
     ap.add_argument("--state", default="ground", choices=["ground", "early"],
                     help="TEBD: time from the converged ground state (default) or the early state")
+    ap.add_argument("--state-file", default=None,
+                    help="TEBD: .npz of the prepared state - loaded if it exists, else written after the "
+                         "preparation (lets a profiler run skip the ground-state preparation)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32"], help="mixed workload: operand precision")
     ap.add_argument("--policy", default="estimate", choices=["estimate", "maximal", "adaptive"],
                     help="sectors workload: per-block trial ranks")
