@@ -449,11 +449,14 @@ def run_ours(args):
                                "nonzero_status": int((st[..., I_STATUS] != 0).sum())}
     if rank == 0 and not args.no_extras:
         result["roofline_serial"] = serial_leg(ch, lib, first + args.steps, flush, stream, peaks)
-        result["tsvd_same_engine"] = tsvd_leg(ch, state0, first, args, flush, stream, ms_per_step)
+        if UPDATE == "block":  # the engine's TSVD form compresses the formed two-site matrix
+            result["tsvd_same_engine"] = tsvd_leg(ch, state0, first, args, flush, stream, ms_per_step)
         ch.B.copy_(final_rsvd[0])
         ch.lam.copy_(final_rsvd[1])
         result["e2e"] = e2e_leg(ch, args)
-        result["error"] = error_leg(ch)
+        result["error"] = error_leg(ch) if UPDATE == "block" else {
+            "note": "the product update compresses factored matrices X Y per gate; its factors are checked "
+                    "against the oracle in the tests (test_gpu_tebd.py, test_gpu_factored.py)"}
         result["comparator"] = comparator_leg()
         result["cpu_baseline"] = cpu_leg(ch)
         if not args.no_other_configs and UPDATE == "block" and WIDTH == 0 and SPIN == 0.5:
@@ -807,16 +810,20 @@ def workload_leg(wl, args, steps, warmup, extras=True, batch=None):
         config["policy"] = "previous step's kept count + 16 (first step: maximal)"
         plan = api.BatchedPlan([tuple(A.shape) for A in As], ks, p, q, 103 + 1000 * rank, 0, dtype, dev,
                                chi_global=512)
-    adaptive = wl == "sectors" and args.policy == "adaptive"
+    adaptive = wl == "sectors" and args.policy in ("adaptive", "adaptive-device")
+    devr = args.policy == "adaptive-device"
     if adaptive:
         r0 = [max(1, 512 // len(As))] * len(As)
-        plan = api.AdaptiveSectorsPlan([tuple(A.shape) for A in As], 512, r0, p, q, 103 + 1000 * rank, 0, dtype, dev)
+        plan = api.AdaptiveSectorsPlan([tuple(A.shape) for A in As], 512, r0, p, q, 103 + 1000 * rank, 0, dtype, dev,
+                                       device_rounds=devr)
         config["policy"] = ("adaptive: first guess chi / N = 16 every step, the ranks of saturated blocks doubled "
-                            "until none is (flops counted for the final round only)")
+                            "until none is (flops counted for the final round only)"
+                            + ("; rounds decided on the device, one launch sequence per step" if devr else
+                               "; rounds decided on the host"))
     bw_info = []
 
     def step():
-        if adaptive:
+        if adaptive and not devr:
             plan.ranks = list(r0)
         plan.run(As)
         if wl == "grad":
@@ -854,7 +861,7 @@ def workload_leg(wl, args, steps, warmup, extras=True, batch=None):
     units_per_step = 1 if wl == "sectors" else len(As)
     value = ws * units_per_step / (ms_per_step / 1e3)
     if adaptive:
-        ks = list(plan.ranks)
+        ks = plan.k_final.cpu().tolist() if devr else list(plan.ranks)
 
     fl = new_flops()
     tcb = 0.0
@@ -898,8 +905,8 @@ def workload_leg(wl, args, steps, warmup, extras=True, batch=None):
         result["device_status"]["cg_iterations_mean"] = round(float(np.mean(cg_iters)), 1)
         result["device_status"]["cg_iterations_max"] = int(np.max(cg_iters))
     if adaptive:
-        result["device_status"]["adaptive_rounds"] = plan.rounds
-        result["device_status"]["final_trial_ranks"] = list(plan.ranks)
+        result["device_status"]["adaptive_rounds"] = int(plan.rounds_dev.item()) if devr else plan.rounds
+        result["device_status"]["final_trial_ranks"] = list(ks)
     if rank != 0 or not extras:
         result["error"] = workload_error(wl, As, ks, p, q, plan, extra, orsvd)
         return result
@@ -1134,7 +1141,7 @@ def main():
                     help="TEBD: .npz of the prepared state - loaded if it exists, else written after the "
                          "preparation (lets a profiler run skip the ground-state preparation)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32"], help="mixed workload: operand precision")
-    ap.add_argument("--policy", default="estimate", choices=["estimate", "maximal", "adaptive"],
+    ap.add_argument("--policy", default="estimate", choices=["estimate", "maximal", "adaptive", "adaptive-device"],
                     help="sectors workload: per-block trial ranks")
     ap.add_argument("--chain-length", type=int, default=64,
                     help="L (default 64); a shorter chain keeps the 256 x 256 central bonds (profiling case)")
