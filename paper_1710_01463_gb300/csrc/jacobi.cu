@@ -44,8 +44,14 @@ constexpr int kTeamDot = 4;  // lanes per row pair in the inner-product phase: t
                              // additions per pair instead of three (an FP64 warp instruction holds
                              // the pipe for 16 cycles, so the reduction's additions cost as much
                              // as the products themselves with 8 lanes)
+constexpr int kScalarThreads = 128;  // warps 0-3 form the rotation scalars (0-1: half A, 2-3: half B)
+// threads at the barrier of a half: its scalar warps (arrive) and the worker warps (wait)
+constexpr int kHalfBarThreads = kScalarThreads / 2 + (kJacobiThreads - kScalarThreads);
 constexpr size_t kSmemBudget = 220 * 1024;
 
+// Round r of the circle ordering over lp (even) rows: pair s is (m, r) for s = 0 and
+// ((r + s) mod m, (r - s) mod m) otherwise, m = lp - 1; 0 <= r, s < m, so each reduction is
+// one conditional subtraction or addition
 __device__ __forceinline__ void round_pair(int r, int s, int lp, int& i, int& j) {
   const int m = lp - 1;
   int a, bb;
@@ -53,8 +59,10 @@ __device__ __forceinline__ void round_pair(int r, int s, int lp, int& i, int& j)
     a = m;
     bb = r;
   } else {
-    a = (r + s) % m;
-    bb = (r - s + m) % m;
+    a = r + s;
+    a -= a >= m ? m : 0;
+    bb = r - s;
+    bb += bb < 0 ? m : 0;
   }
   i = min(a, bb);
   j = max(a, bb);
@@ -78,9 +86,9 @@ __host__ __device__ inline size_t jsmem_small(int l, const JLayout& L) {
   // norms, nrm_part, gpart[2][cluster size][npairs] (every CTA's partial of every
   // pair, pushed), order (int, padded to doubles), the rotations' two update
   // coefficients [npairs] and flags (int, padded), the rows' scale factors and their
-  // inverses [l each]
+  // inverses [l each], the rotations' tangents and inner products [npairs each]
   return sizeof(double) * ((size_t)2 * l + (2 * (size_t)L.cs + 2) * L.npairs + (size_t)(l + 1) / 2 + 1 +
-                           (size_t)(L.npairs + 1) / 2 + 1 + (size_t)2 * l);
+                           (size_t)(L.npairs + 1) / 2 + 1 + (size_t)2 * l + (size_t)2 * L.npairs);
 }
 
 // Sum over the CTAs of the cluster of v[i] in their shared memory: every
@@ -95,6 +103,44 @@ __device__ __forceinline__ double cluster_tree_sum(cg::cluster_group& cluster, c
 #pragma unroll
     for (int r = 0; r + w < kMaxCluster; r += 2 * w) pv[r] += pv[r + w];
   return pv[0];
+}
+
+// Sum of the C partials slot[q * stride], q < C, by a fixed pairwise tree over 4, 8 or 16
+// slots (the slots past C read as zero, which leaves every partial sum unchanged), so every
+// CTA gets the same bits with log2 depth and no more FP64 additions than the padded width
+__device__ __forceinline__ double tree_sum(const double* slot, int stride, int C) {
+  double v[kMaxCluster];
+  if (C <= 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = q < C ? slot[q * stride] : 0.0;
+    return (v[0] + v[1]) + (v[2] + v[3]);
+  }
+  if (C <= 8) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = q < C ? slot[q * stride] : 0.0;
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = q < C ? slot[q * stride] : 0.0;
+#pragma unroll
+  for (int w = 1; w < 16; w <<= 1)
+#pragma unroll
+    for (int q = 0; q + w < 16; q += 2 * w) v[q] += v[q + w];
+  return v[0];
+}
+
+// Named barriers between the scalar warps (arrive) and the worker warps (sync): the
+// workers wait until the scalars of a half are written; bar.arrive orders the arriving
+// threads' shared-memory writes before the waiters' reads
+template <int kId, int kThreads>
+__device__ __forceinline__ void named_sync() {
+  __syncwarp();  // the barrier instructions are warp-aligned: reconverge first
+  asm volatile("bar.sync %0, %1;" ::"n"(kId), "n"(kThreads) : "memory");
+}
+template <int kId, int kThreads>
+__device__ __forceinline__ void named_arrive() {
+  __syncwarp();
+  asm volatile("bar.arrive %0, %1;" ::"n"(kId), "n"(kThreads) : "memory");
 }
 
 // Point-to-point signals between the CTAs of a cluster: a value stored into
@@ -161,6 +207,8 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   // per rotation and are folded back into the rows at every sweep head and every 64 rounds.
   double* dsc = rsn + L.npairs + (L.npairs + 1) / 2 + 1;
   double* isc = dsc + l;
+  double* rtan = isc + l;           // per pair of the round: the tangent t and the inner product g,
+  double* rgam = rtan + L.npairs;   // kept for the scale and norm updates after the coefficients
   double* Bs;
   double* Ps;
   if (b.use_global) {
@@ -178,8 +226,10 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   int* live = order;  // live-row list during the sweeps; the sort order afterwards
 
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
-  const int team = tid / kTeam, tl = tid % kTeam, nteam = kJacobiThreads / kTeam;
-  const int dteam = tid / kTeamDot, dl = tid % kTeamDot, ndteam = kJacobiThreads / kTeamDot;
+  // the worker warps' teams (wid < 0 in the scalar warps, which never use them)
+  const int wid = tid - kScalarThreads;
+  const int team = wid / kTeam, tl = wid % kTeam, nteam = (kJacobiThreads - kScalarThreads) / kTeam;
+  const int dteam = wid / kTeamDot, dl = wid % kTeamDot, ndteam = (kJacobiThreads - kScalarThreads) / kTeamDot;
   const unsigned dmask = 0xfu << ((tid % 32) / kTeamDot * kTeamDot);  // this inner-product team's lanes
   for (int e = tid; e < l * L.nc; e += kJacobiThreads) {
     const int i = e / L.nc, c = e % L.nc;
@@ -208,13 +258,15 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
     }
     __syncthreads();
   };
-  __shared__ uint64_t mbR[2];  // round exchanges of even / odd global round number
+  __shared__ uint64_t mbR[2][2];  // round exchanges of even / odd global round number, halves A / B
   __shared__ int rerr;         // a round exchange timed out
   if (tid == 0) {
     nonfinite = 0;
     rerr = 0;
-    mb_init(&mbR[0]);
-    mb_init(&mbR[1]);
+    mb_init(&mbR[0][0]);
+    mb_init(&mbR[0][1]);
+    mb_init(&mbR[1][0]);
+    mb_init(&mbR[1][1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   uint32_t gr = 0;  // rounds done over all sweeps: the exchange buffer and mbarrier phase
@@ -227,6 +279,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
   int sweeps = 0;
   long long total_rot = 0;
   long long total_pairs = 0;  // inner products formed: nlive (nlive - 1) / 2 per sweep
+  int myrot = 0;              // rotations of this sweep formed by this thread
   bool converged = false;
   for (;;) {
     if (sweeps > 0) rescale();
@@ -296,6 +349,13 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
     const int lpl = nlive + (nlive & 1);
     const int npl2 = lpl / 2;
     total_pairs += (long long)nlive * (nlive - 1) / 2;
+    // the round's pairs in two halves, A = [0, hA) and B = [hA, npl2): the worker warps form
+    // half A's inner products and send them, then half B's, while the scalar warps of
+    // half A wait for A's partials and form its rotations; the workers then rotate half A
+    // while the scalar warps of half B finish, and rotate half B last.  So the scalars'
+    // dependent FP64 chains run beside the products and rotations of the other half
+    // instead of holding the whole CTA
+    const int hA = (npl2 + 1) / 2;
     for (int r = 0; r < lpl - 1; ++r, ++gr) {
       // after a timed-out exchange (rerr is uniform in the CTA after the round's last
       // __syncthreads) this CTA sends and waits no more; the sweep head then ends the
@@ -303,122 +363,155 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
       if (rerr) break;
       // this round's partials: slot [q][s] holds CTA q's partial of pair s, stored by
       // that CTA with st.async completing bytes on this CTA's mbarrier of the round's
-      // parity; only the rotation lanes wait for them, and every CTA sums them in the
-      // same order.  A slot (and the mbarrier) of parity gr & 1 is reused two rounds
-      // later: a CTA stores round gr + 2 only after receiving everyone's round gr + 1,
-      // which each CTA sends after it has read its round gr partials
+      // parity and the pair's half; only the scalar warps wait for them, and every CTA
+      // sums them in the same order.  A slot (and its mbarriers) of parity gr & 1 is
+      // reused two rounds later: a CTA stores round gr + 2 only after receiving
+      // everyone's round gr + 1, which each CTA sends after it has read its round gr
+      // partials
       double* gp = gpart + (gr & 1) * C * L.npairs;
-      uint64_t* mb = &mbR[gr & 1];
-      if (tid == 0) mb_expect(mb, (uint32_t)C * npl2 * 8);
-      for (int s = dteam; s < npl2; s += ndteam) {
-        int a, bq;
-        round_pair(r, s, lpl, a, bq);
-        double g0 = 0.0, g1 = 0.0;
-        if (bq < nlive) {
-          const double* xi = Bs + live[a] * L.nc;
-          const double* xj = Bs + live[bq] * L.nc;
-          int c = dl;
-          for (; c + kTeamDot < ncl; c += 2 * kTeamDot) {
-            g0 = fma(xi[c], xj[c], g0);
-            g1 = fma(xi[c + kTeamDot], xj[c + kTeamDot], g1);
-          }
-          if (c < ncl) g0 = fma(xi[c], xj[c], g0);
-        }
-        double g = g0 + g1;
-#pragma unroll
-        for (int o = kTeamDot / 2; o > 0; o >>= 1) g += __shfl_xor_sync(dmask, g, o, kTeamDot);
-        if (!J.no_exchange)
-          for (int q = dl; q < C; q += kTeamDot) push_f64(&gp[rank * L.npairs + s], mb, q, g);
+      uint64_t* mbA = &mbR[gr & 1][0];
+      uint64_t* mbB = &mbR[gr & 1][1];
+      if (tid == 0) {
+        mb_expect(mbA, (uint32_t)C * hA * 8);
+        mb_expect(mbB, (uint32_t)C * (npl2 - hA) * 8);
       }
-      if (tid < npl2 && !mb_wait_cluster(mb, (gr >> 1) & 1)) atomicExch(&rerr, 1);
-      // rotation scalars, one lane per pair, in as few warps as possible (a
-      // warp's FP64 instruction holds the SM's FP64 pipe for 16 cycles whatever
-      // the number of active lanes); every CTA sums the partials in rank order,
-      // so all CTAs of the cluster take bit-identical decisions
-      for (int s = tid; s < npl2; s += kJacobiThreads) {
-        int a, bq;
-        round_pair(r, s, lpl, a, bq);
-        int rot = 0;
-        double cs = 1.0, sn = 0.0;
-        if (bq < nlive) {
+      if (tid >= kScalarThreads) {
+        // worker warps: inner products of half A, then of half B, pushed to every CTA
+        for (int h = 0; h < 2; ++h) {
+          const int s0 = h ? hA : 0, s1 = h ? npl2 : hA;
+          uint64_t* mb = h ? mbB : mbA;
+          for (int s = s0 + dteam; s < s1; s += ndteam) {
+            int a, bq;
+            round_pair(r, s, lpl, a, bq);
+            double g0 = 0.0, g1 = 0.0;
+            if (bq < nlive) {
+              const double* xi = Bs + live[a] * L.nc;
+              const double* xj = Bs + live[bq] * L.nc;
+              int c = dl;
+              for (; c + kTeamDot < ncl; c += 2 * kTeamDot) {
+                g0 = fma(xi[c], xj[c], g0);
+                g1 = fma(xi[c + kTeamDot], xj[c + kTeamDot], g1);
+              }
+              if (c < ncl) g0 = fma(xi[c], xj[c], g0);
+            }
+            double g = g0 + g1;
+#pragma unroll
+            for (int o = kTeamDot / 2; o > 0; o >>= 1) g += __shfl_xor_sync(dmask, g, o, kTeamDot);
+            if (!J.no_exchange)
+              for (int q = dl; q < C; q += kTeamDot) push_f64(&gp[rank * L.npairs + s], mb, q, g);
+          }
+        }
+        // rotations of half A once its scalars are ready, then of half B
+        for (int h = 0; h < 2; ++h) {
+          if (h == 0)
+            named_sync<1, kHalfBarThreads>();
+          else
+            named_sync<2, kHalfBarThreads>();
+          const int s0 = h ? hA : 0, s1 = h ? npl2 : hA;
+          for (int s = s0 + team; s < s1; s += nteam) {
+            if (!rfl[s]) continue;  // team-uniform
+            int a, bq;
+            round_pair(r, s, lpl, a, bq);
+            const int i = live[a], j = live[bq];
+            const double ca = rcs[s], cb = rsn[s];
+            for (int c = tl; c < ncl; c += kTeam) {
+              const double x = Bs[i * L.nc + c], y = Bs[j * L.nc + c];
+              Bs[i * L.nc + c] = fma(-ca, y, x);
+              Bs[j * L.nc + c] = fma(cb, x, y);
+            }
+            for (int c = tl; want_p && c < npl; c += kTeam) {
+              const double x = Ps[i * L.np + c], y = Ps[j * L.np + c];
+              Ps[i * L.np + c] = fma(-ca, y, x);
+              Ps[j * L.np + c] = fma(cb, x, y);
+            }
+          }
+        }
+      } else {
+        // scalar warps: the first half of them for half A, the second for half B; one
+        // lane per pair, every CTA summing the partials in rank order, so all CTAs of
+        // the cluster take bit-identical decisions
+        const int h = tid >= kScalarThreads / 2 ? 1 : 0;
+        const int s0 = h ? hA : 0, s1 = h ? npl2 : hA;
+        const int sl = tid - h * (kScalarThreads / 2);
+        if (s0 + sl < s1 && !mb_wait_cluster(h ? mbB : mbA, (gr >> 1) & 1)) atomicExch(&rerr, 1);
+        for (int s = s0 + sl; s < s1; s += kScalarThreads / 2) {
+          int a, bq;
+          round_pair(r, s, lpl, a, bq);
+          int rot = 0;
+          double cs = 1.0, sn = 0.0;
+          if (bq < nlive) {
+            const int i = live[a], j = live[bq];
+            const double al = norms[i], be = norms[j];
+            const double di = dsc[i], dj = dsc[j];
+            const double g = tree_sum(gp + s, L.npairs, C) * (di * dj);  // the inner product of the (unscaled) rows
+            // al, be > 0 and g^2 > tol^2 al be, compared as bit patterns (all >= +0)
+            if (__double_as_longlong(al) > 0 && __double_as_longlong(be) > 0 &&
+                __double_as_longlong(g * g) > __double_as_longlong(tol2 * (al * be))) {
+              rot = 1;
+              // tangent of the annihilating angle, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+              // zeta = (be - al) / (2g), formed in FP32 (a dependent FP64 chain of
+              // square roots and divisions would hold the round for microseconds).
+              // Any angle gives an exactly orthogonal rotation once cs, sn come from
+              // the same t in FP64; the FP32 angle leaves |g| at about 1e-7 of its
+              // value instead of 0, and the FP64 stopping test above decides
+              // convergence, so the result keeps FP64 accuracy.
+              // h and 2g are scaled by a power of two (from the exponent bits) into
+              // FP32 range; live rows differ by at most 2^104 in squared norm
+              // (deflation), so |zeta| < 1e29 and only zeta^2 needs the guard
+              const double hd = be - al, g2 = 2.0 * g;
+              const double mx = fmax(fabs(hd), fabs(g2));
+              const long long ex = min(((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023, 1022LL);
+              const double sc = __longlong_as_double((1023 - ex) << 52);  // 2^-ex
+              const float zf = (float)(hd * sc) / (float)(g2 * sc);
+              const float tf = fabsf(zf) < 1e18f ? copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)))
+                                                 : 0.5f / zf;
+              const double t = (double)tf;
+              // (c, c t) rotation in scaled form: x_i <- x_i - t (d_j / d_i) x_j,
+              // x_j <- x_j + t (d_i / d_j) x_i, d_i, d_j <- c d_i, c d_j: the workers
+              // need only the two coefficients; c and the new scales and norms follow
+              // after the coefficients are published
+              cs = t * dj * isc[i];
+              sn = t * di * isc[j];
+              rtan[s] = t;
+              rgam[s] = g;
+              if (__double_as_longlong(g * g) > __double_as_longlong(thr2 * (al * be))) big_rot = 1;
+            }
+          }
+          rcs[s] = cs;
+          rsn[s] = sn;
+          rfl[s] = rot;
+        }
+        if (h == 0)
+          named_arrive<1, kHalfBarThreads>();
+        else
+          named_arrive<2, kHalfBarThreads>();
+        // the rotated rows' scales and norms for the next round (the rows of a round's
+        // pairs are disjoint, and only this lane touches those of its pairs), while the
+        // workers rotate
+        for (int s = s0 + sl; s < s1; s += kScalarThreads / 2) {
+          if (!rfl[s]) continue;
+          int a, bq;
+          round_pair(r, s, lpl, a, bq);
           const int i = live[a], j = live[bq];
-          const double al = norms[i], be = norms[j];
-          // the CTAs' partials by the same fixed tree in every CTA, over the cluster's
-          // size only (an FP64 instruction costs its warp a full pipe slot even with one
-          // active lane, so no additions of padding zeros)
-          double pv[kMaxCluster];
-#pragma unroll
-          for (int q = 0; q < kMaxCluster; ++q) pv[q] = q < C ? gp[q * L.npairs + s] : 0.0;
-#pragma unroll
-          for (int w = 1; w < kMaxCluster; w <<= 1)
-#pragma unroll
-            for (int q = 0; q + w < kMaxCluster; q += 2 * w)
-              if (q + w < C) pv[q] += pv[q + w];
-          const double di = dsc[i], dj = dsc[j];
-          const double g = pv[0] * (di * dj);  // the inner product of the (unscaled) rows
-          // al, be > 0 and g^2 > tol^2 al be, compared as bit patterns (all >= +0)
-          if (__double_as_longlong(al) > 0 && __double_as_longlong(be) > 0 &&
-              __double_as_longlong(g * g) > __double_as_longlong(tol2 * (al * be))) {
-            rot = 1;
-            // tangent of the annihilating angle, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-            // zeta = (be - al) / (2g), formed in FP32 (a dependent FP64 chain of
-            // square roots and divisions would hold the round for microseconds).
-            // Any angle gives an exactly orthogonal rotation once cs, sn come from
-            // the same t in FP64; the FP32 angle leaves |g| at about 1e-7 of its
-            // value instead of 0, and the FP64 stopping test above decides
-            // convergence, so the result keeps FP64 accuracy.
-            // h and 2g are scaled by a power of two (from the exponent bits) into
-            // FP32 range; live rows differ by at most 2^104 in squared norm
-            // (deflation), so |zeta| < 1e29 and only zeta^2 needs the guard
-            const double h = be - al, g2 = 2.0 * g;
-            const double mx = fmax(fabs(h), fabs(g2));
-            const long long ex = min(((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023, 1022LL);
-            const double sc = __longlong_as_double((1023 - ex) << 52);  // 2^-ex
-            const float zf = (float)(h * sc) / (float)(g2 * sc);
-            const float tf = fabsf(zf) < 1e18f ? copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)))
-                                               : 0.5f / zf;
-            const double t = (double)tf;
-            const double t2 = fma(t, t, 1.0);
-            const double c = rsqrt(t2);
-            // (c, c t) rotation in scaled form: x_i <- x_i - t (d_j / d_i) x_j,
-            // x_j <- x_j + t (d_i / d_j) x_i, d_i, d_j <- c d_i, c d_j
-            cs = t * dj * isc[i];
-            sn = t * di * isc[j];
-            dsc[i] = c * di;
-            dsc[j] = c * dj;
-            isc[i] *= t2 * c;
-            isc[j] *= t2 * c;
-            norms[i] = al - t * g;
-            norms[j] = be + t * g;
-            atomicAdd(&rot_count, 1);
-            if (__double_as_longlong(g * g) > __double_as_longlong(thr2 * (al * be))) big_rot = 1;
-          }
-        }
-        rcs[s] = cs;
-        rsn[s] = sn;
-        rfl[s] = rot;
-      }
-      __syncthreads();
-      for (int s = team; s < npl2; s += nteam) {
-        if (!rfl[s]) continue;  // team-uniform
-        int a, bq;
-        round_pair(r, s, lpl, a, bq);
-        const int i = live[a], j = live[bq];
-        const double ca = rcs[s], cb = rsn[s];
-        for (int c = tl; c < ncl; c += kTeam) {
-          const double x = Bs[i * L.nc + c], y = Bs[j * L.nc + c];
-          Bs[i * L.nc + c] = fma(-ca, y, x);
-          Bs[j * L.nc + c] = fma(cb, x, y);
-        }
-        for (int c = tl; want_p && c < npl; c += kTeam) {
-          const double x = Ps[i * L.np + c], y = Ps[j * L.np + c];
-          Ps[i * L.np + c] = fma(-ca, y, x);
-          Ps[j * L.np + c] = fma(cb, x, y);
+          const double t = rtan[s], g = rgam[s];
+          const double t2 = fma(t, t, 1.0);
+          const double c = rsqrt(t2);
+          const double tc = t2 * c;  // 1 / c
+          dsc[i] *= c;
+          dsc[j] *= c;
+          isc[i] *= tc;
+          isc[j] *= tc;
+          norms[i] = fma(-t, g, norms[i]);
+          norms[j] = fma(t, g, norms[j]);
+          ++myrot;
         }
       }
       __syncthreads();
       if ((r & 63) == 63) rescale();  // the scales stay above 2^-32 between foldings
     }
+    if (myrot) atomicAdd(&rot_count, myrot);
+    myrot = 0;
+    __syncthreads();
     ++sweeps;
     total_rot += rot_count;
     // A rotation leaves its pair's inner product at about 2e-7 of what it was
