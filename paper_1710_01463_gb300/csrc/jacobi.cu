@@ -44,9 +44,9 @@ constexpr int kTeamDot = 4;  // lanes per row pair in the inner-product phase: t
                              // additions per pair instead of three (an FP64 warp instruction holds
                              // the pipe for 16 cycles, so the reduction's additions cost as much
                              // as the products themselves with 8 lanes)
-constexpr int kScalarThreads = 128;  // warps 0-3 form the rotation scalars (0-1: half A, 2-3: half B)
+constexpr int kScalarThreads = 128;  // warps 0-3 form the rotation scalars, up to two per half of a round
 // threads at the barrier of a half: its scalar warps (arrive) and the worker warps (wait)
-constexpr int kHalfBarThreads = kScalarThreads / 2 + (kJacobiThreads - kScalarThreads);
+constexpr int kWorkerThreads = kJacobiThreads - kScalarThreads;
 constexpr size_t kSmemBudget = 220 * 1024;
 
 // Round r of the circle ordering over lp (even) rows: pair s is (m, r) for s = 0 and
@@ -132,15 +132,21 @@ __device__ __forceinline__ double tree_sum(const double* slot, int stride, int C
 // Named barriers between the scalar warps (arrive) and the worker warps (sync): the
 // workers wait until the scalars of a half are written; bar.arrive orders the arriving
 // threads' shared-memory writes before the waiters' reads
-template <int kId, int kThreads>
-__device__ __forceinline__ void named_sync() {
+// (ids 1 and 2 for halves A and B; id 0 is __syncthreads), over n threads: the half's
+// scalar warps and the worker warps
+__device__ __forceinline__ void half_sync(int h, int n) {
   __syncwarp();  // the barrier instructions are warp-aligned: reconverge first
-  asm volatile("bar.sync %0, %1;" ::"n"(kId), "n"(kThreads) : "memory");
+  if (h == 0)
+    asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+  else
+    asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
 }
-template <int kId, int kThreads>
-__device__ __forceinline__ void named_arrive() {
+__device__ __forceinline__ void half_arrive(int h, int n) {
   __syncwarp();
-  asm volatile("bar.arrive %0, %1;" ::"n"(kId), "n"(kThreads) : "memory");
+  if (h == 0)
+    asm volatile("bar.arrive 1, %0;" ::"r"(n) : "memory");
+  else
+    asm volatile("bar.arrive 2, %0;" ::"r"(n) : "memory");
 }
 
 // Point-to-point signals between the CTAs of a cluster: a value stored into
@@ -355,7 +361,12 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
     // while the scalar warps of half B finish, and rotate half B last.  So the scalars'
     // dependent FP64 chains run beside the products and rotations of the other half
     // instead of holding the whole CTA
-    const int hA = (npl2 + 1) / 2;
+    // Half A is a whole number of warps of pairs where it can be, and each half has at
+    // most two scalar warps (their lanes loop when a half holds more than 64 pairs): an
+    // FP64 warp instruction costs its 16 pipe cycles whatever the active lanes, so a
+    // warp with few pairs costs as much as a full one
+    const int hA = npl2 >= 64 ? npl2 / 64 * 32 : (npl2 + 1) / 2;
+    const int pw0 = min(2, (hA + 31) / 32), pw1 = min(2, (npl2 - hA + 31) / 32);
     for (int r = 0; r < lpl - 1; ++r, ++gr) {
       // after a timed-out exchange (rerr is uniform in the CTA after the round's last
       // __syncthreads) this CTA sends and waits no more; the sweep head then ends the
@@ -403,10 +414,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
         }
         // rotations of half A once its scalars are ready, then of half B
         for (int h = 0; h < 2; ++h) {
-          if (h == 0)
-            named_sync<1, kHalfBarThreads>();
-          else
-            named_sync<2, kHalfBarThreads>();
+          half_sync(h, 32 * (h ? pw1 : pw0) + kWorkerThreads);
           const int s0 = h ? hA : 0, s1 = h ? npl2 : hA;
           for (int s = s0 + team; s < s1; s += nteam) {
             if (!rfl[s]) continue;  // team-uniform
@@ -426,15 +434,15 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
             }
           }
         }
-      } else {
-        // scalar warps: the first half of them for half A, the second for half B; one
-        // lane per pair, every CTA summing the partials in rank order, so all CTAs of
-        // the cluster take bit-identical decisions
-        const int h = tid >= kScalarThreads / 2 ? 1 : 0;
+      } else if (warp < pw0 + pw1) {
+        // scalar warps: pw0 of them for half A, pw1 for half B; one lane per pair, every
+        // CTA summing the partials in rank order, so all CTAs of the cluster take
+        // bit-identical decisions
+        const int h = warp < pw0 ? 0 : 1;
         const int s0 = h ? hA : 0, s1 = h ? npl2 : hA;
-        const int sl = tid - h * (kScalarThreads / 2);
+        const int nl = 32 * (h ? pw1 : pw0), sl = tid - (h ? 32 * pw0 : 0);
         if (s0 + sl < s1 && !mb_wait_cluster(h ? mbB : mbA, (gr >> 1) & 1)) atomicExch(&rerr, 1);
-        for (int s = s0 + sl; s < s1; s += kScalarThreads / 2) {
+        for (int s = s0 + sl; s < s1; s += nl) {
           int a, bq;
           round_pair(r, s, lpl, a, bq);
           int rot = 0;
@@ -481,14 +489,11 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
           rsn[s] = sn;
           rfl[s] = rot;
         }
-        if (h == 0)
-          named_arrive<1, kHalfBarThreads>();
-        else
-          named_arrive<2, kHalfBarThreads>();
+        half_arrive(h, nl + kWorkerThreads);
         // the rotated rows' scales and norms for the next round (the rows of a round's
         // pairs are disjoint, and only this lane touches those of its pairs), while the
         // workers rotate
-        for (int s = s0 + sl; s < s1; s += kScalarThreads / 2) {
+        for (int s = s0 + sl; s < s1; s += nl) {
           if (!rfl[s]) continue;
           int a, bq;
           round_pair(r, s, lpl, a, bq);
