@@ -589,9 +589,11 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   const int C = csize;
   const int rank = (int)cluster.block_rank();
   const int rows = J.rows, l = J.l;
-  const int rs = (rows + C - 1) / C;
-  const int r0 = rank * rs;
-  const int nr = max(0, min(rows, r0 + rs) - r0);
+  // rows are dealt to the CTAs cyclically - CTA q holds rows q, q + C, q + 2C, ... - so
+  // that every CTA keeps its share of the rows below the diagonal as the factorization
+  // moves down (with contiguous blocks the first CTAs ran out of work in the trailing
+  // updates and the formation of Q while the last ones carried all of theirs)
+  const int nr = rank < rows ? (rows - rank + C - 1) / C : 0;
   const PanelLayout L = panel_layout(rows, l, C);
   extern __shared__ double sm[];
   double* Ys = sm + L.ys;      // own rows of Y, later of Q   (rs x l)
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   __shared__ double Gv[kNb][kNb];                  // V^T V of the panel (strictly upper part)
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = kHhThreads / 32;
 
-  for (int e = tid; e < nr * l; e += kHhThreads) Ys[e] = (double)J.Y[(size_t)r0 * l + e];
+  for (int e = tid; e < nr * l; e += kHhThreads) Ys[e] = (double)J.Y[(size_t)(rank + C * (e / l)) * l + e % l];
   // every CTA must apply the same column signs: columns left unfactored by an
   // early end keep alpha = 0 (sign +1) everywhere
   for (int c = tid; c < l; c += kHhThreads) alpha[c] = 0.0;
@@ -633,7 +635,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       double a = 0.0;
       for (int e = tid; e < nr * (lc - j0); e += kHhThreads) {
         const int rr = e / (lc - j0), c = j0 + e % (lc - j0);
-        if (r0 + rr >= j0) a = fma(Ys[rr * l + c], Ys[rr * l + c], a);
+        if (rank + C * rr >= j0) a = fma(Ys[rr * l + c], Ys[rr * l + c], a);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -685,7 +687,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       const int c = warp;
       const int rA = lane, rB = lane + 32;
       const bool inA = rA < nr, inB = rB < nr;
-      const int gA = r0 + rA, gB = r0 + rB;
+      const int gA = rank + C * rA, gB = rank + C * rB;
       double xA = (inA && c < nb) ? Ys[rA * l + j0 + c] : 0.0;
       double xB = (inB && c < nb) ? Ys[rB * l + j0 + c] : 0.0;
       for (int jj = 0; jj < nb; ++jj) {
@@ -695,8 +697,8 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
           vbuf[rA] = (inA && gA >= gd) ? xA : 0.0;
           vbuf[rB] = (inB && gB >= gd) ? xB : 0.0;
         }
-        if (gd >= r0 && gd < r0 + nr && c < nb) {  // this CTA holds the diagonal row
-          const int rd = gd - r0;
+        if (gd % C == rank && gd / C < nr && c < nb) {  // this CTA holds the diagonal row
+          const int rd = gd / C;
           const double xd = __shfl_sync(0xffffffffu, rd < 32 ? xA : xB, rd & 31);
           if (lane < C) *cluster.map_shared_rank(&xrowp[buf][c], lane) = xd;  // lane q pushes to CTA q
         }
@@ -792,11 +794,11 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
       if (c < nb) {
         if (inA) {
           Vo[rA * kNb + c] = xA;
-          Vg[(size_t)(r0 + rA) * l + j0 + c] = xA;
+          Vg[(size_t)gA * l + j0 + c] = xA;
         }
         if (inB) {
           Vo[rB * kNb + c] = xB;
-          Vg[(size_t)(r0 + rB) * l + j0 + c] = xB;
+          Vg[(size_t)gB * l + j0 + c] = xB;
         }
       }
       __syncthreads();
@@ -807,7 +809,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
     // trailing update of columns j0 + nb .. l-1: Y <- Y - V T^T (V^T Y); V is
     // zero on the rows above j0, which neither contribute nor change
     const int c1 = j0 + nb, wcols = lc - c1;
-    const int rr0 = max(0, min(nr, j0 - r0));  // first own row at or below j0
+    const int rr0 = max(0, min(nr, (j0 - rank + C - 1) / C));  // first own row at or below j0
     double* Wb = Wp;
     if (wcols > 0) {
       for (int e = tid; e < nb * wcols; e += kHhThreads) {
@@ -832,20 +834,20 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   cluster.sync();  // every remote read of Ys / Wp above is done
   for (int e = tid; e < nr * l; e += kHhThreads) {
     const int rr = e / l, c = e % l;
-    Ys[e] = (r0 + rr == c) ? 1.0 : 0.0;
+    Ys[e] = (rank + C * rr == c) ? 1.0 : 0.0;
   }
   __syncthreads();
   for (int p = npanel_used - 1; p >= 0; --p) {
     const int j0 = p * kNb, nb = min(kNb, lc - j0);
     const double* Tp = Tall + (size_t)p * kNb * kNb;
     const int wcols = qc - j0;
-    const int rr0 = max(0, min(nr, j0 - r0));  // rows above j0: V is zero there
+    const int rr0 = max(0, min(nr, (j0 - rank + C - 1) / C));  // rows above j0: V is zero there
     double* Wb = Wp;
     cluster.sync();  // the previous panel's remote reads of Wp are done
     if (tid < kNb * kNb) Ts[tid / kNb][tid % kNb] = Tp[tid];
     for (int e = tid; e < nr * kNb; e += kHhThreads) {  // this panel's V, own rows
       const int rr = e / kNb, c = e % kNb;
-      Vo[e] = c < nb ? Vg[(size_t)(r0 + rr) * l + j0 + c] : 0.0;
+      Vo[e] = c < nb ? Vg[(size_t)(rank + C * rr) * l + j0 + c] : 0.0;
     }
     __syncthreads();
     for (int e = tid; e < nb * wcols; e += kHhThreads) {
@@ -863,7 +865,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
   for (int e = tid; e < nr * l; e += kHhThreads) {
     const int c = e % l;
     const double sg = alpha[c] < 0.0 ? -1.0 : 1.0;
-    J.Y[(size_t)r0 * l + e] = c < qc ? (T)(sg * Ys[e]) : (T)0;
+    J.Y[(size_t)(rank + C * (e / l)) * l + c] = c < qc ? (T)(sg * Ys[e]) : (T)0;
   }
   if (rank == 0 && tid == 0) {
     if (!J.hh_first) atomicAdd(&J.info->chol_fallbacks, 1);
