@@ -231,7 +231,9 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
   std::vector<Prob*> wide;
   for (auto& p : probs)
     if (p.wide) wide.push_back(&p);
-  if (!wide.empty()) {
+  // the wide matrices' preparation: Q_b = orth(B^T), M = B Q_b, Q_b^T
+  auto wide_prep = [&]() -> int {
+    if (wide.empty()) return RSVD_OK;
     const int wc = (int)wide.size();
     {  // B^T (n x l)
       XposeBatch x;
@@ -278,14 +280,19 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       }
       RSVD_TRY((launch_transpose<double, T>(x, s)));
     }
-  }
-  // one launch per (cluster size, storage) group; the groups are independent
-  // and run concurrently, the first on s and the others on side streams
+      return RSVD_OK;
+  };
+  // one launch per (cluster size, storage, wide or not) group; the groups are
+  // independent and run concurrently (one after another on s with RSVD_FLAG_SERIAL: the
+  // same groups, so the same results bit for bit)
+  const bool serial = cnt > 0 && probs[0].serial;
   std::vector<int> done(cnt, 0);
   std::vector<JacobiBatch<T>> groups;
+  std::vector<int> gwide;
   for (int i0 = 0; i0 < cnt; ++i0) {
     if (done[i0]) continue;
     groups.emplace_back();
+    gwide.push_back(probs[i0].wide);
     JacobiBatch<T>& b = groups.back();
     b.count = 0;
     b.csize = probs[i0].csize;
@@ -293,7 +300,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
     const int csize0 = b.csize;
     for (int i = i0; i < cnt; ++i) {
       Prob& p = probs[i];
-      if (done[i] || p.csize != csize0 || p.use_global != b.use_global) continue;
+      if (done[i] || p.csize != csize0 || p.use_global != b.use_global || p.wide != probs[i0].wide) continue;
       done[i] = 1;
       JacobiJob<T>& J = b.job[b.count++];
       J.l = p.l; J.n = p.wide ? p.l : p.n; J.k = p.k;
@@ -330,9 +337,29 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
       if (cmin <= cmax) b.csize = spread_cluster(b.count, cmin, cmax, rep);
     }
   }
-  {
-    const int ng = (int)groups.size();
-    const int nside = (cnt > 0 && probs[0].serial) ? 0 : std::min(ng - 1, kSideStreams);
+  const int ng = (int)groups.size();
+  int nnarrow = 0;
+  for (int g = 0; g < ng; ++g) nnarrow += gwide[g] ? 0 : 1;
+  if (!wide.empty() && nnarrow > 0 && !serial) {
+    // the SVDs of the matrices that need no preparation start at once on side streams
+    // 1.., while the caller's stream prepares the wide matrices (whose orthonormalisation
+    // may use side stream 0) and then runs their SVDs
+    SideStreams* ss = side_streams();
+    if (!ss) return RSVD_ERR_LAUNCH;
+    RSVD_TRY(fork_side(ss, kSideStreams, s));
+    int k = 0;
+    for (int g = 0; g < ng; ++g)
+      if (!gwide[g]) RSVD_TRY(launch_jacobi<T>(groups[g], ss->stream[1 + (k++) % (kSideStreams - 1)]));
+    const int rc = wide_prep();
+    if (rc != RSVD_OK) return rc;
+    for (int g = 0; g < ng; ++g)
+      if (gwide[g]) RSVD_TRY(launch_jacobi<T>(groups[g], s));
+    RSVD_TRY(join_side(ss, kSideStreams, s));
+  } else {
+    const int rc = wide_prep();
+    if (rc != RSVD_OK) return rc;
+    // the first group on s and the others on side streams
+    const int nside = serial ? 0 : std::min(ng - 1, kSideStreams);
     SideStreams* ss = nullptr;
     if (nside > 0) {
       ss = side_streams();
