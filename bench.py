@@ -397,8 +397,12 @@ def run_ours(args):
             B_h, lam_h = ch.state_to_host()
             np.savez(state_file, B=B_h, lam=lam_h, step=nxt, workload=WORKLOAD)
     ch.set_dt(DT)
+    if args.autotune:  # the first warm-up step times the candidate tiles of every new shape class
+        lib.rsvd_autotune_enable(1)
     for s in range(args.warmup):
         ch.step(nxt + s)
+        if args.autotune:
+            lib.rsvd_autotune_enable(0)
     first = nxt + args.warmup
     torch.cuda.synchronize()
     prep_s = time.time() - t_prep
@@ -833,10 +837,17 @@ def workload_leg(wl, args, steps, warmup, extras=True, batch=None):
                                                           tol=1e-6)
             bw_info.append(binfo)
 
+    tuned = getattr(args, "autotune", False)
+    if tuned:  # the first warm-up step times the candidate tiles of every new shape class
+        lib.rsvd_autotune_enable(1)
     for _ in range(warmup):
         step()
+        if tuned:
+            lib.rsvd_autotune_enable(0)
     torch.cuda.synchronize()
     bw_info.clear()
+    if tuned:
+        config["gemm_tiles"] = f"measured autotuner ({lib.rsvd_autotune_entries()} shape classes cached in warm-up)"
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -1137,6 +1148,9 @@ def main():
                     help="tebd (default): the TEBD bond-update workload; the others time the remaining configurations")
     ap.add_argument("--state", default="ground", choices=["ground", "early"],
                     help="TEBD: time from the converged ground state (default) or the early state")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose the SIMT products' tiles with the library's measured autotuner in the first "
+                         "warm-up step (cached choices are used in the timed steps)")
     ap.add_argument("--state-file", default=None,
                     help="TEBD: .npz of the prepared state - loaded if it exists, else written after the "
                          "preparation (lets a profiler run skip the ground-state preparation)")
