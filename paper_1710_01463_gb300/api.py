@@ -195,7 +195,7 @@ class BatchedPlan:
     """Preallocated outputs and workspace of rsvd_truncate_batched for fixed shapes."""
 
     def __init__(self, shapes, ks, p=8, q=2, seed=0, stream=0, dtype=torch.float64, device="cuda",
-                 max_sweeps=0, chi_global=0, tf32=False, simt=False):
+                 max_sweeps=0, chi_global=0, tf32=False, simt=False, flags=0):
         lib = _lib.load()
         self.shapes = [(int(m), int(n)) for m, n in shapes]
         self.ks = [int(k) for k in ks]
@@ -203,7 +203,7 @@ class BatchedPlan:
         self.chi_global = int(chi_global)
         prec = _lib.RSVD_TF32 if tf32 else _DTYPE_PREC[dtype]
         out = torch.float64 if dtype == torch.float64 else torch.float32
-        self.par = _params(self.ks[0], p, q, prec, seed, stream, max_sweeps, simt)
+        self.par = _params(self.ks[0], p, q, prec, seed, stream, max_sweeps, simt, flags)
         B = len(self.shapes)
         self.m_arr = _lib.int_array([s[0] for s in self.shapes])
         self.n_arr = _lib.int_array([s[1] for s in self.shapes])
@@ -242,10 +242,10 @@ class BatchedPlan:
         return self.U, self.S, self.Vt
 
 
-def rsvd_truncate_batched(As, ks, p=8, q=2, seed=0, stream=0, chi_global=0, max_sweeps=0, tf32=False):
+def rsvd_truncate_batched(As, ks, p=8, q=2, seed=0, stream=0, chi_global=0, max_sweeps=0, tf32=False, flags=0):
     """Alg. RSVD on a list of matrices; returns (U list, S list, Vt list, k_out, info)."""
     plan = BatchedPlan([tuple(A.shape) for A in As], ks, p, q, seed, stream, As[0].dtype, As[0].device,
-                       max_sweeps, chi_global, tf32)
+                       max_sweeps, chi_global, tf32, flags=flags)
     U, S, Vt = plan.run(As)
     return U, S, Vt, plan.k_out, plan.info
 

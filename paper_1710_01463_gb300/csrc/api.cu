@@ -766,16 +766,42 @@ int run_batched(std::vector<Prob>& probs, const rsvd_params* p, char* work, size
     off += layout(&pr, pr.m, pr.n, pr.k, pr.l, ts, work + off, tcb, pr.r ? 0 : use_oz(pr.m, pr.n, pr.l, pr.exact, p), pr.r);
   }
   const size_t step = is_tc(p->prec) ? (size_t)kMaxTcJobs : (size_t)kMaxJobs;
-  for (size_t c0 = 0; c0 < probs.size(); c0 += step) {
-    std::vector<Prob> chunk(probs.begin() + c0, probs.begin() + std::min(probs.size(), c0 + step));
-    int rc;
-    if (p->prec == RSVD_F64) rc = run_chunk<double>(chunk, p->q, s);
-    else if (p->prec == RSVD_F32) rc = run_chunk<float>(chunk, p->q, s);
-    else if (p->prec == RSVD_BF16) rc = run_chunk_tc<__nv_bfloat16>(chunk, p->q, s);
-    else rc = run_chunk_tc<float>(chunk, p->q, s);
-    if (rc != RSVD_OK) return rc;
+  const int nchunks = (int)((probs.size() + step - 1) / step);
+  // the chunks of a large batch are independent (own workspace, own matrices): they run
+  // concurrently on the chunk streams, forked from s and joined back to it, each chunk's
+  // own groups on the side-stream set of its chunk stream; RSVD_FLAG_SERIAL keeps them
+  // on s one after another
+  const int nstreams = (nchunks > 1 && !(p->flags & RSVD_FLAG_SERIAL)) ? std::min(nchunks, kChunkStreams) : 0;
+  SideStreams* cs = nullptr;
+  if (nstreams > 0) {
+    cs = side_set(kChunkSet);
+    if (!cs) return RSVD_ERR_LAUNCH;
+    RSVD_TRY(fork_side(cs, nstreams, s));
   }
-  return RSVD_OK;
+  int rc = RSVD_OK;
+  for (int c = 0; c < nchunks && rc == RSVD_OK; ++c) {
+    const size_t c0 = (size_t)c * step;
+    std::vector<Prob> chunk(probs.begin() + c0, probs.begin() + std::min(probs.size(), c0 + step));
+    cudaStream_t cst = s;
+    if (cs) {
+      cst = cs->stream[c % nstreams];
+      select_side_set(c % nstreams);
+    }
+    if (p->prec == RSVD_F64) rc = run_chunk<double>(chunk, p->q, cst);
+    else if (p->prec == RSVD_F32) rc = run_chunk<float>(chunk, p->q, cst);
+    else if (p->prec == RSVD_BF16) rc = run_chunk_tc<__nv_bfloat16>(chunk, p->q, cst);
+    else rc = run_chunk_tc<float>(chunk, p->q, cst);
+  }
+  select_side_set(0);
+  // joined on every path, so that s never runs ahead of work already enqueued
+  if (cs) {
+    const cudaError_t e = join_side(cs, nstreams, s);
+    if (e != cudaSuccess && rc == RSVD_OK) {
+      last_cuda_error() = e;
+      rc = RSVD_ERR_LAUNCH;
+    }
+  }
+  return rc;
 }
 
 }  // namespace

@@ -453,7 +453,15 @@ struct SideStreams {
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kSideStreams] = {};
 };
-SideStreams* side_streams();                               // this thread's, for the current device; null on failure
+// Chunks of a large batch run concurrently on kChunkStreams chunk streams (set
+// kChunkSet); chunk stream c's work forks onto side-stream set c, so that the groups
+// of different chunks never share a side stream.  Set 0 also serves unchunked calls.
+constexpr int kChunkStreams = 4;
+constexpr int kChunkSet = kChunkStreams;
+constexpr int kSideSets = kChunkStreams + 1;
+SideStreams* side_set(int set);   // this thread's set `set` for the current device; null on failure
+SideStreams* side_streams();      // the set chosen by select_side_set (0 unless a chunk runs)
+void select_side_set(int set);    // per host thread
 void* current_context();  // the calling thread's current CUDA context (driver handle), null if none
 cudaError_t fork_side(SideStreams* ss, int n, cudaStream_t s);  // side streams 0..n-1 wait for s's work so far
 cudaError_t join_side(SideStreams* ss, int n, cudaStream_t s);  // s waits for side streams 0..n-1

@@ -23,14 +23,19 @@ void* current_context() {
   return fn(&ctx) == 0 ? ctx : nullptr;
 }
 
-SideStreams* side_streams() {
+namespace {
+thread_local int t_side_set = 0;  // the set that side_streams() returns (per host thread)
+}
+
+SideStreams* side_set(int set) {
   constexpr int kMaxDevices = 64;
-  thread_local SideStreams ss[kMaxDevices];  // per host thread: concurrent callers never share events
+  thread_local SideStreams ss[kMaxDevices][kSideSets];  // per host thread: concurrent callers never share events
   int dev = 0;
+  if (set < 0 || set >= kSideSets) return nullptr;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-  SideStreams& x = ss[dev];
-  // created once per host thread and device, and again when the device's context was
-  // replaced (cudaDeviceReset): handles of a destroyed context are not reused
+  SideStreams& x = ss[dev][set];
+  // created once per host thread, device and set, and again when the device's context
+  // was replaced (cudaDeviceReset): handles of a destroyed context are not reused
   if (!x.ready || x.ctx != current_context()) {
     SideStreams y;
     if (cudaEventCreateWithFlags(&y.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
@@ -44,6 +49,10 @@ SideStreams* side_streams() {
   }
   return &x;
 }
+
+SideStreams* side_streams() { return side_set(t_side_set); }
+
+void select_side_set(int set) { t_side_set = set; }
 
 cudaError_t fork_side(SideStreams* ss, int n, cudaStream_t s) {
   cudaError_t e = cudaEventRecord(ss->fork, s);

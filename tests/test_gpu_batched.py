@@ -173,3 +173,29 @@ def test_adaptive_device_rounds_replay_bit_identically(api):
     for a, b, r in zip(plan.U, ref[1], ref[3].tolist()):
         assert torch.equal(a[:, :r], b[:, :r])
     assert all(d["status"] == 0 for d in api.info_dicts(plan.info))
+
+
+def test_large_batch_chunks_concurrent(api):
+    # a batch above 64 matrices runs in chunks of 64, concurrently on the chunk streams:
+    # bit-identical to the serial run (RSVD_FLAG_SERIAL, every chunk and group on the
+    # caller's stream), and sampled members at the FP64 bar against the oracle
+    from paper_1710_01463_gb300 import _lib
+    rng = np.random.default_rng(71)
+    shapes = [(int(m), int(n)) for m, n in zip(rng.integers(40, 97, 150), rng.integers(40, 97, 150))]
+    blocks = [inputs.spectral_matrix(m, n, inputs.exp_spectrum(min(m, n), 6.0), 500 + b)
+              for b, (m, n) in enumerate(shapes)]
+    ks = [min(10, m, n) for m, n in shapes]
+    As = [torch.from_numpy(b).cuda() for b in blocks]
+    _, S, Vt, _, info = api.rsvd_truncate_batched(As, ks, p=6, q=2, seed=13, stream=2)
+    S = [s.clone() for s in S]
+    Vt = [v.clone() for v in Vt]
+    _, S2, Vt2, _, info2 = api.rsvd_truncate_batched(As, ks, p=6, q=2, seed=13, stream=2,
+                                                     flags=_lib.RSVD_FLAG_SERIAL)
+    torch.cuda.synchronize()
+    for b in range(len(blocks)):
+        assert torch.equal(S[b], S2[b]) and torch.equal(Vt[b], Vt2[b])
+    assert all(d["status"] == 0 for d in api.info_dicts(info))
+    assert all(d["status"] == 0 for d in api.info_dicts(info2))
+    for b in (0, 63, 64, 100, 127, 128, 149):
+        _, So, _ = orsvd.rsvd(blocks[b], ks[b], 6, 2, 13, 2 + b)
+        assert np.all(np.abs(S[b].cpu().numpy() - So) <= sigma_tol(So)), b
