@@ -8,13 +8,19 @@
 // the l columns of the rotation accumulator P) are split across the CTAs of
 // the cluster and stay in each CTA's shared memory for the whole
 // factorization.  Rows are paired by the round-robin (circle) ordering, l/2
-// disjoint pairs per round, one team of 8 lanes per pair.  Per round every CTA
-// forms the partial inner products <b_i, b_j> of its column slice, the cluster
-// exchanges them through distributed shared memory (one cluster barrier per
-// round, double-buffered), one lane per pair sums them in rank order and forms
-// the rotation - so all CTAs take bit-identical decisions, and the FP64
-// scalar work (square roots, divisions) occupies as few warps as possible -
-// and the teams rotate their own slice.
+// disjoint pairs per round.  Per round every CTA forms the partial inner
+// products <b_i, b_j> of its column slice (teams of 4 lanes per pair), pushes
+// them to every CTA of the cluster through distributed shared memory, one lane
+// per pair sums them in rank order and forms the rotation - so all CTAs take
+// bit-identical decisions, and the FP64 scalar work (square roots, divisions)
+// occupies as few warps as possible - and teams of 8 lanes rotate their own
+// slice.
+//
+// On this part a warp issues at most one FP64 instruction per 64 cycles, with
+// any number of active lanes and whatever its independent work, and an SM
+// about one per 16-19 cycles over all its warps (measured): the kernel's time
+// follows its count of FP64 warp instructions, so sums over the cluster take
+// exactly C - 1 additions.
 //
 // Row norms are recomputed exactly at the start of every sweep and updated by
 // the rotation identities (alpha - t gamma, beta + t gamma) inside it.  A pair
@@ -105,27 +111,29 @@ __device__ __forceinline__ double cluster_tree_sum(cg::cluster_group& cluster, c
   return pv[0];
 }
 
-// Sum of the C partials slot[q * stride], q < C, by a fixed pairwise tree over 4, 8 or 16
-// slots (the slots past C read as zero, which leaves every partial sum unchanged), so every
-// CTA gets the same bits with log2 depth and no more FP64 additions than the padded width
+// Sum of the C partials slot[q * stride], q < C, by a fixed pairwise tree over exactly C
+// terms (C - 1 FP64 additions: each costs a whole warp instruction, about 64 cycles of its
+// warp's issue, whatever its active lanes), so every CTA gets the same bits with log2 depth
 __device__ __forceinline__ double tree_sum(const double* slot, int stride, int C) {
   double v[kMaxCluster];
-  if (C <= 4) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = q < C ? slot[q * stride] : 0.0;
-    return (v[0] + v[1]) + (v[2] + v[3]);
+  for (int q = 0; q < kMaxCluster; ++q) v[q] = q < C ? slot[q * stride] : 0.0;
+  switch (C) {  // cluster-uniform
+    case 1: return v[0];
+    case 2: return v[0] + v[1];
+    case 3: return (v[0] + v[1]) + v[2];
+    case 4: return (v[0] + v[1]) + (v[2] + v[3]);
+    case 5: return ((v[0] + v[1]) + (v[2] + v[3])) + v[4];
+    case 6: return ((v[0] + v[1]) + (v[2] + v[3])) + (v[4] + v[5]);
+    case 7: return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + v[6]);
+    case 8: return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    default: break;
   }
-  if (C <= 8) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = q < C ? slot[q * stride] : 0.0;
-    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-  }
+  for (int w = 1; w < kMaxCluster; w <<= 1)
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = q < C ? slot[q * stride] : 0.0;
-#pragma unroll
-  for (int w = 1; w < 16; w <<= 1)
-#pragma unroll
-    for (int q = 0; q + w < 16; q += 2 * w) v[q] += v[q + w];
+    for (int q = 0; q + w < kMaxCluster; q += 2 * w)
+      if (q + w < C) v[q] += v[q + w];
   return v[0];
 }
 

@@ -525,6 +525,24 @@ __device__ __forceinline__ double dot_panel(const double* v, const double* w, in
 // sums and transforms its own slice of the columns only (no FP64 work is
 // repeated across the cluster) and then gathers the other slices.  Called by
 // every CTA of the cluster (it contains a cluster barrier).
+// Sum of the C partials v[q * stride], q < C, by a fixed pairwise tree of exactly C - 1
+// FP64 additions (every CTA of the cluster gets the same bits)
+__device__ __forceinline__ double panel_tree_sum(const double* v, int stride, int C) {
+  double p[kPanelMaxCluster];
+#pragma unroll
+  for (int q = 0; q < kPanelMaxCluster; ++q) p[q] = q < C ? v[q * stride] : 0.0;
+  switch (C) {  // cluster-uniform
+    case 1: return p[0];
+    case 2: return p[0] + p[1];
+    case 3: return (p[0] + p[1]) + p[2];
+    case 4: return (p[0] + p[1]) + (p[2] + p[3]);
+    case 5: return ((p[0] + p[1]) + (p[2] + p[3])) + p[4];
+    case 6: return ((p[0] + p[1]) + (p[2] + p[3])) + (p[4] + p[5]);
+    case 7: return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + p[6]);
+    default: return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+  }
+}
+
 template <bool kTW>
 __device__ void cluster_sum_apply_t(cg::cluster_group& cluster, int rank, int C, const double* Wb, double* Ws,
                                     const double (*Ts)[kNb], int nb, int l, int c0, int wcols) {
@@ -536,11 +554,7 @@ __device__ void cluster_sum_apply_t(cg::cluster_group& cluster, int rank, int C,
     double pv[kPanelMaxCluster];  // every remote load in flight at once, summed by a fixed tree
 #pragma unroll
     for (int r = 0; r < kPanelMaxCluster; ++r) pv[r] = r < C ? cluster.map_shared_rank(Wb, r)[jj * l + c] : 0.0;
-#pragma unroll
-    for (int w2 = 1; w2 < kPanelMaxCluster; w2 <<= 1)
-#pragma unroll
-      for (int r = 0; r + w2 < kPanelMaxCluster; r += 2 * w2) pv[r] += pv[r + w2];
-    Ws[jj * l + c] = pv[0];
+    Ws[jj * l + c] = panel_tree_sum(pv, 1, C);
   }
   __syncthreads();
   double mreg[(kNb * 256 + kHhThreads - 1) / kHhThreads];
@@ -704,25 +718,21 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
         }
         __syncthreads();
         const double wA = vbuf[rA], wB = vbuf[rB];
-        // each warp leaves its lanes' products, and warp 0 sums all columns (lanes 2i and
-        // 2i + 1 half of column i each) and pushes them, lane-parallel - 17 FP64
-        // instructions in one warp instead of a 5-level shuffle tree in each of 16
+        // each warp leaves its lanes' products, and warps 0-3 sum them, four columns per
+        // warp, eight lanes per column (four products each, then three shuffle levels):
+        // six FP64 instructions per warp.  A warp issues at most one FP64 instruction per
+        // 64 cycles whatever its active lanes and independent work, so the sums are
+        // spread over four warps rather than done in one (about 20 instructions)
         double (*prod)[kProdStride] = (double (*)[kProdStride])Wp;  // the V^T Y buffer is idle here
         prod[c][lane] = c < nb ? fma(xA, wA, xB * wB) : 0.0;
         __syncthreads();
-        if (warp == 0) {
-          const int cc = lane >> 1, h = (lane & 1) * 16;
-          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-#pragma unroll
-          for (int t = 0; t < 16; t += 4) {
-            s0 += prod[cc][h + t];
-            s1 += prod[cc][h + t + 1];
-            s2 += prod[cc][h + t + 2];
-            s3 += prod[cc][h + t + 3];
-          }
-          double sp = (s0 + s1) + (s2 + s3);
+        if (warp < kNb / 4) {
+          const int cc = 4 * warp + (lane >> 3), h = (lane & 7) * 4;
+          double sp = (prod[cc][h] + prod[cc][h + 1]) + (prod[cc][h + 2] + prod[cc][h + 3]);
+          sp += __shfl_xor_sync(0xffffffffu, sp, 4);
+          sp += __shfl_xor_sync(0xffffffffu, sp, 2);
           sp += __shfl_xor_sync(0xffffffffu, sp, 1);
-          for (int q = lane & 1; q < C; q += 2) *cluster.map_shared_rank(&spart[buf][rank][cc], q) = sp;
+          for (int q = lane & 7; q < C; q += 8) *cluster.map_shared_rank(&spart[buf][rank][cc], q) = sp;
         }
         cluster.sync();
         // one warp, lane c: the sum of column c's partials (a fixed tree over the
@@ -731,15 +741,7 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
         // tests on the bit patterns (an FP64 compare-and-branch costs hundreds of
         // cycles on this part), and ||x|| = a rsqrt(a)
         if (warp == 0 && lane < kNb) {
-          double pv[kPanelMaxCluster];
-#pragma unroll
-          for (int q = 0; q < kPanelMaxCluster; ++q) pv[q] = q < C ? spart[buf][q][lane] : 0.0;
-#pragma unroll
-          for (int w2 = 1; w2 < kPanelMaxCluster; w2 <<= 1)
-#pragma unroll
-            for (int q = 0; q + w2 < kPanelMaxCluster; q += 2 * w2)
-              if (q + w2 < C) pv[q] += pv[q + w2];
-          const double dc = pv[0];
+          const double dc = panel_tree_sum(&spart[buf][0][lane], kNb, C);
           const double a = __shfl_sync(0x0000ffffu, dc, jj);  // ||x_jj||^2 below the diagonal
           const double x0 = xrowp[buf][jj];
           double al = 0.0, inv = 0.0;
