@@ -71,9 +71,10 @@ extern "C" {
  * RSVD_ERR_INVALID_SIZE. */
 #define RSVD_FLAG_FULL_SVD      2
 /* Measurement aid: the independent groups of work of a call (Householder-first and
- * CholeskyQR2 orthonormalisations, Jacobi SVDs of different cluster sizes) run one after
- * another on the caller's stream instead of concurrently on side streams, so that the
- * kernels' durations add up to the call's time.  Same results bit for bit. */
+ * CholeskyQR2 orthonormalisations, Jacobi SVDs of different cluster sizes, the chunks of
+ * a large batch) run one after another on the caller's stream instead of concurrently on
+ * side streams, so that the kernels' durations add up to the call's time.  Same results
+ * bit for bit. */
 #define RSVD_FLAG_SERIAL        4
 /* Test of a failure path, not for production use: the CTAs of the Jacobi SVD's
  * thread-block clusters send none of their round partials, so every exchange wait
@@ -192,6 +193,13 @@ int rsvd_batched_workspace_size(int batch, const int* m, const int* n, const int
  * values are kept; the leading k_out[b] triplets of each matrix are the kept
  * ones.  chi_global == 0: k_out may be NULL; nothing is selected.
  * info: DEVICE array of `batch` records.
+ * Batches above 64 matrices (16 for RSVD_BF16 / RSVD_TF32) are processed in
+ * chunks that run concurrently on four chunk streams of the library, forked
+ * from cuda_stream and joined back to it (so the call stays ordered on
+ * cuda_stream and can be captured); RSVD_FLAG_SERIAL keeps the chunks in order
+ * on cuda_stream, with bit-identical results.  The first chunked call from a
+ * host thread on a device creates that thread's chunk streams and their
+ * side streams (cudaStreamCreate, cudaEventCreate; no device memory).
  * Errors as rsvd_truncate.
  */
 int rsvd_truncate_batched(int batch, const int* m, const int* n, const void* const* A, const int* lda,
