@@ -183,6 +183,100 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
   }
 }
 
+// FP32 products with a 128 x 128 output tile per CTA and an 8 x 8 register tile per thread
+// (rows ty * 4 + {0..3} and 64 + ty * 4 + {0..3}, columns likewise with tx), so that a
+// thread reads its eight values of A and of X for one k as two 128-bit shared loads each:
+// four shared loads per 64 FFMA (the stride-16 tiles above issue one scalar load per two
+// FFMA and are bound by the shared-memory pipe for FP32).  K slices of 16 through shared
+// memory, double-buffered via registers.
+constexpr int kVM = 128, kVN = 128, kVK = 16, kVPad = 4;
+
+template <bool TA, bool TX>
+__global__ void __launch_bounds__(NT, 2) gemm_v_kernel(const __grid_constant__ GemmBatch<float, float> b) {
+  const GemmJob<float, float>& J = b.job[blockIdx.z];
+  const int m0 = blockIdx.y * kVM, n0 = blockIdx.x * kVN;
+  if (m0 >= J.M || n0 >= J.N) return;
+  if (J.gate && *J.gate != J.gate_val) return;
+  if (J.active && !*J.active) return;
+  if ((J.m_eff && m0 >= *J.m_eff) || (J.n_eff && n0 >= *J.n_eff)) {  // a tile of exact zeros
+    if (!J.accumulate)
+      for (int e = threadIdx.x; e < kVM * kVN; e += NT) {
+        const int gi = m0 + e / kVN, gj = n0 + e % kVN;
+        if (gi < J.M && gj < J.N) J.C[(long long)gi * J.ldc + gj] = 0.0f;
+      }
+    return;
+  }
+  __shared__ __align__(16) float As[2][kVK][kVM + kVPad];
+  __shared__ __align__(16) float Xs[2][kVK][kVN + kVPad];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  float ra[kVM * kVK / NT], rx[kVN * kVK / NT];
+  const int K = J.k_eff ? min(J.K, *J.k_eff) : J.K;
+  load_a<float, TA, kVM, kVK>(J.A, J.lda, J.M, K, m0, 0, ra);
+  load_x<float, TX, kVN, kVK>(J.X, J.ldx, J.N, K, n0, 0, rx);
+  // the element orders of load_a / load_x (idx = t + q * NT)
+  auto put = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < kVM * kVK / NT; ++q) {
+      const int idx = threadIdx.x + q * NT;
+      const int i = TA ? idx % kVM : idx / kVK, kk = TA ? idx / kVM : idx % kVK;
+      As[buf][kk][i] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kVN * kVK / NT; ++q) {
+      const int idx = threadIdx.x + q * NT;
+      const int j = TX ? idx / kVK : idx % kVN, kk = TX ? idx % kVK : idx / kVN;
+      Xs[buf][kk][j] = rx[q];
+    }
+  };
+  put(0);
+  __syncthreads();
+  const int nk = (K + kVK - 1) / kVK;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) {
+      load_a<float, TA, kVM, kVK>(J.A, J.lda, J.M, K, m0, (kt + 1) * kVK, ra);
+      load_x<float, TX, kVN, kVK>(J.X, J.ldx, J.N, K, n0, (kt + 1) * kVK, rx);
+    }
+#pragma unroll
+    for (int kk = 0; kk < kVK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[cur][kk][tx * 4]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[cur][kk][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+    }
+    if (kt + 1 < nk) put(cur ^ 1);
+    __syncthreads();
+  }
+  double scale = 1.0;
+  if (J.div) scale = 1.0 / *J.div;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gi = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (gi >= J.M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gj = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (gj < J.N) {
+        float v = J.div ? (float)((double)acc[i][j] * scale) : acc[i][j];
+        if (J.alpha != 1.0) v = (float)(J.alpha * (double)v);
+        float* c = J.C + (long long)gi * J.ldc + gj;
+        *c = J.accumulate ? *c + v : v;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 template <typename Tin, typename Tout, bool TA, bool TX, int BM, int BN>
@@ -206,6 +300,19 @@ int sm_count() {
       n = 1;
   }
   return n;
+}
+
+template <bool TA, bool TX>
+cudaError_t launch_v_tile(const GemmBatch<float, float>& b, cudaStream_t s) {
+  int tm = 1, tn = 1;
+  for (int i = 0; i < b.count; ++i) {
+    tm = max(tm, ceil_div(b.job[i].M, kVM));
+    tn = max(tn, ceil_div(b.job[i].N, kVN));
+  }
+  prof_begin(KC_GEMM, s);
+  gemm_v_kernel<TA, TX><<<dim3(tn, tm, b.count), NT, 0, s>>>(b);
+  prof_end(KC_GEMM, s);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -243,7 +350,10 @@ cudaError_t launch_choice(const GemmBatch<Tin, Tout>& b, int c, cudaStream_t s) 
   switch (c) {
     case 1: return launch_tile<Tin, Tout, TA, TX, 64, 48>(b, s);
     case 2: return launch_tile<Tin, Tout, TA, TX, 48, 64>(b, s);
-    case 3: if constexpr (sizeof(Tin) == 8) return launch_tile<Tin, Tout, TA, TX, 48, 32>(b, s); break;
+    case 3:
+      if constexpr (sizeof(Tin) == 8) return launch_tile<Tin, Tout, TA, TX, 48, 32>(b, s);
+      if constexpr (sizeof(Tin) == 4 && sizeof(Tout) == 4) return launch_v_tile<TA, TX>(b, s);
+      break;
     case 4: if constexpr (sizeof(Tin) == 8) return launch_tile<Tin, Tout, TA, TX, 32, 48>(b, s); break;
     case 5: if constexpr (sizeof(Tin) == 8) return launch_tile<Tin, Tout, TA, TX, 32, 32>(b, s); break;
     default: break;
@@ -262,10 +372,13 @@ template <typename Tin, typename Tout, bool TA, bool TX>
 cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
   if (b.count <= 0) return cudaSuccess;
   constexpr bool f64 = sizeof(Tin) == 8;
-  constexpr int ns = f64 ? 6 : 3;
-  const int bm[6] = {64, 64, 48, 48, 32, 32}, bn[6] = {64, 48, 64, 32, 48, 32};
+  constexpr bool v32 = sizeof(Tin) == 4 && sizeof(Tout) == 4;  // the 128 x 128 FP32 tile is choice 3
+  constexpr int ns = f64 ? 6 : (v32 ? 4 : 3);
+  const int bm[6] = {64, 64, 48, f64 ? 48 : 128, 32, 32}, bn[6] = {64, 48, 64, f64 ? 32 : 128, 48, 32};
   long long cost[6];
   const long long sms = sm_count();
+  int kmax = 0;
+  for (int i = 0; i < b.count; ++i) kmax = max(kmax, b.job[i].K);
   for (int t = 0; t < ns; ++t) {
     long long tiles = 0, padded = 0;
     for (int i = 0; i < b.count; ++i) {
@@ -274,6 +387,12 @@ cudaError_t launch_gemm(const GemmBatch<Tin, Tout>& b, cudaStream_t s) {
       padded += tm * bm[t] * tn * bn[t];
     }
     cost[t] = f64 ? (tiles + sms - 1) / sms * bm[t] * bn[t] : padded;
+    if (!f64 && t == 3) {
+      // about 2.5x the FFMA rate of the stride-16 tiles per output, once the GPU holds two
+      // such CTAs per SM and the K loop is long enough to amortise the tile's set-up
+      const double fill = std::max(1.0, (double)(2 * sms) / (double)std::max(tiles, 1LL));
+      cost[t] = kmax >= 256 ? (long long)(0.4 * fill * (double)padded) : (1LL << 62);
+    }
   }
   int best = 0;
   for (int t = 1; t < ns; ++t)
@@ -392,7 +511,7 @@ extern "C" int rsvd_autotune_load(const char* path) {
     int c = 0;
     if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &k.tin, &k.tout, &k.ta, &k.tx, &k.count, &k.M, &k.N, &k.K,
                     &c) == 9 &&
-        c >= 0 && c < 6 && (c < 3 || k.tin == 8)) {
+        c >= 0 && c < 6 && (c < 3 || k.tin == 8 || (c == 3 && k.tout == 4))) {
       T.best[k] = c;
       ++n;
     }
