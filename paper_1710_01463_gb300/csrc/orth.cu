@@ -761,15 +761,19 @@ __global__ void __launch_bounds__(kHhThreads, 2) householder_panel_kernel(const 
           }
         }
         __syncthreads();  // fin and the scalars complete
-        // the unit reflector v on the own rows (zero above the diagonal)
-        const double vA = !inA ? 0.0 : gA == gd ? sc[1] : gA > gd ? wA * sc[0] : 0.0;
-        const double vB = !inB ? 0.0 : gB == gd ? sc[1] : gB > gd ? wB * sc[0] : 0.0;
-        if (c > jj && c < nb) {
-          xA = fma(fin[c], vA, xA);
-          xB = fma(fin[c], vB, xB);
-        } else if (c == jj) {
-          xA = vA;
-          xB = vB;
+        // the unit reflector v on the own rows (zero above the diagonal), formed only in the
+        // warps of columns jj .. nb-1 (warp-uniform: the columns before jj hold earlier
+        // reflectors, and every FP64 warp instruction costs the SM's FP64 issue)
+        if (c >= jj && c < nb) {
+          const double vA = !inA ? 0.0 : gA == gd ? sc[1] : gA > gd ? wA * sc[0] : 0.0;
+          const double vB = !inB ? 0.0 : gB == gd ? sc[1] : gB > gd ? wB * sc[0] : 0.0;
+          if (c > jj) {
+            xA = fma(fin[c], vA, xA);
+            xB = fma(fin[c], vB, xB);
+          } else {
+            xA = vA;
+            xB = vB;
+          }
         }
       }
       // T of the panel (H_0 ... H_nb-1 = I - V T V^T, unit reflectors, tau = 2) by the
