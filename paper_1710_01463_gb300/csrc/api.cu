@@ -334,7 +334,7 @@ int svd_of_B(std::vector<Prob>& probs, cudaStream_t s, bool tc_err) {
         const double np = (l + 1) / 2;
         rep = std::max(rep, (std::ceil(np / 32.0) * 40.0 + np / 4.0) / (np * n * 1.5 / 32.0));
       }
-      if (cmin <= cmax) b.csize = spread_cluster(b.count, cmin, cmax, rep, jacobi_kernel_func<T>(), jacobi_threads());
+      if (cmin <= cmax) b.csize = spread_cluster(b.count, cmin, cmax, rep);
     }
   }
   const int ng = (int)groups.size();

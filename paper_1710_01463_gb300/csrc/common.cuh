@@ -377,9 +377,6 @@ cudaError_t launch_orth(const OrthBatch<T>& b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_jacobi(const JacobiBatch<T>& b, cudaStream_t s);
 template <typename T>
-const void* jacobi_kernel_func();  // the Jacobi kernel, for occupancy queries
-int jacobi_threads();
-template <typename T>
 cudaError_t launch_sign(const SignBatch<T>& b, cudaStream_t s);
 cudaError_t launch_select(const SelectBatch& b, cudaStream_t s);
 cudaError_t launch_tebd_theta(const TebdBatch& b, cudaStream_t s);
@@ -471,35 +468,21 @@ cudaError_t join_side(SideStreams* ss, int n, cudaStream_t s);  // s waits for s
 
 // number of SMs of the current device
 int sm_count();
-// Clusters of c CTAs of `threads` threads of kernel `func` that the GPU holds at once with
-// ONE CTA per SM: the occupancy API under a shared-memory request that admits one CTA per SM.
-// GPC packing makes this smaller than SMs / c (on GB300: 23 clusters of 6 CTAs, 28 of 5).
-// Cached per (kernel, c); 0 when the query fails.
-int coresident_clusters(const void* func, int threads, int c);
-
 // Cluster size for a launch of `count` independent matrices, each split over c CTAs
-// (cmin <= c <= cmax).  With `func` given, the clusters beyond those the GPU holds at one CTA
-// per SM share SMs with others (two CTAs per SM where the resources allow), and a cluster
-// that shares runs at about half speed while the whole launch waits for it: a launch costs
-// ceil(count / fit(c)) x (rep + 1/c), fit(c) = coresident_clusters(func, threads, c)
-// (measured with 25 Jacobi SVDs of 138 x 256 with the rotations accumulated: clusters of 6
-// CTAs ran their rounds in 21.2k cycles, clusters of 5 in 14.9k; on the TEBD layers the
-// central group then leaves SMs to the edge groups beside it, 36.6 -> 35.6 ms per Trotter
-// step).  Without `func`, the CTAs are assumed to spread one per SM:
-// ceil(count c / SMs) x (rep + 1/c).  The smallest c that minimises the load is taken (fewer
-// CTAs per cluster: cheaper barriers and fewer partials to exchange).  The choice depends on
-// the batch, so a matrix's rounding (the order of its cluster sums) can differ between
-// batches of different sizes.  `rep` is the work every CTA of a cluster repeats (in units
-// of one whole matrix's divisible work): a CTA then carries rep + 1/c.
-inline int spread_cluster(int count, int cmin, int cmax, double rep = 0.0, const void* func = nullptr,
-                          int threads = 0) {
+// (cmin <= c <= cmax): the busiest SM of a launch with count * c CTAs placed one per SM
+// before any SM takes a second carries ceil(count c / SMs) CTAs of 1/c of a matrix each;
+// the smallest c that minimises that load is taken (fewer CTAs per cluster: cheaper
+// barriers and fewer partials to exchange; measured faster than two CTAs per SM on the
+// TEBD layers).  The choice depends on the batch, so a matrix's rounding (the order of its
+// cluster sums) can differ between batches of different sizes.  `rep` is the work every
+// CTA of a cluster repeats (in units of one whole matrix's divisible work): a CTA then
+// carries rep + 1/c.
+inline int spread_cluster(int count, int cmin, int cmax, double rep = 0.0) {
   const long long sms = sm_count();
   int best = cmax;
   double bl = 1e300;
   for (int c = cmin; c <= cmax; ++c) {
-    const int fit = func ? coresident_clusters(func, threads, c) : 0;
-    const long long waves = fit > 0 ? (count + fit - 1) / fit : (count * (long long)c + sms - 1) / sms;
-    const double load = (double)waves * (rep + 1.0 / c);
+    const double load = (double)((count * (long long)c + sms - 1) / sms) * (rep + 1.0 / c);
     if (load < bl * (1.0 - 1e-12)) {
       bl = load;
       best = c;

@@ -315,46 +315,6 @@ cudaError_t launch_v_tile(const GemmBatch<float, float>& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int coresident_clusters(const void* func, int threads, int c) {
-  static std::mutex mu;
-  static std::map<std::pair<const void*, int>, int> cache;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find({func, c});
-    if (it != cache.end()) return it->second;
-  }
-  int dev = 0, per_sm = 0, fit = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess &&
-      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess && per_sm > 0) {
-    // a request of more than half an SM's shared memory admits one CTA per SM
-    const int smem = per_sm / 2 + 1024;
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, func) == cudaSuccess && smem + (int)fa.sharedSizeBytes <= per_sm &&
-        cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
-        (c <= 8 || cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(c, 64, 1);
-      cfg.blockDim = dim3(threads, 1, 1);
-      cfg.dynamicSmemBytes = smem;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = c;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      if (cudaOccupancyMaxActiveClusters(&fit, func, &cfg) != cudaSuccess) fit = 0;
-    }
-  }
-  if (fit <= 0) {
-    fit = 0;
-    cudaGetLastError();  // a failed query leaves no error behind for the next launch check
-  }
-  std::lock_guard<std::mutex> lock(mu);
-  cache[{func, c}] = fit;
-  return fit;
-}
-
 // ---------------------------------------------------------------- autotuner
 // Host cache of measured tile choices, keyed by the launch's shape class: operand and
 // output types, transposes, batch size and the largest M, N, K of the batch (rounded up

@@ -601,14 +601,6 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
 
 }  // namespace
 
-template <typename T>
-const void* jacobi_kernel_func() {
-  return (const void*)jacobi_kernel<T>;
-}
-template const void* jacobi_kernel_func<double>();
-template const void* jacobi_kernel_func<float>();
-int jacobi_threads() { return kJacobiThreads; }
-
 // One CTA per 32 columns, up to eight (sixteen when a slice of eight does not
 // fit in shared memory).  Depends on the matrix alone, so no matrix's rounding
 // depends on the rest of its batch.

@@ -988,8 +988,7 @@ cudaError_t launch_householder(const OrthBatch<T>& b, cudaStream_t s) {
         ++c;
       cmin = max(cmin, c);
     }
-    const int pcs = spread_cluster(pb.count, min(cmin, kPanelMaxCluster), kPanelMaxCluster, 0.0,
-                                   (const void*)householder_panel_kernel<T>, kHhThreads);
+    const int pcs = spread_cluster(pb.count, min(cmin, kPanelMaxCluster), kPanelMaxCluster);
     size_t psmem = 0;
     for (int i = 0; i < pb.count; ++i)
       psmem = max(psmem, panel_layout(pb.job[i].rows, pb.job[i].l, pcs).total * sizeof(double));
