@@ -65,3 +65,28 @@ def test_mixed_precision_rejects_unaligned_rows(api):
     A = torch.zeros((300, 301), dtype=torch.bfloat16, device="cuda")  # 602-byte rows: not a TMA stride
     with pytest.raises(Exception):
         api.rsvd_truncate(A, 8, 8, 1, 0, 0)
+
+
+def test_mixed_precision_large_batch_chunks_concurrent(api):
+    # BF16 batches are processed in chunks of 16 matrices; above that the chunks run
+    # concurrently on the library's chunk streams: bit-identical to RSVD_FLAG_SERIAL (every
+    # chunk on the caller's stream), and sampled members within the BF16 bound of the oracle
+    shapes = [(320 + 16 * (b % 5), 256 + 8 * (b % 7)) for b in range(37)]
+    A64 = [inputs.spectral_matrix(m, n, inputs.power_spectrum(min(m, n), 1.5), 900 + b)
+           for b, (m, n) in enumerate(shapes)]
+    As = [torch.from_numpy(a).to(torch.bfloat16).cuda() for a in A64]
+    ks = [24] * len(As)
+    _, S, Vt, _, info = api.rsvd_truncate_batched(As, ks, p=16, q=2, seed=21, stream=0)
+    S = [s.clone() for s in S]
+    Vt = [v.clone() for v in Vt]
+    from paper_1710_01463_gb300 import _lib as lib_mod
+    _, S2, Vt2, _, info2 = api.rsvd_truncate_batched(As, ks, p=16, q=2, seed=21, stream=0,
+                                                     flags=lib_mod.RSVD_FLAG_SERIAL)
+    torch.cuda.synchronize()
+    for b in range(len(As)):
+        assert torch.equal(S[b], S2[b]) and torch.equal(Vt[b], Vt2[b])
+    assert all(d["status"] == 0 for d in api.info_dicts(info))
+    for b in (0, 15, 16, 36):
+        Ab = As[b].double().cpu().numpy()
+        _, So, _ = orsvd.rsvd(Ab, 24, 16, 2, 21, b)
+        assert np.all(np.abs(S[b].cpu().numpy() - So) <= 1e-4 * So[0]), b
