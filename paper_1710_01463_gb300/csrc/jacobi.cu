@@ -137,14 +137,6 @@ __device__ __forceinline__ double tree_sum(const double* slot, int stride, int C
   return v[0];
 }
 
-// x 2^-ex for |x| < 2^(ex + 1), by subtracting ex from the exponent field; 0 for a zero x or
-// a result below the FP64 normal range (far below FP32's, where the result is used)
-__device__ __forceinline__ double pow2_down(double x, long long ex) {
-  const long long b = __double_as_longlong(x);
-  const long long e = (b >> 52) & 0x7ff;
-  return (e == 0 || e - ex <= 0) ? 0.0 : __longlong_as_double(b - (ex << 52));
-}
-
 // Named barriers between the scalar warps (arrive) and the worker warps (sync): the
 // workers wait until the scalars of a half are written; bar.arrive orders the arriving
 // threads' shared-memory writes before the waiters' reads
@@ -296,6 +288,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
 
   const double tol = (double)max(n, 1) * 0x1.0p-53;
   const double tol2 = tol * tol;
+  const double thr2 = tol2 * 1e8;  // (1e4 tol)^2
   const int max_sweeps = J.max_sweeps;
   int sweeps = 0;
   long long total_rot = 0;
@@ -467,10 +460,9 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
             const double al = norms[i], be = norms[j];
             const double di = dsc[i], dj = dsc[j];
             const double g = tree_sum(gp + s, L.npairs, C) * (di * dj);  // the inner product of the (unscaled) rows
-            const double gg = g * g, tab = tol2 * (al * be);
             // al, be > 0 and g^2 > tol^2 al be, compared as bit patterns (all >= +0)
             if (__double_as_longlong(al) > 0 && __double_as_longlong(be) > 0 &&
-                __double_as_longlong(gg) > __double_as_longlong(tab)) {
+                __double_as_longlong(g * g) > __double_as_longlong(tol2 * (al * be))) {
               rot = 1;
               // tangent of the annihilating angle, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
               // zeta = (be - al) / (2g), formed in FP32 (a dependent FP64 chain of
@@ -479,14 +471,14 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
               // the same t in FP64; the FP32 angle leaves |g| at about 1e-7 of its
               // value instead of 0, and the FP64 stopping test above decides
               // convergence, so the result keeps FP64 accuracy.
-              // h and g are scaled by the same power of two into FP32 range by exponent
-              // arithmetic on their bit patterns (no FP64 multiply: every FP64 instruction
-              // of this chain costs its warp 64 cycles); live rows differ by at most 2^104
-              // in squared norm (deflation), so |zeta| < 1e29 and only zeta^2 needs the guard
-              const double hd = be - al;
-              const double mx = fmax(fabs(hd), fabs(g));
+              // h and 2g are scaled by a power of two (from the exponent bits) into
+              // FP32 range; live rows differ by at most 2^104 in squared norm
+              // (deflation), so |zeta| < 1e29 and only zeta^2 needs the guard
+              const double hd = be - al, g2 = 2.0 * g;
+              const double mx = fmax(fabs(hd), fabs(g2));
               const long long ex = min(((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023, 1022LL);
-              const float zf = 0.5f * ((float)pow2_down(hd, ex) / (float)pow2_down(g, ex));
+              const double sc = __longlong_as_double((1023 - ex) << 52);  // 2^-ex
+              const float zf = (float)(hd * sc) / (float)(g2 * sc);
               const float tf = fabsf(zf) < 1e18f ? copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)))
                                                  : 0.5f / zf;
               const double t = (double)tf;
@@ -498,13 +490,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
               sn = t * di * isc[j];
               rtan[s] = t;
               rgam[s] = g;
-              // a large rotation: g^2 > 2^27 tol^2 al be, the factor 2^27 added to the exponent
-              // field (2^27 tol^2 al be stays far inside the normal range for live rows)
-              const long long tb = __double_as_longlong(tab);
-              const long long te = (tb >> 52) & 0x7ff;
-              const long long thr_bits = te == 0 ? __double_as_longlong(tab * 0x1.0p27)
-                                                 : (te < 2047 - 27 ? tb + (27LL << 52) : 0x7ff0000000000000LL);
-              if (__double_as_longlong(gg) > thr_bits) big_rot = 1;
+              if (__double_as_longlong(g * g) > __double_as_longlong(thr2 * (al * be))) big_rot = 1;
             }
           }
           rcs[s] = cs;
@@ -544,8 +530,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 2) jacobi_kernel(const __grid_
     // A rotation leaves its pair's inner product at about 2e-7 of what it was
     // (FP32 angle); the other pairs it touches change to second order.  So
     // after a sweep whose rotations all had |g| <= thr sqrt(alpha beta),
-    // thr^2 = 2^27 tol^2 (thr about 1.2e4 tol), every pair is far below tol (about
-    // 3e-3 tol): the sweep
+    // thr = 1e4 tol, every pair is far below tol (about 2e-3 tol): the sweep
     // that would only confirm it is skipped (the norms are still recomputed
     // exactly before the singular values are taken).
     converged = (rot_count == 0) || (big_rot == 0);
