@@ -261,3 +261,22 @@ def test_autotune_cache_round_trip(lib, tmp_path):
     assert lib.rsvd_autotune_load(str(tmp_path / "missing.txt").encode()) == -1
     assert lib.rsvd_autotune_enable(1) == 0 and lib.rsvd_autotune_enable(0) == 0
     assert lib.rsvd_autotune_clear() == 0 and lib.rsvd_autotune_entries() == 0
+
+
+def test_autotune_cache_wide_fp32_tile(lib, tmp_path):
+    # tile choice 3 is the 128 x 128 FP32 tile for FP32 -> FP32 products and the 48 x 32 tile
+    # for FP64; the FP32 -> FP64 products (the projection B = Q^T A) have no choice 3, so the
+    # loader skips such a line
+    assert lib.rsvd_autotune_clear() == 0
+    path = tmp_path / "tiles.txt"
+    path.write_text("4 4 0 0 64 1024 128 1024 3\n"   # FP32 -> FP32: the wide tile
+                    "4 4 1 0 64 1024 144 1024 3\n"   # FP32 -> FP32, A transposed
+                    "4 8 1 0 64 144 1024 1024 3\n"   # FP32 -> FP64: no choice 3, skipped
+                    "4 4 0 0 64 1024 128 1024 4\n"   # FP32 has no choice 4, skipped
+                    "8 8 0 0 2 256 144 256 3\n")     # FP64: the 48 x 32 tile
+    assert lib.rsvd_autotune_load(str(path).encode()) == 3
+    out = tmp_path / "out.txt"
+    assert lib.rsvd_autotune_save(str(out).encode()) == 0
+    rows = sorted(r for r in out.read_text().splitlines() if not r.startswith("#"))
+    assert rows == sorted(["4 4 0 0 64 1024 128 1024 3", "4 4 1 0 64 1024 144 1024 3", "8 8 0 0 2 256 144 256 3"])
+    assert lib.rsvd_autotune_clear() == 0
